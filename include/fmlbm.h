@@ -1,0 +1,192 @@
+/*
+ * fmlbm.h -- C ABI of the GB300 (sm_103a) fugacity-based multicomponent lattice
+ * Boltzmann library (libfmlbm.so).
+ *
+ * The library advances N-component D2Q9 lattices with the fugacity-based
+ * free-energy method of Soomro, Ayala, Peng & Ayala (arXiv:2212.10680):
+ * per node, the component densities give ln f_i from a cubic EOS with van der
+ * Waals mixing rules (Appendix C; density-explicit forms of Section IV,
+ * Eqs. eqfugupdatePR / eqfugupdateSRK / eqfugupdateVDW), finite-difference
+ * gradients of ln f_i and of sum_j kappa_ij lap(rho~_j) give the component
+ * forces (Eqs. eqforcefinal, eqChemPotI2, eqkappa, eq1stder, eq2ndder), and
+ * the forces drive the well-balanced multicomponent BGK update (Eqs. eqLBEMCa,
+ * eqLBEMCb with rho_0 = 0, eqLBEMCfinal3) in the order of the implementation
+ * procedure of Section III.B.
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ * - Every function returns fmlbm_status; FMLBM_OK == 0.  No C++ exception ever
+ *   crosses this interface.  fmlbm_status_str() names a status;
+ *   fmlbm_last_error() returns a handle-owned message for the last failure on
+ *   that handle (valid until the next call on it).
+ * - Host arrays are owned by the caller and only read/written during the call.
+ *   Field arrays are float64, C order, component-major: a field f_i(x, y) of an
+ *   nx-by-ny lattice is stored at [i][y][x], i.e. index (i*ny + y)*nx + x.
+ *   Vector fields (velocity, force) are [2][ny][nx] with x-components first.
+ * - Distributions are exchanged as [i][a][y][x] with the D2Q9 direction order
+ *   a = 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1)
+ *   8:(1,-1) (a convention of this library; the paper fixes only the lattice).
+ * - The lattice is periodic in x and y.
+ * - Device memory of a handle is owned by the library and released by
+ *   fmlbm_destroy.  Work is enqueued on the CUDA stream given at creation (NULL:
+ *   the legacy default stream); calls that return host data synchronise that
+ *   stream.  A handle is not thread-safe: one thread at a time.
+ * - Errors raised inside kernels (a node leaving the EOS domain: rho_i <= 0,
+ *   rho~ b_m >= 1, or a non-finite value) are latched on the device and
+ *   reported as FMLBM_E_NONPHYSICAL by the next synchronising call.
+ */
+#ifndef FMLBM_H
+#define FMLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FMLBM_MAX_COMPONENTS 4
+
+typedef enum fmlbm_status {
+    FMLBM_OK = 0,
+    FMLBM_E_INVALID_ARG = 1,    /* a NULL pointer, a size out of range, an unknown enum value   */
+    FMLBM_E_OOM = 2,            /* device or pinned host allocation failed                      */
+    FMLBM_E_CUDA = 3,           /* a CUDA runtime call failed (message in fmlbm_last_error)     */
+    FMLBM_E_NONPHYSICAL = 4,    /* a node left the EOS domain; see fmlbm_error_node             */
+    FMLBM_E_TIMEOUT = 5,        /* a bounded device-side wait ran out                           */
+    FMLBM_E_BUSY = 6,           /* no free slot / budget (never blocks)                         */
+    FMLBM_E_NOT_CONVERGED = 7,  /* a solve reached its step limit above its tolerance           */
+    FMLBM_E_UNSUPPORTED = 8     /* a valid option this build does not provide                   */
+} fmlbm_status;
+
+typedef enum fmlbm_eos { FMLBM_EOS_PR = 0, FMLBM_EOS_SRK = 1, FMLBM_EOS_VDW = 2 } fmlbm_eos;
+
+/* Finite differences for grad and lap.  CENTRAL: the 1-D second-order central
+ * differences along each axis of Eqs. eq1stder / eq2ndder.  ISOTROPIC: the D2Q9
+ * weighted stencils grad h = 3 sum_a w_a e_a h(r+e_a), lap h = 6 sum_a w_a
+ * (h(r+e_a) - h(r)); both coincide on fields uniform along y. */
+typedef enum fmlbm_stencil { FMLBM_STENCIL_ISOTROPIC = 0, FMLBM_STENCIL_CENTRAL = 1 } fmlbm_stencil;
+
+/* Storage and arithmetic.  FP64: distributions and all arithmetic in double.
+ * FP32: float storage and arithmetic.  FP16DEV / BF16DEV: g_0 stored as float,
+ * g_a (a != 0) stored as 16-bit deviations from the rest value w_a rho_0 (= 0),
+ * collide/stream arithmetic in float, the fugacity-coefficient terms of ln f in
+ * double. */
+typedef enum fmlbm_precision {
+    FMLBM_FP64 = 0, FMLBM_FP32 = 1, FMLBM_FP16DEV = 2, FMLBM_BF16DEV = 3
+} fmlbm_precision;
+
+/* Which body force enters the velocity of step 1 of Section III.B.  LAGGED
+ * (default): the total force sum_i F_i of the previous step, as the procedure
+ * states ("body forces ... from the previous time step"); zero before the first
+ * step.  CURRENT: the force of the current densities.  The forcing term of step 8
+ * always uses the current force. */
+typedef enum fmlbm_velocity_force { FMLBM_FORCE_LAGGED = 0, FMLBM_FORCE_CURRENT = 1 } fmlbm_velocity_force;
+
+/* A mixture at fixed temperature in consistent units (the paper's lattice units:
+ * R = 1 and a = 2/49, b = 2/21 for the most volatile component, Section V).
+ * a_i, b_i, alpha_i follow from Tc, Pc, omega and T by Appendix C. kij is the
+ * binary interaction matrix (delta_ij of Appendix C), row-major with a fixed row
+ * stride of FMLBM_MAX_COMPONENTS: kij[i*FMLBM_MAX_COMPONENTS + j]. */
+typedef struct fmlbm_mixture {
+    int32_t n_components;                 /* 1 .. FMLBM_MAX_COMPONENTS               */
+    int32_t eos;                          /* fmlbm_eos                               */
+    double R, T;                          /* gas constant, temperature               */
+    double Tc[FMLBM_MAX_COMPONENTS];
+    double Pc[FMLBM_MAX_COMPONENTS];
+    double omega[FMLBM_MAX_COMPONENTS];   /* acentric factors                        */
+    double M[FMLBM_MAX_COMPONENTS];       /* molar masses, rho~_i = rho_i / M_i      */
+    double kappa[FMLBM_MAX_COMPONENTS];   /* interface strengths, Eq. eqkappa        */
+    double kij[FMLBM_MAX_COMPONENTS * FMLBM_MAX_COMPONENTS];
+} fmlbm_mixture;
+
+typedef struct fmlbm_lattice {
+    int32_t nx, ny;                       /* 1 .. 2^16 each, nx*ny*N*9 < 2^31        */
+    double tau;                           /* BGK relaxation time, > 0.5              */
+    int32_t stencil;                      /* fmlbm_stencil                           */
+    int32_t precision;                    /* fmlbm_precision                         */
+    int32_t velocity_force;               /* fmlbm_velocity_force                    */
+    int32_t reserved;                     /* must be 0                               */
+} fmlbm_lattice;
+
+typedef struct fmlbm_handle fmlbm_handle;
+
+/* Creates a lattice: validates the mixture (Appendix C parameters) and lattice,
+ * allocates its device buffers (two distribution buffers, two force buffers,
+ * a density snapshot for the residual and reduction scratch) on the current
+ * device, and leaves it uninitialised.  cuda_stream: a cudaStream_t (may be
+ * NULL), owned by the caller, must outlive the handle. */
+fmlbm_status fmlbm_create(const fmlbm_mixture* mixture, const fmlbm_lattice* lattice,
+                          void* cuda_stream, fmlbm_handle** out);
+
+/* Fluid at rest: g_{a,i} = g^eq_{a,i}(rho_i, u = 0) (Eq. eqLBEMCb with rho_0 = 0,
+ * i.e. rho_i in a = 0 and 0 elsewhere), stored force 0, step counter 0.
+ * rho_host: [N][ny][nx] component MASS densities on the host, copied. */
+fmlbm_status fmlbm_init(fmlbm_handle* h, const double* rho_host);
+
+/* As fmlbm_init, with rho_device a device pointer of the same layout (read on
+ * the handle's stream before the call's work completes; not retained). */
+fmlbm_status fmlbm_init_device(fmlbm_handle* h, const double* rho_device);
+
+/* Enqueues nsteps (>= 0) full time steps (steps 1-9 of Section III.B, one fused
+ * kernel launch per step) on the handle's stream.  Asynchronous: kernel-side
+ * errors surface at the next synchronising call. */
+fmlbm_status fmlbm_step(fmlbm_handle* h, int64_t nsteps);
+
+/* Macroscopic fields of the current state (steps 1-7 without collision):
+ * rho [N][ny][nx] mass densities, u [2][ny][nx] the velocity of step 1 (with half
+ * the force chosen by velocity_force), lnf [N][ny][nx].  Any pointer may be NULL.
+ * Host outputs; synchronises. */
+fmlbm_status fmlbm_moments(fmlbm_handle* h, double* rho, double* u, double* lnf);
+
+/* Post-streaming distributions g_{a,i}(x, y, t) [N][9][ny][nx] and the stored
+ * force [2][ny][nx] (either may be NULL).  Host outputs; synchronises. */
+fmlbm_status fmlbm_get_distributions(fmlbm_handle* h, double* g, double* force);
+
+/* Replaces the state with the given post-streaming distributions [N][9][ny][nx]
+ * and stored force [2][ny][nx] (NULL: zero), converting to the storage precision.
+ * Resets the step counter to 0 and clears the residual snapshot. */
+fmlbm_status fmlbm_set_distributions(fmlbm_handle* h, const double* g, const double* force);
+
+/* Reductions over the lattice (deterministic, fixed-order, FP64 accumulation):
+ * mass[N] = sum_x rho_i; residual = ||rho(t) - rho(t_prev)||_2 / ||rho(t)||_2
+ * where t_prev is the state at the previous fmlbm_diagnostics call (+inf on the
+ * first call after init); step = steps taken since init.  Then snapshots rho(t).
+ * Any pointer may be NULL.  Host outputs; synchronises; reports a latched
+ * FMLBM_E_NONPHYSICAL. */
+fmlbm_status fmlbm_diagnostics(fmlbm_handle* h, double* mass, double* residual, int64_t* step);
+
+/* First node that left the EOS domain since the last init (after a call returned
+ * FMLBM_E_NONPHYSICAL): component, x, y. */
+fmlbm_status fmlbm_error_node(fmlbm_handle* h, int32_t* comp, int32_t* x, int32_t* y);
+
+/* Checkpoint / resume: the raw device state (distributions in storage precision,
+ * stored force, step counter, a header with N, nx, ny, precision).  state_size
+ * gives the byte count; get_state copies it to host memory; set_state restores a
+ * state taken from a handle with the same N, nx, ny and precision.  A restored
+ * run continues bit-identically to an uninterrupted one. */
+fmlbm_status fmlbm_state_size(fmlbm_handle* h, size_t* bytes);
+fmlbm_status fmlbm_get_state(fmlbm_handle* h, void* buf, size_t bytes);
+fmlbm_status fmlbm_set_state(fmlbm_handle* h, const void* buf, size_t bytes);
+
+/* Waits for the handle's stream and reports latched kernel errors. */
+fmlbm_status fmlbm_synchronize(fmlbm_handle* h);
+
+/* Device bytes one lattice of this shape and precision holds (for admission
+ * control). */
+fmlbm_status fmlbm_lattice_bytes(int32_t n_components, const fmlbm_lattice* lattice, size_t* bytes);
+
+/* Releases all device memory of the handle.  NULL-safe. */
+void fmlbm_destroy(fmlbm_handle* h);
+
+const char* fmlbm_status_str(fmlbm_status s);
+const char* fmlbm_last_error(const fmlbm_handle* h);
+
+/* Library version string, e.g. "fmlbm 0.1 sm_103a". */
+const char* fmlbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMLBM_H */

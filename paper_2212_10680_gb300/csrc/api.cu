@@ -1,0 +1,521 @@
+// C ABI of libfmlbm (declared in include/fmlbm.h): handle management, mixture
+// constants (Appendix C of arXiv:2212.10680), step enqueueing, reductions,
+// checkpoints.  All device work runs in the kernels of fmlbm_kernels.cuh.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "fmlbm.h"
+#include "fmlbm_launch.cuh"
+
+using namespace fmlbm;
+
+struct fmlbm_handle {
+    int nc = 0;
+    fmlbm_mixture mixture{};
+    fmlbm_lattice lattice{};
+    MixConst mc{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    void* g[2] = {nullptr, nullptr};    // F64/F32: all planes; DEV: 16-bit planes
+    float* g0[2] = {nullptr, nullptr};  // DEV: float planes a = 0
+    void* F[2] = {nullptr, nullptr};
+    int cur = 0;
+    double* rho_prev = nullptr;
+    int have_prev = 0;
+    double* partial = nullptr;
+    double* diag_dev = nullptr;
+    double* diag_host = nullptr;     // pinned
+    ErrorLatch* err_dev = nullptr;
+    ErrorLatch* err_host = nullptr;  // pinned
+    int64_t step = 0;
+    std::string last_error;
+};
+
+namespace {
+
+constexpr uint32_t kStateMagic = 0x464d4c42u;  // "FMLB"
+constexpr uint32_t kStateVersion = 1;
+
+struct StateHeader {
+    uint32_t magic, version;
+    int32_t nc, nx, ny, precision;
+    int64_t step;
+    uint64_t g_bytes, g0_bytes, f_bytes;
+};
+
+size_t real_size(int precision) { return precision == FMLBM_FP64 ? 8 : 4; }
+
+// bytes of one distribution buffer (g) and, for the 16-bit forms, of its float g_0 planes
+void buffer_bytes(int nc, const fmlbm_lattice& L, size_t* g_bytes, size_t* g0_bytes, size_t* f_bytes) {
+    const size_t nxy = (size_t)L.nx * (size_t)L.ny;
+    if (L.precision == FMLBM_FP64 || L.precision == FMLBM_FP32) {
+        *g_bytes = (size_t)nc * 9 * nxy * real_size(L.precision);
+        *g0_bytes = 0;
+    } else {
+        *g_bytes = (size_t)nc * 8 * nxy * 2;
+        *g0_bytes = (size_t)nc * nxy * 4;
+    }
+    *f_bytes = 2 * nxy * real_size(L.precision);
+}
+
+fmlbm_status fail(fmlbm_handle* h, fmlbm_status s, const std::string& msg) {
+    if (h) h->last_error = msg;
+    return s;
+}
+
+fmlbm_status cuda_fail(fmlbm_handle* h, cudaError_t e, const char* where) {
+    return fail(h, FMLBM_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define FM_CUDA(h, call)                                      \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+    } while (0)
+
+// Appendix C: a_i = Omega_a R^2 Tc^2 / Pc, b_i = Omega_b R Tc / Pc, alpha_i(T);
+// (a alpha)_ij = sqrt((a alpha)_i (a alpha)_j) (1 - k_ij).
+bool mixture_constants(const fmlbm_mixture& m, MixConst* mc, std::string* why) {
+    const int n = m.n_components;
+    if (n < 1 || n > FMLBM_MAX_COMPONENTS) { *why = "n_components must be 1..4"; return false; }
+    if (m.eos < 0 || m.eos > 2) { *why = "unknown eos"; return false; }
+    if (!(m.R > 0) || !(m.T > 0)) { *why = "R and T must be positive"; return false; }
+    double Oa, Ob;
+    if (m.eos == FMLBM_EOS_PR) { Oa = 0.457235529; Ob = 0.077796074; }
+    else if (m.eos == FMLBM_EOS_SRK) { Oa = 0.4274802; Ob = 0.08664035; }
+    else { Oa = 27.0 / 64.0; Ob = 1.0 / 8.0; }
+    std::memset(mc, 0, sizeof(*mc));
+    mc->nc = n;
+    mc->eos = m.eos;
+    mc->RT = m.R * m.T;
+    double aa[FMLBM_MAX_COMPONENTS];
+    for (int i = 0; i < n; ++i) {
+        if (!(m.Tc[i] > 0) || !(m.Pc[i] > 0) || !(m.M[i] > 0) || !(m.kappa[i] >= 0)) {
+            *why = "Tc, Pc, M must be positive and kappa non-negative";
+            return false;
+        }
+        const double a = Oa * m.R * m.R * m.Tc[i] * m.Tc[i] / m.Pc[i];
+        const double b = Ob * m.R * m.Tc[i] / m.Pc[i];
+        const double sq = 1.0 - std::sqrt(m.T / m.Tc[i]);
+        double alpha = 1.0;
+        const double w = m.omega[i];
+        if (m.eos == FMLBM_EOS_PR) {
+            const double k = w <= 0.49 ? 0.374640 + 1.54226 * w - 0.26992 * w * w
+                                       : 0.379642 + 1.48503 * w - 0.164423 * w * w + 0.016666 * w * w * w;
+            alpha = (1.0 + k * sq) * (1.0 + k * sq);
+        } else if (m.eos == FMLBM_EOS_SRK) {
+            const double k = 0.48 + 1.574 * w - 0.176 * w * w;
+            alpha = (1.0 + k * sq) * (1.0 + k * sq);
+        }
+        aa[i] = a * alpha;
+        mc->b[i] = b;
+        mc->M[i] = m.M[i];
+        mc->invM[i] = 1.0 / m.M[i];
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            mc->aij[i * kMaxC + j] = std::sqrt(aa[i] * aa[j]) * (1.0 - m.kij[i * FMLBM_MAX_COMPONENTS + j]);
+            mc->kap[i * kMaxC + j] = std::sqrt(m.kappa[i] * m.kappa[j]);
+        }
+    return true;
+}
+
+bool lattice_ok(const fmlbm_lattice& L, int nc, std::string* why) {
+    if (L.nx < 1 || L.ny < 1 || L.nx > 65536 || L.ny > 65536) { *why = "nx, ny must be 1..65536"; return false; }
+    if ((double)L.nx * L.ny * nc * 9 >= 2147483647.0) { *why = "lattice too large"; return false; }
+    if (!(L.tau > 0.5)) { *why = "tau must exceed 0.5"; return false; }
+    if (L.stencil != FMLBM_STENCIL_ISOTROPIC && L.stencil != FMLBM_STENCIL_CENTRAL) { *why = "unknown stencil"; return false; }
+    if (L.precision < FMLBM_FP64 || L.precision > FMLBM_BF16DEV) { *why = "unknown precision"; return false; }
+    if (L.velocity_force != FMLBM_FORCE_LAGGED && L.velocity_force != FMLBM_FORCE_CURRENT) {
+        *why = "unknown velocity_force";
+        return false;
+    }
+    if (L.reserved != 0) { *why = "reserved must be 0"; return false; }
+    return true;
+}
+
+StepArgs make_args(const fmlbm_handle* h, int src) {
+    StepArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.nx = h->lattice.nx;
+    A.ny = h->lattice.ny;
+    A.stencil = h->lattice.stencil;
+    A.lagged = h->lattice.velocity_force == FMLBM_FORCE_LAGGED;
+    A.omega = 1.0 / h->lattice.tau;
+    A.fcoef = 1.0 - 0.5 / h->lattice.tau;
+    A.gin = h->g[src];
+    A.g0in = h->g0[src];
+    A.gout = h->g[src ^ 1];
+    A.g0out = h->g0[src ^ 1];
+    A.Fin = h->F[src];
+    A.Fout = h->F[src ^ 1];
+    A.err = h->err_dev;
+    A.mix = h->mc;
+    return A;
+}
+
+cudaError_t dispatch_step(const fmlbm_handle* h, const StepArgs& A, bool moments) {
+    switch (h->lattice.precision) {
+        case FMLBM_FP64: return launch_step<ST_F64>(A, h->nc, moments, h->stream);
+        case FMLBM_FP32: return launch_step<ST_F32>(A, h->nc, moments, h->stream);
+        case FMLBM_FP16DEV: return launch_step<ST_F16DEV>(A, h->nc, moments, h->stream);
+        default: return launch_step<ST_BF16DEV>(A, h->nc, moments, h->stream);
+    }
+}
+cudaError_t dispatch_init(const fmlbm_handle* h, const StepArgs& A, const double* rho) {
+    switch (h->lattice.precision) {
+        case FMLBM_FP64: return launch_init<ST_F64>(A, h->nc, rho, h->stream);
+        case FMLBM_FP32: return launch_init<ST_F32>(A, h->nc, rho, h->stream);
+        case FMLBM_FP16DEV: return launch_init<ST_F16DEV>(A, h->nc, rho, h->stream);
+        default: return launch_init<ST_BF16DEV>(A, h->nc, rho, h->stream);
+    }
+}
+cudaError_t dispatch_convert(const fmlbm_handle* h, const StepArgs& A, const double* gi, double* go, bool to) {
+    switch (h->lattice.precision) {
+        case FMLBM_FP64: return launch_convert<ST_F64>(A, h->nc, gi, go, to, h->stream);
+        case FMLBM_FP32: return launch_convert<ST_F32>(A, h->nc, gi, go, to, h->stream);
+        case FMLBM_FP16DEV: return launch_convert<ST_F16DEV>(A, h->nc, gi, go, to, h->stream);
+        default: return launch_convert<ST_BF16DEV>(A, h->nc, gi, go, to, h->stream);
+    }
+}
+cudaError_t dispatch_reduce(fmlbm_handle* h, const StepArgs& A) {
+    switch (h->lattice.precision) {
+        case FMLBM_FP64: return launch_reduce<ST_F64>(A, h->nc, h->rho_prev, h->have_prev, h->partial, h->diag_dev, h->stream);
+        case FMLBM_FP32: return launch_reduce<ST_F32>(A, h->nc, h->rho_prev, h->have_prev, h->partial, h->diag_dev, h->stream);
+        case FMLBM_FP16DEV: return launch_reduce<ST_F16DEV>(A, h->nc, h->rho_prev, h->have_prev, h->partial, h->diag_dev, h->stream);
+        default: return launch_reduce<ST_BF16DEV>(A, h->nc, h->rho_prev, h->have_prev, h->partial, h->diag_dev, h->stream);
+    }
+}
+
+// Synchronise the stream and turn a latched kernel error into a status.
+fmlbm_status sync_and_check(fmlbm_handle* h) {
+    FM_CUDA(h, cudaMemcpyAsync(h->err_host, h->err_dev, sizeof(ErrorLatch), cudaMemcpyDeviceToHost, h->stream));
+    FM_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (h->err_host->flag) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "node left the EOS domain: component %d at (x=%d, y=%d)", h->err_host->comp,
+                      h->err_host->x, h->err_host->y);
+        return fail(h, FMLBM_E_NONPHYSICAL, buf);
+    }
+    return FMLBM_OK;
+}
+
+void release(fmlbm_handle* h) {
+    for (int k = 0; k < 2; ++k) {
+        if (h->g[k]) cudaFree(h->g[k]);
+        if (h->g0[k]) cudaFree(h->g0[k]);
+        if (h->F[k]) cudaFree(h->F[k]);
+    }
+    if (h->rho_prev) cudaFree(h->rho_prev);
+    if (h->partial) cudaFree(h->partial);
+    if (h->diag_dev) cudaFree(h->diag_dev);
+    if (h->err_dev) cudaFree(h->err_dev);
+    if (h->diag_host) cudaFreeHost(h->diag_host);
+    if (h->err_host) cudaFreeHost(h->err_host);
+}
+
+fmlbm_status reset_state_flags(fmlbm_handle* h) {
+    FM_CUDA(h, cudaMemsetAsync(h->err_dev, 0, sizeof(ErrorLatch), h->stream));
+    h->have_prev = 0;
+    h->step = 0;
+    h->cur = 0;
+    return FMLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fmlbm_version(void) { return "fmlbm 0.1 sm_103a"; }
+
+const char* fmlbm_status_str(fmlbm_status s) {
+    switch (s) {
+        case FMLBM_OK: return "FMLBM_OK";
+        case FMLBM_E_INVALID_ARG: return "FMLBM_E_INVALID_ARG";
+        case FMLBM_E_OOM: return "FMLBM_E_OOM";
+        case FMLBM_E_CUDA: return "FMLBM_E_CUDA";
+        case FMLBM_E_NONPHYSICAL: return "FMLBM_E_NONPHYSICAL";
+        case FMLBM_E_TIMEOUT: return "FMLBM_E_TIMEOUT";
+        case FMLBM_E_BUSY: return "FMLBM_E_BUSY";
+        case FMLBM_E_NOT_CONVERGED: return "FMLBM_E_NOT_CONVERGED";
+        case FMLBM_E_UNSUPPORTED: return "FMLBM_E_UNSUPPORTED";
+    }
+    return "unknown fmlbm_status";
+}
+
+const char* fmlbm_last_error(const fmlbm_handle* h) { return h ? h->last_error.c_str() : ""; }
+
+fmlbm_status fmlbm_lattice_bytes(int32_t n_components, const fmlbm_lattice* lattice, size_t* bytes) {
+    if (!lattice || !bytes || n_components < 1 || n_components > FMLBM_MAX_COMPONENTS) return FMLBM_E_INVALID_ARG;
+    size_t gb, g0b, fb;
+    buffer_bytes(n_components, *lattice, &gb, &g0b, &fb);
+    const size_t nxy = (size_t)lattice->nx * lattice->ny;
+    *bytes = 2 * (gb + g0b + fb) + (size_t)n_components * nxy * 8 +
+             (size_t)kReduceBlocks * (FMLBM_MAX_COMPONENTS + 2) * 8 + 256;
+    return FMLBM_OK;
+}
+
+fmlbm_status fmlbm_create(const fmlbm_mixture* mixture, const fmlbm_lattice* lattice, void* cuda_stream,
+                          fmlbm_handle** out) {
+    if (!mixture || !lattice || !out) return FMLBM_E_INVALID_ARG;
+    *out = nullptr;
+    fmlbm_handle* h = new (std::nothrow) fmlbm_handle();
+    if (!h) return FMLBM_E_OOM;
+    std::string why;
+    if (!mixture_constants(*mixture, &h->mc, &why) || !lattice_ok(*lattice, mixture->n_components, &why)) {
+        delete h;
+        return FMLBM_E_INVALID_ARG;
+    }
+    h->nc = mixture->n_components;
+    h->mixture = *mixture;
+    h->lattice = *lattice;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        delete h;
+        return FMLBM_E_CUDA;
+    }
+    size_t gb, g0b, fb;
+    buffer_bytes(h->nc, h->lattice, &gb, &g0b, &fb);
+    const size_t nxy = (size_t)lattice->nx * lattice->ny;
+    bool ok = true;
+    for (int k = 0; k < 2 && ok; ++k) {
+        ok = ok && cudaMalloc(&h->g[k], gb) == cudaSuccess;
+        if (g0b) ok = ok && cudaMalloc((void**)&h->g0[k], g0b) == cudaSuccess;
+        ok = ok && cudaMalloc(&h->F[k], fb) == cudaSuccess;
+    }
+    ok = ok && cudaMalloc((void**)&h->rho_prev, (size_t)h->nc * nxy * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&h->partial, (size_t)kReduceBlocks * (kMaxC + 2) * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&h->diag_dev, (kMaxC + 2) * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&h->err_dev, sizeof(ErrorLatch)) == cudaSuccess;
+    ok = ok && cudaMallocHost((void**)&h->diag_host, (kMaxC + 2) * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMallocHost((void**)&h->err_host, sizeof(ErrorLatch)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        release(h);
+        delete h;
+        return FMLBM_E_OOM;
+    }
+    if (cudaMemsetAsync(h->err_dev, 0, sizeof(ErrorLatch), h->stream) != cudaSuccess) {
+        release(h);
+        delete h;
+        return FMLBM_E_CUDA;
+    }
+    *out = h;
+    return FMLBM_OK;
+}
+
+void fmlbm_destroy(fmlbm_handle* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    release(h);
+    delete h;
+}
+
+fmlbm_status fmlbm_init_device(fmlbm_handle* h, const double* rho_device) {
+    if (!h || !rho_device) return fail(h, FMLBM_E_INVALID_ARG, "null argument");
+    fmlbm_status s = reset_state_flags(h);
+    if (s != FMLBM_OK) return s;
+    StepArgs A = make_args(h, 1);  // writes into buffer 0
+    FM_CUDA(h, dispatch_init(h, A, rho_device));
+    h->cur = 0;
+    return FMLBM_OK;
+}
+
+fmlbm_status fmlbm_init(fmlbm_handle* h, const double* rho_host) {
+    if (!h || !rho_host) return fail(h, FMLBM_E_INVALID_ARG, "null argument");
+    const size_t bytes = (size_t)h->nc * h->lattice.nx * h->lattice.ny * sizeof(double);
+    double* d = nullptr;
+    FM_CUDA(h, cudaMallocAsync((void**)&d, bytes, h->stream));
+    cudaError_t e = cudaMemcpyAsync(d, rho_host, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(d, h->stream);
+        return cuda_fail(h, e, "cudaMemcpyAsync(rho)");
+    }
+    fmlbm_status s = fmlbm_init_device(h, d);
+    cudaFreeAsync(d, h->stream);
+    return s;
+}
+
+fmlbm_status fmlbm_step(fmlbm_handle* h, int64_t nsteps) {
+    if (!h || nsteps < 0) return fail(h, FMLBM_E_INVALID_ARG, "bad argument");
+    for (int64_t k = 0; k < nsteps; ++k) {
+        StepArgs A = make_args(h, h->cur);
+        FM_CUDA(h, dispatch_step(h, A, false));
+        h->cur ^= 1;
+        ++h->step;
+    }
+    return FMLBM_OK;
+}
+
+fmlbm_status fmlbm_synchronize(fmlbm_handle* h) {
+    if (!h) return FMLBM_E_INVALID_ARG;
+    return sync_and_check(h);
+}
+
+fmlbm_status fmlbm_moments(fmlbm_handle* h, double* rho, double* u, double* lnf) {
+    if (!h) return FMLBM_E_INVALID_ARG;
+    const size_t nxy = (size_t)h->lattice.nx * h->lattice.ny;
+    const size_t fb = (size_t)h->nc * nxy * sizeof(double);
+    double* d = nullptr;
+    FM_CUDA(h, cudaMallocAsync((void**)&d, 2 * fb + 2 * nxy * sizeof(double), h->stream));
+    StepArgs A = make_args(h, h->cur);
+    A.rho_out = d;
+    A.lnf_out = d + (size_t)h->nc * nxy;
+    A.u_out = d + 2 * (size_t)h->nc * nxy;
+    A.gout = nullptr;
+    A.g0out = nullptr;
+    A.Fout = nullptr;
+    cudaError_t e = dispatch_step(h, A, true);
+    if (e == cudaSuccess && rho) e = cudaMemcpyAsync(rho, A.rho_out, fb, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && lnf) e = cudaMemcpyAsync(lnf, A.lnf_out, fb, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, A.u_out, 2 * nxy * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    cudaFreeAsync(d, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "moments");
+    return sync_and_check(h);
+}
+
+fmlbm_status fmlbm_get_distributions(fmlbm_handle* h, double* g, double* force) {
+    if (!h) return FMLBM_E_INVALID_ARG;
+    const size_t nxy = (size_t)h->lattice.nx * h->lattice.ny;
+    cudaError_t e = cudaSuccess;
+    if (g) {
+        const size_t gbytes = (size_t)h->nc * 9 * nxy * sizeof(double);
+        double* d = nullptr;
+        FM_CUDA(h, cudaMallocAsync((void**)&d, gbytes, h->stream));
+        StepArgs A = make_args(h, h->cur);
+        e = dispatch_convert(h, A, nullptr, d, false);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g, d, gbytes, cudaMemcpyDeviceToHost, h->stream);
+        cudaFreeAsync(d, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "get_distributions");
+    }
+    if (force) {
+        if (h->lattice.precision == FMLBM_FP64) {
+            FM_CUDA(h, cudaMemcpyAsync(force, h->F[h->cur], 2 * nxy * 8, cudaMemcpyDeviceToHost, h->stream));
+            FM_CUDA(h, cudaStreamSynchronize(h->stream));
+        } else {
+            float* tmp = new (std::nothrow) float[2 * nxy];
+            if (!tmp) return FMLBM_E_OOM;
+            e = cudaMemcpyAsync(tmp, h->F[h->cur], 2 * nxy * 4, cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            if (e == cudaSuccess)
+                for (size_t k = 0; k < 2 * nxy; ++k) force[k] = tmp[k];
+            delete[] tmp;
+            if (e != cudaSuccess) return cuda_fail(h, e, "get force");
+        }
+    }
+    return sync_and_check(h);
+}
+
+fmlbm_status fmlbm_set_distributions(fmlbm_handle* h, const double* g, const double* force) {
+    if (!h || !g) return fail(h, FMLBM_E_INVALID_ARG, "null argument");
+    fmlbm_status s = reset_state_flags(h);
+    if (s != FMLBM_OK) return s;
+    const size_t nxy = (size_t)h->lattice.nx * h->lattice.ny;
+    const size_t gbytes = (size_t)h->nc * 9 * nxy * sizeof(double);
+    double* d = nullptr;
+    FM_CUDA(h, cudaMallocAsync((void**)&d, gbytes, h->stream));
+    cudaError_t e = cudaMemcpyAsync(d, g, gbytes, cudaMemcpyHostToDevice, h->stream);
+    StepArgs A = make_args(h, 1);  // writes buffer 0
+    if (e == cudaSuccess) e = dispatch_convert(h, A, d, nullptr, true);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFreeAsync(d, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_distributions");
+    const size_t rs = real_size(h->lattice.precision);
+    if (!force) {
+        FM_CUDA(h, cudaMemsetAsync(h->F[0], 0, 2 * nxy * rs, h->stream));
+    } else if (rs == 8) {
+        FM_CUDA(h, cudaMemcpyAsync(h->F[0], force, 2 * nxy * 8, cudaMemcpyHostToDevice, h->stream));
+    } else {
+        float* tmp = new (std::nothrow) float[2 * nxy];
+        if (!tmp) return FMLBM_E_OOM;
+        for (size_t k = 0; k < 2 * nxy; ++k) tmp[k] = (float)force[k];
+        e = cudaMemcpyAsync(h->F[0], tmp, 2 * nxy * 4, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        delete[] tmp;
+        if (e != cudaSuccess) return cuda_fail(h, e, "set force");
+    }
+    return sync_and_check(h);
+}
+
+fmlbm_status fmlbm_diagnostics(fmlbm_handle* h, double* mass, double* residual, int64_t* step) {
+    if (!h) return FMLBM_E_INVALID_ARG;
+    StepArgs A = make_args(h, h->cur);
+    FM_CUDA(h, dispatch_reduce(h, A));
+    FM_CUDA(h, cudaMemcpyAsync(h->diag_host, h->diag_dev, (h->nc + 2) * sizeof(double), cudaMemcpyDeviceToHost,
+                               h->stream));
+    fmlbm_status s = sync_and_check(h);
+    const double* d = h->diag_host;
+    if (mass)
+        for (int i = 0; i < h->nc; ++i) mass[i] = d[i];
+    if (residual) *residual = h->have_prev ? std::sqrt(d[h->nc]) / std::sqrt(d[h->nc + 1]) : INFINITY;
+    if (step) *step = h->step;
+    h->have_prev = 1;
+    return s;
+}
+
+fmlbm_status fmlbm_error_node(fmlbm_handle* h, int32_t* comp, int32_t* x, int32_t* y) {
+    if (!h) return FMLBM_E_INVALID_ARG;
+    FM_CUDA(h, cudaMemcpyAsync(h->err_host, h->err_dev, sizeof(ErrorLatch), cudaMemcpyDeviceToHost, h->stream));
+    FM_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (comp) *comp = h->err_host->flag ? h->err_host->comp : -1;
+    if (x) *x = h->err_host->flag ? h->err_host->x : -1;
+    if (y) *y = h->err_host->flag ? h->err_host->y : -1;
+    return FMLBM_OK;
+}
+
+fmlbm_status fmlbm_state_size(fmlbm_handle* h, size_t* bytes) {
+    if (!h || !bytes) return FMLBM_E_INVALID_ARG;
+    size_t gb, g0b, fb;
+    buffer_bytes(h->nc, h->lattice, &gb, &g0b, &fb);
+    *bytes = sizeof(StateHeader) + gb + g0b + fb;
+    return FMLBM_OK;
+}
+
+fmlbm_status fmlbm_get_state(fmlbm_handle* h, void* buf, size_t bytes) {
+    if (!h || !buf) return FMLBM_E_INVALID_ARG;
+    size_t need;
+    fmlbm_state_size(h, &need);
+    if (bytes < need) return fail(h, FMLBM_E_INVALID_ARG, "state buffer too small");
+    size_t gb, g0b, fb;
+    buffer_bytes(h->nc, h->lattice, &gb, &g0b, &fb);
+    StateHeader hd{kStateMagic, kStateVersion, h->nc, h->lattice.nx, h->lattice.ny, h->lattice.precision,
+                   h->step, gb, g0b, fb};
+    char* p = static_cast<char*>(buf);
+    std::memcpy(p, &hd, sizeof hd);
+    p += sizeof hd;
+    FM_CUDA(h, cudaMemcpyAsync(p, h->g[h->cur], gb, cudaMemcpyDeviceToHost, h->stream));
+    p += gb;
+    if (g0b) FM_CUDA(h, cudaMemcpyAsync(p, h->g0[h->cur], g0b, cudaMemcpyDeviceToHost, h->stream));
+    p += g0b;
+    FM_CUDA(h, cudaMemcpyAsync(p, h->F[h->cur], fb, cudaMemcpyDeviceToHost, h->stream));
+    return sync_and_check(h);
+}
+
+fmlbm_status fmlbm_set_state(fmlbm_handle* h, const void* buf, size_t bytes) {
+    if (!h || !buf || bytes < sizeof(StateHeader)) return FMLBM_E_INVALID_ARG;
+    StateHeader hd;
+    std::memcpy(&hd, buf, sizeof hd);
+    size_t gb, g0b, fb;
+    buffer_bytes(h->nc, h->lattice, &gb, &g0b, &fb);
+    if (hd.magic != kStateMagic || hd.version != kStateVersion || hd.nc != h->nc || hd.nx != h->lattice.nx ||
+        hd.ny != h->lattice.ny || hd.precision != h->lattice.precision || hd.g_bytes != gb ||
+        hd.g0_bytes != g0b || hd.f_bytes != fb || bytes < sizeof hd + gb + g0b + fb)
+        return fail(h, FMLBM_E_INVALID_ARG, "state does not match this lattice");
+    const char* p = static_cast<const char*>(buf) + sizeof hd;
+    FM_CUDA(h, cudaMemcpyAsync(h->g[0], p, gb, cudaMemcpyHostToDevice, h->stream));
+    p += gb;
+    if (g0b) FM_CUDA(h, cudaMemcpyAsync(h->g0[0], p, g0b, cudaMemcpyHostToDevice, h->stream));
+    p += g0b;
+    FM_CUDA(h, cudaMemcpyAsync(h->F[0], p, fb, cudaMemcpyHostToDevice, h->stream));
+    FM_CUDA(h, cudaMemsetAsync(h->err_dev, 0, sizeof(ErrorLatch), h->stream));
+    h->cur = 0;
+    h->step = hd.step;
+    h->have_prev = 0;
+    return sync_and_check(h);
+}
+
+}  // extern "C"

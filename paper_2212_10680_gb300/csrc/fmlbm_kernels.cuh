@@ -1,0 +1,575 @@
+// Device code of libfmlbm: the fused lattice update and its helpers (sm_103a).
+//
+// One launch of `fused_step` performs one full time step of the fugacity-based
+// free-energy LBM (Section III.B, steps 1-9) for every node of a lattice:
+//
+//   phase 1  pull the 9N post-collision values of the previous step into
+//            registers (streaming, step 9 of the previous step), sum them to
+//            rho_i (step 1) and rho~_i = rho_i / M_i (step 2); the same for a
+//            2-node halo ring, whose rho~ goes to shared memory only;
+//   phase 2  on the tile plus a 1-node halo: mixing rules, pressure and ln f_i
+//            (steps 3-5, density-explicit form of Eq. eqfugupdatePR/SRK/VDW) and
+//            G_i = sum_j kappa_ij lap(rho~_j) (step 6, mu_I,i = -G_i);
+//   phase 3  at each node: F_i = -rho~_i RT grad ln f_i + rho~_i grad G_i (step 7,
+//            Eq. eqforcefinal), u from the first moment and half the force
+//            (step 1), g^eq (Eq. eqLBEMCb, rho_0 = 0) and F_{a,i}
+//            (Eq. eqLBEMCfinal3) (step 8), BGK collision (Eq. eqLBEMCa), and a
+//            coalesced store of the post-collision values at the node itself
+//            (the next launch pulls them: streaming happens on the read side).
+//
+// Everything between the one read and the one write of the distributions
+// stays on chip; the only other global traffic is the stored total force
+// sum_i F_i (2 values per node) used by the next step's velocity.
+//
+// Buffer layout (structure of arrays): plane (i, a) of the distributions is a
+// contiguous nx*ny array in row-major (y, x) order; plane index i*9 + a for
+// FP64/FP32 storage.  In the 16-bit deviation forms g_0 planes are float
+// ([N][ny][nx]) and g_a, a = 1..8, planes are 16-bit ([N][8][ny][nx]).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fmlbm {
+
+constexpr int kMaxC = 4;
+constexpr int kTX = 32;  // tile width = one warp
+
+enum Storage { ST_F64 = 0, ST_F32 = 1, ST_F16DEV = 2, ST_BF16DEV = 3 };
+
+// D2Q9: a = 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1)
+__host__ __device__ __forceinline__ constexpr int ex(int a) {
+    return (a == 1 || a == 5 || a == 8) ? 1 : ((a == 3 || a == 6 || a == 7) ? -1 : 0);
+}
+__host__ __device__ __forceinline__ constexpr int ey(int a) {
+    return (a == 2 || a == 5 || a == 6) ? 1 : ((a == 4 || a == 7 || a == 8) ? -1 : 0);
+}
+template <typename R>
+__host__ __device__ __forceinline__ constexpr R wgt(int a) {
+    return a == 0 ? R(4) / R(9) : (a < 5 ? R(1) / R(9) : R(1) / R(36));
+}
+
+// Mixture constants, computed on the host from Appendix C (T fixed).
+struct MixConst {
+    int nc;
+    int eos;          // 0 PR, 1 SRK, 2 vdW
+    double RT;
+    double b[kMaxC];
+    double M[kMaxC];
+    double invM[kMaxC];
+    double aij[kMaxC * kMaxC];   // (a alpha)_ij, row stride kMaxC
+    double kap[kMaxC * kMaxC];   // kappa_ij = sqrt(kappa_i kappa_j), row stride kMaxC
+};
+
+struct ErrorLatch {
+    int flag;         // 0 = clean, 1 = a node left the EOS domain
+    int comp, x, y;
+};
+
+struct StepArgs {
+    int nx, ny;
+    int stencil;      // 0 isotropic, 1 central
+    int lagged;       // 1: u uses the stored force of the previous step
+    double omega;     // 1 / tau
+    double fcoef;     // 1 - 1 / (2 tau)
+    const void* gin;  // F64/F32: all planes; DEV: 16-bit planes a = 1..8
+    const float* g0in;  // DEV: float planes a = 0
+    void* gout;
+    float* g0out;
+    const void* Fin;  // [2][ny][nx] Real
+    void* Fout;
+    // moments mode outputs (double, may be null)
+    double* rho_out;
+    double* u_out;
+    double* lnf_out;
+    ErrorLatch* err;
+    MixConst mix;
+};
+
+template <int ST> struct StoreTraits;
+template <> struct StoreTraits<ST_F64> { using Real = double; using Elem = double; };
+template <> struct StoreTraits<ST_F32> { using Real = float; using Elem = float; };
+template <> struct StoreTraits<ST_F16DEV> { using Real = float; using Elem = __half; };
+template <> struct StoreTraits<ST_BF16DEV> { using Real = float; using Elem = __nv_bfloat16; };
+
+__device__ __forceinline__ float to_real(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_real(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_real(float v) { return v; }
+__device__ __forceinline__ double to_real(double v) { return v; }
+template <typename E> __device__ __forceinline__ E from_real(float v);
+template <> __device__ __forceinline__ __half from_real<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_real<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ float from_real<float>(float v) { return v; }
+
+// Read-only loads through the non-coherent path.
+template <typename E> __device__ __forceinline__ E ldg(const E* p) { return __ldg(p); }
+template <> __device__ __forceinline__ __half ldg<__half>(const __half* p) { return __ldg(p); }
+template <> __device__ __forceinline__ __nv_bfloat16 ldg<__nv_bfloat16>(const __nv_bfloat16* p) {
+    return __ldg(p);
+}
+
+template <int ST>
+__device__ __forceinline__ typename StoreTraits<ST>::Real load_g(const StepArgs& A, int i, int a, size_t node,
+                                                                  size_t nxy) {
+    using Elem = typename StoreTraits<ST>::Elem;
+    if constexpr (ST == ST_F64 || ST == ST_F32) {
+        return to_real(ldg(static_cast<const Elem*>(A.gin) + (size_t)(i * 9 + a) * nxy + node));
+    } else {
+        if (a == 0) return ldg(A.g0in + (size_t)i * nxy + node);
+        return to_real(ldg(static_cast<const Elem*>(A.gin) + (size_t)(i * 8 + a - 1) * nxy + node));
+    }
+}
+
+template <int ST>
+__device__ __forceinline__ void store_g(const StepArgs& A, int i, int a, size_t node, size_t nxy,
+                                        typename StoreTraits<ST>::Real v) {
+    using Elem = typename StoreTraits<ST>::Elem;
+    if constexpr (ST == ST_F64) {
+        static_cast<double*>(A.gout)[(size_t)(i * 9 + a) * nxy + node] = v;
+    } else if constexpr (ST == ST_F32) {
+        static_cast<float*>(A.gout)[(size_t)(i * 9 + a) * nxy + node] = v;
+    } else {
+        if (a == 0)
+            A.g0out[(size_t)i * nxy + node] = v;
+        else
+            static_cast<Elem*>(A.gout)[(size_t)(i * 8 + a - 1) * nxy + node] = from_real<Elem>(v);
+    }
+}
+
+__device__ __forceinline__ int wrap(int v, int n) {
+    int r = v % n;
+    return r < 0 ? r + n : r;
+}
+
+// ln f_i at one node from its molar densities (steps 2-5), written in terms of the
+// packing fraction beta = b_m rho~ so that v = 1 / rho~ never appears:
+//   ln x_i - ln((v - b_m)/RT) = ln(rho~_i RT) - log1p(-beta)
+//   PR : p v / RT - 1 = beta/(1-beta) - (aa_m rho~ / RT) / (1 + 2 beta - beta^2)
+//        ln[(v + (1+sqrt2) b_m)/(v + (1-sqrt2) b_m)] = log1p((1+sqrt2) beta) - log1p((1-sqrt2) beta)
+//   SRK: p v / RT - 1 = beta/(1-beta) - (aa_m rho~ / RT) / (1 + beta),  ln(1 + b_m / v) = log1p(beta)
+//   vdW: b_i / (v - b_m) = b_i rho~ / (1 - beta),  2 S_i / (RT v) = 2 S_i rho~ / RT
+// Returns beta (for the domain check).
+template <int NC, typename E>
+__device__ __forceinline__ E node_lnf(const MixConst& m, const E* rt, E* lnf) {
+    E rtot = E(0);
+#pragma unroll
+    for (int i = 0; i < NC; ++i) rtot += rt[i];
+    const E inv = E(1) / rtot;
+    E x[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) x[i] = rt[i] * inv;
+    E bm = E(0);
+#pragma unroll
+    for (int i = 0; i < NC; ++i) bm += x[i] * E(m.b[i]);
+    E S[NC];
+    E aam = E(0);
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+        E s = E(0);
+#pragma unroll
+        for (int j = 0; j < NC; ++j) s += E(m.aij[i * kMaxC + j]) * x[j];
+        S[i] = s;
+        aam += x[i] * s;
+    }
+    const E RT = E(m.RT);
+    const E beta = bm * rtot;
+    const E l1mb = log1p(-beta);
+    if (m.eos == 2) {
+#pragma unroll
+        for (int i = 0; i < NC; ++i)
+            lnf[i] = log(rt[i] * RT) - l1mb + E(m.b[i]) * rtot / (E(1) - beta) - E(2) * S[i] * rtot / RT;
+        return beta;
+    }
+    const E att = aam * rtot / RT;
+    E rep, lr, pref;
+    if (m.eos == 0) {
+        const E s2 = E(1.4142135623730950488);
+        rep = beta / (E(1) - beta) - att / (E(1) + E(2) * beta - beta * beta);
+        lr = log1p((E(1) + s2) * beta) - log1p((E(1) - s2) * beta);
+        pref = E(1) / (E(2) * s2 * bm * RT);
+    } else {
+        rep = beta / (E(1) - beta) - att / (E(1) + beta);
+        lr = log1p(beta);
+        pref = E(1) / (bm * RT);
+    }
+    const E invbm = E(1) / bm;
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+        const E bi = E(m.b[i]) * invbm;
+        lnf[i] = log(rt[i] * RT) - l1mb + bi * rep + pref * (aam * bi - E(2) * S[i]) * lr;
+    }
+    return beta;
+}
+
+// Shared-memory tile of a field with a halo of H nodes.
+template <typename E, int NC, int TY, int H>
+struct Tile {
+    static constexpr int W = kTX + 2 * H;
+    static constexpr int Hh = TY + 2 * H;
+    E v[NC][Hh][W];
+};
+
+// Finite differences at tile position (cx, cy) of a field tile f (any halo >= 1).
+// stencil 1 = central (Eqs. eq1stder, eq2ndder); 0 = isotropic D2Q9 stencils.
+template <typename E, typename T>
+__device__ __forceinline__ void grad_at(const T& f, int i, int cx, int cy, int stencil, E& gx, E& gy) {
+    const E e = f.v[i][cy][cx + 1], w = f.v[i][cy][cx - 1];
+    const E n = f.v[i][cy + 1][cx], s = f.v[i][cy - 1][cx];
+    if (stencil == 1) {
+        gx = E(0.5) * (e - w);
+        gy = E(0.5) * (n - s);
+    } else {
+        const E ne = f.v[i][cy + 1][cx + 1], nw = f.v[i][cy + 1][cx - 1];
+        const E sw = f.v[i][cy - 1][cx - 1], se = f.v[i][cy - 1][cx + 1];
+        // 3 sum_a w_a e_a h(r + e_a): 1/3 for the axis neighbours, 1/12 for the diagonals
+        gx = (e - w) * E(1.0 / 3.0) + (ne - nw - sw + se) * E(1.0 / 12.0);
+        gy = (n - s) * E(1.0 / 3.0) + (ne + nw - sw - se) * E(1.0 / 12.0);
+    }
+}
+
+template <typename E, typename T>
+__device__ __forceinline__ E lap_at(const T& f, int i, int cx, int cy, int stencil) {
+    const E c = f.v[i][cy][cx];
+    const E ax = f.v[i][cy][cx + 1] + f.v[i][cy][cx - 1] + f.v[i][cy + 1][cx] + f.v[i][cy - 1][cx];
+    if (stencil == 1) return ax - E(4) * c;
+    const E dg = f.v[i][cy + 1][cx + 1] + f.v[i][cy + 1][cx - 1] + f.v[i][cy - 1][cx - 1] + f.v[i][cy - 1][cx + 1];
+    // 6 sum_a w_a (h(r+e_a) - h(r)): 2/3 for axis neighbours, 1/6 for diagonals
+    return (ax - E(4) * c) * E(2.0 / 3.0) + (dg - E(4) * c) * E(1.0 / 6.0);
+}
+
+template <typename E, int NC, int TY>
+struct StepSmem {
+    Tile<E, NC, TY, 2> rt;   // rho~ on tile + 2
+    Tile<E, NC, TY, 1> lf;   // ln f on tile + 1
+    Tile<E, NC, TY, 1> G;    // sum_j kappa_ij lap rho~_j on tile + 1
+};
+
+// MOMENTS = true: compute the macroscopic fields of the current state instead of
+// advancing it (no distribution or force store).
+template <int NC, int ST, int TY, bool MOMENTS>
+__global__ void __launch_bounds__(kTX* TY) fused_step(StepArgs A) {
+    using Real = typename StoreTraits<ST>::Real;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto& S = *reinterpret_cast<StepSmem<Real, NC, TY>*>(smem_raw);
+
+    const int nx = A.nx, ny = A.ny;
+    const size_t nxy = (size_t)nx * ny;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * kTX + tx;
+    constexpr int NT = kTX * TY;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * TY;
+
+    // ---- phase 1: pull and sum (steps 1-2) ----
+    const int gxn = x0 + tx, gyn = y0 + ty;
+    const bool valid = gxn < nx && gyn < ny;
+    Real g[NC][9];
+    {
+        const int wx = wrap(gxn, nx), wy = wrap(gyn, ny);
+        const int xm = wx == 0 ? nx - 1 : wx - 1, xp = wx == nx - 1 ? 0 : wx + 1;
+        const int ym = wy == 0 ? ny - 1 : wy - 1, yp = wy == ny - 1 ? 0 : wy + 1;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            // g_a(r, t) = g*_a(r - e_a, t - 1)
+            const int sx = ex(a) == 1 ? xm : (ex(a) == -1 ? xp : wx);
+            const int sy = ey(a) == 1 ? ym : (ey(a) == -1 ? yp : wy);
+            const size_t src = (size_t)sy * nx + sx;
+#pragma unroll
+            for (int i = 0; i < NC; ++i) g[i][a] = load_g<ST>(A, i, a, src, nxy);
+        }
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+            Real r = Real(0);
+#pragma unroll
+            for (int a = 0; a < 9; ++a) r += g[i][a];
+            S.rt.v[i][ty + 2][tx + 2] = r * Real(A.mix.invM[i]);
+        }
+    }
+    {
+        constexpr int WB = kTX + 4;
+        constexpr int RING = 4 * WB + 4 * TY;
+        for (int r = tid; r < RING; r += NT) {
+            int bx, by;
+            if (r < 2 * WB) {
+                by = r / WB;
+                bx = r % WB;
+            } else if (r < 4 * WB) {
+                by = TY + 2 + (r - 2 * WB) / WB;
+                bx = (r - 2 * WB) % WB;
+            } else {
+                const int q = r - 4 * WB;
+                by = 2 + (q >> 2);
+                const int c = q & 3;
+                bx = c < 2 ? c : kTX + c;  // 0, 1, TX+2, TX+3
+            }
+            const int wx = wrap(x0 - 2 + bx, nx), wy = wrap(y0 - 2 + by, ny);
+            const int xm = wx == 0 ? nx - 1 : wx - 1, xp = wx == nx - 1 ? 0 : wx + 1;
+            const int ym = wy == 0 ? ny - 1 : wy - 1, yp = wy == ny - 1 ? 0 : wy + 1;
+            Real rs[NC];
+#pragma unroll
+            for (int i = 0; i < NC; ++i) rs[i] = Real(0);
+#pragma unroll
+            for (int a = 0; a < 9; ++a) {
+                const int sx = ex(a) == 1 ? xm : (ex(a) == -1 ? xp : wx);
+                const int sy = ey(a) == 1 ? ym : (ey(a) == -1 ? yp : wy);
+                const size_t src = (size_t)sy * nx + sx;
+#pragma unroll
+                for (int i = 0; i < NC; ++i) rs[i] += load_g<ST>(A, i, a, src, nxy);
+            }
+#pragma unroll
+            for (int i = 0; i < NC; ++i) S.rt.v[i][by][bx] = rs[i] * Real(A.mix.invM[i]);
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 2: ln f (steps 3-5) and G = sum_j kappa_ij lap rho~_j (step 6) ----
+    {
+        constexpr int W1 = kTX + 2;
+        constexpr int N1 = W1 * (TY + 2);
+        for (int q = tid; q < N1; q += NT) {
+            const int cy = q / W1, cx = q % W1;  // tile+1 coordinates
+            Real rt[NC], lnf[NC], L[NC];
+#pragma unroll
+            for (int i = 0; i < NC; ++i) rt[i] = S.rt.v[i][cy + 1][cx + 1];
+            const Real beta = node_lnf<NC, Real>(A.mix, rt, lnf);
+#pragma unroll
+            for (int j = 0; j < NC; ++j) L[j] = lap_at<Real>(S.rt, j, cx + 1, cy + 1, A.stencil);
+#pragma unroll
+            for (int i = 0; i < NC; ++i) {
+                Real Gi = Real(0);
+#pragma unroll
+                for (int j = 0; j < NC; ++j) Gi += Real(A.mix.kap[i * kMaxC + j]) * L[j];
+                S.lf.v[i][cy][cx] = lnf[i];
+                S.G.v[i][cy][cx] = Gi;
+            }
+            // domain check at the nodes this block owns
+            const int ix = cx - 1, iy = cy - 1;
+            if (ix >= 0 && ix < kTX && iy >= 0 && iy < TY && x0 + ix < nx && y0 + iy < ny) {
+                bool bad = !(beta < Real(1));
+                int badc = 0;
+#pragma unroll
+                for (int i = 0; i < NC; ++i) {
+                    if (!(rt[i] > Real(0)) || !isfinite(lnf[i])) {
+                        if (!bad) badc = i;
+                        bad = true;
+                    }
+                }
+                if (bad && atomicCAS(&A.err->flag, 0, 1) == 0) {
+                    A.err->comp = badc;
+                    A.err->x = x0 + ix;
+                    A.err->y = y0 + iy;
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    if (!valid) return;
+
+    // ---- phase 3: force (step 7), velocity (step 1), equilibrium and forcing (step 8),
+    //      collision (step 9) ----
+    const int cx = tx + 1, cy = ty + 1;  // tile+1 coordinates of this node
+    Real Fx[NC], Fy[NC], grx[NC], gry[NC];
+    Real rho = Real(0), jx = Real(0), jy = Real(0), Ftx = Real(0), Fty = Real(0);
+    const Real RT = Real(A.mix.RT);
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+        Real lx, ly, Gx, Gy, rx, ry;
+        grad_at<Real>(S.lf, i, cx, cy, A.stencil, lx, ly);
+        grad_at<Real>(S.G, i, cx, cy, A.stencil, Gx, Gy);
+        grad_at<Real>(S.rt, i, cx + 1, cy + 1, A.stencil, rx, ry);
+        const Real rti = S.rt.v[i][cy + 1][cx + 1];
+        // Eq. eqforcefinal: F_i = -rho~_i RT grad ln f_i + rho~_i grad(sum_j kappa_ij lap rho~_j)
+        Fx[i] = rti * (Gx - RT * lx);
+        Fy[i] = rti * (Gy - RT * ly);
+        Ftx += Fx[i];
+        Fty += Fy[i];
+        // grad rho_i = M_i grad rho~_i
+        grx[i] = rx * Real(A.mix.M[i]);
+        gry[i] = ry * Real(A.mix.M[i]);
+        Real r = Real(0);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            r += g[i][a];
+            jx += Real(ex(a)) * g[i][a];
+            jy += Real(ey(a)) * g[i][a];
+        }
+        rho += r;
+    }
+    const size_t node = (size_t)gyn * nx + gxn;
+    Real Fux = Ftx, Fuy = Fty;
+    if (A.lagged) {
+        const Real* Fin = static_cast<const Real*>(A.Fin);
+        Fux = __ldg(Fin + node);
+        Fuy = __ldg(Fin + nxy + node);
+    }
+    const Real inv_rho = Real(1) / rho;
+    const Real ux = (jx + Real(0.5) * Fux) * inv_rho;
+    const Real uy = (jy + Real(0.5) * Fuy) * inv_rho;
+
+    if constexpr (MOMENTS) {
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+            Real r = Real(0);
+#pragma unroll
+            for (int a = 0; a < 9; ++a) r += g[i][a];
+            if (A.rho_out) A.rho_out[(size_t)i * nxy + node] = (double)r;
+            if (A.lnf_out) A.lnf_out[(size_t)i * nxy + node] = (double)S.lf.v[i][cy][cx];
+        }
+        if (A.u_out) {
+            A.u_out[node] = (double)ux;
+            A.u_out[nxy + node] = (double)uy;
+        }
+        return;
+    } else {
+        const Real omega = Real(A.omega), fcoef = Real(A.fcoef);
+        const Real usq = ux * ux + uy * uy;
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+            Real rhoi = Real(0);
+#pragma unroll
+            for (int a = 0; a < 9; ++a) rhoi += g[i][a];
+            const Real uF = ux * Fx[i] + uy * Fy[i];
+            const Real ug = ux * grx[i] + uy * gry[i];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) {
+                const Real cxa = Real(ex(a)), cya = Real(ey(a));
+                const Real eu = cxa * ux + cya * uy;
+                const Real eF = cxa * Fx[i] + cya * Fy[i];
+                const Real eg = cxa * grx[i] + cya * gry[i];
+                const Real w = wgt<Real>(a);
+                // Eq. eqLBEMCb (rho_0 = 0): S_a = 3 (e.u) + 4.5 (e.u)^2 - 1.5 u^2
+                const Real Sa = Real(3) * eu + Real(4.5) * eu * eu - Real(1.5) * usq;
+                const Real geq = (a == 0 ? rhoi : Real(0)) + w * rhoi * Sa;
+                // Eq. eqLBEMCfinal3: F.w[(e-u)/cs2 + (u.e) e/cs4] + grad rho.w[-u + (u.e) e/cs2 + (e^2/cs2 - D) u/2]
+                const int e2 = ex(a) * ex(a) + ey(a) * ey(a);
+                const Real cD = Real(0.5) * Real(3 * e2 - 2);
+                const Real Fa = w * (Real(3) * (eF - uF) + Real(9) * eu * eF + (cD - Real(1)) * ug +
+                                     Real(3) * eu * eg);
+                const Real gn = g[i][a] - omega * (g[i][a] - geq) + fcoef * Fa;
+                store_g<ST>(A, i, a, node, nxy, gn);
+            }
+        }
+        Real* Fout = static_cast<Real*>(A.Fout);
+        Fout[node] = Ftx;
+        Fout[nxy + node] = Fty;
+    }
+}
+
+// g = g^eq(rho, u = 0): rho_i in a = 0, zero elsewhere; stored force zero.
+template <int NC, int ST>
+__global__ void init_rest(StepArgs A, const double* __restrict__ rho) {
+    using Real = typename StoreTraits<ST>::Real;
+    const size_t nxy = (size_t)A.nx * A.ny;
+    for (size_t node = blockIdx.x * (size_t)blockDim.x + threadIdx.x; node < nxy;
+         node += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+            const Real r = (Real)rho[(size_t)i * nxy + node];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) store_g<ST>(A, i, a, node, nxy, a == 0 ? r : Real(0));
+        }
+        Real* F = static_cast<Real*>(A.Fout);
+        F[node] = Real(0);
+        F[nxy + node] = Real(0);
+    }
+}
+
+// Post-streaming distributions <-> storage: g_a(r) = g*_a(r - e_a).
+// to_storage = true: gin_d (double, [N][9][ny][nx] post-streaming) -> storage (A.gout);
+// false: storage (A.gin) -> gout_d.
+template <int NC, int ST>
+__global__ void convert_g(StepArgs A, const double* __restrict__ gin_d, double* __restrict__ gout_d,
+                          bool to_storage) {
+    using Real = typename StoreTraits<ST>::Real;
+    const int nx = A.nx, ny = A.ny;
+    const size_t nxy = (size_t)nx * ny;
+    for (size_t node = blockIdx.x * (size_t)blockDim.x + threadIdx.x; node < nxy;
+         node += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(node % nx), y = (int)(node / nx);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            if (to_storage) {
+                // storage at r holds g_a(r + e_a)
+                const size_t src = (size_t)wrap(y + ey(a), ny) * nx + wrap(x + ex(a), nx);
+#pragma unroll
+                for (int i = 0; i < NC; ++i)
+                    store_g<ST>(A, i, a, node, nxy, (Real)gin_d[(size_t)(i * 9 + a) * nxy + src]);
+            } else {
+                const size_t src = (size_t)wrap(y - ey(a), ny) * nx + wrap(x - ex(a), nx);
+#pragma unroll
+                for (int i = 0; i < NC; ++i)
+                    gout_d[(size_t)(i * 9 + a) * nxy + node] = (double)load_g<ST>(A, i, a, src, nxy);
+            }
+        }
+    }
+}
+
+// Deterministic reductions: per block, sums over a fixed grid-stride set of nodes of
+// rho_i (component mass), (rho - rho_prev)^2 and rho^2 in double, then writes
+// rho_prev <- rho.  partial has kReduceBlocks rows of NC + 2 doubles.
+constexpr int kReduceBlocks = 296;
+constexpr int kReduceThreads = 256;
+
+template <int NC, int ST>
+__global__ void __launch_bounds__(kReduceThreads) reduce_partial(StepArgs A, double* __restrict__ rho_prev,
+                                                                  int have_prev, double* __restrict__ partial) {
+    const int nx = A.nx, ny = A.ny;
+    const size_t nxy = (size_t)nx * ny;
+    double acc[NC + 2];
+#pragma unroll
+    for (int k = 0; k < NC + 2; ++k) acc[k] = 0.0;
+    for (size_t node = blockIdx.x * (size_t)blockDim.x + threadIdx.x; node < nxy;
+         node += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(node % nx), y = (int)(node / nx);
+        const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+        const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+            double r = 0.0;
+#pragma unroll
+            for (int a = 0; a < 9; ++a) {
+                const int sx = ex(a) == 1 ? xm : (ex(a) == -1 ? xp : x);
+                const int sy = ey(a) == 1 ? ym : (ey(a) == -1 ? yp : y);
+                r += (double)load_g<ST>(A, i, a, (size_t)sy * nx + sx, nxy);
+            }
+            acc[i] += r;
+            acc[NC + 1] += r * r;
+            const size_t k = (size_t)i * nxy + node;
+            if (have_prev) {
+                const double d = r - rho_prev[k];
+                acc[NC] += d * d;
+            }
+            rho_prev[k] = r;
+        }
+    }
+    __shared__ double red[kReduceThreads / 32][NC + 2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NC + 2; ++k) {
+        double v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NC + 2) {
+        double v = 0.0;
+        for (int w = 0; w < kReduceThreads / 32; ++w) v += red[w][threadIdx.x];
+        partial[(size_t)blockIdx.x * (NC + 2) + threadIdx.x] = v;
+    }
+}
+
+template <int NC>
+__global__ void reduce_final(const double* __restrict__ partial, int nblocks, double* __restrict__ out) {
+    // one warp per quantity, fixed order
+    const int k = blockIdx.x;
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += 32) v += partial[(size_t)b * (NC + 2) + k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) out[k] = v;
+}
+
+}  // namespace fmlbm

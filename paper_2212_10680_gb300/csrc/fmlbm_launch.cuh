@@ -1,0 +1,96 @@
+// Host-side launchers of the device kernels, one explicit instantiation set per
+// storage precision (step_f64.cu, step_f32.cu, step_f16.cu, step_bf16.cu).
+#pragma once
+
+#include "fmlbm_kernels.cuh"
+
+namespace fmlbm {
+
+constexpr int kTileY = 8;
+
+template <int ST>
+cudaError_t launch_step(const StepArgs& A, int nc, bool moments, cudaStream_t s);
+template <int ST>
+cudaError_t launch_init(const StepArgs& A, int nc, const double* rho, cudaStream_t s);
+template <int ST>
+cudaError_t launch_convert(const StepArgs& A, int nc, const double* gin_d, double* gout_d, bool to_storage,
+                           cudaStream_t s);
+template <int ST>
+cudaError_t launch_reduce(const StepArgs& A, int nc, double* rho_prev, int have_prev, double* partial,
+                          double* out, cudaStream_t s);
+
+#define FMLBM_DEFINE_LAUNCHERS(ST)                                                                        \
+    template <int NC, bool MOM>                                                                           \
+    static cudaError_t launch_step_nc_##ST(const StepArgs& A, cudaStream_t s) {                           \
+        using Real = typename StoreTraits<ST>::Real;                                                      \
+        constexpr size_t smem = sizeof(StepSmem<Real, NC, kTileY>);                                       \
+        auto k = fused_step<NC, ST, kTileY, MOM>;                                                         \
+        static bool attr_done = false;                                                                    \
+        if (!attr_done) {                                                                                 \
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+            if (e != cudaSuccess) return e;                                                               \
+            attr_done = true;                                                                             \
+        }                                                                                                 \
+        dim3 grid((A.nx + kTX - 1) / kTX, (A.ny + kTileY - 1) / kTileY);                                  \
+        k<<<grid, dim3(kTX, kTileY), smem, s>>>(A);                                                       \
+        return cudaGetLastError();                                                                        \
+    }                                                                                                     \
+    template <>                                                                                           \
+    cudaError_t launch_step<ST>(const StepArgs& A, int nc, bool moments, cudaStream_t s) {                \
+        switch (nc) {                                                                                     \
+            case 1: return moments ? launch_step_nc_##ST<1, true>(A, s) : launch_step_nc_##ST<1, false>(A, s); \
+            case 2: return moments ? launch_step_nc_##ST<2, true>(A, s) : launch_step_nc_##ST<2, false>(A, s); \
+            case 3: return moments ? launch_step_nc_##ST<3, true>(A, s) : launch_step_nc_##ST<3, false>(A, s); \
+            case 4: return moments ? launch_step_nc_##ST<4, true>(A, s) : launch_step_nc_##ST<4, false>(A, s); \
+        }                                                                                                 \
+        return cudaErrorInvalidValue;                                                                     \
+    }                                                                                                     \
+    static int grid_1d(size_t n) {                                                                        \
+        size_t b = (n + 255) / 256;                                                                       \
+        return (int)(b > 4096 ? 4096 : (b == 0 ? 1 : b));                                                 \
+    }                                                                                                     \
+    template <>                                                                                           \
+    cudaError_t launch_init<ST>(const StepArgs& A, int nc, const double* rho, cudaStream_t s) {           \
+        const int g = grid_1d((size_t)A.nx * A.ny);                                                       \
+        switch (nc) {                                                                                     \
+            case 1: init_rest<1, ST><<<g, 256, 0, s>>>(A, rho); break;                                    \
+            case 2: init_rest<2, ST><<<g, 256, 0, s>>>(A, rho); break;                                    \
+            case 3: init_rest<3, ST><<<g, 256, 0, s>>>(A, rho); break;                                    \
+            case 4: init_rest<4, ST><<<g, 256, 0, s>>>(A, rho); break;                                    \
+            default: return cudaErrorInvalidValue;                                                        \
+        }                                                                                                 \
+        return cudaGetLastError();                                                                        \
+    }                                                                                                     \
+    template <>                                                                                           \
+    cudaError_t launch_convert<ST>(const StepArgs& A, int nc, const double* gin_d, double* gout_d,        \
+                                   bool to_storage, cudaStream_t s) {                                     \
+        const int g = grid_1d((size_t)A.nx * A.ny);                                                       \
+        switch (nc) {                                                                                     \
+            case 1: convert_g<1, ST><<<g, 256, 0, s>>>(A, gin_d, gout_d, to_storage); break;              \
+            case 2: convert_g<2, ST><<<g, 256, 0, s>>>(A, gin_d, gout_d, to_storage); break;              \
+            case 3: convert_g<3, ST><<<g, 256, 0, s>>>(A, gin_d, gout_d, to_storage); break;              \
+            case 4: convert_g<4, ST><<<g, 256, 0, s>>>(A, gin_d, gout_d, to_storage); break;              \
+            default: return cudaErrorInvalidValue;                                                        \
+        }                                                                                                 \
+        return cudaGetLastError();                                                                        \
+    }                                                                                                     \
+    template <int NC>                                                                                     \
+    static cudaError_t launch_reduce_nc_##ST(const StepArgs& A, double* rho_prev, int have_prev,          \
+                                             double* partial, double* out, cudaStream_t s) {              \
+        reduce_partial<NC, ST><<<kReduceBlocks, kReduceThreads, 0, s>>>(A, rho_prev, have_prev, partial); \
+        reduce_final<NC><<<NC + 2, 32, 0, s>>>(partial, kReduceBlocks, out);                              \
+        return cudaGetLastError();                                                                        \
+    }                                                                                                     \
+    template <>                                                                                           \
+    cudaError_t launch_reduce<ST>(const StepArgs& A, int nc, double* rho_prev, int have_prev,             \
+                                  double* partial, double* out, cudaStream_t s) {                         \
+        switch (nc) {                                                                                     \
+            case 1: return launch_reduce_nc_##ST<1>(A, rho_prev, have_prev, partial, out, s);             \
+            case 2: return launch_reduce_nc_##ST<2>(A, rho_prev, have_prev, partial, out, s);             \
+            case 3: return launch_reduce_nc_##ST<3>(A, rho_prev, have_prev, partial, out, s);             \
+            case 4: return launch_reduce_nc_##ST<4>(A, rho_prev, have_prev, partial, out, s);             \
+        }                                                                                                 \
+        return cudaErrorInvalidValue;                                                                     \
+    }
+
+}  // namespace fmlbm

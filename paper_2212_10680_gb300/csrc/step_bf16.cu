@@ -1,0 +1,6 @@
+// Kernel instantiations for storage precision ST_BF16DEV.
+#include "fmlbm_launch.cuh"
+
+namespace fmlbm {
+FMLBM_DEFINE_LAUNCHERS(ST_BF16DEV)
+}  // namespace fmlbm

@@ -1,0 +1,6 @@
+// Kernel instantiations for storage precision ST_F32.
+#include "fmlbm_launch.cuh"
+
+namespace fmlbm {
+FMLBM_DEFINE_LAUNCHERS(ST_F32)
+}  // namespace fmlbm

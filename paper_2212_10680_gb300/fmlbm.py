@@ -1,0 +1,272 @@
+"""Thin ctypes binding of libfmlbm.so (the C ABI in include/fmlbm.h).
+
+Only argument marshalling lives here: every step of the lattice update runs in the
+library's CUDA kernels.  The functions carry the C names; each raises FmlbmError on
+a non-zero status.  If the shared library is missing, importing this module fails
+loudly; there is no CPU fallback.
+
+Host arrays are numpy float64, C order, with the layouts documented in fmlbm.h:
+fields [N][ny][nx], vectors [2][ny][nx], distributions [N][9][ny][nx].
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+MAX_COMPONENTS = 4
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfmlbm.so")
+
+EOS = {"pr": 0, "srk": 1, "vdw": 2}
+STENCIL = {"isotropic": 0, "central": 1}
+PRECISION = {"fp64": 0, "fp32": 1, "fp16dev": 2, "bf16dev": 3}
+VELOCITY_FORCE = {"lagged": 0, "current": 1}
+STATUS = {0: "FMLBM_OK", 1: "FMLBM_E_INVALID_ARG", 2: "FMLBM_E_OOM", 3: "FMLBM_E_CUDA",
+          4: "FMLBM_E_NONPHYSICAL", 5: "FMLBM_E_TIMEOUT", 6: "FMLBM_E_BUSY", 7: "FMLBM_E_NOT_CONVERGED",
+          8: "FMLBM_E_UNSUPPORTED"}
+E_NONPHYSICAL = 4
+E_NOT_CONVERGED = 7
+E_BUSY = 6
+
+
+class FmlbmError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str = ""):
+        super().__init__(f"{where}: {STATUS.get(status, status)} {message}".strip())
+        self.status = status
+
+
+class fmlbm_mixture(ctypes.Structure):
+    _fields_ = [("n_components", ctypes.c_int32), ("eos", ctypes.c_int32), ("R", ctypes.c_double),
+                ("T", ctypes.c_double), ("Tc", ctypes.c_double * MAX_COMPONENTS),
+                ("Pc", ctypes.c_double * MAX_COMPONENTS), ("omega", ctypes.c_double * MAX_COMPONENTS),
+                ("M", ctypes.c_double * MAX_COMPONENTS), ("kappa", ctypes.c_double * MAX_COMPONENTS),
+                ("kij", ctypes.c_double * (MAX_COMPONENTS * MAX_COMPONENTS))]
+
+
+class fmlbm_lattice(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("tau", ctypes.c_double),
+                ("stencil", ctypes.c_int32), ("precision", ctypes.c_int32), ("velocity_force", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libfmlbm.so is not built ({_LIB_PATH}); run "
+                          "`python -m paper_2212_10680_gb300.build` first")
+    lib = ctypes.CDLL(_LIB_PATH)
+    H = ctypes.c_void_p
+    dp = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "fmlbm_create": ([ctypes.POINTER(fmlbm_mixture), ctypes.POINTER(fmlbm_lattice), ctypes.c_void_p,
+                          ctypes.POINTER(H)], ctypes.c_int),
+        "fmlbm_init": ([H, dp], ctypes.c_int),
+        "fmlbm_init_device": ([H, ctypes.c_void_p], ctypes.c_int),
+        "fmlbm_step": ([H, ctypes.c_int64], ctypes.c_int),
+        "fmlbm_moments": ([H, dp, dp, dp], ctypes.c_int),
+        "fmlbm_get_distributions": ([H, dp, dp], ctypes.c_int),
+        "fmlbm_set_distributions": ([H, dp, dp], ctypes.c_int),
+        "fmlbm_diagnostics": ([H, dp, dp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "fmlbm_error_node": ([H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                              ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "fmlbm_state_size": ([H, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+        "fmlbm_get_state": ([H, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+        "fmlbm_set_state": ([H, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+        "fmlbm_synchronize": ([H], ctypes.c_int),
+        "fmlbm_lattice_bytes": ([ctypes.c_int32, ctypes.POINTER(fmlbm_lattice), ctypes.POINTER(ctypes.c_size_t)],
+                                ctypes.c_int),
+        "fmlbm_destroy": ([H], None),
+        "fmlbm_status_str": ([ctypes.c_int], ctypes.c_char_p),
+        "fmlbm_last_error": ([H], ctypes.c_char_p),
+        "fmlbm_version": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+LIB = _load()
+
+
+def _ptr(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(status: int, where: str, h=None):
+    if status != 0:
+        msg = LIB.fmlbm_last_error(h).decode() if h else ""
+        raise FmlbmError(status, where, msg)
+
+
+def make_mixture(eos: str, R: float, T: float, Tc: Sequence[float], Pc: Sequence[float], omega: Sequence[float],
+                 M: Sequence[float] = None, kappa: Sequence[float] = None, kij=None) -> fmlbm_mixture:
+    n = len(Tc)
+    m = fmlbm_mixture()
+    m.n_components = n
+    m.eos = EOS[eos.lower()]
+    m.R, m.T = R, T
+    M = [1.0] * n if M is None else M
+    kappa = [0.0] * n if kappa is None else kappa
+    kij = np.zeros((n, n)) if kij is None else np.asarray(kij, dtype=np.float64).reshape(n, n)
+    for i in range(n):
+        m.Tc[i], m.Pc[i], m.omega[i], m.M[i], m.kappa[i] = Tc[i], Pc[i], omega[i], M[i], kappa[i]
+        for j in range(n):
+            m.kij[i * MAX_COMPONENTS + j] = kij[i, j]
+    return m
+
+
+def mixture_from_dict(d: dict) -> fmlbm_mixture:
+    return make_mixture(d["eos"], d["R"], d["T"], d["Tc"], d["Pc"], d["omega"], d.get("M"), d.get("kappa"),
+                        d.get("kij"))
+
+
+def make_lattice(nx: int, ny: int, tau: float, stencil: str = "isotropic", precision: str = "fp32",
+                 velocity_force: str = "lagged") -> fmlbm_lattice:
+    L = fmlbm_lattice()
+    L.nx, L.ny, L.tau = nx, ny, tau
+    L.stencil = STENCIL[stencil]
+    L.precision = PRECISION[precision]
+    L.velocity_force = VELOCITY_FORCE[velocity_force]
+    L.reserved = 0
+    return L
+
+
+# ---- the C entry points, one wrapper each ----
+
+def fmlbm_create(mixture: fmlbm_mixture, lattice: fmlbm_lattice, stream: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(LIB.fmlbm_create(ctypes.byref(mixture), ctypes.byref(lattice), ctypes.c_void_p(stream or None),
+                            ctypes.byref(h)), "fmlbm_create")
+    return h
+
+
+def fmlbm_init(h, rho: np.ndarray):
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    _check(LIB.fmlbm_init(h, _ptr(rho)), "fmlbm_init", h)
+
+
+def fmlbm_init_device(h, rho_device_ptr: int):
+    _check(LIB.fmlbm_init_device(h, ctypes.c_void_p(rho_device_ptr)), "fmlbm_init_device", h)
+
+
+def fmlbm_step(h, nsteps: int):
+    _check(LIB.fmlbm_step(h, ctypes.c_int64(nsteps)), "fmlbm_step", h)
+
+
+def fmlbm_moments(h, rho: np.ndarray = None, u: np.ndarray = None, lnf: np.ndarray = None):
+    _check(LIB.fmlbm_moments(h, _ptr(rho), _ptr(u), _ptr(lnf)), "fmlbm_moments", h)
+
+
+def fmlbm_get_distributions(h, g: np.ndarray = None, force: np.ndarray = None):
+    _check(LIB.fmlbm_get_distributions(h, _ptr(g), _ptr(force)), "fmlbm_get_distributions", h)
+
+
+def fmlbm_set_distributions(h, g: np.ndarray, force: np.ndarray = None):
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    force = None if force is None else np.ascontiguousarray(force, dtype=np.float64)
+    _check(LIB.fmlbm_set_distributions(h, _ptr(g), _ptr(force)), "fmlbm_set_distributions", h)
+
+
+def fmlbm_diagnostics(h, n_components: int):
+    mass = np.empty(n_components)
+    res = ctypes.c_double()
+    step = ctypes.c_int64()
+    st = LIB.fmlbm_diagnostics(h, _ptr(mass), ctypes.byref(res), ctypes.byref(step))
+    _check(st, "fmlbm_diagnostics", h)
+    return mass, res.value, step.value
+
+
+def fmlbm_error_node(h):
+    c, x, y = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(LIB.fmlbm_error_node(h, ctypes.byref(c), ctypes.byref(x), ctypes.byref(y)), "fmlbm_error_node", h)
+    return c.value, x.value, y.value
+
+
+def fmlbm_state_size(h) -> int:
+    n = ctypes.c_size_t()
+    _check(LIB.fmlbm_state_size(h, ctypes.byref(n)), "fmlbm_state_size", h)
+    return n.value
+
+
+def fmlbm_get_state(h) -> bytes:
+    n = fmlbm_state_size(h)
+    buf = ctypes.create_string_buffer(n)
+    _check(LIB.fmlbm_get_state(h, buf, n), "fmlbm_get_state", h)
+    return buf.raw
+
+
+def fmlbm_set_state(h, state: bytes):
+    buf = ctypes.create_string_buffer(state, len(state))
+    _check(LIB.fmlbm_set_state(h, buf, len(state)), "fmlbm_set_state", h)
+
+
+def fmlbm_synchronize(h):
+    _check(LIB.fmlbm_synchronize(h), "fmlbm_synchronize", h)
+
+
+def fmlbm_lattice_bytes(n_components: int, lattice: fmlbm_lattice) -> int:
+    n = ctypes.c_size_t()
+    _check(LIB.fmlbm_lattice_bytes(n_components, ctypes.byref(lattice), ctypes.byref(n)), "fmlbm_lattice_bytes")
+    return n.value
+
+
+def fmlbm_destroy(h):
+    LIB.fmlbm_destroy(h)
+
+
+def fmlbm_version() -> str:
+    return LIB.fmlbm_version().decode()
+
+
+class Lattice:
+    """One lattice on the current CUDA device; a convenience owner of a handle."""
+
+    def __init__(self, mixture: fmlbm_mixture, nx: int, ny: int, tau: float, stencil: str = "isotropic",
+                 precision: str = "fp32", velocity_force: str = "lagged", stream: int = 0):
+        self.n = mixture.n_components
+        self.nx, self.ny = nx, ny
+        self.h = fmlbm_create(mixture, make_lattice(nx, ny, tau, stencil, precision, velocity_force), stream)
+
+    def init(self, rho: np.ndarray):
+        fmlbm_init(self.h, rho)
+
+    def step(self, n: int = 1):
+        fmlbm_step(self.h, n)
+
+    def moments(self):
+        rho = np.empty((self.n, self.ny, self.nx))
+        u = np.empty((2, self.ny, self.nx))
+        lnf = np.empty((self.n, self.ny, self.nx))
+        fmlbm_moments(self.h, rho, u, lnf)
+        return rho, u, lnf
+
+    def distributions(self):
+        g = np.empty((self.n, 9, self.ny, self.nx))
+        F = np.empty((2, self.ny, self.nx))
+        fmlbm_get_distributions(self.h, g, F)
+        return g, F
+
+    def set_distributions(self, g, F=None):
+        fmlbm_set_distributions(self.h, g, F)
+
+    def diagnostics(self):
+        return fmlbm_diagnostics(self.h, self.n)
+
+    def synchronize(self):
+        fmlbm_synchronize(self.h)
+
+    def close(self):
+        if self.h:
+            fmlbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

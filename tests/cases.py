@@ -1,0 +1,72 @@
+"""Shared test cases: mixtures and initial states used by both the oracle and the
+CUDA path (test-side helpers only; the two implementations share nothing else)."""
+import json
+import os
+
+import numpy as np
+
+from oracle import lbm
+from oracle.eos import Mixture, OMEGA
+from paper_2212_10680_gb300 import inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+WORKLOADS = os.path.join(HERE, "golden", "workloads.json")
+
+OA, OB = OMEGA["pr"]
+TC1 = (2.0 / 49.0) / (2.0 / 21.0) * OB / OA
+PC1 = OB * TC1 / (2.0 / 21.0)
+
+
+def workloads() -> dict:
+    with open(WORKLOADS) as f:
+        return json.load(f)
+
+
+def mixture_dict(n=2, eos="pr", Tr=0.8, kappa_scale=1.0, M=None, kij=0.0):
+    tc = [1.0, 1.5, 1.3, 1.2][:n]
+    pc = [1.0, 0.9, 0.85, 0.95][:n]
+    om = [0.011, 0.2, 0.1, 0.15][:n]
+    ka = [0.10, 0.15, 0.12, 0.08][:n]
+    return dict(eos=eos, R=1.0, T=Tr * TC1, Tc=[r * TC1 for r in tc], Pc=[r * PC1 for r in pc], omega=om,
+                M=list(M) if M is not None else [1.0] * n, kappa=[k * kappa_scale for k in ka],
+                kij=(np.full((n, n), kij) - kij * np.eye(n)).ravel().tolist())
+
+
+def oracle_mixture(d: dict) -> Mixture:
+    n = len(d["Tc"])
+    return Mixture(d["eos"], d["R"], d["T"], Tc=d["Tc"], Pc=d["Pc"], omega=d["omega"], M=d["M"],
+                   kappa=d["kappa"], kij=np.asarray(d["kij"]).reshape(n, n))
+
+
+def smooth_state(n, nx, ny, seed=3, base=(1.0, 1.2, 0.8, 0.6), amp=0.25):
+    """A smooth single-phase-ish density field with 1% seeded noise."""
+    y, x = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    rho = np.stack([base[i] * (1 + amp * np.sin(2 * np.pi * (x / nx + (i + 1) * y / max(ny, 1)) + i))
+                    for i in range(n)])
+    return inputs.with_noise(rho, 0.01, seed)
+
+
+def slab_state_binary(nx, ny, seed=1, W=4.0):
+    wl = workloads()["binary"]
+    rho = inputs.slab(wl["slab"]["rt_vapour"], wl["slab"]["rt_liquid"], nx, ny, 0.5, W)
+    return wl["mixture"], inputs.with_noise(rho, 0.01, seed)
+
+
+def run_oracle(mixd, rho, tau, stencil, velocity_force, steps, record=()):
+    mix = oracle_mixture(mixd)
+    lat = lbm.Lattice(tau=tau, stencil=stencil, velocity_force=velocity_force)
+    g, F = lbm.init_at_rest(rho)
+    out = {}
+    for k in range(1, steps + 1):
+        g, F = lbm.step(g, mix, lat, F)
+        if k in record:
+            m = lbm.moments(g, F, mix, lat)
+            out[k] = dict(g=g.copy(), F=F.copy(), rho=m["rho"], u=np.stack([m["ux"], m["uy"]]), lnf=m["lnf"])
+    return out
+
+
+def normwise(a, b):
+    """max |a - b| / max |b| (0 if both vanish)."""
+    den = np.max(np.abs(b))
+    num = np.max(np.abs(a - b))
+    return num / den if den > 0 else num

@@ -1,0 +1,232 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by
+element on the same seeded inputs.
+
+Tolerances (normwise, max |gpu - oracle| / max |oracle| per field): FP64 storage
+1e-12, FP32 storage 1e-5.  Grid sizes span several 32 x 8 tiles with ragged tails
+in both directions, plus degenerate lattices (one row, one column, a single node).
+"""
+import numpy as np
+import pytest
+
+from cases import (mixture_dict, normwise, oracle_mixture, run_oracle, slab_state_binary, smooth_state,
+                   workloads)
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def fm():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2212_10680_gb300 import fmlbm
+    return fmlbm
+
+
+def _gpu_run(fm, mixd, rho, tau, stencil, precision, velocity_force, steps, record):
+    lat = fm.Lattice(fm.mixture_from_dict(mixd), rho.shape[2], rho.shape[1], tau, stencil, precision, velocity_force)
+    lat.init(rho)
+    out = {}
+    done = 0
+    for k in sorted(record):
+        lat.step(k - done)
+        done = k
+        g, F = lat.distributions()
+        r, u, lnf = lat.moments()
+        out[k] = dict(g=g, F=F, rho=r, u=u, lnf=lnf)
+    lat.close()
+    return out
+
+
+def _compare(gpu, ora, tol, fields=("rho", "u", "lnf", "g", "F")):
+    worst = {}
+    for k in ora:
+        for f in fields:
+            e = normwise(gpu[k][f], ora[k][f])
+            worst[f] = max(worst.get(f, 0.0), e)
+            assert e <= tol, f"step {k} field {f}: normwise error {e:.3e} > {tol:.1e}"
+    return worst
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("stencil", ["isotropic", "central"])
+def test_binary_slab_parity(fm, precision, stencil):
+    # two-phase binary slab of the flat-interface workloads: 70 x 37 spans 3 x 5 tiles
+    mixd, rho = slab_state_binary(70, 37, seed=11)
+    rec = (1, 2, 10, 40)
+    ora = run_oracle(mixd, rho, 1.0, stencil, "lagged", max(rec), rec)
+    gpu = _gpu_run(fm, mixd, rho, 1.0, stencil, precision, "lagged", max(rec), rec)
+    _compare(gpu, ora, TOL[precision])
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+@pytest.mark.parametrize("eos", ["pr", "srk", "vdw"])
+def test_components_and_eos_parity(fm, n, eos):
+    mixd = mixture_dict(n=n, eos=eos, Tr=1.05, kappa_scale=0.5, M=[1.0, 1.7, 0.8, 2.2][:n], kij=0.03)
+    rho = smooth_state(n, 45, 19, seed=5 + n)
+    rec = (1, 5, 20)
+    ora = run_oracle(mixd, rho, 0.9, "isotropic", "lagged", max(rec), rec)
+    gpu = _gpu_run(fm, mixd, rho, 0.9, "isotropic", "fp64", "lagged", max(rec), rec)
+    _compare(gpu, ora, TOL["fp64"])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_current_force_reading_parity(fm, precision):
+    mixd = mixture_dict(n=2, Tr=1.1, kappa_scale=0.2)
+    rho = smooth_state(2, 33, 9, seed=2)
+    rec = (1, 3, 15)
+    ora = run_oracle(mixd, rho, 0.8, "central", "current", max(rec), rec)
+    gpu = _gpu_run(fm, mixd, rho, 0.8, "central", precision, "current", max(rec), rec)
+    _compare(gpu, ora, TOL[precision])
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 40), (40, 1), (2, 3), (5, 7), (64, 2), (3, 33)])
+def test_degenerate_lattices(fm, shape):
+    nx, ny = shape
+    mixd = mixture_dict(n=2, Tr=1.05, kappa_scale=0.5)
+    rho = smooth_state(2, nx, ny, seed=nx * 100 + ny)
+    rec = (1, 4)
+    ora = run_oracle(mixd, rho, 1.0, "isotropic", "lagged", max(rec), rec)
+    gpu = _gpu_run(fm, mixd, rho, 1.0, "isotropic", "fp64", "lagged", max(rec), rec)
+    _compare(gpu, ora, TOL["fp64"])
+
+
+def test_ternary_slab_parity(fm):
+    wl = workloads()["ternary"]
+    from paper_2212_10680_gb300 import inputs
+    rho = inputs.with_noise(inputs.slab(wl["slab"]["rt_vapour"], wl["slab"]["rt_liquid"], 96, 20, 0.5, 4.0),
+                            0.01, 3)
+    rec = (1, 25)
+    for precision in ("fp64", "fp32"):
+        ora = run_oracle(wl["mixture"], rho, 1.0, "isotropic", "lagged", max(rec), rec)
+        gpu = _gpu_run(fm, wl["mixture"], rho, 1.0, "isotropic", precision, "lagged", max(rec), rec)
+        _compare(gpu, ora, TOL[precision])
+
+
+def test_set_distributions_mid_run(fm):
+    # start both sides from an oracle state with flow (not a rest state)
+    mixd, rho = slab_state_binary(40, 24, seed=4)
+    from oracle import lbm
+    mix = oracle_mixture(mixd)
+    lat_o = lbm.Lattice(tau=1.0, stencil="isotropic")
+    g, F = lbm.init_at_rest(rho)
+    g, F = lbm.run(g, F, mix, lat_o, 15)
+    lat = fm.Lattice(fm.mixture_from_dict(mixd), 40, 24, 1.0, "isotropic", "fp64", "lagged")
+    lat.set_distributions(g, F)
+    g0, F0 = lat.distributions()
+    assert normwise(g0, g) == 0.0 and normwise(F0, F) == 0.0
+    lat.step(5)
+    g1, F1 = lbm.run(g, F, mix, lat_o, 5)
+    gg, FF = lat.distributions()
+    assert normwise(gg, g1) < 1e-12 and normwise(FF, F1) < 1e-12
+    lat.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_mass_conservation_and_diagnostics(fm, precision):
+    mixd, rho = slab_state_binary(96, 40, seed=8)
+    lat = fm.Lattice(fm.mixture_from_dict(mixd), 96, 40, 1.0, "isotropic", precision, "lagged")
+    lat.init(rho)
+    m0, r0, s0 = lat.diagnostics()
+    assert s0 == 0 and np.isinf(r0)
+    assert np.allclose(m0, rho.sum(axis=(1, 2)), rtol=1e-7 if precision == "fp32" else 1e-13)
+    lat.step(300)
+    rho_a, _, _ = lat.moments()
+    m1, r1, s1 = lat.diagnostics()
+    assert s1 == 300
+    tol = 1e-13 if precision == "fp64" else 2e-5
+    assert np.max(np.abs(m1 / m0 - 1)) < tol
+    # residual definition: ||rho(t) - rho(t_prev)|| / ||rho(t)||
+    lat.step(50)
+    rho_b, _, _ = lat.moments()
+    m2, r2, s2 = lat.diagnostics()
+    expect = np.sqrt(np.sum((rho_b - rho_a) ** 2)) / np.sqrt(np.sum(rho_b ** 2))
+    assert abs(r2 / expect - 1) < (1e-10 if precision == "fp64" else 1e-5)
+    lat.close()
+
+
+def test_checkpoint_resume_is_bitwise(fm):
+    mixd, rho = slab_state_binary(50, 30, seed=9)
+    for precision in ("fp64", "fp32"):
+        a = fm.Lattice(fm.mixture_from_dict(mixd), 50, 30, 1.0, "isotropic", precision, "lagged")
+        a.init(rho)
+        a.step(20)
+        state = fm.fmlbm_get_state(a.h)
+        a.step(30)
+        ga, Fa = a.distributions()
+        b = fm.Lattice(fm.mixture_from_dict(mixd), 50, 30, 1.0, "isotropic", precision, "lagged")
+        fm.fmlbm_set_state(b.h, state)
+        b.step(30)
+        gb, Fb = b.distributions()
+        assert np.array_equal(ga, gb) and np.array_equal(Fa, Fb)
+        a.close()
+        b.close()
+
+
+def test_nonphysical_state_is_reported(fm):
+    mixd = mixture_dict(n=2, Tr=1.05)
+    rho = smooth_state(2, 20, 10, seed=1)
+    rho[1, 6, 13] = -1e-3
+    lat = fm.Lattice(fm.mixture_from_dict(mixd), 20, 10, 1.0, "isotropic", "fp64", "lagged")
+    lat.init(rho)
+    lat.step(1)
+    with pytest.raises(fm.FmlbmError) as ei:
+        lat.synchronize()
+    assert ei.value.status == fm.E_NONPHYSICAL
+    assert fm.fmlbm_error_node(lat.h) == (1, 13, 6)
+    # a fresh init clears the latch
+    lat.init(smooth_state(2, 20, 10, seed=2))
+    lat.step(2)
+    lat.synchronize()
+    lat.close()
+
+
+def test_invalid_arguments_are_rejected(fm):
+    mixd = mixture_dict(n=2)
+    with pytest.raises(fm.FmlbmError) as ei:
+        fm.Lattice(fm.mixture_from_dict(mixd), 0, 10, 1.0)
+    assert ei.value.status == 1
+    with pytest.raises(fm.FmlbmError):
+        fm.Lattice(fm.mixture_from_dict(mixd), 10, 10, 0.5)
+    bad = fm.mixture_from_dict(mixd)
+    bad.n_components = 5
+    with pytest.raises(fm.FmlbmError):
+        fm.Lattice(bad, 10, 10, 1.0)
+
+
+def test_full_size_sampled_parity(fm):
+    # the 1024 x 1024 binary droplet in FP32 (the throughput configuration): after some
+    # steps, one more GPU step is compared at sampled nodes with the oracle applied to a
+    # periodic patch of radius 5 around each node (the update of a node depends only on
+    # the state within 4 nodes).
+    from oracle import lbm
+    from paper_2212_10680_gb300 import inputs
+    wl = workloads()["binary"]
+    n = 1024
+    rho = inputs.with_noise(inputs.droplet(wl["slab"]["rt_vapour"], wl["slab"]["rt_liquid"], n, n, 200.0, 4.0),
+                            0.01, 2)
+    lat = fm.Lattice(fm.mixture_from_dict(wl["mixture"]), n, n, 1.0, "isotropic", "fp32", "lagged")
+    lat.init(rho)
+    lat.step(30)
+    g, F = lat.distributions()
+    lat.step(1)
+    g1, F1 = lat.distributions()
+    lat.close()
+    mix = oracle_mixture(wl["mixture"])
+    olat = lbm.Lattice(tau=1.0, stencil="isotropic", velocity_force="lagged")
+    rng = np.random.default_rng(0)
+    # nodes on the droplet interface, in the bulk and at the periodic edges
+    pts = [(0, 0), (n - 1, n - 1), (0, n - 1), (512, 512 + 200), (512 + 141, 512 + 141)]
+    pts += [tuple(p) for p in rng.integers(0, n, (20, 2))]
+    R = 5
+    for (y, x) in pts:
+        ys = np.arange(y - R, y + R + 1) % n
+        xs = np.arange(x - R, x + R + 1) % n
+        gp = g[:, :, ys][:, :, :, xs].astype(np.float64)
+        Fp = F[:, ys][:, :, xs]
+        go, Fo = lbm.step(gp, mix, olat, Fp)
+        ref = go[:, :, R, R]
+        got = g1[:, :, y, x]
+        assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(g1)), (y, x)
+        assert np.max(np.abs(F1[:, y, x] - Fo[:, R, R])) <= 1e-5 * max(np.max(np.abs(F1)), 1e-12), (y, x)
