@@ -47,7 +47,7 @@ def state(d, z):
 
 
 def main():
-    binary = mixture_dict(0.8, [1.0, 1.5], [1.0, 0.9], [0.011, 0.2], [0.10, 0.15], 0.0)
+    binary = mixture_dict(0.8, [1.0, 1.3], [1.0, 0.9], [0.011, 0.2], [0.05, 0.075], 0.0)
     ternary = mixture_dict(0.85, [1.0, 1.3, 1.6], [1.0, 0.85, 0.7], [0.011, 0.1, 0.25], [0.05, 0.10, 0.15], 0.02)
     out = dict(
         lattice_units=dict(R=1.0, a1=2.0 / 49.0, b1=2.0 / 21.0, Tc1=TC1, Pc1=PC1),

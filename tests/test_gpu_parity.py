@@ -39,13 +39,23 @@ def _gpu_run(fm, mixd, rho, tau, stencil, precision, velocity_force, steps, reco
     return out
 
 
-def _compare(gpu, ora, tol, fields=("rho", "u", "lnf", "g", "F")):
+EPS32 = float(np.finfo(np.float32).eps)
+
+
+def _compare(gpu, ora, tol, RT=None, fields=("rho", "u", "lnf", "g", "F")):
+    """Normwise comparison per field.  In FP32 the force F_i = rho~_i (G_i - RT grad ln f_i)
+    is a difference quotient of ln f, so its error is bounded by the rounding of ln f rather
+    than by the size of F: |dF| <= tol max|F| + 32 eps32 RT max(rho~) max|ln f|."""
     worst = {}
     for k in ora:
         for f in fields:
-            e = normwise(gpu[k][f], ora[k][f])
-            worst[f] = max(worst.get(f, 0.0), e)
-            assert e <= tol, f"step {k} field {f}: normwise error {e:.3e} > {tol:.1e}"
+            a, b = gpu[k][f], ora[k][f]
+            err = np.max(np.abs(a - b))
+            bound = tol * np.max(np.abs(b))
+            if f == "F" and tol >= 1e-6 and RT is not None:
+                bound += 32 * EPS32 * RT * np.max(ora[k]["rho"]) * np.max(np.abs(ora[k]["lnf"]))
+            worst[f] = max(worst.get(f, 0.0), err / max(bound, 1e-300))
+            assert err <= bound, f"step {k} field {f}: max error {err:.3e} > bound {bound:.3e}"
     return worst
 
 
@@ -57,7 +67,7 @@ def test_binary_slab_parity(fm, precision, stencil):
     rec = (1, 2, 10, 40)
     ora = run_oracle(mixd, rho, 1.0, stencil, "lagged", max(rec), rec)
     gpu = _gpu_run(fm, mixd, rho, 1.0, stencil, precision, "lagged", max(rec), rec)
-    _compare(gpu, ora, TOL[precision])
+    _compare(gpu, ora, TOL[precision], RT=mixd["R"] * mixd["T"])
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 4])
@@ -78,7 +88,7 @@ def test_current_force_reading_parity(fm, precision):
     rec = (1, 3, 15)
     ora = run_oracle(mixd, rho, 0.8, "central", "current", max(rec), rec)
     gpu = _gpu_run(fm, mixd, rho, 0.8, "central", precision, "current", max(rec), rec)
-    _compare(gpu, ora, TOL[precision])
+    _compare(gpu, ora, TOL[precision], RT=mixd["R"] * mixd["T"])
 
 
 @pytest.mark.parametrize("shape", [(1, 1), (1, 40), (40, 1), (2, 3), (5, 7), (64, 2), (3, 33)])
@@ -101,7 +111,7 @@ def test_ternary_slab_parity(fm):
     for precision in ("fp64", "fp32"):
         ora = run_oracle(wl["mixture"], rho, 1.0, "isotropic", "lagged", max(rec), rec)
         gpu = _gpu_run(fm, wl["mixture"], rho, 1.0, "isotropic", precision, "lagged", max(rec), rec)
-        _compare(gpu, ora, TOL[precision])
+        _compare(gpu, ora, TOL[precision], RT=wl["mixture"]["R"] * wl["mixture"]["T"])
 
 
 def test_set_distributions_mid_run(fm):
