@@ -225,6 +225,8 @@ def run_ours(args, w, rank, world, dist):
     nodes = nx * ny
     lat = fmlbm.Lattice(fmlbm.mixture_from_dict(w["mixture"]), nx, ny, w["tau"], w["stencil"], prec, "lagged",
                         stream=stream.cuda_stream)
+    if args.tile_y:
+        fmlbm.fmlbm_set_tile_height(lat.h, args.tile_y)
     rho_dev = torch.from_numpy(w["rho"]).to(dev)
     fmlbm.fmlbm_init_device(lat.h, rho_dev.data_ptr())
     lat.step(args.warmup)
@@ -316,6 +318,7 @@ def main():
     ap.add_argument("--precision", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--tile-y", type=int, default=0, help="override the fused step's tile height (8 or 16)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -31,6 +31,7 @@ struct fmlbm_handle {
     ErrorLatch* err_dev = nullptr;
     ErrorLatch* err_host = nullptr;  // pinned
     int64_t step = 0;
+    int tile_y = kTileYSmall;
     std::string last_error;
 };
 
@@ -144,8 +145,6 @@ StepArgs make_args(const fmlbm_handle* h, int src) {
     A.ny = h->lattice.ny;
     A.stencil = h->lattice.stencil;
     A.lagged = h->lattice.velocity_force == FMLBM_FORCE_LAGGED;
-    A.omega = 1.0 / h->lattice.tau;
-    A.fcoef = 1.0 - 0.5 / h->lattice.tau;
     A.gin = h->g[src];
     A.g0in = h->g0[src];
     A.gout = h->g[src ^ 1];
@@ -153,16 +152,20 @@ StepArgs make_args(const fmlbm_handle* h, int src) {
     A.Fin = h->F[src];
     A.Fout = h->F[src ^ 1];
     A.err = h->err_dev;
-    A.mix = h->mc;
+    MixConst mc = h->mc;
+    mc.omega = 1.0 / h->lattice.tau;
+    mc.fcoef = 1.0 - 0.5 / h->lattice.tau;
+    A.mixd = mc;
+    A.mixf = cast_mix<float>(mc);
     return A;
 }
 
 cudaError_t dispatch_step(const fmlbm_handle* h, const StepArgs& A, bool moments) {
     switch (h->lattice.precision) {
-        case FMLBM_FP64: return launch_step<ST_F64>(A, h->nc, moments, h->stream);
-        case FMLBM_FP32: return launch_step<ST_F32>(A, h->nc, moments, h->stream);
-        case FMLBM_FP16DEV: return launch_step<ST_F16DEV>(A, h->nc, moments, h->stream);
-        default: return launch_step<ST_BF16DEV>(A, h->nc, moments, h->stream);
+        case FMLBM_FP64: return launch_step<ST_F64>(A, h->nc, moments, h->tile_y, h->stream);
+        case FMLBM_FP32: return launch_step<ST_F32>(A, h->nc, moments, h->tile_y, h->stream);
+        case FMLBM_FP16DEV: return launch_step<ST_F16DEV>(A, h->nc, moments, h->tile_y, h->stream);
+        default: return launch_step<ST_BF16DEV>(A, h->nc, moments, h->tile_y, h->stream);
     }
 }
 cudaError_t dispatch_init(const fmlbm_handle* h, const StepArgs& A, const double* rho) {
@@ -254,7 +257,7 @@ fmlbm_status fmlbm_lattice_bytes(int32_t n_components, const fmlbm_lattice* latt
     buffer_bytes(n_components, *lattice, &gb, &g0b, &fb);
     const size_t nxy = (size_t)lattice->nx * lattice->ny;
     *bytes = 2 * (gb + g0b + fb) + (size_t)n_components * nxy * 8 +
-             (size_t)kReduceBlocks * (FMLBM_MAX_COMPONENTS + 2) * 8 + 256;
+             (size_t)reduce_blocks(lattice->nx, lattice->ny) * (FMLBM_MAX_COMPONENTS + 2) * 8 + 256;
     return FMLBM_OK;
 }
 
@@ -273,6 +276,7 @@ fmlbm_status fmlbm_create(const fmlbm_mixture* mixture, const fmlbm_lattice* lat
     h->mixture = *mixture;
     h->lattice = *lattice;
     h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->tile_y = lattice->ny >= 64 ? kTileYLarge : kTileYSmall;
     if (cudaGetDevice(&h->device) != cudaSuccess) {
         delete h;
         return FMLBM_E_CUDA;
@@ -287,7 +291,8 @@ fmlbm_status fmlbm_create(const fmlbm_mixture* mixture, const fmlbm_lattice* lat
         ok = ok && cudaMalloc(&h->F[k], fb) == cudaSuccess;
     }
     ok = ok && cudaMalloc((void**)&h->rho_prev, (size_t)h->nc * nxy * sizeof(double)) == cudaSuccess;
-    ok = ok && cudaMalloc((void**)&h->partial, (size_t)kReduceBlocks * (kMaxC + 2) * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&h->partial,
+                          (size_t)reduce_blocks(lattice->nx, lattice->ny) * (kMaxC + 2) * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMalloc((void**)&h->diag_dev, (kMaxC + 2) * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMalloc((void**)&h->err_dev, sizeof(ErrorLatch)) == cudaSuccess;
     ok = ok && cudaMallocHost((void**)&h->diag_host, (kMaxC + 2) * sizeof(double)) == cudaSuccess;
@@ -348,6 +353,13 @@ fmlbm_status fmlbm_step(fmlbm_handle* h, int64_t nsteps) {
         h->cur ^= 1;
         ++h->step;
     }
+    return FMLBM_OK;
+}
+
+fmlbm_status fmlbm_set_tile_height(fmlbm_handle* h, int32_t tile_y) {
+    if (!h || (tile_y != kTileYSmall && tile_y != kTileYLarge))
+        return fail(h, FMLBM_E_INVALID_ARG, "tile height must be 8 or 16");
+    h->tile_y = tile_y;
     return FMLBM_OK;
 }
 

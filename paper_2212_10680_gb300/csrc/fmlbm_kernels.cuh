@@ -51,17 +51,43 @@ __host__ __device__ __forceinline__ constexpr R wgt(int a) {
     return a == 0 ? R(4) / R(9) : (a < 5 ? R(1) / R(9) : R(1) / R(36));
 }
 
-// Mixture constants, computed on the host from Appendix C (T fixed).
-struct MixConst {
+// Mixture constants, computed on the host from Appendix C (T fixed).  Kernels read
+// the copy in their own arithmetic type (no double -> float conversions on device,
+// which would run on the FP64 pipe).
+template <typename E>
+struct MixConstT {
     int nc;
     int eos;          // 0 PR, 1 SRK, 2 vdW
-    double RT;
-    double b[kMaxC];
-    double M[kMaxC];
-    double invM[kMaxC];
-    double aij[kMaxC * kMaxC];   // (a alpha)_ij, row stride kMaxC
-    double kap[kMaxC * kMaxC];   // kappa_ij = sqrt(kappa_i kappa_j), row stride kMaxC
+    E RT;
+    E b[kMaxC];
+    E M[kMaxC];
+    E invM[kMaxC];
+    E aij[kMaxC * kMaxC];   // (a alpha)_ij, row stride kMaxC
+    E kap[kMaxC * kMaxC];   // kappa_ij = sqrt(kappa_i kappa_j), row stride kMaxC
+    E omega;                // 1 / tau
+    E fcoef;                // 1 - 1 / (2 tau)
 };
+using MixConst = MixConstT<double>;
+
+template <typename E>
+MixConstT<E> cast_mix(const MixConst& m) {
+    MixConstT<E> r;
+    r.nc = m.nc;
+    r.eos = m.eos;
+    r.RT = (E)m.RT;
+    for (int i = 0; i < kMaxC; ++i) {
+        r.b[i] = (E)m.b[i];
+        r.M[i] = (E)m.M[i];
+        r.invM[i] = (E)m.invM[i];
+    }
+    for (int k = 0; k < kMaxC * kMaxC; ++k) {
+        r.aij[k] = (E)m.aij[k];
+        r.kap[k] = (E)m.kap[k];
+    }
+    r.omega = (E)m.omega;
+    r.fcoef = (E)m.fcoef;
+    return r;
+}
 
 struct ErrorLatch {
     int flag;         // 0 = clean, 1 = a node left the EOS domain
@@ -72,8 +98,6 @@ struct StepArgs {
     int nx, ny;
     int stencil;      // 0 isotropic, 1 central
     int lagged;       // 1: u uses the stored force of the previous step
-    double omega;     // 1 / tau
-    double fcoef;     // 1 - 1 / (2 tau)
     const void* gin;  // F64/F32: all planes; DEV: 16-bit planes a = 1..8
     const float* g0in;  // DEV: float planes a = 0
     void* gout;
@@ -85,8 +109,13 @@ struct StepArgs {
     double* u_out;
     double* lnf_out;
     ErrorLatch* err;
-    MixConst mix;
+    MixConstT<double> mixd;
+    MixConstT<float> mixf;
 };
+
+template <typename E> __device__ __forceinline__ const MixConstT<E>& mixc(const StepArgs& A);
+template <> __device__ __forceinline__ const MixConstT<double>& mixc<double>(const StepArgs& A) { return A.mixd; }
+template <> __device__ __forceinline__ const MixConstT<float>& mixc<float>(const StepArgs& A) { return A.mixf; }
 
 template <int ST> struct StoreTraits;
 template <> struct StoreTraits<ST_F64> { using Real = double; using Elem = double; };
@@ -145,60 +174,63 @@ __device__ __forceinline__ int wrap(int v, int n) {
 
 // ln f_i at one node from its molar densities (steps 2-5), written in terms of the
 // packing fraction beta = b_m rho~ so that v = 1 / rho~ never appears:
-//   ln x_i - ln((v - b_m)/RT) = ln(rho~_i RT) - log1p(-beta)
+//   ln x_i - ln((v - b_m)/RT) = ln(rho~_i RT / (1 - beta))
 //   PR : p v / RT - 1 = beta/(1-beta) - (aa_m rho~ / RT) / (1 + 2 beta - beta^2)
-//        ln[(v + (1+sqrt2) b_m)/(v + (1-sqrt2) b_m)] = log1p((1+sqrt2) beta) - log1p((1-sqrt2) beta)
+//        ln[(v + (1+sqrt2) b_m)/(v + (1-sqrt2) b_m)] = ln[(1 + (1+sqrt2) beta)/(1 + (1-sqrt2) beta)]
 //   SRK: p v / RT - 1 = beta/(1-beta) - (aa_m rho~ / RT) / (1 + beta),  ln(1 + b_m / v) = log1p(beta)
 //   vdW: b_i / (v - b_m) = b_i rho~ / (1 - beta),  2 S_i / (RT v) = 2 S_i rho~ / RT
-// Returns beta (for the domain check).
+// (each logarithm takes a ratio whose relative rounding is a few ulp, so merging the
+// printed logarithms pairwise costs no accuracy).  Returns beta (for the domain check).
 template <int NC, typename E>
-__device__ __forceinline__ E node_lnf(const MixConst& m, const E* rt, E* lnf) {
+__device__ __forceinline__ E node_lnf(const MixConstT<E>& m, const E* rt, E* lnf) {
     E rtot = E(0);
 #pragma unroll
     for (int i = 0; i < NC; ++i) rtot += rt[i];
     const E inv = E(1) / rtot;
-    E x[NC];
+    E bm_rt = E(0);   // b_m rho~ = sum_i b_i rho~_i
 #pragma unroll
-    for (int i = 0; i < NC; ++i) x[i] = rt[i] * inv;
-    E bm = E(0);
-#pragma unroll
-    for (int i = 0; i < NC; ++i) bm += x[i] * E(m.b[i]);
-    E S[NC];
-    E aam = E(0);
+    for (int i = 0; i < NC; ++i) bm_rt += m.b[i] * rt[i];
+    E S[NC];          // rho~ S_i = sum_j (a alpha)_ij rho~_j
+    E aam_rt2 = E(0); // (a alpha)_m rho~^2
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
         E s = E(0);
 #pragma unroll
-        for (int j = 0; j < NC; ++j) s += E(m.aij[i * kMaxC + j]) * x[j];
+        for (int j = 0; j < NC; ++j) s += m.aij[i * kMaxC + j] * rt[j];
         S[i] = s;
-        aam += x[i] * s;
+        aam_rt2 += rt[i] * s;
     }
-    const E RT = E(m.RT);
-    const E beta = bm * rtot;
-    const E l1mb = log1p(-beta);
+    const E RT = m.RT;
+    const E beta = bm_rt;
+    const E omb = E(1) - beta;
+    const E lead = RT / omb;
     if (m.eos == 2) {
 #pragma unroll
         for (int i = 0; i < NC; ++i)
-            lnf[i] = log(rt[i] * RT) - l1mb + E(m.b[i]) * rtot / (E(1) - beta) - E(2) * S[i] * rtot / RT;
+            lnf[i] = log(rt[i] * lead) + m.b[i] * rtot / omb - E(2) * S[i] / RT;
         return beta;
     }
-    const E att = aam * rtot / RT;
+    const E att = aam_rt2 * inv / RT;   // (a alpha)_m rho~ / RT
     E rep, lr, pref;
     if (m.eos == 0) {
         const E s2 = E(1.4142135623730950488);
-        rep = beta / (E(1) - beta) - att / (E(1) + E(2) * beta - beta * beta);
-        lr = log1p((E(1) + s2) * beta) - log1p((E(1) - s2) * beta);
-        pref = E(1) / (E(2) * s2 * bm * RT);
+        rep = beta / omb - att / (E(1) + E(2) * beta - beta * beta);
+        lr = log((E(1) + (E(1) + s2) * beta) / (E(1) + (E(1) - s2) * beta));
+        pref = E(1) / (E(2) * s2 * RT);
     } else {
-        rep = beta / (E(1) - beta) - att / (E(1) + beta);
+        rep = beta / omb - att / (E(1) + beta);
         lr = log1p(beta);
-        pref = E(1) / (bm * RT);
+        pref = E(1) / RT;
     }
-    const E invbm = E(1) / bm;
+    // with b_m = beta / rho~ the coefficient of lr, ((a alpha)_m b_i/b_m - 2 sum_j x_j (a alpha)_ij)
+    // / (c b_m RT), becomes pref ((a alpha)_m b_i/b_m - 2 S_i / rho~) rho~ / beta
+    const E invb = E(1) / beta;
+    const E aam = aam_rt2 * inv * inv;  // (a alpha)_m
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
-        const E bi = E(m.b[i]) * invbm;
-        lnf[i] = log(rt[i] * RT) - l1mb + bi * rep + pref * (aam * bi - E(2) * S[i]) * lr;
+        const E bi = m.b[i] * rtot * invb;             // b_i / b_m
+        const E Si = S[i] * inv;                        // sum_j x_j (a alpha)_ij
+        lnf[i] = log(rt[i] * lead) + bi * rep + pref * (aam * bi - E(2) * Si) * rtot * invb * lr;
     }
     return beta;
 }
@@ -246,6 +278,36 @@ struct StepSmem {
     Tile<E, NC, TY, 1> G;    // sum_j kappa_ij lap rho~_j on tile + 1
 };
 
+// Pull offsets: g_a(r, t) = g*_a(r - e_a, t - 1).
+__device__ __forceinline__ int pull_src(int a, int wx, int wy, int xm, int xp, int ym, int yp, int nx) {
+    const int sx = ex(a) == 1 ? xm : (ex(a) == -1 ? xp : wx);
+    const int sy = ey(a) == 1 ? ym : (ey(a) == -1 ? yp : wy);
+    return sy * nx + sx;
+}
+
+// Sum of the pulled distributions of component i at node (wx, wy) (wrapped coordinates).
+template <int NC, int ST>
+__device__ __forceinline__ void pull_rho(const StepArgs& A, int wx, int wy, bool inner, int nx, int ny, int nxy,
+                                         typename StoreTraits<ST>::Real* rs) {
+    using Real = typename StoreTraits<ST>::Real;
+    const int node = wy * nx + wx;
+    int xm = wx - 1, xp = wx + 1, ym = wy - 1, yp = wy + 1;
+    if (!inner) {
+        xm = wx == 0 ? nx - 1 : xm;
+        xp = wx == nx - 1 ? 0 : xp;
+        ym = wy == 0 ? ny - 1 : ym;
+        yp = wy == ny - 1 ? 0 : yp;
+    }
+#pragma unroll
+    for (int i = 0; i < NC; ++i) rs[i] = Real(0);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const int src = inner ? node - ey(a) * nx - ex(a) : pull_src(a, wx, wy, xm, xp, ym, yp, nx);
+#pragma unroll
+        for (int i = 0; i < NC; ++i) rs[i] += load_g<ST>(A, i, a, (size_t)src, (size_t)nxy);
+    }
+}
+
 // MOMENTS = true: compute the macroscopic fields of the current state instead of
 // advancing it (no distribution or force store).
 template <int NC, int ST, int TY, bool MOMENTS>
@@ -253,37 +315,43 @@ __global__ void __launch_bounds__(kTX* TY) fused_step(StepArgs A) {
     using Real = typename StoreTraits<ST>::Real;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto& S = *reinterpret_cast<StepSmem<Real, NC, TY>*>(smem_raw);
+    const MixConstT<Real>& m = mixc<Real>(A);
 
     const int nx = A.nx, ny = A.ny;
-    const size_t nxy = (size_t)nx * ny;
+    const int nxy = nx * ny;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * kTX + tx;
     constexpr int NT = kTX * TY;
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * TY;
+    // no periodic wrap anywhere in this block's reach (tile + 2 halo + 1 pull)
+    const bool inner = x0 >= 3 && x0 + kTX + 3 <= nx && y0 >= 3 && y0 + TY + 3 <= ny;
 
     // ---- phase 1: pull and sum (steps 1-2) ----
     const int gxn = x0 + tx, gyn = y0 + ty;
     const bool valid = gxn < nx && gyn < ny;
     Real g[NC][9];
     {
-        const int wx = wrap(gxn, nx), wy = wrap(gyn, ny);
-        const int xm = wx == 0 ? nx - 1 : wx - 1, xp = wx == nx - 1 ? 0 : wx + 1;
-        const int ym = wy == 0 ? ny - 1 : wy - 1, yp = wy == ny - 1 ? 0 : wy + 1;
+        const int wx = inner ? gxn : wrap(gxn, nx), wy = inner ? gyn : wrap(gyn, ny);
+        const int node = wy * nx + wx;
+        int xm = wx - 1, xp = wx + 1, ym = wy - 1, yp = wy + 1;
+        if (!inner) {
+            xm = wx == 0 ? nx - 1 : xm;
+            xp = wx == nx - 1 ? 0 : xp;
+            ym = wy == 0 ? ny - 1 : ym;
+            yp = wy == ny - 1 ? 0 : yp;
+        }
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
-            // g_a(r, t) = g*_a(r - e_a, t - 1)
-            const int sx = ex(a) == 1 ? xm : (ex(a) == -1 ? xp : wx);
-            const int sy = ey(a) == 1 ? ym : (ey(a) == -1 ? yp : wy);
-            const size_t src = (size_t)sy * nx + sx;
+            const int src = inner ? node - ey(a) * nx - ex(a) : pull_src(a, wx, wy, xm, xp, ym, yp, nx);
 #pragma unroll
-            for (int i = 0; i < NC; ++i) g[i][a] = load_g<ST>(A, i, a, src, nxy);
+            for (int i = 0; i < NC; ++i) g[i][a] = load_g<ST>(A, i, a, (size_t)src, (size_t)nxy);
         }
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
             Real r = Real(0);
 #pragma unroll
             for (int a = 0; a < 9; ++a) r += g[i][a];
-            S.rt.v[i][ty + 2][tx + 2] = r * Real(A.mix.invM[i]);
+            S.rt.v[i][ty + 2][tx + 2] = r * m.invM[i];
         }
     }
     {
@@ -303,22 +371,12 @@ __global__ void __launch_bounds__(kTX* TY) fused_step(StepArgs A) {
                 const int c = q & 3;
                 bx = c < 2 ? c : kTX + c;  // 0, 1, TX+2, TX+3
             }
-            const int wx = wrap(x0 - 2 + bx, nx), wy = wrap(y0 - 2 + by, ny);
-            const int xm = wx == 0 ? nx - 1 : wx - 1, xp = wx == nx - 1 ? 0 : wx + 1;
-            const int ym = wy == 0 ? ny - 1 : wy - 1, yp = wy == ny - 1 ? 0 : wy + 1;
+            const int wx = inner ? x0 - 2 + bx : wrap(x0 - 2 + bx, nx);
+            const int wy = inner ? y0 - 2 + by : wrap(y0 - 2 + by, ny);
             Real rs[NC];
+            pull_rho<NC, ST>(A, wx, wy, inner, nx, ny, nxy, rs);
 #pragma unroll
-            for (int i = 0; i < NC; ++i) rs[i] = Real(0);
-#pragma unroll
-            for (int a = 0; a < 9; ++a) {
-                const int sx = ex(a) == 1 ? xm : (ex(a) == -1 ? xp : wx);
-                const int sy = ey(a) == 1 ? ym : (ey(a) == -1 ? yp : wy);
-                const size_t src = (size_t)sy * nx + sx;
-#pragma unroll
-                for (int i = 0; i < NC; ++i) rs[i] += load_g<ST>(A, i, a, src, nxy);
-            }
-#pragma unroll
-            for (int i = 0; i < NC; ++i) S.rt.v[i][by][bx] = rs[i] * Real(A.mix.invM[i]);
+            for (int i = 0; i < NC; ++i) S.rt.v[i][by][bx] = rs[i] * m.invM[i];
         }
     }
     __syncthreads();
@@ -332,14 +390,14 @@ __global__ void __launch_bounds__(kTX* TY) fused_step(StepArgs A) {
             Real rt[NC], lnf[NC], L[NC];
 #pragma unroll
             for (int i = 0; i < NC; ++i) rt[i] = S.rt.v[i][cy + 1][cx + 1];
-            const Real beta = node_lnf<NC, Real>(A.mix, rt, lnf);
+            const Real beta = node_lnf<NC, Real>(m, rt, lnf);
 #pragma unroll
             for (int j = 0; j < NC; ++j) L[j] = lap_at<Real>(S.rt, j, cx + 1, cy + 1, A.stencil);
 #pragma unroll
             for (int i = 0; i < NC; ++i) {
                 Real Gi = Real(0);
 #pragma unroll
-                for (int j = 0; j < NC; ++j) Gi += Real(A.mix.kap[i * kMaxC + j]) * L[j];
+                for (int j = 0; j < NC; ++j) Gi += m.kap[i * kMaxC + j] * L[j];
                 S.lf.v[i][cy][cx] = lnf[i];
                 S.G.v[i][cy][cx] = Gi;
             }
@@ -372,7 +430,7 @@ __global__ void __launch_bounds__(kTX* TY) fused_step(StepArgs A) {
     const int cx = tx + 1, cy = ty + 1;  // tile+1 coordinates of this node
     Real Fx[NC], Fy[NC], grx[NC], gry[NC];
     Real rho = Real(0), jx = Real(0), jy = Real(0), Ftx = Real(0), Fty = Real(0);
-    const Real RT = Real(A.mix.RT);
+    const Real RT = m.RT;
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
         Real lx, ly, Gx, Gy, rx, ry;
@@ -386,8 +444,8 @@ __global__ void __launch_bounds__(kTX* TY) fused_step(StepArgs A) {
         Ftx += Fx[i];
         Fty += Fy[i];
         // grad rho_i = M_i grad rho~_i
-        grx[i] = rx * Real(A.mix.M[i]);
-        gry[i] = ry * Real(A.mix.M[i]);
+        grx[i] = rx * m.M[i];
+        gry[i] = ry * m.M[i];
         Real r = Real(0);
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
@@ -397,7 +455,7 @@ __global__ void __launch_bounds__(kTX* TY) fused_step(StepArgs A) {
         }
         rho += r;
     }
-    const size_t node = (size_t)gyn * nx + gxn;
+    const int node = gyn * nx + gxn;
     Real Fux = Ftx, Fuy = Fty;
     if (A.lagged) {
         const Real* Fin = static_cast<const Real*>(A.Fin);
@@ -419,11 +477,11 @@ __global__ void __launch_bounds__(kTX* TY) fused_step(StepArgs A) {
         }
         if (A.u_out) {
             A.u_out[node] = (double)ux;
-            A.u_out[nxy + node] = (double)uy;
+            A.u_out[(size_t)nxy + node] = (double)uy;
         }
         return;
     } else {
-        const Real omega = Real(A.omega), fcoef = Real(A.fcoef);
+        const Real omega = m.omega, fcoef = m.fcoef;
         const Real usq = ux * ux + uy * uy;
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
@@ -448,7 +506,7 @@ __global__ void __launch_bounds__(kTX* TY) fused_step(StepArgs A) {
                 const Real Fa = w * (Real(3) * (eF - uF) + Real(9) * eu * eF + (cD - Real(1)) * ug +
                                      Real(3) * eu * eg);
                 const Real gn = g[i][a] - omega * (g[i][a] - geq) + fcoef * Fa;
-                store_g<ST>(A, i, a, node, nxy, gn);
+                store_g<ST>(A, i, a, (size_t)node, (size_t)nxy, gn);
             }
         }
         Real* Fout = static_cast<Real*>(A.Fout);
@@ -506,70 +564,79 @@ __global__ void convert_g(StepArgs A, const double* __restrict__ gin_d, double* 
     }
 }
 
-// Deterministic reductions: per block, sums over a fixed grid-stride set of nodes of
-// rho_i (component mass), (rho - rho_prev)^2 and rho^2 in double, then writes
-// rho_prev <- rho.  partial has kReduceBlocks rows of NC + 2 doubles.
-constexpr int kReduceBlocks = 296;
-constexpr int kReduceThreads = 256;
+// Deterministic reductions over a lattice: one thread per node on the same 32 x 8 tiling
+// as the step (so the block count, and with it the summation order, depends only on
+// the lattice shape).  Each block writes NC + 2 doubles: sum rho_i, sum (rho - rho_prev)^2,
+// sum rho^2; then rho_prev <- rho.  reduce_final adds the block rows in a fixed order.
+constexpr int kRedTY = 8;
 
 template <int NC, int ST>
-__global__ void __launch_bounds__(kReduceThreads) reduce_partial(StepArgs A, double* __restrict__ rho_prev,
-                                                                  int have_prev, double* __restrict__ partial) {
-    const int nx = A.nx, ny = A.ny;
-    const size_t nxy = (size_t)nx * ny;
+__global__ void __launch_bounds__(kTX* kRedTY) reduce_partial(StepArgs A, double* __restrict__ rho_prev,
+                                                               int have_prev, double* __restrict__ partial) {
+    using Real = typename StoreTraits<ST>::Real;
+    const int nx = A.nx, ny = A.ny, nxy = nx * ny;
+    const int x = blockIdx.x * kTX + threadIdx.x, y = blockIdx.y * kRedTY + threadIdx.y;
     double acc[NC + 2];
 #pragma unroll
     for (int k = 0; k < NC + 2; ++k) acc[k] = 0.0;
-    for (size_t node = blockIdx.x * (size_t)blockDim.x + threadIdx.x; node < nxy;
-         node += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(node % nx), y = (int)(node / nx);
-        const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-        const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    if (x < nx && y < ny) {
+        const bool inner = x >= 1 && x + 1 < nx && y >= 1 && y + 1 < ny;
+        Real r[NC];
+        pull_rho<NC, ST>(A, x, y, inner, nx, ny, nxy, r);
+        const int node = y * nx + x;
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
-            double r = 0.0;
-#pragma unroll
-            for (int a = 0; a < 9; ++a) {
-                const int sx = ex(a) == 1 ? xm : (ex(a) == -1 ? xp : x);
-                const int sy = ey(a) == 1 ? ym : (ey(a) == -1 ? yp : y);
-                r += (double)load_g<ST>(A, i, a, (size_t)sy * nx + sx, nxy);
-            }
-            acc[i] += r;
-            acc[NC + 1] += r * r;
+            const double ri = (double)r[i];
+            acc[i] = ri;
+            acc[NC + 1] += ri * ri;
             const size_t k = (size_t)i * nxy + node;
             if (have_prev) {
-                const double d = r - rho_prev[k];
+                const double d = ri - rho_prev[k];
                 acc[NC] += d * d;
             }
-            rho_prev[k] = r;
+            rho_prev[k] = ri;
         }
     }
-    __shared__ double red[kReduceThreads / 32][NC + 2];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ double red[kRedTY][NC + 2];
+    const int lane = threadIdx.x;
 #pragma unroll
     for (int k = 0; k < NC + 2; ++k) {
         double v = acc[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[warp][k] = v;
+        if (lane == 0) red[threadIdx.y][k] = v;
     }
     __syncthreads();
-    if (threadIdx.x < NC + 2) {
+    const int tid = threadIdx.y * kTX + threadIdx.x;
+    if (tid < NC + 2) {
         double v = 0.0;
-        for (int w = 0; w < kReduceThreads / 32; ++w) v += red[w][threadIdx.x];
-        partial[(size_t)blockIdx.x * (NC + 2) + threadIdx.x] = v;
+#pragma unroll
+        for (int w = 0; w < kRedTY; ++w) v += red[w][tid];
+        partial[(size_t)(blockIdx.y * gridDim.x + blockIdx.x) * (NC + 2) + tid] = v;
     }
 }
 
+constexpr int kFinalThreads = 256;
+
 template <int NC>
-__global__ void reduce_final(const double* __restrict__ partial, int nblocks, double* __restrict__ out) {
-    // one warp per quantity, fixed order
+__global__ void __launch_bounds__(kFinalThreads) reduce_final(const double* __restrict__ partial, int nblocks,
+                                                               double* __restrict__ out) {
+    // block k sums quantity k over all block rows: fixed strided order, then a fixed tree
     const int k = blockIdx.x;
     double v = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += 32) v += partial[(size_t)b * (NC + 2) + k];
+    for (int b = threadIdx.x; b < nblocks; b += kFinalThreads) v += partial[(size_t)b * (NC + 2) + k];
+    __shared__ double red[kFinalThreads / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (threadIdx.x == 0) out[k] = v;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kFinalThreads / 32; ++w) t += red[w];
+        out[k] = t;
+    }
 }
+
+inline int reduce_blocks(int nx, int ny) { return ((nx + kTX - 1) / kTX) * ((ny + kRedTY - 1) / kRedTY); }
 
 }  // namespace fmlbm

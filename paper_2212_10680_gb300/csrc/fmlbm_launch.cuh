@@ -6,10 +6,13 @@
 
 namespace fmlbm {
 
-constexpr int kTileY = 8;
+// Tile heights of the fused step (tile width is one warp).  The host picks one per
+// lattice (fmlbm_set_tile_height / the batch autotuner).
+constexpr int kTileYSmall = 8;
+constexpr int kTileYLarge = 16;
 
 template <int ST>
-cudaError_t launch_step(const StepArgs& A, int nc, bool moments, cudaStream_t s);
+cudaError_t launch_step(const StepArgs& A, int nc, bool moments, int tile_y, cudaStream_t s);
 template <int ST>
 cudaError_t launch_init(const StepArgs& A, int nc, const double* rho, cudaStream_t s);
 template <int ST>
@@ -20,28 +23,36 @@ cudaError_t launch_reduce(const StepArgs& A, int nc, double* rho_prev, int have_
                           double* out, cudaStream_t s);
 
 #define FMLBM_DEFINE_LAUNCHERS(ST)                                                                        \
-    template <int NC, bool MOM>                                                                           \
+    template <int NC, bool MOM, int TY>                                                                   \
     static cudaError_t launch_step_nc_##ST(const StepArgs& A, cudaStream_t s) {                           \
         using Real = typename StoreTraits<ST>::Real;                                                      \
-        constexpr size_t smem = sizeof(StepSmem<Real, NC, kTileY>);                                       \
-        auto k = fused_step<NC, ST, kTileY, MOM>;                                                         \
+        constexpr size_t smem = sizeof(StepSmem<Real, NC, TY>);                                           \
+        auto k = fused_step<NC, ST, TY, MOM>;                                                             \
         static bool attr_done = false;                                                                    \
         if (!attr_done) {                                                                                 \
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
             if (e != cudaSuccess) return e;                                                               \
             attr_done = true;                                                                             \
         }                                                                                                 \
-        dim3 grid((A.nx + kTX - 1) / kTX, (A.ny + kTileY - 1) / kTileY);                                  \
-        k<<<grid, dim3(kTX, kTileY), smem, s>>>(A);                                                       \
+        dim3 grid((A.nx + kTX - 1) / kTX, (A.ny + TY - 1) / TY);                                          \
+        k<<<grid, dim3(kTX, TY), smem, s>>>(A);                                                           \
         return cudaGetLastError();                                                                        \
     }                                                                                                     \
+    template <int NC>                                                                                     \
+    static cudaError_t launch_step_ty_##ST(const StepArgs& A, bool moments, int tile_y, cudaStream_t s) { \
+        if (tile_y == kTileYLarge)                                                                        \
+            return moments ? launch_step_nc_##ST<NC, true, kTileYLarge>(A, s)                             \
+                           : launch_step_nc_##ST<NC, false, kTileYLarge>(A, s);                           \
+        return moments ? launch_step_nc_##ST<NC, true, kTileYSmall>(A, s)                                 \
+                       : launch_step_nc_##ST<NC, false, kTileYSmall>(A, s);                               \
+    }                                                                                                     \
     template <>                                                                                           \
-    cudaError_t launch_step<ST>(const StepArgs& A, int nc, bool moments, cudaStream_t s) {                \
+    cudaError_t launch_step<ST>(const StepArgs& A, int nc, bool moments, int tile_y, cudaStream_t s) {    \
         switch (nc) {                                                                                     \
-            case 1: return moments ? launch_step_nc_##ST<1, true>(A, s) : launch_step_nc_##ST<1, false>(A, s); \
-            case 2: return moments ? launch_step_nc_##ST<2, true>(A, s) : launch_step_nc_##ST<2, false>(A, s); \
-            case 3: return moments ? launch_step_nc_##ST<3, true>(A, s) : launch_step_nc_##ST<3, false>(A, s); \
-            case 4: return moments ? launch_step_nc_##ST<4, true>(A, s) : launch_step_nc_##ST<4, false>(A, s); \
+            case 1: return launch_step_ty_##ST<1>(A, moments, tile_y, s);                                 \
+            case 2: return launch_step_ty_##ST<2>(A, moments, tile_y, s);                                 \
+            case 3: return launch_step_ty_##ST<3>(A, moments, tile_y, s);                                 \
+            case 4: return launch_step_ty_##ST<4>(A, moments, tile_y, s);                                 \
         }                                                                                                 \
         return cudaErrorInvalidValue;                                                                     \
     }                                                                                                     \
@@ -77,8 +88,9 @@ cudaError_t launch_reduce(const StepArgs& A, int nc, double* rho_prev, int have_
     template <int NC>                                                                                     \
     static cudaError_t launch_reduce_nc_##ST(const StepArgs& A, double* rho_prev, int have_prev,          \
                                              double* partial, double* out, cudaStream_t s) {              \
-        reduce_partial<NC, ST><<<kReduceBlocks, kReduceThreads, 0, s>>>(A, rho_prev, have_prev, partial); \
-        reduce_final<NC><<<NC + 2, 32, 0, s>>>(partial, kReduceBlocks, out);                              \
+        dim3 grid((A.nx + kTX - 1) / kTX, (A.ny + kRedTY - 1) / kRedTY);                                  \
+        reduce_partial<NC, ST><<<grid, dim3(kTX, kRedTY), 0, s>>>(A, rho_prev, have_prev, partial);       \
+        reduce_final<NC><<<NC + 2, kFinalThreads, 0, s>>>(partial, reduce_blocks(A.nx, A.ny), out);       \
         return cudaGetLastError();                                                                        \
     }                                                                                                     \
     template <>                                                                                           \

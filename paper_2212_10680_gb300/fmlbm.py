@@ -74,6 +74,7 @@ def _load() -> ctypes.CDLL:
         "fmlbm_get_state": ([H, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
         "fmlbm_set_state": ([H, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
         "fmlbm_synchronize": ([H], ctypes.c_int),
+        "fmlbm_set_tile_height": ([H, ctypes.c_int32], ctypes.c_int),
         "fmlbm_lattice_bytes": ([ctypes.c_int32, ctypes.POINTER(fmlbm_lattice), ctypes.POINTER(ctypes.c_size_t)],
                                 ctypes.c_int),
         "fmlbm_destroy": ([H], None),
@@ -203,6 +204,10 @@ def fmlbm_get_state(h) -> bytes:
 def fmlbm_set_state(h, state: bytes):
     buf = ctypes.create_string_buffer(state, len(state))
     _check(LIB.fmlbm_set_state(h, buf, len(state)), "fmlbm_set_state", h)
+
+
+def fmlbm_set_tile_height(h, tile_y: int):
+    _check(LIB.fmlbm_set_tile_height(h, tile_y), "fmlbm_set_tile_height", h)
 
 
 def fmlbm_synchronize(h):

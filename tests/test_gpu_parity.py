@@ -45,15 +45,18 @@ EPS32 = float(np.finfo(np.float32).eps)
 def _compare(gpu, ora, tol, RT=None, fields=("rho", "u", "lnf", "g", "F")):
     """Normwise comparison per field.  In FP32 the force F_i = rho~_i (G_i - RT grad ln f_i)
     is a difference quotient of ln f, so its error is bounded by the rounding of ln f rather
-    than by the size of F: |dF| <= tol max|F| + 32 eps32 RT max(rho~) max|ln f|."""
+    than by the size of F: |dF| <= tol max|F| + dF with dF = 32 eps32 RT max(rho~) max|ln f|;
+    the velocity inherits dF / (2 min rho)."""
     worst = {}
     for k in ora:
         for f in fields:
             a, b = gpu[k][f], ora[k][f]
             err = np.max(np.abs(a - b))
             bound = tol * np.max(np.abs(b))
-            if f == "F" and tol >= 1e-6 and RT is not None:
-                bound += 32 * EPS32 * RT * np.max(ora[k]["rho"]) * np.max(np.abs(ora[k]["lnf"]))
+            if tol >= 1e-6 and RT is not None and f in ("F", "u"):
+                dF = 32 * EPS32 * RT * np.max(ora[k]["rho"]) * np.max(np.abs(ora[k]["lnf"]))
+                # u carries half the stored force divided by the total density
+                bound += dF if f == "F" else 0.5 * dF / np.min(ora[k]["rho"].sum(axis=0))
             worst[f] = max(worst.get(f, 0.0), err / max(bound, 1e-300))
             assert err <= bound, f"step {k} field {f}: max error {err:.3e} > bound {bound:.3e}"
     return worst
@@ -239,4 +242,20 @@ def test_full_size_sampled_parity(fm):
         ref = go[:, :, R, R]
         got = g1[:, :, y, x]
         assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(g1)), (y, x)
-        assert np.max(np.abs(F1[:, y, x] - Fo[:, R, R])) <= 1e-5 * max(np.max(np.abs(F1)), 1e-12), (y, x)
+        # force bound as in _compare: FP32 rounding of ln f enters through its gradient
+        lnf_scale = 20.0  # |ln f| of the binary workload stays below this (ln of the trace density)
+        dF = 32 * float(np.finfo(np.float32).eps) * mix.RT * float(np.max(rho)) * lnf_scale
+        assert np.max(np.abs(F1[:, y, x] - Fo[:, R, R])) <= 1e-5 * np.max(np.abs(F1)) + dF, (y, x)
+
+
+def test_tile_heights_are_bit_identical(fm):
+    mixd, rho = slab_state_binary(100, 70, seed=12)
+    out = []
+    for ty in (8, 16):
+        lat = fm.Lattice(fm.mixture_from_dict(mixd), 100, 70, 1.0, "isotropic", "fp32", "lagged")
+        fm.fmlbm_set_tile_height(lat.h, ty)
+        lat.init(rho)
+        lat.step(25)
+        out.append(lat.distributions())
+        lat.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
