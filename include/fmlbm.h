@@ -181,6 +181,38 @@ fmlbm_status fmlbm_synchronize(fmlbm_handle* h);
  * control). */
 fmlbm_status fmlbm_lattice_bytes(int32_t n_components, const fmlbm_lattice* lattice, size_t* bytes);
 
+/* Allocation-free variant of the reductions of fmlbm_diagnostics, for callers that
+ * cannot allocate device memory (a host callback or real-time loop that must not
+ * block on cudaMalloc, a process whose device memory is already reserved by
+ * another pool, an embedding that forbids allocation after start-up).  The paper
+ * has no counterpart; it is an interface convenience of this library.
+ *
+ * The caller passes every buffer as a device pointer on the current device:
+ *   g_device        the distributions in the library's storage layout (the buffer a
+ *                   handle steps: [N][9][ny][nx] post-collision values of the last
+ *                   step, so that g_a(r) = g_device[a](r - e_a); FP64 double, FP32
+ *                   float; for FP16DEV/BF16DEV the 16-bit planes a = 1..8), read only;
+ *   g0_device       FP16DEV/BF16DEV only: the float planes a = 0 ([N][ny][nx]); else NULL;
+ *   rho_prev_device [N][ny][nx] doubles: read when have_prev != 0, then overwritten
+ *                   with this state's densities;
+ *   out_device      N + 2 doubles written: sum rho_i for each i, sum (rho - rho_prev)^2
+ *                   (0 when have_prev == 0), sum rho^2; residual = sqrt(out[N] / out[N+1]).
+ * Work is enqueued on cuda_stream (NULL: legacy default stream); the call returns
+ * without waiting.  It allocates nothing: its per-block partial sums live in one
+ * fixed device array of 65536 doubles (512 KiB) that every GPU which loads the
+ * library keeps until the process exits, so a lattice may have at most
+ * 65536 / (N + 2) tiles of 32 x 8 nodes (about 4.2 million nodes for N = 2);
+ * larger lattices are rejected with FMLBM_E_INVALID_ARG, as are NULL buffers or
+ * out-of-range sizes.  The first call on each device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make that first call
+ * before capturing work into a CUDA graph.  All calls share the one array and each
+ * call overwrites every entry it later reads, so nothing needs clearing; calls that
+ * overlap on the GPU (on different streams) race on it and must be serialised by
+ * the caller. */
+fmlbm_status fmlbm_diagnostics_noalloc(int32_t n_components, int32_t nx, int32_t ny, int32_t precision,
+                                       const void* g_device, const float* g0_device, double* rho_prev_device,
+                                       int32_t have_prev, double* out_device, void* cuda_stream);
+
 /* Releases all device memory of the handle.  NULL-safe. */
 void fmlbm_destroy(fmlbm_handle* h);
 

@@ -77,6 +77,9 @@ def _load() -> ctypes.CDLL:
         "fmlbm_set_tile_height": ([H, ctypes.c_int32], ctypes.c_int),
         "fmlbm_lattice_bytes": ([ctypes.c_int32, ctypes.POINTER(fmlbm_lattice), ctypes.POINTER(ctypes.c_size_t)],
                                 ctypes.c_int),
+        "fmlbm_diagnostics_noalloc": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                       ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
         "fmlbm_destroy": ([H], None),
         "fmlbm_status_str": ([ctypes.c_int], ctypes.c_char_p),
         "fmlbm_last_error": ([H], ctypes.c_char_p),
@@ -218,6 +221,16 @@ def fmlbm_lattice_bytes(n_components: int, lattice: fmlbm_lattice) -> int:
     n = ctypes.c_size_t()
     _check(LIB.fmlbm_lattice_bytes(n_components, ctypes.byref(lattice), ctypes.byref(n)), "fmlbm_lattice_bytes")
     return n.value
+
+
+def fmlbm_diagnostics_noalloc(n_components: int, nx: int, ny: int, precision: str, g_device: int,
+                              g0_device: int, rho_prev_device: int, have_prev: bool, out_device: int,
+                              stream: int = 0):
+    """Device pointers in, device results out; allocates nothing (see fmlbm.h)."""
+    _check(LIB.fmlbm_diagnostics_noalloc(n_components, nx, ny, PRECISION[precision], ctypes.c_void_p(g_device),
+                                         ctypes.c_void_p(g0_device or None), ctypes.c_void_p(rho_prev_device),
+                                         int(bool(have_prev)), ctypes.c_void_p(out_device),
+                                         ctypes.c_void_p(stream or None)), "fmlbm_diagnostics_noalloc")
 
 
 def fmlbm_destroy(h):
