@@ -193,7 +193,8 @@ fmlbm_status fmlbm_lattice_bytes(int32_t n_components, const fmlbm_lattice* latt
  *                   step, so that g_a(r) = g_device[a](r - e_a); FP64 double, FP32
  *                   float; for FP16DEV/BF16DEV the 16-bit planes a = 1..8), read only;
  *   g0_device       FP16DEV/BF16DEV only: the float planes a = 0 ([N][ny][nx]); else NULL;
- *   rho_prev_device [N][ny][nx] doubles: read when have_prev != 0, then overwritten
+ *   rho_prev_device [N][ny][nx] values in the arithmetic type of the storage (double for
+ *                   FP64, float otherwise): read when have_prev != 0, then overwritten
  *                   with this state's densities;
  *   out_device      N + 2 doubles written: sum rho_i for each i, sum (rho - rho_prev)^2
  *                   (0 when have_prev == 0), sum rho^2; residual = sqrt(out[N] / out[N+1]).
@@ -210,7 +211,7 @@ fmlbm_status fmlbm_lattice_bytes(int32_t n_components, const fmlbm_lattice* latt
  * overlap on the GPU (on different streams) race on it and must be serialised by
  * the caller. */
 fmlbm_status fmlbm_diagnostics_noalloc(int32_t n_components, int32_t nx, int32_t ny, int32_t precision,
-                                       const void* g_device, const float* g0_device, double* rho_prev_device,
+                                       const void* g_device, const float* g0_device, void* rho_prev_device,
                                        int32_t have_prev, double* out_device, void* cuda_stream);
 
 /* Releases all device memory of the handle.  NULL-safe. */

@@ -23,7 +23,7 @@ struct fmlbm_handle {
     float* g0[2] = {nullptr, nullptr};  // DEV: float planes a = 0
     void* F[2] = {nullptr, nullptr};
     int cur = 0;
-    double* rho_prev = nullptr;
+    void* rho_prev = nullptr;     // storage arithmetic type
     int have_prev = 0;
     double* partial = nullptr;
     double* diag_dev = nullptr;
@@ -155,6 +155,7 @@ StepArgs make_args(const fmlbm_handle* h, int src) {
     MixConst mc = h->mc;
     mc.omega = 1.0 / h->lattice.tau;
     mc.fcoef = 1.0 - 0.5 / h->lattice.tau;
+    mc.invRT = 1.0 / mc.RT;
     A.mixd = mc;
     A.mixf = cast_mix<float>(mc);
     return A;
@@ -256,7 +257,7 @@ fmlbm_status fmlbm_lattice_bytes(int32_t n_components, const fmlbm_lattice* latt
     size_t gb, g0b, fb;
     buffer_bytes(n_components, *lattice, &gb, &g0b, &fb);
     const size_t nxy = (size_t)lattice->nx * lattice->ny;
-    *bytes = 2 * (gb + g0b + fb) + (size_t)n_components * nxy * 8 +
+    *bytes = 2 * (gb + g0b + fb) + (size_t)n_components * nxy * real_size(lattice->precision) +
              (size_t)reduce_blocks(lattice->nx, lattice->ny) * (FMLBM_MAX_COMPONENTS + 2) * 8 + 256;
     return FMLBM_OK;
 }
@@ -290,7 +291,7 @@ fmlbm_status fmlbm_create(const fmlbm_mixture* mixture, const fmlbm_lattice* lat
         if (g0b) ok = ok && cudaMalloc((void**)&h->g0[k], g0b) == cudaSuccess;
         ok = ok && cudaMalloc(&h->F[k], fb) == cudaSuccess;
     }
-    ok = ok && cudaMalloc((void**)&h->rho_prev, (size_t)h->nc * nxy * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->rho_prev, (size_t)h->nc * nxy * real_size(lattice->precision)) == cudaSuccess;
     ok = ok && cudaMalloc((void**)&h->partial,
                           (size_t)reduce_blocks(lattice->nx, lattice->ny) * (kMaxC + 2) * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMalloc((void**)&h->diag_dev, (kMaxC + 2) * sizeof(double)) == cudaSuccess;

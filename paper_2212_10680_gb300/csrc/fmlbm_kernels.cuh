@@ -66,6 +66,7 @@ struct MixConstT {
     E kap[kMaxC * kMaxC];   // kappa_ij = sqrt(kappa_i kappa_j), row stride kMaxC
     E omega;                // 1 / tau
     E fcoef;                // 1 - 1 / (2 tau)
+    E invRT;                // 1 / (R T)
 };
 using MixConst = MixConstT<double>;
 
@@ -86,6 +87,7 @@ MixConstT<E> cast_mix(const MixConst& m) {
     }
     r.omega = (E)m.omega;
     r.fcoef = (E)m.fcoef;
+    r.invRT = (E)m.invRT;
     return r;
 }
 
@@ -167,6 +169,11 @@ __device__ __forceinline__ void store_g(const StepArgs& A, int i, int a, size_t 
     }
 }
 
+// Reciprocal: exact in double (the FP64 path is the parity reference), the fast
+// 2-ulp hardware form in float (well inside the FP32 path's error budget).
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+
 __device__ __forceinline__ int wrap(int v, int n) {
     int r = v % n;
     return r < 0 ? r + n : r;
@@ -186,10 +193,10 @@ __device__ __forceinline__ E node_lnf(const MixConstT<E>& m, const E* rt, E* lnf
     E rtot = E(0);
 #pragma unroll
     for (int i = 0; i < NC; ++i) rtot += rt[i];
-    const E inv = E(1) / rtot;
-    E bm_rt = E(0);   // b_m rho~ = sum_i b_i rho~_i
+    const E inv = rcp(rtot);
+    E beta = E(0);    // b_m rho~ = sum_i b_i rho~_i (the packing fraction)
 #pragma unroll
-    for (int i = 0; i < NC; ++i) bm_rt += m.b[i] * rt[i];
+    for (int i = 0; i < NC; ++i) beta += m.b[i] * rt[i];
     E S[NC];          // rho~ S_i = sum_j (a alpha)_ij rho~_j
     E aam_rt2 = E(0); // (a alpha)_m rho~^2
 #pragma unroll
@@ -200,37 +207,35 @@ __device__ __forceinline__ E node_lnf(const MixConstT<E>& m, const E* rt, E* lnf
         S[i] = s;
         aam_rt2 += rt[i] * s;
     }
-    const E RT = m.RT;
-    const E beta = bm_rt;
-    const E omb = E(1) - beta;
-    const E lead = RT / omb;
+    const E invomb = rcp(E(1) - beta);
+    const E lead = m.RT * invomb;
     if (m.eos == 2) {
 #pragma unroll
         for (int i = 0; i < NC; ++i)
-            lnf[i] = log(rt[i] * lead) + m.b[i] * rtot / omb - E(2) * S[i] / RT;
+            lnf[i] = log(rt[i] * lead) + m.b[i] * rtot * invomb - E(2) * S[i] * m.invRT;
         return beta;
     }
-    const E att = aam_rt2 * inv / RT;   // (a alpha)_m rho~ / RT
+    const E att = aam_rt2 * inv * m.invRT;   // (a alpha)_m rho~ / RT
     E rep, lr, pref;
     if (m.eos == 0) {
         const E s2 = E(1.4142135623730950488);
-        rep = beta / omb - att / (E(1) + E(2) * beta - beta * beta);
-        lr = log((E(1) + (E(1) + s2) * beta) / (E(1) + (E(1) - s2) * beta));
-        pref = E(1) / (E(2) * s2 * RT);
+        rep = beta * invomb - att * rcp(E(1) + E(2) * beta - beta * beta);
+        lr = log((E(1) + (E(1) + s2) * beta) * rcp(E(1) + (E(1) - s2) * beta));
+        pref = m.invRT * E(0.35355339059327376220);  // 1 / (2 sqrt2 RT)
     } else {
-        rep = beta / omb - att / (E(1) + beta);
+        rep = beta * invomb - att * rcp(E(1) + beta);
         lr = log1p(beta);
-        pref = E(1) / RT;
+        pref = m.invRT;
     }
     // with b_m = beta / rho~ the coefficient of lr, ((a alpha)_m b_i/b_m - 2 sum_j x_j (a alpha)_ij)
     // / (c b_m RT), becomes pref ((a alpha)_m b_i/b_m - 2 S_i / rho~) rho~ / beta
-    const E invb = E(1) / beta;
-    const E aam = aam_rt2 * inv * inv;  // (a alpha)_m
+    const E rb = rtot * rcp(beta);                 // 1 / b_m
+    const E aam = aam_rt2 * inv * inv;             // (a alpha)_m
+    const E plr = pref * rb * lr;
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
-        const E bi = m.b[i] * rtot * invb;             // b_i / b_m
-        const E Si = S[i] * inv;                        // sum_j x_j (a alpha)_ij
-        lnf[i] = log(rt[i] * lead) + bi * rep + pref * (aam * bi - E(2) * Si) * rtot * invb * lr;
+        const E bi = m.b[i] * rb;                  // b_i / b_m
+        lnf[i] = log(rt[i] * lead) + bi * rep + plr * (aam * bi - E(2) * S[i] * inv);
     }
     return beta;
 }
@@ -308,6 +313,26 @@ __device__ __forceinline__ void pull_rho(const StepArgs& A, int wx, int wy, bool
     }
 }
 
+// Latch the first node that left the EOS domain (rho~_i <= 0, beta >= 1, non-finite ln f).
+template <int NC, typename Real>
+__device__ __forceinline__ void domain_check(const StepArgs& A, const Real* rt, const Real* lnf, Real beta, int x,
+                                             int y) {
+    bool bad = !(beta < Real(1));
+    int badc = 0;
+#pragma unroll
+    for (int i = NC - 1; i >= 0; --i) {
+        if (!(rt[i] > Real(0)) || !isfinite(lnf[i])) {
+            badc = i;
+            bad = true;
+        }
+    }
+    if (bad && atomicCAS(&A.err->flag, 0, 1) == 0) {
+        A.err->comp = badc;
+        A.err->x = x;
+        A.err->y = y;
+    }
+}
+
 // MOMENTS = true: compute the macroscopic fields of the current state instead of
 // advancing it (no distribution or force store).
 template <int NC, int ST, int TY, bool MOMENTS>
@@ -326,7 +351,7 @@ __global__ void __launch_bounds__(kTX* TY) fused_step(StepArgs A) {
     // no periodic wrap anywhere in this block's reach (tile + 2 halo + 1 pull)
     const bool inner = x0 >= 3 && x0 + kTX + 3 <= nx && y0 >= 3 && y0 + TY + 3 <= ny;
 
-    // ---- phase 1: pull and sum (steps 1-2) ----
+    // ---- phase 1: pull and sum (steps 1-2), ln f of each node (steps 3-5) ----
     const int gxn = x0 + tx, gyn = y0 + ty;
     const bool valid = gxn < nx && gyn < ny;
     Real g[NC][9];
@@ -346,15 +371,22 @@ __global__ void __launch_bounds__(kTX* TY) fused_step(StepArgs A) {
 #pragma unroll
             for (int i = 0; i < NC; ++i) g[i][a] = load_g<ST>(A, i, a, (size_t)src, (size_t)nxy);
         }
+        Real rt[NC], lnf[NC];
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
             Real r = Real(0);
 #pragma unroll
             for (int a = 0; a < 9; ++a) r += g[i][a];
-            S.rt.v[i][ty + 2][tx + 2] = r * m.invM[i];
+            rt[i] = r * m.invM[i];
+            S.rt.v[i][ty + 2][tx + 2] = rt[i];
         }
+        const Real beta = node_lnf<NC, Real>(m, rt, lnf);
+#pragma unroll
+        for (int i = 0; i < NC; ++i) S.lf.v[i][ty + 1][tx + 1] = lnf[i];
+        if (valid) domain_check<NC, Real>(A, rt, lnf, beta, gxn, gyn);
     }
     {
+        // the 2-node ring around the tile: rho~ everywhere, ln f on its inner 1-node ring
         constexpr int WB = kTX + 4;
         constexpr int RING = 4 * WB + 4 * TY;
         for (int r = tid; r < RING; r += NT) {
@@ -373,24 +405,30 @@ __global__ void __launch_bounds__(kTX* TY) fused_step(StepArgs A) {
             }
             const int wx = inner ? x0 - 2 + bx : wrap(x0 - 2 + bx, nx);
             const int wy = inner ? y0 - 2 + by : wrap(y0 - 2 + by, ny);
-            Real rs[NC];
-            pull_rho<NC, ST>(A, wx, wy, inner, nx, ny, nxy, rs);
+            Real rt[NC];
+            pull_rho<NC, ST>(A, wx, wy, inner, nx, ny, nxy, rt);
 #pragma unroll
-            for (int i = 0; i < NC; ++i) S.rt.v[i][by][bx] = rs[i] * m.invM[i];
+            for (int i = 0; i < NC; ++i) {
+                rt[i] *= m.invM[i];
+                S.rt.v[i][by][bx] = rt[i];
+            }
+            if (bx >= 1 && bx <= kTX + 2 && by >= 1 && by <= TY + 2) {
+                Real lnf[NC];
+                node_lnf<NC, Real>(m, rt, lnf);
+#pragma unroll
+                for (int i = 0; i < NC; ++i) S.lf.v[i][by - 1][bx - 1] = lnf[i];
+            }
         }
     }
     __syncthreads();
 
-    // ---- phase 2: ln f (steps 3-5) and G = sum_j kappa_ij lap rho~_j (step 6) ----
+    // ---- phase 2: G_i = sum_j kappa_ij lap rho~_j on tile + 1 (step 6, mu_I,i = -G_i) ----
     {
         constexpr int W1 = kTX + 2;
         constexpr int N1 = W1 * (TY + 2);
         for (int q = tid; q < N1; q += NT) {
             const int cy = q / W1, cx = q % W1;  // tile+1 coordinates
-            Real rt[NC], lnf[NC], L[NC];
-#pragma unroll
-            for (int i = 0; i < NC; ++i) rt[i] = S.rt.v[i][cy + 1][cx + 1];
-            const Real beta = node_lnf<NC, Real>(m, rt, lnf);
+            Real L[NC];
 #pragma unroll
             for (int j = 0; j < NC; ++j) L[j] = lap_at<Real>(S.rt, j, cx + 1, cy + 1, A.stencil);
 #pragma unroll
@@ -398,26 +436,7 @@ __global__ void __launch_bounds__(kTX* TY) fused_step(StepArgs A) {
                 Real Gi = Real(0);
 #pragma unroll
                 for (int j = 0; j < NC; ++j) Gi += m.kap[i * kMaxC + j] * L[j];
-                S.lf.v[i][cy][cx] = lnf[i];
                 S.G.v[i][cy][cx] = Gi;
-            }
-            // domain check at the nodes this block owns
-            const int ix = cx - 1, iy = cy - 1;
-            if (ix >= 0 && ix < kTX && iy >= 0 && iy < TY && x0 + ix < nx && y0 + iy < ny) {
-                bool bad = !(beta < Real(1));
-                int badc = 0;
-#pragma unroll
-                for (int i = 0; i < NC; ++i) {
-                    if (!(rt[i] > Real(0)) || !isfinite(lnf[i])) {
-                        if (!bad) badc = i;
-                        bad = true;
-                    }
-                }
-                if (bad && atomicCAS(&A.err->flag, 0, 1) == 0) {
-                    A.err->comp = badc;
-                    A.err->x = x0 + ix;
-                    A.err->y = y0 + iy;
-                }
             }
         }
     }
@@ -428,7 +447,7 @@ __global__ void __launch_bounds__(kTX* TY) fused_step(StepArgs A) {
     // ---- phase 3: force (step 7), velocity (step 1), equilibrium and forcing (step 8),
     //      collision (step 9) ----
     const int cx = tx + 1, cy = ty + 1;  // tile+1 coordinates of this node
-    Real Fx[NC], Fy[NC], grx[NC], gry[NC];
+    Real Fx[NC], Fy[NC], grx[NC], gry[NC], rhoi[NC];
     Real rho = Real(0), jx = Real(0), jy = Real(0), Ftx = Real(0), Fty = Real(0);
     const Real RT = m.RT;
 #pragma unroll
@@ -453,6 +472,7 @@ __global__ void __launch_bounds__(kTX* TY) fused_step(StepArgs A) {
             jx += Real(ex(a)) * g[i][a];
             jy += Real(ey(a)) * g[i][a];
         }
+        rhoi[i] = r;
         rho += r;
     }
     const int node = gyn * nx + gxn;
@@ -469,10 +489,7 @@ __global__ void __launch_bounds__(kTX* TY) fused_step(StepArgs A) {
     if constexpr (MOMENTS) {
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
-            Real r = Real(0);
-#pragma unroll
-            for (int a = 0; a < 9; ++a) r += g[i][a];
-            if (A.rho_out) A.rho_out[(size_t)i * nxy + node] = (double)r;
+            if (A.rho_out) A.rho_out[(size_t)i * nxy + node] = (double)rhoi[i];
             if (A.lnf_out) A.lnf_out[(size_t)i * nxy + node] = (double)S.lf.v[i][cy][cx];
         }
         if (A.u_out) {
@@ -481,32 +498,40 @@ __global__ void __launch_bounds__(kTX* TY) fused_step(StepArgs A) {
         }
         return;
     } else {
-        const Real omega = m.omega, fcoef = m.fcoef;
+        // Collision g' = g - omega (g - g^eq) + fcoef F_a, with g^eq of Eq. eqLBEMCb (rho_0 = 0)
+        // and F_a of Eq. eqLBEMCfinal3, evaluated for each pair of opposite directions
+        // (e_abar = -e_a): the parts even in e are shared, the odd parts change sign.
+        //   g^eq_a = w rho [3 eu + 4.5 eu^2 - 1.5 u^2]
+        //   F_a    = w [3 eF - 3 uF + 9 eu eF + (c_a - 1) ug + 3 eu eg],  c_a = (3 e^2 - 2)/2
+        const Real omega = m.omega, fc = m.fcoef, keep = Real(1) - omega;
         const Real usq = ux * ux + uy * uy;
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
-            Real rhoi = Real(0);
-#pragma unroll
-            for (int a = 0; a < 9; ++a) rhoi += g[i][a];
+            const Real rw = omega * rhoi[i];
             const Real uF = ux * Fx[i] + uy * Fy[i];
             const Real ug = ux * grx[i] + uy * gry[i];
+            const Real base = rw * Real(1.5) * usq;          // omega rho 1.5 u^2
+            const Real c_ax = fc * (Real(-3) * uF - Real(0.5) * ug);   // c - 1 = -1/2 on the axes
+            const Real c_dg = fc * (Real(-3) * uF + ug);                // c - 1 = +1 on the diagonals
+            // a = 0: g^eq_0 = rho - (4/9) rho 1.5 u^2, F_0 = (4/9)(-3 uF - 2 ug)
+            const Real g0 = keep * g[i][0] + rw - Real(4.0 / 9.0) * base +
+                            Real(4.0 / 9.0) * fc * (Real(-3) * uF - Real(2) * ug);
+            store_g<ST>(A, i, 0, (size_t)node, (size_t)nxy, g0);
 #pragma unroll
-            for (int a = 0; a < 9; ++a) {
+            for (int p = 0; p < 4; ++p) {
+                // pairs (1,3), (2,4), (5,7), (6,8)
+                const int a = p < 2 ? 1 + p : 5 + (p - 2);
+                const int b = a + 2;
+                const Real w = wgt<Real>(a);
                 const Real cxa = Real(ex(a)), cya = Real(ey(a));
                 const Real eu = cxa * ux + cya * uy;
                 const Real eF = cxa * Fx[i] + cya * Fy[i];
                 const Real eg = cxa * grx[i] + cya * gry[i];
-                const Real w = wgt<Real>(a);
-                // Eq. eqLBEMCb (rho_0 = 0): S_a = 3 (e.u) + 4.5 (e.u)^2 - 1.5 u^2
-                const Real Sa = Real(3) * eu + Real(4.5) * eu * eu - Real(1.5) * usq;
-                const Real geq = (a == 0 ? rhoi : Real(0)) + w * rhoi * Sa;
-                // Eq. eqLBEMCfinal3: F.w[(e-u)/cs2 + (u.e) e/cs4] + grad rho.w[-u + (u.e) e/cs2 + (e^2/cs2 - D) u/2]
-                const int e2 = ex(a) * ex(a) + ey(a) * ey(a);
-                const Real cD = Real(0.5) * Real(3 * e2 - 2);
-                const Real Fa = w * (Real(3) * (eF - uF) + Real(9) * eu * eF + (cD - Real(1)) * ug +
-                                     Real(3) * eu * eg);
-                const Real gn = g[i][a] - omega * (g[i][a] - geq) + fcoef * Fa;
-                store_g<ST>(A, i, a, (size_t)node, (size_t)nxy, gn);
+                const Real even = w * (eu * (Real(4.5) * rw * eu + fc * (Real(9) * eF + Real(3) * eg)) - base +
+                                       (p < 2 ? c_ax : c_dg));
+                const Real odd = Real(3) * w * (rw * eu + fc * eF);
+                store_g<ST>(A, i, a, (size_t)node, (size_t)nxy, keep * g[i][a] + even + odd);
+                store_g<ST>(A, i, b, (size_t)node, (size_t)nxy, keep * g[i][b] + even - odd);
             }
         }
         Real* Fout = static_cast<Real*>(A.Fout);
@@ -568,17 +593,21 @@ __global__ void convert_g(StepArgs A, const double* __restrict__ gin_d, double* 
 // as the step (so the block count, and with it the summation order, depends only on
 // the lattice shape).  Each block writes NC + 2 doubles: sum rho_i, sum (rho - rho_prev)^2,
 // sum rho^2; then rho_prev <- rho.  reduce_final adds the block rows in a fixed order.
+// Per node and within a warp the sums run in the storage arithmetic type (a pairwise
+// shuffle tree); block sums are promoted to double, so FP32 lattices pay no FP64
+// arithmetic per node.  rho_prev holds values of that same type.
 constexpr int kRedTY = 8;
 
 template <int NC, int ST>
-__global__ void __launch_bounds__(kTX* kRedTY) reduce_partial(StepArgs A, double* __restrict__ rho_prev,
+__global__ void __launch_bounds__(kTX* kRedTY) reduce_partial(StepArgs A,
+                                                               typename StoreTraits<ST>::Real* __restrict__ rho_prev,
                                                                int have_prev, double* __restrict__ partial) {
     using Real = typename StoreTraits<ST>::Real;
     const int nx = A.nx, ny = A.ny, nxy = nx * ny;
     const int x = blockIdx.x * kTX + threadIdx.x, y = blockIdx.y * kRedTY + threadIdx.y;
-    double acc[NC + 2];
+    Real acc[NC + 2];
 #pragma unroll
-    for (int k = 0; k < NC + 2; ++k) acc[k] = 0.0;
+    for (int k = 0; k < NC + 2; ++k) acc[k] = Real(0);
     if (x < nx && y < ny) {
         const bool inner = x >= 1 && x + 1 < nx && y >= 1 && y + 1 < ny;
         Real r[NC];
@@ -586,25 +615,24 @@ __global__ void __launch_bounds__(kTX* kRedTY) reduce_partial(StepArgs A, double
         const int node = y * nx + x;
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
-            const double ri = (double)r[i];
-            acc[i] = ri;
-            acc[NC + 1] += ri * ri;
+            acc[i] = r[i];
+            acc[NC + 1] += r[i] * r[i];
             const size_t k = (size_t)i * nxy + node;
             if (have_prev) {
-                const double d = ri - rho_prev[k];
+                const Real d = r[i] - rho_prev[k];
                 acc[NC] += d * d;
             }
-            rho_prev[k] = ri;
+            rho_prev[k] = r[i];
         }
     }
     __shared__ double red[kRedTY][NC + 2];
     const int lane = threadIdx.x;
 #pragma unroll
     for (int k = 0; k < NC + 2; ++k) {
-        double v = acc[k];
+        Real v = acc[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[threadIdx.y][k] = v;
+        if (lane == 0) red[threadIdx.y][k] = (double)v;
     }
     __syncthreads();
     const int tid = threadIdx.y * kTX + threadIdx.x;

@@ -18,8 +18,9 @@ cudaError_t launch_init(const StepArgs& A, int nc, const double* rho, cudaStream
 template <int ST>
 cudaError_t launch_convert(const StepArgs& A, int nc, const double* gin_d, double* gout_d, bool to_storage,
                            cudaStream_t s);
+// rho_prev: NC * nx * ny values of the storage arithmetic type (double for FP64, else float)
 template <int ST>
-cudaError_t launch_reduce(const StepArgs& A, int nc, double* rho_prev, int have_prev, double* partial,
+cudaError_t launch_reduce(const StepArgs& A, int nc, void* rho_prev, int have_prev, double* partial,
                           double* out, cudaStream_t s);
 
 #define FMLBM_DEFINE_LAUNCHERS(ST)                                                                        \
@@ -86,15 +87,17 @@ cudaError_t launch_reduce(const StepArgs& A, int nc, double* rho_prev, int have_
         return cudaGetLastError();                                                                        \
     }                                                                                                     \
     template <int NC>                                                                                     \
-    static cudaError_t launch_reduce_nc_##ST(const StepArgs& A, double* rho_prev, int have_prev,          \
+    static cudaError_t launch_reduce_nc_##ST(const StepArgs& A, void* rho_prev, int have_prev,            \
                                              double* partial, double* out, cudaStream_t s) {              \
+        using Real = typename StoreTraits<ST>::Real;                                                      \
         dim3 grid((A.nx + kTX - 1) / kTX, (A.ny + kRedTY - 1) / kRedTY);                                  \
-        reduce_partial<NC, ST><<<grid, dim3(kTX, kRedTY), 0, s>>>(A, rho_prev, have_prev, partial);       \
+        reduce_partial<NC, ST><<<grid, dim3(kTX, kRedTY), 0, s>>>(A, static_cast<Real*>(rho_prev),        \
+                                                                   have_prev, partial);                   \
         reduce_final<NC><<<NC + 2, kFinalThreads, 0, s>>>(partial, reduce_blocks(A.nx, A.ny), out);       \
         return cudaGetLastError();                                                                        \
     }                                                                                                     \
     template <>                                                                                           \
-    cudaError_t launch_reduce<ST>(const StepArgs& A, int nc, double* rho_prev, int have_prev,             \
+    cudaError_t launch_reduce<ST>(const StepArgs& A, int nc, void* rho_prev, int have_prev,               \
                                   double* partial, double* out, cudaStream_t s) {                         \
         switch (nc) {                                                                                     \
             case 1: return launch_reduce_nc_##ST<1>(A, rho_prev, have_prev, partial, out, s);             \

@@ -46,7 +46,7 @@ cudaError_t scratch_address(int device, double** out) {
 }
 
 template <int ST>
-cudaError_t run(const StepArgs& A, int nc, double* rho_prev, int have_prev, double* partial, double* out,
+cudaError_t run(const StepArgs& A, int nc, void* rho_prev, int have_prev, double* partial, double* out,
                 cudaStream_t s) {
     return launch_reduce<ST>(A, nc, rho_prev, have_prev, partial, out, s);
 }
@@ -55,7 +55,7 @@ cudaError_t run(const StepArgs& A, int nc, double* rho_prev, int have_prev, doub
 
 extern "C" fmlbm_status fmlbm_diagnostics_noalloc(int32_t n_components, int32_t nx, int32_t ny,
                                                   int32_t precision, const void* g_device,
-                                                  const float* g0_device, double* rho_prev_device,
+                                                  const float* g0_device, void* rho_prev_device,
                                                   int32_t have_prev, double* out_device, void* cuda_stream) {
     if (n_components < 1 || n_components > FMLBM_MAX_COMPONENTS || nx < 1 || ny < 1 || nx > 65536 ||
         ny > 65536 || !g_device || !rho_prev_device || !out_device)

@@ -50,7 +50,7 @@ def test_noalloc_matches_diagnostics_twice(env, precision):
     dtype = torch.float64 if precision == "fp64" else torch.float32
     lat = fm.Lattice(fm.mixture_from_dict(mixd), nx, ny, 1.0, "isotropic", precision, "lagged")
     lat.init(rho)
-    rho_prev = torch.zeros(n * ny * nx, dtype=torch.float64, device="cuda")
+    rho_prev = torch.zeros(n * ny * nx, dtype=dtype, device="cuda")   # the storage arithmetic type
     out = torch.zeros(n + 2, dtype=torch.float64, device="cuda")
     have_prev = False
     for steps in (10, 7):
