@@ -613,17 +613,20 @@ __global__ void __launch_bounds__(kTX* kRedTY) reduce_partial(StepArgs A,
         Real r[NC];
         pull_rho<NC, ST>(A, x, y, inner, nx, ny, nxy, r);
         const int node = y * nx + x;
+        // read every snapshot value before the first store (the stores may alias later
+        // reads as far as the compiler can tell, which would serialise them)
+        Real prev[NC];
+#pragma unroll
+        for (int i = 0; i < NC; ++i) prev[i] = have_prev ? rho_prev[(size_t)i * nxy + node] : r[i];
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
             acc[i] = r[i];
             acc[NC + 1] += r[i] * r[i];
-            const size_t k = (size_t)i * nxy + node;
-            if (have_prev) {
-                const Real d = r[i] - rho_prev[k];
-                acc[NC] += d * d;
-            }
-            rho_prev[k] = r[i];
+            const Real d = r[i] - prev[i];
+            acc[NC] += d * d;
         }
+#pragma unroll
+        for (int i = 0; i < NC; ++i) rho_prev[(size_t)i * nxy + node] = r[i];
     }
     __shared__ double red[kRedTY][NC + 2];
     const int lane = threadIdx.x;
