@@ -32,8 +32,8 @@ sys.path.insert(0, ROOT)
 
 ALGO_BYTES = {"fp64": 144.0, "fp32": 72.0, "fp16dev": 40.0, "bf16dev": 40.0}  # per component-node update
 L2_FLUSH_BYTES = 256 << 20
-PROFILE = os.path.join(ROOT, "profiles", "fused_step_droplet1024_fp32.md")
-KERNEL_SOURCES = ["paper_2212_10680_gb300/csrc/fmlbm_kernels.cuh", "paper_2212_10680_gb300/csrc/fmlbm_launch.cuh"]
+KERNEL_SOURCES = ["paper_2212_10680_gb300/csrc/fmlbm_kernels.cuh", "paper_2212_10680_gb300/csrc/fmlbm_launch.cuh",
+                  "paper_2212_10680_gb300/csrc/fmlbm_tma.cuh"]
 
 
 def kernel_hash() -> str:
@@ -53,12 +53,14 @@ def measured_peaks() -> dict:
     return dict(hbm_gbs=6800.0, source="fallback")
 
 
-def profile_traffic(precision: str):
-    """DRAM bytes per launch of the fused kernel from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
-    if not os.path.exists(PROFILE):
+def profile_traffic(kernel: str, workload_key: str, precision: str):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary
+    profiles/<kernel>_<workload>_<precision>.md, if it was taken on the current kernel
+    source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload_key}_{precision}.md")
+    if not os.path.exists(path):
         return None
-    text = open(PROFILE).read()
+    text = open(path).read()
     m_hash = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
     m_bytes = re.search(r"dram_bytes_per_launch_%s:\s*([0-9.eE+]+)" % precision, text)
     if not m_hash or not m_bytes or m_hash.group(1) != kernel_hash():
@@ -231,6 +233,9 @@ def run_ours(args, w, rank, world, dist):
                         stream=stream.cuda_stream)
     if args.tile_y:
         fmlbm.fmlbm_set_tile_height(lat.h, args.tile_y)
+    if args.variant:
+        fmlbm.fmlbm_set_step_variant(lat.h, args.variant)
+    variant = fmlbm.fmlbm_get_step_variant(lat.h)
     rho_dev = torch.from_numpy(w["rho"]).to(dev)
     fmlbm.fmlbm_init_device(lat.h, rho_dev.data_ptr())
     lat.step(args.warmup)
@@ -264,7 +269,8 @@ def run_ours(args, w, rank, world, dist):
     algo = ALGO_BYTES[prec] * n * nodes
     peak = measured_peaks()
     achieved = algo / per_launch_s / 1e9
-    traffic = profile_traffic(prec)
+    kernel_name = "fused_step_tma" if variant == "tma" else "fused_step"
+    traffic = profile_traffic(kernel_name, args.workload, prec)
 
     # end to end through the public API with host buffers: H2D of the initial field from
     # pinned memory, then per step one fused update and a D2H read of the step's
@@ -298,11 +304,13 @@ def run_ours(args, w, rank, world, dist):
         vs_baseline=None, dtype="f64" if prec == "fp64" else "f32",
         data="synthetic (seeded droplet/slab initial fields from oracle flash densities)",
         config=dict(workload=w["name"], nx=nx, ny=ny, n_components=n, tau=w["tau"], stencil=w["stencil"],
-                    precision=prec, velocity_force="lagged", l2="flushed between timed steps (256 MB write)",
+                    precision=prec, velocity_force="lagged", step_kernel=variant,
+                    l2="flushed between timed steps (256 MB write)",
                     timing="CUDA events around each fused launch on the launching stream"),
         roofline=dict(bound="hbm", achieved=achieved, peak=peak["hbm_gbs"], unit="GB/s",
                       frac=achieved / peak["hbm_gbs"], traffic=traffic, peak_source=peak["source"],
-                      algorithmic_bytes_per_component_node=ALGO_BYTES[prec], kernel="fused_step"),
+                      algorithmic_bytes_per_component_node=ALGO_BYTES[prec],
+                      kernel=kernel_name),
         cpu_baseline=cpu,
         e2e=dict(value=e2e_value, unit="component-GLUPS",
                  h2d_bytes_per_step=n * nodes * 8 / e2e_steps, d2h_bytes_per_step=(n + 2) * 8 + 16),
@@ -323,6 +331,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--tile-y", type=int, default=0, help="override the fused step's tile height (8 or 16)")
+    ap.add_argument("--variant", default=None, choices=["auto", "plain", "tma"], help="step kernel variant")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

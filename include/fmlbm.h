@@ -174,6 +174,22 @@ fmlbm_status fmlbm_set_state(fmlbm_handle* h, const void* buf, size_t bytes);
  * ny >= 64, else 8. */
 fmlbm_status fmlbm_set_tile_height(fmlbm_handle* h, int32_t tile_y);
 
+/* Which kernel advances the lattice.  PLAIN: the fused step with per-thread pulls from
+ * global memory.  TMA: a persistent fused step whose blocks copy each wrap-free tile
+ * (every plane plus a 3-node halo) into shared memory with one bulk tensor copy,
+ * double-buffered so the next tile's copy overlaps the current tile's arithmetic; tiles
+ * on the periodic edges take the plain path.  Both give bit-identical results.  TMA is
+ * available for FP32 and 16-bit storage with nx a multiple of 4 (FP32) or 8 (16-bit) and a
+ * lattice of at least 38 x 22.  AUTO (default): TMA where available and the lattice has
+ * at least 48 tiles of 32 x 16 per multiprocessor (where its pipelining pays), else
+ * PLAIN.  Asking for TMA where it is not available returns FMLBM_E_UNSUPPORTED. */
+typedef enum fmlbm_step_variant {
+    FMLBM_VARIANT_AUTO = 0, FMLBM_VARIANT_PLAIN = 1, FMLBM_VARIANT_TMA = 2
+} fmlbm_step_variant;
+fmlbm_status fmlbm_set_step_variant(fmlbm_handle* h, int32_t variant);
+/* The kernel fmlbm_step will use (PLAIN or TMA). */
+fmlbm_status fmlbm_get_step_variant(fmlbm_handle* h, int32_t* variant);
+
 /* Waits for the handle's stream and reports latched kernel errors. */
 fmlbm_status fmlbm_synchronize(fmlbm_handle* h);
 

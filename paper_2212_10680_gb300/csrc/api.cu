@@ -7,6 +7,8 @@
 #include <new>
 #include <string>
 
+#include <cudaTypedefs.h>
+
 #include "fmlbm.h"
 #include "fmlbm_launch.cuh"
 
@@ -32,6 +34,10 @@ struct fmlbm_handle {
     ErrorLatch* err_host = nullptr;  // pinned
     int64_t step = 0;
     int tile_y = kTileYSmall;
+    int variant = FMLBM_VARIANT_AUTO;
+    int sms = 1;                     // multiprocessors of the handle's device
+    bool tma_maps = false;           // tensor maps of both buffers were encoded
+    CUtensorMap tmap[2][2];          // [buffer][0: float planes, 1: 16-bit planes]
     std::string last_error;
 };
 
@@ -161,7 +167,95 @@ StepArgs make_args(const fmlbm_handle* h, int src) {
     return A;
 }
 
+bool tma_supported_for(int precision, int nc) {
+    switch (precision) {
+        case FMLBM_FP32: return tma_supported<ST_F32>(nc);
+        case FMLBM_FP16DEV: return tma_supported<ST_F16DEV>(nc);
+        case FMLBM_BF16DEV: return tma_supported<ST_BF16DEV>(nc);
+        default: return false;
+    }
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 3-D map (x, y, plane) of one buffer: box = the stage of the TMA step kernel.
+bool encode_map(CUtensorMap* map, void* base, CUtensorMapDataType type, size_t esize, int nx, int ny, int planes,
+                int box_x, int box_y) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)planes};
+    cuuint64_t strides[2] = {(cuuint64_t)nx * esize, (cuuint64_t)nx * ny * esize};
+    cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, (cuuint32_t)planes};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, type, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Tensor maps for the TMA step, when the layout allows them: 16-byte row strides
+// (nx a multiple of 4 for float planes, of 8 for 16-bit planes), planes within the box
+// limit, lattices tall and wide enough to have wrap-free tiles.
+void setup_tma(fmlbm_handle* h) {
+    h->tma_maps = false;
+    const int p = h->lattice.precision, nc = h->nc, nx = h->lattice.nx, ny = h->lattice.ny;
+    if (!tma_supported_for(p, nc) || nx < kTX + 6 || ny < kTmaTileY + 6) return;
+    const int H = kTmaTileY + 6;
+    bool ok = true;
+    for (int b = 0; b < 2 && ok; ++b) {
+        if (p == FMLBM_FP32) {
+            ok = nx % 4 == 0 && encode_map(&h->tmap[b][0], h->g[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, nx, ny, 9 * nc,
+                                           kTX + 8, H);
+            h->tmap[b][1] = h->tmap[b][0];
+        } else {
+            const CUtensorMapDataType t16 =
+                p == FMLBM_FP16DEV ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+            ok = nx % 8 == 0 &&
+                 encode_map(&h->tmap[b][0], h->g0[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, nx, ny, nc, kTX + 8, H) &&
+                 encode_map(&h->tmap[b][1], h->g[b], t16, 2, nx, ny, 8 * nc, kTX + 16, H);
+        }
+    }
+    h->tma_maps = ok;
+}
+
+cudaError_t dispatch_step_tma(const fmlbm_handle* h, const StepArgs& A) {
+    const CUtensorMap* maps = h->tmap[h->cur];
+    switch (h->lattice.precision) {
+        case FMLBM_FP32: return launch_step_tma<ST_F32>(A, h->nc, maps, 1, h->stream);
+        case FMLBM_FP16DEV: return launch_step_tma<ST_F16DEV>(A, h->nc, maps, 1, h->stream);
+        case FMLBM_BF16DEV: return launch_step_tma<ST_BF16DEV>(A, h->nc, maps, 1, h->stream);
+        default: return cudaErrorNotSupported;
+    }
+}
+
+// AUTO takes the persistent TMA step only when each SM gets many tiles to pipeline
+// (measured on GB300: slower than the plain step at 1024^2, 13 tiles per SM; faster at
+// 4096^2, 215 tiles per SM).
+constexpr int kTmaMinTilesPerSM = 48;
+
+bool use_tma(const fmlbm_handle* h) {
+    if (!h->tma_maps || h->variant == FMLBM_VARIANT_PLAIN) return false;
+    if (h->variant == FMLBM_VARIANT_TMA) return true;
+    const long tiles = (long)((h->lattice.nx + kTX - 1) / kTX) * ((h->lattice.ny + kTmaTileY - 1) / kTmaTileY);
+    return tiles >= (long)kTmaMinTilesPerSM * h->sms;
+}
+
 cudaError_t dispatch_step(const fmlbm_handle* h, const StepArgs& A, bool moments) {
+    if (!moments && use_tma(h)) return dispatch_step_tma(h, A);
     switch (h->lattice.precision) {
         case FMLBM_FP64: return launch_step<ST_F64>(A, h->nc, moments, h->tile_y, h->stream);
         case FMLBM_FP32: return launch_step<ST_F32>(A, h->nc, moments, h->tile_y, h->stream);
@@ -198,6 +292,12 @@ cudaError_t dispatch_reduce(fmlbm_handle* h, const StepArgs& A) {
 fmlbm_status sync_and_check(fmlbm_handle* h) {
     FM_CUDA(h, cudaMemcpyAsync(h->err_host, h->err_dev, sizeof(ErrorLatch), cudaMemcpyDeviceToHost, h->stream));
     FM_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (h->err_host->flag == 2) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "a bounded wait for a tile copy ran out (tile at x=%d, y=%d)", h->err_host->x,
+                      h->err_host->y);
+        return fail(h, FMLBM_E_TIMEOUT, buf);
+    }
     if (h->err_host->flag) {
         char buf[160];
         std::snprintf(buf, sizeof buf, "node left the EOS domain: component %d at (x=%d, y=%d)", h->err_host->comp,
@@ -309,6 +409,8 @@ fmlbm_status fmlbm_create(const fmlbm_mixture* mixture, const fmlbm_lattice* lat
         delete h;
         return FMLBM_E_CUDA;
     }
+    cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+    setup_tma(h);
     *out = h;
     return FMLBM_OK;
 }
@@ -361,6 +463,21 @@ fmlbm_status fmlbm_set_tile_height(fmlbm_handle* h, int32_t tile_y) {
     if (!h || (tile_y != kTileYSmall && tile_y != kTileYLarge))
         return fail(h, FMLBM_E_INVALID_ARG, "tile height must be 8 or 16");
     h->tile_y = tile_y;
+    return FMLBM_OK;
+}
+
+fmlbm_status fmlbm_set_step_variant(fmlbm_handle* h, int32_t variant) {
+    if (!h || variant < FMLBM_VARIANT_AUTO || variant > FMLBM_VARIANT_TMA)
+        return fail(h, FMLBM_E_INVALID_ARG, "unknown step variant");
+    if (variant == FMLBM_VARIANT_TMA && !h->tma_maps)
+        return fail(h, FMLBM_E_UNSUPPORTED, "no TMA step for this precision, component count or lattice shape");
+    h->variant = variant;
+    return FMLBM_OK;
+}
+
+fmlbm_status fmlbm_get_step_variant(fmlbm_handle* h, int32_t* variant) {
+    if (!h || !variant) return FMLBM_E_INVALID_ARG;
+    *variant = use_tma(h) ? FMLBM_VARIANT_TMA : FMLBM_VARIANT_PLAIN;
     return FMLBM_OK;
 }
 

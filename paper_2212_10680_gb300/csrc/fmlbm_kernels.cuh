@@ -92,7 +92,7 @@ MixConstT<E> cast_mix(const MixConst& m) {
 }
 
 struct ErrorLatch {
-    int flag;         // 0 = clean, 1 = a node left the EOS domain
+    int flag;         // 0 = clean, 1 = a node left the EOS domain, 2 = a bounded wait ran out
     int comp, x, y;
 };
 
@@ -333,119 +333,95 @@ __device__ __forceinline__ void domain_check(const StepArgs& A, const Real* rt, 
     }
 }
 
-// MOMENTS = true: compute the macroscopic fields of the current state instead of
-// advancing it (no distribution or force store).
-template <int NC, int ST, int TY, bool MOMENTS>
-__global__ void __launch_bounds__(kTX* TY) fused_step(StepArgs A) {
-    using Real = typename StoreTraits<ST>::Real;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto& S = *reinterpret_cast<StepSmem<Real, NC, TY>*>(smem_raw);
-    const MixConstT<Real>& m = mixc<Real>(A);
+// ---- the phases of one tile, shared by every variant of the step kernel (so all variants
+//      perform the same arithmetic in the same order and agree bit for bit) ----
 
-    const int nx = A.nx, ny = A.ny;
-    const int nxy = nx * ny;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = ty * kTX + tx;
+// Phase 1, the node owned by this thread: rho~ and ln f from its nine pulled values per
+// component (steps 1-5).
+template <int NC, int TY, typename Real>
+__device__ __forceinline__ void phase1_node(const StepArgs& A, const MixConstT<Real>& m, StepSmem<Real, NC, TY>& S,
+                                            const Real (&g)[NC][9], int tx, int ty, bool valid, int gx, int gy) {
+    Real rt[NC], lnf[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+        Real r = Real(0);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) r += g[i][a];
+        rt[i] = r * m.invM[i];
+        S.rt.v[i][ty + 2][tx + 2] = rt[i];
+    }
+    const Real beta = node_lnf<NC, Real>(m, rt, lnf);
+#pragma unroll
+    for (int i = 0; i < NC; ++i) S.lf.v[i][ty + 1][tx + 1] = lnf[i];
+    if (valid) domain_check<NC, Real>(A, rt, lnf, beta, gx, gy);
+}
+
+// Ring position r (0 <= r < 4 (32 + 4) + 4 TY) -> box coordinates (bx, by) of the 2-node halo
+// ring around the tile (box origin at tile origin - (2, 2)).
+template <int TY>
+__device__ __forceinline__ void ring_position(int r, int& bx, int& by) {
+    constexpr int WB = kTX + 4;
+    if (r < 2 * WB) {
+        by = r / WB;
+        bx = r % WB;
+    } else if (r < 4 * WB) {
+        by = TY + 2 + (r - 2 * WB) / WB;
+        bx = (r - 2 * WB) % WB;
+    } else {
+        const int q = r - 4 * WB;
+        by = 2 + (q >> 2);
+        const int c = q & 3;
+        bx = c < 2 ? c : kTX + c;  // 0, 1, TX+2, TX+3
+    }
+}
+
+// Phase 1, a halo ring node: rho~ from its summed densities; ln f on the inner 1-node ring.
+template <int NC, int TY, typename Real>
+__device__ __forceinline__ void phase1_ring(const MixConstT<Real>& m, StepSmem<Real, NC, TY>& S, Real (&rt)[NC],
+                                            int bx, int by) {
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+        rt[i] *= m.invM[i];
+        S.rt.v[i][by][bx] = rt[i];
+    }
+    if (bx >= 1 && bx <= kTX + 2 && by >= 1 && by <= TY + 2) {
+        Real lnf[NC];
+        node_lnf<NC, Real>(m, rt, lnf);
+#pragma unroll
+        for (int i = 0; i < NC; ++i) S.lf.v[i][by - 1][bx - 1] = lnf[i];
+    }
+}
+
+// Phase 2: G_i = sum_j kappa_ij lap rho~_j on tile + 1 (step 6, mu_I,i = -G_i).
+template <int NC, int TY, typename Real>
+__device__ __forceinline__ void phase2(const MixConstT<Real>& m, StepSmem<Real, NC, TY>& S, int stencil, int tid) {
     constexpr int NT = kTX * TY;
-    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * TY;
-    // no periodic wrap anywhere in this block's reach (tile + 2 halo + 1 pull)
-    const bool inner = x0 >= 3 && x0 + kTX + 3 <= nx && y0 >= 3 && y0 + TY + 3 <= ny;
-
-    // ---- phase 1: pull and sum (steps 1-2), ln f of each node (steps 3-5) ----
-    const int gxn = x0 + tx, gyn = y0 + ty;
-    const bool valid = gxn < nx && gyn < ny;
-    Real g[NC][9];
-    {
-        const int wx = inner ? gxn : wrap(gxn, nx), wy = inner ? gyn : wrap(gyn, ny);
-        const int node = wy * nx + wx;
-        int xm = wx - 1, xp = wx + 1, ym = wy - 1, yp = wy + 1;
-        if (!inner) {
-            xm = wx == 0 ? nx - 1 : xm;
-            xp = wx == nx - 1 ? 0 : xp;
-            ym = wy == 0 ? ny - 1 : ym;
-            yp = wy == ny - 1 ? 0 : yp;
-        }
+    constexpr int W1 = kTX + 2;
+    constexpr int N1 = W1 * (TY + 2);
+    for (int q = tid; q < N1; q += NT) {
+        const int cy = q / W1, cx = q % W1;  // tile+1 coordinates
+        Real L[NC];
 #pragma unroll
-        for (int a = 0; a < 9; ++a) {
-            const int src = inner ? node - ey(a) * nx - ex(a) : pull_src(a, wx, wy, xm, xp, ym, yp, nx);
-#pragma unroll
-            for (int i = 0; i < NC; ++i) g[i][a] = load_g<ST>(A, i, a, (size_t)src, (size_t)nxy);
-        }
-        Real rt[NC], lnf[NC];
+        for (int j = 0; j < NC; ++j) L[j] = lap_at<Real>(S.rt, j, cx + 1, cy + 1, stencil);
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
-            Real r = Real(0);
+            Real Gi = Real(0);
 #pragma unroll
-            for (int a = 0; a < 9; ++a) r += g[i][a];
-            rt[i] = r * m.invM[i];
-            S.rt.v[i][ty + 2][tx + 2] = rt[i];
-        }
-        const Real beta = node_lnf<NC, Real>(m, rt, lnf);
-#pragma unroll
-        for (int i = 0; i < NC; ++i) S.lf.v[i][ty + 1][tx + 1] = lnf[i];
-        if (valid) domain_check<NC, Real>(A, rt, lnf, beta, gxn, gyn);
-    }
-    {
-        // the 2-node ring around the tile: rho~ everywhere, ln f on its inner 1-node ring
-        constexpr int WB = kTX + 4;
-        constexpr int RING = 4 * WB + 4 * TY;
-        for (int r = tid; r < RING; r += NT) {
-            int bx, by;
-            if (r < 2 * WB) {
-                by = r / WB;
-                bx = r % WB;
-            } else if (r < 4 * WB) {
-                by = TY + 2 + (r - 2 * WB) / WB;
-                bx = (r - 2 * WB) % WB;
-            } else {
-                const int q = r - 4 * WB;
-                by = 2 + (q >> 2);
-                const int c = q & 3;
-                bx = c < 2 ? c : kTX + c;  // 0, 1, TX+2, TX+3
-            }
-            const int wx = inner ? x0 - 2 + bx : wrap(x0 - 2 + bx, nx);
-            const int wy = inner ? y0 - 2 + by : wrap(y0 - 2 + by, ny);
-            Real rt[NC];
-            pull_rho<NC, ST>(A, wx, wy, inner, nx, ny, nxy, rt);
-#pragma unroll
-            for (int i = 0; i < NC; ++i) {
-                rt[i] *= m.invM[i];
-                S.rt.v[i][by][bx] = rt[i];
-            }
-            if (bx >= 1 && bx <= kTX + 2 && by >= 1 && by <= TY + 2) {
-                Real lnf[NC];
-                node_lnf<NC, Real>(m, rt, lnf);
-#pragma unroll
-                for (int i = 0; i < NC; ++i) S.lf.v[i][by - 1][bx - 1] = lnf[i];
-            }
+            for (int j = 0; j < NC; ++j) Gi += m.kap[i * kMaxC + j] * L[j];
+            S.G.v[i][cy][cx] = Gi;
         }
     }
-    __syncthreads();
+}
 
-    // ---- phase 2: G_i = sum_j kappa_ij lap rho~_j on tile + 1 (step 6, mu_I,i = -G_i) ----
-    {
-        constexpr int W1 = kTX + 2;
-        constexpr int N1 = W1 * (TY + 2);
-        for (int q = tid; q < N1; q += NT) {
-            const int cy = q / W1, cx = q % W1;  // tile+1 coordinates
-            Real L[NC];
-#pragma unroll
-            for (int j = 0; j < NC; ++j) L[j] = lap_at<Real>(S.rt, j, cx + 1, cy + 1, A.stencil);
-#pragma unroll
-            for (int i = 0; i < NC; ++i) {
-                Real Gi = Real(0);
-#pragma unroll
-                for (int j = 0; j < NC; ++j) Gi += m.kap[i * kMaxC + j] * L[j];
-                S.G.v[i][cy][cx] = Gi;
-            }
-        }
-    }
-    __syncthreads();
-
-    if (!valid) return;
-
-    // ---- phase 3: force (step 7), velocity (step 1), equilibrium and forcing (step 8),
-    //      collision (step 9) ----
+// Phase 3 at one valid node: force (step 7), velocity (step 1), equilibrium and forcing
+// (step 8), collision (step 9), coalesced stores at the node.
+template <int NC, int ST, int TY, bool MOMENTS>
+__device__ __forceinline__ void phase3(const StepArgs& A, const MixConstT<typename StoreTraits<ST>::Real>& m,
+                                       StepSmem<typename StoreTraits<ST>::Real, NC, TY>& S,
+                                       const typename StoreTraits<ST>::Real (&g)[NC][9], int tx, int ty, int gxn,
+                                       int gyn) {
+    using Real = typename StoreTraits<ST>::Real;
+    const int nx = A.nx, nxy = A.nx * A.ny;
     const int cx = tx + 1, cy = ty + 1;  // tile+1 coordinates of this node
     Real Fx[NC], Fy[NC], grx[NC], gry[NC], rhoi[NC];
     Real rho = Real(0), jx = Real(0), jy = Real(0), Ftx = Real(0), Fty = Real(0);
@@ -496,7 +472,6 @@ __global__ void __launch_bounds__(kTX* TY) fused_step(StepArgs A) {
             A.u_out[node] = (double)ux;
             A.u_out[(size_t)nxy + node] = (double)uy;
         }
-        return;
     } else {
         // Collision g' = g - omega (g - g^eq) + fcoef F_a, with g^eq of Eq. eqLBEMCb (rho_0 = 0)
         // and F_a of Eq. eqLBEMCfinal3, evaluated for each pair of opposite directions
@@ -510,9 +485,9 @@ __global__ void __launch_bounds__(kTX* TY) fused_step(StepArgs A) {
             const Real rw = omega * rhoi[i];
             const Real uF = ux * Fx[i] + uy * Fy[i];
             const Real ug = ux * grx[i] + uy * gry[i];
-            const Real base = rw * Real(1.5) * usq;          // omega rho 1.5 u^2
+            const Real base = rw * Real(1.5) * usq;                    // omega rho 1.5 u^2
             const Real c_ax = fc * (Real(-3) * uF - Real(0.5) * ug);   // c - 1 = -1/2 on the axes
-            const Real c_dg = fc * (Real(-3) * uF + ug);                // c - 1 = +1 on the diagonals
+            const Real c_dg = fc * (Real(-3) * uF + ug);               // c - 1 = +1 on the diagonals
             // a = 0: g^eq_0 = rho - (4/9) rho 1.5 u^2, F_0 = (4/9)(-3 uF - 2 ug)
             const Real g0 = keep * g[i][0] + rw - Real(4.0 / 9.0) * base +
                             Real(4.0 / 9.0) * fc * (Real(-3) * uF - Real(2) * ug);
@@ -538,6 +513,71 @@ __global__ void __launch_bounds__(kTX* TY) fused_step(StepArgs A) {
         Fout[node] = Ftx;
         Fout[nxy + node] = Fty;
     }
+}
+
+// Phase 1 from global memory for one tile: pull of the owned node (into g) and of the halo
+// ring (rho~ only), with periodic wrap unless the tile is inner.
+template <int NC, int ST, int TY>
+__device__ __forceinline__ void phase1_global(const StepArgs& A, const MixConstT<typename StoreTraits<ST>::Real>& m,
+                                              StepSmem<typename StoreTraits<ST>::Real, NC, TY>& S,
+                                              typename StoreTraits<ST>::Real (&g)[NC][9], int x0, int y0,
+                                              bool inner, int tx, int ty, int tid) {
+    using Real = typename StoreTraits<ST>::Real;
+    constexpr int NT = kTX * TY;
+    const int nx = A.nx, ny = A.ny, nxy = nx * ny;
+    const int gxn = x0 + tx, gyn = y0 + ty;
+    const bool valid = gxn < nx && gyn < ny;
+    {
+        const int wx = inner ? gxn : wrap(gxn, nx), wy = inner ? gyn : wrap(gyn, ny);
+        const int node = wy * nx + wx;
+        int xm = wx - 1, xp = wx + 1, ym = wy - 1, yp = wy + 1;
+        if (!inner) {
+            xm = wx == 0 ? nx - 1 : xm;
+            xp = wx == nx - 1 ? 0 : xp;
+            ym = wy == 0 ? ny - 1 : ym;
+            yp = wy == ny - 1 ? 0 : yp;
+        }
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            const int src = inner ? node - ey(a) * nx - ex(a) : pull_src(a, wx, wy, xm, xp, ym, yp, nx);
+#pragma unroll
+            for (int i = 0; i < NC; ++i) g[i][a] = load_g<ST>(A, i, a, (size_t)src, (size_t)nxy);
+        }
+        phase1_node<NC, TY, Real>(A, m, S, g, tx, ty, valid, gxn, gyn);
+    }
+    constexpr int RING = 4 * (kTX + 4) + 4 * TY;
+    for (int r = tid; r < RING; r += NT) {
+        int bx, by;
+        ring_position<TY>(r, bx, by);
+        const int wx = inner ? x0 - 2 + bx : wrap(x0 - 2 + bx, nx);
+        const int wy = inner ? y0 - 2 + by : wrap(y0 - 2 + by, ny);
+        Real rt[NC];
+        pull_rho<NC, ST>(A, wx, wy, inner, nx, ny, nxy, rt);
+        phase1_ring<NC, TY, Real>(m, S, rt, bx, by);
+    }
+}
+
+// MOMENTS = true: compute the macroscopic fields of the current state instead of
+// advancing it (no distribution or force store).
+template <int NC, int ST, int TY, bool MOMENTS>
+__global__ void __launch_bounds__(kTX* TY) fused_step(StepArgs A) {
+    using Real = typename StoreTraits<ST>::Real;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto& S = *reinterpret_cast<StepSmem<Real, NC, TY>*>(smem_raw);
+    const MixConstT<Real>& m = mixc<Real>(A);
+    const int nx = A.nx, ny = A.ny;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * kTX + tx;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * TY;
+    // no periodic wrap anywhere in this block's reach (tile + 2 halo + 1 pull)
+    const bool inner = x0 >= 3 && x0 + kTX + 3 <= nx && y0 >= 3 && y0 + TY + 3 <= ny;
+    Real g[NC][9];
+    phase1_global<NC, ST, TY>(A, m, S, g, x0, y0, inner, tx, ty, tid);
+    __syncthreads();
+    phase2<NC, TY, Real>(m, S, A.stencil, tid);
+    __syncthreads();
+    const int gxn = x0 + tx, gyn = y0 + ty;
+    if (gxn < nx && gyn < ny) phase3<NC, ST, TY, MOMENTS>(A, m, S, g, tx, ty, gxn, gyn);
 }
 
 // g = g^eq(rho, u = 0): rho_i in a = 0, zero elsewhere; stored force zero.

@@ -2,7 +2,7 @@
 // storage precision (step_f64.cu, step_f32.cu, step_f16.cu, step_bf16.cu).
 #pragma once
 
-#include "fmlbm_kernels.cuh"
+#include "fmlbm_tma.cuh"
 
 namespace fmlbm {
 
@@ -13,6 +13,14 @@ constexpr int kTileYLarge = 16;
 
 template <int ST>
 cudaError_t launch_step(const StepArgs& A, int nc, bool moments, int tile_y, cudaStream_t s);
+// Persistent TMA-fed step (float and 16-bit storage); maps[0]: float planes, maps[1]:
+// 16-bit planes (deviation forms).  tma_ok = 0 sends every tile down the plain pull path.
+template <int ST>
+cudaError_t launch_step_tma(const StepArgs& A, int nc, const CUtensorMap* maps, int tma_ok, cudaStream_t s);
+// Whether the TMA variant exists for this storage and component count (shared memory).
+template <int ST>
+bool tma_supported(int nc);
+
 template <int ST>
 cudaError_t launch_init(const StepArgs& A, int nc, const double* rho, cudaStream_t s);
 template <int ST>
@@ -106,6 +114,56 @@ cudaError_t launch_reduce(const StepArgs& A, int nc, void* rho_prev, int have_pr
             case 4: return launch_reduce_nc_##ST<4>(A, rho_prev, have_prev, partial, out, s);             \
         }                                                                                                 \
         return cudaErrorInvalidValue;                                                                     \
+    }
+
+#define FMLBM_DEFINE_TMA_LAUNCHER(ST)                                                                     \
+    template <int NC>                                                                                     \
+    static cudaError_t launch_tma_nc_##ST(const StepArgs& A, const CUtensorMap* maps, int tma_ok,         \
+                                          cudaStream_t s) {                                               \
+        using L = TmaLayout<NC, ST, kTmaTileY>;                                                           \
+        if constexpr (!L::fits) {                                                                         \
+            return cudaErrorNotSupported;                                                                 \
+        } else {                                                                                          \
+            auto k = fused_step_tma<NC, ST, kTmaTileY, L::stages>;                                        \
+            static int per_sm = 0, sms = 0;                                                               \
+            if (per_sm == 0) {                                                                            \
+                cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                                                     (int)L::smem_bytes);                                 \
+                if (e != cudaSuccess) return e;                                                           \
+                int dev = 0;                                                                              \
+                cudaGetDevice(&dev);                                                                      \
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);                        \
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTX * kTmaTileY,            \
+                                                                  L::smem_bytes);                         \
+                if (e != cudaSuccess) return e;                                                           \
+                if (per_sm < 1) return cudaErrorInvalidConfiguration;                                     \
+            }                                                                                             \
+            const int ntiles = ((A.nx + kTX - 1) / kTX) * ((A.ny + kTmaTileY - 1) / kTmaTileY);           \
+            const int grid = ntiles < sms * per_sm ? ntiles : sms * per_sm;                               \
+            k<<<grid, dim3(kTX, kTmaTileY), L::smem_bytes, s>>>(A, maps[0], maps[1], tma_ok);             \
+            return cudaGetLastError();                                                                    \
+        }                                                                                                 \
+    }                                                                                                     \
+    template <>                                                                                           \
+    cudaError_t launch_step_tma<ST>(const StepArgs& A, int nc, const CUtensorMap* maps, int tma_ok,       \
+                                    cudaStream_t s) {                                                     \
+        switch (nc) {                                                                                     \
+            case 1: return launch_tma_nc_##ST<1>(A, maps, tma_ok, s);                                     \
+            case 2: return launch_tma_nc_##ST<2>(A, maps, tma_ok, s);                                     \
+            case 3: return launch_tma_nc_##ST<3>(A, maps, tma_ok, s);                                     \
+            case 4: return launch_tma_nc_##ST<4>(A, maps, tma_ok, s);                                     \
+        }                                                                                                 \
+        return cudaErrorInvalidValue;                                                                     \
+    }                                                                                                     \
+    template <>                                                                                           \
+    bool tma_supported<ST>(int nc) {                                                                      \
+        switch (nc) {                                                                                     \
+            case 1: return TmaLayout<1, ST, kTmaTileY>::fits;                                             \
+            case 2: return TmaLayout<2, ST, kTmaTileY>::fits;                                             \
+            case 3: return TmaLayout<3, ST, kTmaTileY>::fits;                                             \
+            case 4: return TmaLayout<4, ST, kTmaTileY>::fits;                                             \
+        }                                                                                                 \
+        return false;                                                                                     \
     }
 
 }  // namespace fmlbm

@@ -1,0 +1,221 @@
+// TMA-fed persistent variant of the fused step (sm_103a, float and 16-bit storage).
+//
+// Each block stays resident and walks a strided list of 32 x TY tiles.  For a tile that
+// needs no periodic wrap, one elected thread issues a single 3-D bulk tensor copy
+// (cp.async.bulk.tensor) of every distribution plane of the tile plus its 3-node pull
+// halo into shared memory, completing on an mbarrier; with two stages the copy of the
+// next tile is in flight while the current one is computed.  Tiles on the periodic
+// edges take the plain pull path of fused_step.  Both paths run the same phase
+// functions, so the results are bit-identical to fused_step.
+//
+// Box of one stage: columns x0 - 4 .. x0 + 35 (x0 - 8 .. x0 + 39 for 16-bit planes, so
+// that the innermost coordinate times the element size is a multiple of 16 bytes), rows
+// y0 - 3 .. y0 + TY + 2, all planes.  Every wait on an mbarrier is bounded; a wait that
+// runs out latches error code 2 and the block waits (bounded) for its copies in flight
+// and returns.
+#pragma once
+
+#include <cuda.h>
+
+#include "fmlbm_kernels.cuh"
+
+namespace fmlbm {
+
+constexpr int kTmaTileY = 16;
+constexpr long long kMaxPolls = 1ll << 24;  // try_wait polls before a wait is declared failed
+
+template <int ST> struct TmaGeom;
+template <> struct TmaGeom<ST_F32> {
+    static constexpr int W = kTX + 8;        // float planes, origin x0 - 4
+    static constexpr int W16 = 0;
+};
+template <> struct TmaGeom<ST_F16DEV> {
+    static constexpr int W = kTX + 8;        // float a = 0 planes, origin x0 - 4
+    static constexpr int W16 = kTX + 16;     // 16-bit planes, origin x0 - 8
+};
+template <> struct TmaGeom<ST_BF16DEV> : TmaGeom<ST_F16DEV> {};
+
+template <int NC, int ST, int TY>
+struct TmaLayout {
+    static constexpr int H = TY + 6;
+    static constexpr int W = TmaGeom<ST>::W;
+    static constexpr int W16 = TmaGeom<ST>::W16;
+    static constexpr bool dev = ST != ST_F32;
+    static constexpr size_t f32_planes = dev ? NC : 9 * NC;
+    static constexpr size_t f32_bytes = f32_planes * H * W * 4;
+    static constexpr size_t b16_bytes = dev ? (size_t)8 * NC * H * W16 * 2 : 0;
+    static constexpr size_t align128(size_t v) { return (v + 127) & ~size_t(127); }
+    static constexpr size_t stage_bytes = align128(f32_bytes) + align128(b16_bytes);
+    static constexpr size_t scratch_bytes = align128(sizeof(StepSmem<float, NC, TY>));
+    static constexpr int stages = (scratch_bytes + 2 * stage_bytes + 64 <= 220 * 1024) ? 2 : 1;
+    static constexpr size_t smem_bytes = scratch_bytes + stages * stage_bytes + 64;
+    static constexpr bool fits = smem_bytes <= 227 * 1024;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: true once the phase with this parity has completed, false after kMaxPolls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    for (long long k = 0; k < kMaxPolls; ++k)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Pulled value of plane (i, a) for box position (col, row) of the x0 - 4 origin.
+template <int NC, int ST, int TY>
+__device__ __forceinline__ typename StoreTraits<ST>::Real stage_value(const unsigned char* stage, int i, int a,
+                                                                      int row, int col) {
+    using L = TmaLayout<NC, ST, TY>;
+    const float* f = reinterpret_cast<const float*>(stage);
+    if constexpr (ST == ST_F32) {
+        return f[((i * 9 + a) * L::H + row) * L::W + col];
+    } else {
+        using Elem = typename StoreTraits<ST>::Elem;
+        if (a == 0) return f[(i * L::H + row) * L::W + col];
+        const Elem* h = reinterpret_cast<const Elem*>(stage + L::align128(L::f32_bytes));
+        return to_real(h[((i * 8 + a - 1) * L::H + row) * L::W16 + col + 4]);
+    }
+}
+
+template <int NC, int ST, int TY, int NSTAGE>
+__global__ void __launch_bounds__(kTX* TY, 1)
+    fused_step_tma(const __grid_constant__ StepArgs A, const __grid_constant__ CUtensorMap map_f32,
+                   const __grid_constant__ CUtensorMap map_b16, int tma_ok) {
+    using Real = typename StoreTraits<ST>::Real;
+    using L = TmaLayout<NC, ST, TY>;
+    extern __shared__ __align__(128) unsigned char smem_tma[];
+    auto& S = *reinterpret_cast<StepSmem<Real, NC, TY>*>(smem_tma);
+    unsigned char* stages = smem_tma + L::scratch_bytes;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(stages + NSTAGE * L::stage_bytes);
+    const MixConstT<Real>& m = mixc<Real>(A);
+
+    const int nx = A.nx, ny = A.ny;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * kTX + tx;
+    const int tiles_x = (nx + kTX - 1) / kTX;
+    const int ntiles = tiles_x * ((ny + TY - 1) / TY);
+
+    auto origin = [&](int t, int& x0, int& y0) {
+        x0 = (t % tiles_x) * kTX;
+        y0 = (t / tiles_x) * TY;
+    };
+    auto is_inner = [&](int x0, int y0) { return x0 >= 3 && x0 + kTX + 3 <= nx && y0 >= 3 && y0 + TY + 3 <= ny; };
+    auto use_tma = [&](int t) {
+        int x0, y0;
+        origin(t, x0, y0);
+        return tma_ok && is_inner(x0, y0);
+    };
+    auto issue = [&](int t, int s) {  // one elected thread
+        int x0, y0;
+        origin(t, x0, y0);
+        unsigned char* st = stages + s * L::stage_bytes;
+        mbar_expect_tx(&bar[s], (uint32_t)(L::f32_bytes + L::b16_bytes));
+        tma_load_3d(st, &map_f32, &bar[s], x0 - 4, y0 - 3, 0);
+        if constexpr (L::dev) tma_load_3d(st + L::align128(L::f32_bytes), &map_b16, &bar[s], x0 - 8, y0 - 3, 0);
+    };
+
+    if (tid == 0) {
+        for (int s = 0; s < NSTAGE; ++s) mbar_init(&bar[s]);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    uint32_t parity = 0u;   // bit s: phase parity the next wait on stage s expects
+    uint32_t pending = 0u;  // bit s: a copy into stage s is in flight
+    int t = blockIdx.x;
+    if (NSTAGE == 2 && t < ntiles && use_tma(t)) {
+        if (tid == 0) issue(t, 0);
+        pending |= 1u;
+    }
+    for (int k = 0; t < ntiles; t += gridDim.x, ++k) {
+        const int s = NSTAGE == 2 ? (k & 1) : 0;
+        const bool tma_here = use_tma(t);
+        if (NSTAGE == 2) {
+            const int tn = t + gridDim.x;
+            if (tn < ntiles && use_tma(tn)) {
+                if (tid == 0) issue(tn, s ^ 1);
+                pending |= 1u << (s ^ 1);
+            }
+        } else if (tma_here) {
+            if (tid == 0) issue(t, 0);
+            pending |= 1u;
+        }
+        int x0, y0;
+        origin(t, x0, y0);
+        const int gxn = x0 + tx, gyn = y0 + ty;
+        Real g[NC][9];
+        if (tma_here) {
+            const bool ok = mbar_wait_bounded(&bar[s], (parity >> s) & 1u);
+            if (__syncthreads_or(!ok)) {
+                // a copy never completed: report, give the copies in flight a bounded
+                // chance to land, and leave
+                if (tid == 0 && atomicCAS(&A.err->flag, 0, 2) == 0) {
+                    A.err->comp = -1;
+                    A.err->x = x0;
+                    A.err->y = y0;
+                }
+#pragma unroll
+                for (int q = 0; q < NSTAGE; ++q)
+                    if (((pending >> q) & 1u) && q != s) mbar_wait_bounded(&bar[q], (parity >> q) & 1u);
+                return;
+            }
+            parity ^= 1u << s;
+            pending &= ~(1u << s);
+            const unsigned char* st = stages + s * L::stage_bytes;
+#pragma unroll
+            for (int a = 0; a < 9; ++a)
+#pragma unroll
+                for (int i = 0; i < NC; ++i)
+                    g[i][a] = stage_value<NC, ST, TY>(st, i, a, ty + 3 - ey(a), tx + 4 - ex(a));
+            phase1_node<NC, TY, Real>(A, m, S, g, tx, ty, gxn < nx && gyn < ny, gxn, gyn);
+            constexpr int RING = 4 * (kTX + 4) + 4 * TY;
+            for (int r = tid; r < RING; r += kTX * TY) {
+                int bx, by;
+                ring_position<TY>(r, bx, by);
+                Real rt[NC];
+#pragma unroll
+                for (int i = 0; i < NC; ++i) rt[i] = Real(0);
+#pragma unroll
+                for (int a = 0; a < 9; ++a)
+#pragma unroll
+                    for (int i = 0; i < NC; ++i) rt[i] += stage_value<NC, ST, TY>(st, i, a, by + 1 - ey(a), bx + 2 - ex(a));
+                phase1_ring<NC, TY, Real>(m, S, rt, bx, by);
+            }
+        } else {
+            phase1_global<NC, ST, TY>(A, m, S, g, x0, y0, is_inner(x0, y0), tx, ty, tid);
+        }
+        __syncthreads();
+        phase2<NC, TY, Real>(m, S, A.stencil, tid);
+        __syncthreads();
+        if (gxn < nx && gyn < ny) phase3<NC, ST, TY, false>(A, m, S, g, tx, ty, gxn, gyn);
+        __syncthreads();  // shared tiles and the stage are free again
+    }
+}
+
+}  // namespace fmlbm

@@ -3,4 +3,5 @@
 
 namespace fmlbm {
 FMLBM_DEFINE_LAUNCHERS(ST_F16DEV)
+FMLBM_DEFINE_TMA_LAUNCHER(ST_F16DEV)
 }  // namespace fmlbm

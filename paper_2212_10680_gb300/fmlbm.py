@@ -27,6 +27,7 @@ STATUS = {0: "FMLBM_OK", 1: "FMLBM_E_INVALID_ARG", 2: "FMLBM_E_OOM", 3: "FMLBM_E
           4: "FMLBM_E_NONPHYSICAL", 5: "FMLBM_E_TIMEOUT", 6: "FMLBM_E_BUSY", 7: "FMLBM_E_NOT_CONVERGED",
           8: "FMLBM_E_UNSUPPORTED"}
 E_NONPHYSICAL = 4
+E_TIMEOUT = 5
 E_NOT_CONVERGED = 7
 E_BUSY = 6
 
@@ -75,6 +76,8 @@ def _load() -> ctypes.CDLL:
         "fmlbm_set_state": ([H, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
         "fmlbm_synchronize": ([H], ctypes.c_int),
         "fmlbm_set_tile_height": ([H, ctypes.c_int32], ctypes.c_int),
+        "fmlbm_set_step_variant": ([H, ctypes.c_int32], ctypes.c_int),
+        "fmlbm_get_step_variant": ([H, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "fmlbm_lattice_bytes": ([ctypes.c_int32, ctypes.POINTER(fmlbm_lattice), ctypes.POINTER(ctypes.c_size_t)],
                                 ctypes.c_int),
         "fmlbm_diagnostics_noalloc": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -211,6 +214,19 @@ def fmlbm_set_state(h, state: bytes):
 
 def fmlbm_set_tile_height(h, tile_y: int):
     _check(LIB.fmlbm_set_tile_height(h, tile_y), "fmlbm_set_tile_height", h)
+
+
+VARIANT = {"auto": 0, "plain": 1, "tma": 2}
+
+
+def fmlbm_set_step_variant(h, variant: str):
+    _check(LIB.fmlbm_set_step_variant(h, VARIANT[variant]), "fmlbm_set_step_variant", h)
+
+
+def fmlbm_get_step_variant(h) -> str:
+    v = ctypes.c_int32()
+    _check(LIB.fmlbm_get_step_variant(h, ctypes.byref(v)), "fmlbm_get_step_variant", h)
+    return {1: "plain", 2: "tma"}[v.value]
 
 
 def fmlbm_synchronize(h):
