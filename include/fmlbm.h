@@ -233,6 +233,60 @@ fmlbm_status fmlbm_diagnostics_noalloc(int32_t n_components, int32_t nx, int32_t
 /* Releases all device memory of the handle.  NULL-safe. */
 void fmlbm_destroy(fmlbm_handle* h);
 
+/* ------------------------------------------------------------------------------------
+ * Batches: many independent lattices of one component count and storage precision
+ * (any sizes, any mixtures) in slots, advanced together by one persistent kernel per
+ * time step.  Each lattice's arithmetic is that of a single-lattice plain step, so its
+ * results are bit-identical to fmlbm_step on its own handle, whatever else shares the
+ * batch.  fmlbm_batch_run captures chunks of steps as a CUDA graph, checks every
+ * lattice's residual after each chunk and retires it once converged.  Batches are not
+ * thread-safe.  The paper runs its envelope points as independent simulations
+ * (Section V.B); a batch runs such sweeps side by side.
+ * ------------------------------------------------------------------------------------ */
+typedef struct fmlbm_batch fmlbm_batch;
+
+/* capacity: maximum number of slots (1 .. 2^20).  cuda_stream: caller-owned stream, or
+ * NULL for a stream the batch creates (graph capture needs a non-default stream). */
+fmlbm_status fmlbm_batch_create(int32_t n_components, int32_t precision, int32_t capacity, void* cuda_stream,
+                                fmlbm_batch** out);
+/* Adds a lattice in a free slot, initialised at rest from rho_host ([N][ny][nx] mass
+ * densities, copied) and active.  Its device buffers come from the stream-ordered pool.
+ * FMLBM_E_BUSY when every slot is taken, FMLBM_E_OOM when memory runs out. */
+fmlbm_status fmlbm_batch_add(fmlbm_batch* b, const fmlbm_mixture* mixture, const fmlbm_lattice* lattice,
+                             const double* rho_host, int32_t* slot);
+/* Frees a slot and its device memory (synchronises). */
+fmlbm_status fmlbm_batch_remove(fmlbm_batch* b, int32_t slot);
+/* Pauses (0) or resumes (1) stepping of a slot. */
+fmlbm_status fmlbm_batch_set_active(fmlbm_batch* b, int32_t slot, int32_t active);
+/* Enqueues nsteps steps of every active slot (asynchronous). */
+fmlbm_status fmlbm_batch_step(fmlbm_batch* b, int64_t nsteps);
+/* Residual and error check of every active slot (synchronises); results via
+ * fmlbm_batch_slot_info.  The first check after a slot is added sets its snapshot
+ * (residual +inf). */
+fmlbm_status fmlbm_batch_check(fmlbm_batch* b);
+/* Runs every active slot until it retires: residual < tol at a check (every check_every
+ * steps, one graph launch per chunk), a latched error, or max_steps reached
+ * (FMLBM_E_NOT_CONVERGED).  Outputs per slot (arrays of capacity entries, may be NULL):
+ * steps taken, last residual, status. */
+fmlbm_status fmlbm_batch_run(fmlbm_batch* b, int64_t max_steps, int32_t check_every, double tol,
+                             int64_t* steps_out, double* residual_out, int32_t* status_out);
+fmlbm_status fmlbm_batch_slot_info(fmlbm_batch* b, int32_t slot, int64_t* steps, double* residual, int32_t* status,
+                                   int32_t* active);
+/* As fmlbm_moments / fmlbm_get_distributions for one slot (host outputs; synchronises). */
+fmlbm_status fmlbm_batch_moments(fmlbm_batch* b, int32_t slot, double* rho, double* u, double* lnf);
+fmlbm_status fmlbm_batch_get_distributions(fmlbm_batch* b, int32_t slot, double* g, double* force);
+/* Autotuner: times steps_per_trial steps of the current active slots for each tile
+ * height (8, 16) and grid size (1, 2, 4, 8 blocks per multiprocessor) and keeps the
+ * fastest.  The trial steps are real steps of the lattices (the tiling does not change
+ * results).  Outputs (may be NULL): chosen tile height, blocks, ms per step. */
+fmlbm_status fmlbm_batch_autotune(fmlbm_batch* b, int32_t steps_per_trial, int32_t* tile_y, int32_t* blocks,
+                                  double* ms_per_step);
+/* Device bytes held by the batch's lattices. */
+fmlbm_status fmlbm_batch_bytes(fmlbm_batch* b, size_t* bytes);
+const char* fmlbm_batch_last_error(const fmlbm_batch* b);
+/* Synchronises and frees everything.  NULL-safe. */
+void fmlbm_batch_destroy(fmlbm_batch* b);
+
 const char* fmlbm_status_str(fmlbm_status s);
 const char* fmlbm_last_error(const fmlbm_handle* h);
 

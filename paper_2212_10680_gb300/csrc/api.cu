@@ -10,6 +10,7 @@
 #include <cudaTypedefs.h>
 
 #include "fmlbm.h"
+#include "fmlbm_internal.h"
 #include "fmlbm_launch.cuh"
 
 using namespace fmlbm;
@@ -330,6 +331,11 @@ fmlbm_status reset_state_flags(fmlbm_handle* h) {
 }
 
 }  // namespace
+
+bool fmlbm_internal_mixture_constants(const fmlbm_mixture& m, MixConst* mc, std::string* why) {
+    return mixture_constants(m, mc, why);
+}
+bool fmlbm_internal_lattice_ok(const fmlbm_lattice& L, int nc, std::string* why) { return lattice_ok(L, nc, why); }
 
 extern "C" {
 

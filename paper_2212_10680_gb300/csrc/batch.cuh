@@ -1,0 +1,143 @@
+// Batched lattices: many independent lattices (same component count and storage,
+// any sizes, any mixtures) advanced together by one persistent kernel per time step.
+//
+// Every lattice has a device-resident descriptor holding its StepArgs for both
+// step parities (the ping-pong buffers swapped) and its own step counter.  A work list
+// of (lattice, tile) items covers all lattices; a block copies the descriptor of its
+// item's lattice into shared memory and runs the same phase functions as fused_step,
+// so each lattice's arithmetic is exactly that of a single-lattice plain step: results
+// are bit-identical alone and in any mix.  Retired lattices are skipped through a
+// device flag, so a captured graph of the step loop stays valid as lattices retire.
+#pragma once
+
+#include "fmlbm_kernels.cuh"
+
+namespace fmlbm {
+
+struct BatchLattice {
+    StepArgs args[2];    // [step & 1]
+    long long step;      // steps taken (device side, advanced by batch_advance)
+    int active;          // 0: retired or not started
+    int item0, nitems;   // its items in the work list
+    int tile_y;          // the tile height its items were cut with
+    int pad[3];
+};
+
+struct WorkItem {
+    int lattice;
+    int x0, y0;
+};
+
+// One step of every active lattice.
+template <int NC, int ST, int TY>
+__global__ void __launch_bounds__(kTX* TY) batch_step(BatchLattice* __restrict__ lat,
+                                                      const WorkItem* __restrict__ work, int nwork) {
+    using Real = typename StoreTraits<ST>::Real;
+    extern __shared__ __align__(16) unsigned char smem_batch[];
+    auto& S = *reinterpret_cast<StepSmem<Real, NC, TY>*>(smem_batch);
+    __shared__ __align__(16) StepArgs As;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * kTX + tx;
+    constexpr int NT = kTX * TY;
+    constexpr int WORDS = sizeof(StepArgs) / 4;
+    static_assert(sizeof(StepArgs) % 4 == 0, "StepArgs copied as words");
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+        const WorkItem it = work[w];
+        const BatchLattice* L = lat + it.lattice;
+        if (!L->active) continue;  // uniform across the block
+        const int* src = reinterpret_cast<const int*>(&L->args[L->step & 1]);
+        int* dst = reinterpret_cast<int*>(&As);
+        for (int k = tid; k < WORDS; k += NT) dst[k] = src[k];
+        __syncthreads();
+        const StepArgs& A = As;
+        const MixConstT<Real>& m = mixc<Real>(A);
+        const int nx = A.nx, ny = A.ny;
+        const int x0 = it.x0, y0 = it.y0;
+        const bool inner = x0 >= 3 && x0 + kTX + 3 <= nx && y0 >= 3 && y0 + TY + 3 <= ny;
+        Real g[NC][9];
+        phase1_global<NC, ST, TY>(A, m, S, g, x0, y0, inner, tx, ty, tid);
+        __syncthreads();
+        phase2<NC, TY, Real>(m, S, A.stencil, tid);
+        __syncthreads();
+        const int gxn = x0 + tx, gyn = y0 + ty;
+        if (gxn < nx && gyn < ny) phase3<NC, ST, TY, false>(A, m, S, g, tx, ty, gxn, gyn);
+        __syncthreads();  // As and the shared tiles are reused by the next item
+    }
+}
+
+__global__ void batch_advance(BatchLattice* __restrict__ lat, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n && lat[k].active) lat[k].step += 1;
+}
+
+// Per-item partial sums (NC + 2 doubles: sum rho_i, sum (rho - rho_prev)^2, sum rho^2) over
+// the item's tile of 32 x tile_y nodes, then rho_prev <- rho.  The items of one lattice
+// are contiguous, so batch_reduce_final sums each lattice in a fixed order.
+template <int NC, int ST>
+__global__ void __launch_bounds__(kTX* 8) batch_reduce(BatchLattice* __restrict__ lat, const WorkItem* __restrict__ work,
+                                                       int nwork, void* const* __restrict__ rho_prev,
+                                                       double* __restrict__ partial) {
+    using Real = typename StoreTraits<ST>::Real;
+    const int w = blockIdx.x;
+    if (w >= nwork) return;
+    const WorkItem it = work[w];
+    const BatchLattice* L = lat + it.lattice;
+    const StepArgs& A = L->args[L->step & 1];
+    const int nx = A.nx, ny = A.ny, nxy = nx * ny;
+    Real* prev = static_cast<Real*>(rho_prev[it.lattice]);
+    Real acc[NC + 2];
+#pragma unroll
+    for (int k = 0; k < NC + 2; ++k) acc[k] = Real(0);
+    if (L->active) {
+        for (int ry = threadIdx.y; ry < L->tile_y; ry += 8) {
+            const int x = it.x0 + threadIdx.x, y = it.y0 + ry;
+            if (x < nx && y < ny) {
+                const bool inner = x >= 1 && x + 1 < nx && y >= 1 && y + 1 < ny;
+                Real r[NC];
+                pull_rho<NC, ST>(A, x, y, inner, nx, ny, nxy, r);
+                const int node = y * nx + x;
+                Real pv[NC];
+#pragma unroll
+                for (int i = 0; i < NC; ++i) pv[i] = prev[(size_t)i * nxy + node];
+#pragma unroll
+                for (int i = 0; i < NC; ++i) {
+                    acc[i] += r[i];
+                    acc[NC + 1] += r[i] * r[i];
+                    const Real d = r[i] - pv[i];
+                    acc[NC] += d * d;
+                }
+#pragma unroll
+                for (int i = 0; i < NC; ++i) prev[(size_t)i * nxy + node] = r[i];
+            }
+        }
+    }
+    __shared__ double red[8][NC + 2];
+#pragma unroll
+    for (int k = 0; k < NC + 2; ++k) {
+        Real v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) red[threadIdx.y][k] = (double)v;
+    }
+    __syncthreads();
+    const int tid = threadIdx.y * kTX + threadIdx.x;
+    if (tid < NC + 2) {
+        double v = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v += red[q][tid];
+        partial[(size_t)w * (NC + 2) + tid] = v;
+    }
+}
+
+template <int NC>
+__global__ void batch_reduce_final(const BatchLattice* __restrict__ lat, int n, const double* __restrict__ partial,
+                                   double* __restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n * (NC + 2)) return;
+    const int l = k / (NC + 2), q = k % (NC + 2);
+    double v = 0.0;
+    for (int w = lat[l].item0; w < lat[l].item0 + lat[l].nitems; ++w) v += partial[(size_t)w * (NC + 2) + q];
+    out[k] = v;
+}
+
+}  // namespace fmlbm

@@ -1,0 +1,13 @@
+// Host helpers shared between the single-lattice and the batch/serve parts of the C ABI.
+#pragma once
+
+#include <string>
+
+#include "fmlbm.h"
+#include "fmlbm_kernels.cuh"
+
+// Appendix C constants of a mixture (a_i, b_i, alpha_i(T), (a alpha)_ij, kappa_ij);
+// false with a reason when the mixture is invalid.
+bool fmlbm_internal_mixture_constants(const fmlbm_mixture& m, fmlbm::MixConst* mc, std::string* why);
+// Validity of a lattice description for n components.
+bool fmlbm_internal_lattice_ok(const fmlbm_lattice& L, int nc, std::string* why);

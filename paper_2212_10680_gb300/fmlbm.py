@@ -84,6 +84,25 @@ def _load() -> ctypes.CDLL:
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                        ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
         "fmlbm_destroy": ([H], None),
+        "fmlbm_batch_create": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(H)],
+                               ctypes.c_int),
+        "fmlbm_batch_add": ([H, ctypes.POINTER(fmlbm_mixture), ctypes.POINTER(fmlbm_lattice), dp,
+                             ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "fmlbm_batch_remove": ([H, ctypes.c_int32], ctypes.c_int),
+        "fmlbm_batch_set_active": ([H, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+        "fmlbm_batch_step": ([H, ctypes.c_int64], ctypes.c_int),
+        "fmlbm_batch_check": ([H], ctypes.c_int),
+        "fmlbm_batch_run": ([H, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(ctypes.c_int64), dp,
+                             ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "fmlbm_batch_slot_info": ([H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), dp,
+                                   ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "fmlbm_batch_moments": ([H, ctypes.c_int32, dp, dp, dp], ctypes.c_int),
+        "fmlbm_batch_get_distributions": ([H, ctypes.c_int32, dp, dp], ctypes.c_int),
+        "fmlbm_batch_autotune": ([H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                  dp], ctypes.c_int),
+        "fmlbm_batch_bytes": ([H, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+        "fmlbm_batch_last_error": ([H], ctypes.c_char_p),
+        "fmlbm_batch_destroy": ([H], None),
         "fmlbm_status_str": ([ctypes.c_int], ctypes.c_char_p),
         "fmlbm_last_error": ([H], ctypes.c_char_p),
         "fmlbm_version": ([], ctypes.c_char_p),
@@ -255,6 +274,85 @@ def fmlbm_destroy(h):
 
 def fmlbm_version() -> str:
     return LIB.fmlbm_version().decode()
+
+
+def _bcheck(status: int, where: str, b=None):
+    if status != 0:
+        msg = LIB.fmlbm_batch_last_error(b).decode() if b else ""
+        raise FmlbmError(status, where, msg)
+
+
+def fmlbm_batch_create(n_components: int, precision: str, capacity: int, stream: int = 0):
+    b = ctypes.c_void_p()
+    _bcheck(LIB.fmlbm_batch_create(n_components, PRECISION[precision], capacity, ctypes.c_void_p(stream or None),
+                                   ctypes.byref(b)), "fmlbm_batch_create")
+    return b
+
+
+def fmlbm_batch_add(b, mixture: fmlbm_mixture, lattice: fmlbm_lattice, rho: np.ndarray) -> int:
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    slot = ctypes.c_int32()
+    _bcheck(LIB.fmlbm_batch_add(b, ctypes.byref(mixture), ctypes.byref(lattice), _ptr(rho), ctypes.byref(slot)),
+            "fmlbm_batch_add", b)
+    return slot.value
+
+
+def fmlbm_batch_remove(b, slot: int):
+    _bcheck(LIB.fmlbm_batch_remove(b, slot), "fmlbm_batch_remove", b)
+
+
+def fmlbm_batch_set_active(b, slot: int, active: bool):
+    _bcheck(LIB.fmlbm_batch_set_active(b, slot, int(bool(active))), "fmlbm_batch_set_active", b)
+
+
+def fmlbm_batch_step(b, nsteps: int):
+    _bcheck(LIB.fmlbm_batch_step(b, ctypes.c_int64(nsteps)), "fmlbm_batch_step", b)
+
+
+def fmlbm_batch_check(b):
+    _bcheck(LIB.fmlbm_batch_check(b), "fmlbm_batch_check", b)
+
+
+def fmlbm_batch_run(b, capacity: int, max_steps: int, check_every: int, tol: float):
+    steps = np.zeros(capacity, dtype=np.int64)
+    res = np.zeros(capacity)
+    st = np.zeros(capacity, dtype=np.int32)
+    _bcheck(LIB.fmlbm_batch_run(b, ctypes.c_int64(max_steps), check_every, tol,
+                                steps.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _ptr(res),
+                                st.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "fmlbm_batch_run", b)
+    return steps, res, st
+
+
+def fmlbm_batch_slot_info(b, slot: int):
+    steps, res, st, act = ctypes.c_int64(), ctypes.c_double(), ctypes.c_int32(), ctypes.c_int32()
+    _bcheck(LIB.fmlbm_batch_slot_info(b, slot, ctypes.byref(steps), ctypes.byref(res), ctypes.byref(st),
+                                      ctypes.byref(act)), "fmlbm_batch_slot_info", b)
+    return steps.value, res.value, st.value, bool(act.value)
+
+
+def fmlbm_batch_moments(b, slot: int, rho=None, u=None, lnf=None):
+    _bcheck(LIB.fmlbm_batch_moments(b, slot, _ptr(rho), _ptr(u), _ptr(lnf)), "fmlbm_batch_moments", b)
+
+
+def fmlbm_batch_get_distributions(b, slot: int, g=None, force=None):
+    _bcheck(LIB.fmlbm_batch_get_distributions(b, slot, _ptr(g), _ptr(force)), "fmlbm_batch_get_distributions", b)
+
+
+def fmlbm_batch_autotune(b, steps_per_trial: int = 5):
+    ty, blocks, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    _bcheck(LIB.fmlbm_batch_autotune(b, steps_per_trial, ctypes.byref(ty), ctypes.byref(blocks), ctypes.byref(ms)),
+            "fmlbm_batch_autotune", b)
+    return ty.value, blocks.value, ms.value
+
+
+def fmlbm_batch_bytes(b) -> int:
+    n = ctypes.c_size_t()
+    _bcheck(LIB.fmlbm_batch_bytes(b, ctypes.byref(n)), "fmlbm_batch_bytes", b)
+    return n.value
+
+
+def fmlbm_batch_destroy(b):
+    LIB.fmlbm_batch_destroy(b)
 
 
 class Lattice:
