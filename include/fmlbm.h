@@ -270,6 +270,10 @@ fmlbm_status fmlbm_batch_check(fmlbm_batch* b);
  * steps taken, last residual, status. */
 fmlbm_status fmlbm_batch_run(fmlbm_batch* b, int64_t max_steps, int32_t check_every, double tol,
                              int64_t* steps_out, double* residual_out, int32_t* status_out);
+/* One graph-launched chunk of steps for every active slot followed by a check (the body
+ * of fmlbm_batch_run without the retirement decisions; synchronises). */
+fmlbm_status fmlbm_batch_run_chunk(fmlbm_batch* b, int32_t steps);
+/* Steps taken, last residual (+inf before a second check), status and activity of a slot. */
 fmlbm_status fmlbm_batch_slot_info(fmlbm_batch* b, int32_t slot, int64_t* steps, double* residual, int32_t* status,
                                    int32_t* active);
 /* As fmlbm_moments / fmlbm_get_distributions for one slot (host outputs; synchronises). */
@@ -286,6 +290,62 @@ fmlbm_status fmlbm_batch_bytes(fmlbm_batch* b, size_t* bytes);
 const char* fmlbm_batch_last_error(const fmlbm_batch* b);
 /* Synchronises and frees everything.  NULL-safe. */
 void fmlbm_batch_destroy(fmlbm_batch* b);
+
+/* ------------------------------------------------------------------------------------
+ * Serving: vapour-liquid solves submitted as requests and run with continuous batching.
+ * A worker thread owns a batch; between chunks of chunk_steps steps it admits queued
+ * requests in arrival order while a slot is free and their device bytes
+ * (fmlbm_lattice_bytes) fit hbm_budget_bytes, and retires each running lattice at its
+ * own criterion (residual < tol at a check, a latched error, or max_steps).  A request's
+ * result does not depend on what else is running.  All server functions are
+ * thread-safe and never block on the GPU.
+ * ------------------------------------------------------------------------------------ */
+typedef struct fmlbm_server fmlbm_server;
+
+typedef struct fmlbm_server_config {
+    int32_t n_components;      /* every request has this many components          */
+    int32_t precision;         /* and this storage precision                      */
+    int32_t max_slots;         /* lattices running at once                        */
+    int32_t chunk_steps;       /* steps between admission / retirement decisions   */
+    double tol;                /* residual at which a lattice retires             */
+    int64_t max_steps;         /* step limit per request (FMLBM_E_NOT_CONVERGED)  */
+    size_t hbm_budget_bytes;   /* device bytes the running lattices may hold      */
+    int32_t queue_capacity;    /* queued requests beyond which submit is BUSY     */
+    int32_t reserved;
+} fmlbm_server_config;
+
+typedef struct fmlbm_request {
+    fmlbm_mixture mixture;
+    fmlbm_lattice lattice;
+    const double* rho;         /* [N][ny][nx] initial mass densities, copied by submit      */
+    double* rho_out;           /* NULL, or [N][ny][nx] receiving the final densities; the
+                                  caller keeps it valid until the result has been polled   */
+    uint64_t tag;              /* opaque, returned in the result                          */
+} fmlbm_request;
+
+typedef struct fmlbm_result {
+    uint64_t id, tag;
+    int32_t status;            /* FMLBM_OK (converged), FMLBM_E_NOT_CONVERGED, FMLBM_E_NONPHYSICAL, ... */
+    int32_t reserved;
+    int64_t steps;
+    double residual;
+    double t_submit, t_admit, t_done;   /* seconds on the server's steady clock */
+} fmlbm_result;
+
+/* Creates the server on the current device (its own stream and worker thread). */
+fmlbm_status fmlbm_server_create(const fmlbm_server_config* cfg, fmlbm_server** out);
+/* Queues a request (copies rho).  FMLBM_E_BUSY when the queue is full (never blocks);
+ * FMLBM_E_INVALID_ARG when it does not match the server or could never fit the budget. */
+fmlbm_status fmlbm_server_submit(fmlbm_server* s, const fmlbm_request* req, uint64_t* id);
+/* Moves up to capacity finished results into out; *n = how many.  Returns the worker's
+ * error status if it stopped on a CUDA failure. */
+fmlbm_status fmlbm_server_poll(fmlbm_server* s, fmlbm_result* out, int32_t capacity, int32_t* n);
+/* Queue length, running lattices, admitted bytes, seconds spent in GPU chunks, and the
+ * server clock now (any pointer may be NULL). */
+fmlbm_status fmlbm_server_stats(fmlbm_server* s, int32_t* queued, int32_t* running, size_t* bytes_admitted,
+                                double* busy_seconds, double* now_seconds);
+/* Stops the worker (unfinished requests are dropped) and frees everything.  NULL-safe. */
+void fmlbm_server_destroy(fmlbm_server* s);
 
 const char* fmlbm_status_str(fmlbm_status s);
 const char* fmlbm_last_error(const fmlbm_handle* h);

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libfmlbm.so")
 
-SOURCES = ["api.cu", "step_f64.cu", "step_f32.cu", "step_f16.cu", "step_bf16.cu", "noalloc.cu", "batch.cu"]
+SOURCES = ["api.cu", "step_f64.cu", "step_f32.cu", "step_f16.cu", "step_bf16.cu", "noalloc.cu", "batch.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + INCLUDE, "-I" + CSRC]

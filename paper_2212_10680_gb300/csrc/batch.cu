@@ -520,6 +520,15 @@ fmlbm_status fmlbm_batch_run(fmlbm_batch* b, int64_t max_steps, int32_t check_ev
     return FMLBM_OK;
 }
 
+fmlbm_status fmlbm_batch_run_chunk(fmlbm_batch* b, int32_t steps) {
+    if (!b || steps < 1) return bfail(b, FMLBM_E_INVALID_ARG, "bad argument");
+    fmlbm_status st = ensure_work(b);
+    if (st != FMLBM_OK || b->nwork == 0) return st;
+    st = run_chunk(b, steps);
+    if (st != FMLBM_OK) return st;
+    return check_all(b);
+}
+
 fmlbm_status fmlbm_batch_slot_info(fmlbm_batch* b, int32_t slot, int64_t* steps, double* residual, int32_t* status,
                                    int32_t* active) {
     if (!b || slot < 0 || slot >= b->capacity || !b->slots[slot].used) return bfail(b, FMLBM_E_INVALID_ARG, "bad slot");

@@ -52,6 +52,24 @@ class fmlbm_lattice(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class fmlbm_server_config(ctypes.Structure):
+    _fields_ = [("n_components", ctypes.c_int32), ("precision", ctypes.c_int32), ("max_slots", ctypes.c_int32),
+                ("chunk_steps", ctypes.c_int32), ("tol", ctypes.c_double), ("max_steps", ctypes.c_int64),
+                ("hbm_budget_bytes", ctypes.c_size_t), ("queue_capacity", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class fmlbm_request(ctypes.Structure):
+    _fields_ = [("mixture", fmlbm_mixture), ("lattice", fmlbm_lattice), ("rho", ctypes.POINTER(ctypes.c_double)),
+                ("rho_out", ctypes.POINTER(ctypes.c_double)), ("tag", ctypes.c_uint64)]
+
+
+class fmlbm_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("tag", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("steps", ctypes.c_int64), ("residual", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
 def _load() -> ctypes.CDLL:
     if not os.path.exists(_LIB_PATH):
         raise ImportError(f"libfmlbm.so is not built ({_LIB_PATH}); run "
@@ -103,6 +121,14 @@ def _load() -> ctypes.CDLL:
         "fmlbm_batch_bytes": ([H, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
         "fmlbm_batch_last_error": ([H], ctypes.c_char_p),
         "fmlbm_batch_destroy": ([H], None),
+        "fmlbm_batch_run_chunk": ([H, ctypes.c_int32], ctypes.c_int),
+        "fmlbm_server_create": ([ctypes.POINTER(fmlbm_server_config), ctypes.POINTER(H)], ctypes.c_int),
+        "fmlbm_server_submit": ([H, ctypes.POINTER(fmlbm_request), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+        "fmlbm_server_poll": ([H, ctypes.POINTER(fmlbm_result), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)],
+                              ctypes.c_int),
+        "fmlbm_server_stats": ([H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                               ctypes.POINTER(ctypes.c_size_t), dp, dp], ctypes.c_int),
+        "fmlbm_server_destroy": ([H], None),
         "fmlbm_status_str": ([ctypes.c_int], ctypes.c_char_p),
         "fmlbm_last_error": ([H], ctypes.c_char_p),
         "fmlbm_version": ([], ctypes.c_char_p),
@@ -353,6 +379,49 @@ def fmlbm_batch_bytes(b) -> int:
 
 def fmlbm_batch_destroy(b):
     LIB.fmlbm_batch_destroy(b)
+
+
+def fmlbm_batch_run_chunk(b, steps: int):
+    _bcheck(LIB.fmlbm_batch_run_chunk(b, steps), "fmlbm_batch_run_chunk", b)
+
+
+def fmlbm_server_create(n_components: int, precision: str, max_slots: int, chunk_steps: int, tol: float,
+                        max_steps: int, hbm_budget_bytes: int, queue_capacity: int = 4096):
+    cfg = fmlbm_server_config(n_components, PRECISION[precision], max_slots, chunk_steps, tol, max_steps,
+                              hbm_budget_bytes, queue_capacity, 0)
+    s = ctypes.c_void_p()
+    _check(LIB.fmlbm_server_create(ctypes.byref(cfg), ctypes.byref(s)), "fmlbm_server_create")
+    return s
+
+
+def fmlbm_server_submit(s, mixture: fmlbm_mixture, lattice: fmlbm_lattice, rho: np.ndarray, rho_out=None,
+                        tag: int = 0) -> int:
+    """Queues a solve; returns its id.  rho is copied; rho_out (if given) must stay alive until
+    the result has been polled."""
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    req = fmlbm_request(mixture, lattice, _ptr(rho), _ptr(rho_out), tag)
+    rid = ctypes.c_uint64()
+    _check(LIB.fmlbm_server_submit(s, ctypes.byref(req), ctypes.byref(rid)), "fmlbm_server_submit")
+    return rid.value
+
+
+def fmlbm_server_poll(s, capacity: int = 1024):
+    out = (fmlbm_result * capacity)()
+    n = ctypes.c_int32()
+    _check(LIB.fmlbm_server_poll(s, out, capacity, ctypes.byref(n)), "fmlbm_server_poll")
+    return [dict(id=r.id, tag=r.tag, status=r.status, steps=r.steps, residual=r.residual, t_submit=r.t_submit,
+                 t_admit=r.t_admit, t_done=r.t_done) for r in out[:n.value]]
+
+
+def fmlbm_server_stats(s):
+    q, r, b, busy, now = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_size_t(), ctypes.c_double(), ctypes.c_double()
+    _check(LIB.fmlbm_server_stats(s, ctypes.byref(q), ctypes.byref(r), ctypes.byref(b), ctypes.byref(busy),
+                                  ctypes.byref(now)), "fmlbm_server_stats")
+    return dict(queued=q.value, running=r.value, bytes=b.value, busy=busy.value, now=now.value)
+
+
+def fmlbm_server_destroy(s):
+    LIB.fmlbm_server_destroy(s)
 
 
 class Lattice:
