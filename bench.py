@@ -320,6 +320,179 @@ def run_ours(args, w, rank, world, dist):
     print(json.dumps(line), flush=True)
 
 
+def _stats_pct(values, q):
+    return float(np.percentile(np.asarray(values), q)) if len(values) else None
+
+
+def run_batch(args, rank, world):
+    """Batched P-x sweep: 256 independent binary lattices (side ~ U{64..512}, feeds z1 swept
+    0.05..0.95 at fixed T), one persistent multi-lattice step per time step, graph-captured
+    chunks, per-lattice retirement; against the same lattices run one after another with
+    single-lattice handles and the same retirement rule."""
+    import torch
+    from paper_2212_10680_gb300 import fmlbm, inputs
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    wl = json.load(open(os.path.join(ROOT, "tests", "golden", "workloads.json")))
+    mixd = wl["binary"]["mixture"]
+    n = len(mixd["Tc"])
+    nlat = args.batch_lattices
+    rng = np.random.default_rng(4)
+    sides = rng.integers(64, 513, nlat)
+    fields = []
+    for k in range(nlat):
+        st = wl["binary_sweep"][int(round(k * 255 / max(nlat - 1, 1)))]
+        L = int(sides[k])
+        fields.append(inputs.with_noise(inputs.slab(st["rt_vapour"], st["rt_liquid"], L, L, 0.5, 4.0), 0.01, 4,
+                                        lattice=k))
+    mix = fmlbm.mixture_from_dict(mixd)
+    prec = args.precision or "fp32"
+    b = fmlbm.fmlbm_batch_create(n, prec, nlat)
+    for k in range(nlat):
+        L = int(sides[k])
+        fmlbm.fmlbm_batch_add(b, mix, fmlbm.make_lattice(L, L, 1.0, "isotropic", prec), fields[k])
+    ty, blocks, ms_tune = fmlbm.fmlbm_batch_autotune(b, 3)
+    # the autotuner's trial steps are real steps; count them in the work
+    tuned_steps = [fmlbm.fmlbm_batch_slot_info(b, k)[0] for k in range(nlat)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps, res, st = fmlbm.fmlbm_batch_run(b, nlat, args.max_steps, args.check_every, args.tol)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    fmlbm.fmlbm_batch_destroy(b)
+    units = sum(n * int(sides[k]) ** 2 * (int(steps[k]) - tuned_steps[k]) for k in range(nlat))
+
+    # the plain per-lattice loop: one handle at a time, same chunking and retirement rule
+    seq_units, seq_status = 0, []
+    t0 = time.perf_counter()
+    for k in range(nlat):
+        L = int(sides[k])
+        lat = fmlbm.Lattice(mix, L, L, 1.0, "isotropic", prec, "lagged")
+        lat.init(fields[k])
+        lat.diagnostics()
+        done, status = 0, 0
+        try:
+            while done < args.max_steps:
+                lat.step(args.check_every)
+                done += args.check_every
+                _, r, _ = lat.diagnostics()
+                if r < args.tol:
+                    break
+            else:
+                status = fmlbm.E_NOT_CONVERGED
+        except fmlbm.FmlbmError as e:
+            status = e.status
+        seq_units += n * L * L * done
+        seq_status.append(status)
+        lat.close()
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    counts = {fmlbm.STATUS[int(v)]: int((st == v).sum()) for v in np.unique(st)}
+    line = dict(
+        metric="batched VLE solves/sec", value=nlat / t_batch, unit="solves/s", n_gpus=world,
+        steps=int(np.max(steps)), warmup=3, ms_per_step=None, higher_is_better=True, scaling="weak",
+        vs_baseline=None, dtype="f64" if prec == "fp64" else "f32", data="synthetic",
+        config=dict(workload=f"batched P-x sweep: {nlat} binary PR lattices, side U{{64..512}}, z1 0.05..0.95, "
+                             f"flat slab, tau 1.0", precision=prec, max_steps=args.max_steps,
+                    check_every=args.check_every, tol=args.tol, autotune=dict(tile_y=ty, blocks=blocks)),
+        aggregate_glups=units / t_batch / 1e9, seconds=t_batch, statuses=counts,
+        sequential=dict(value=nlat / t_seq, unit="solves/s", seconds=t_seq, aggregate_glups=seq_units / t_seq / 1e9,
+                        kind="plain per-lattice loop, same chunks and retirement rule"),
+        speedup_vs_sequential=t_seq / t_batch,
+    )
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_serve(args, rank, world):
+    """Serving: Poisson arrivals of binary and ternary VLE requests (templates with random T
+    and feed, side ~ U{64..1024}); continuous batching servers, one per component count;
+    against a FIFO loop that runs one request at a time with a single-lattice handle."""
+    import threading as th
+    import torch
+    from paper_2212_10680_gb300 import fmlbm, inputs
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    wl = json.load(open(os.path.join(ROOT, "tests", "golden", "workloads.json")))
+    temps = [t for t in wl["serve_templates"] if "slab" in t]
+    rng = np.random.default_rng(5)
+    R = args.requests
+    gaps = rng.exponential(1.0 / args.rate, R)
+    arrive = np.cumsum(gaps) - gaps[0]
+    reqs = []
+    for k in range(R):
+        t = temps[int(rng.integers(0, len(temps)))]
+        side = int(rng.integers(64, args.max_side + 1))
+        rho = inputs.with_noise(inputs.slab(t["slab"]["rt_vapour"], t["slab"]["rt_liquid"], side, side, 0.5, 4.0),
+                                0.01, 5, lattice=k)
+        reqs.append(dict(k=k, n=len(t["mixture"]["Tc"]), mix=fmlbm.mixture_from_dict(t["mixture"]), side=side,
+                         rho=rho, t=float(arrive[k])))
+    prec = "fp32"
+    servers = {nc: fmlbm.fmlbm_server_create(nc, prec, args.slots, args.check_every, args.tol, args.max_steps,
+                                             int(args.budget_gb * (1 << 30))) for nc in (2, 3)}
+    results = []
+    t0 = time.perf_counter()
+    for r in reqs:
+        wait = r["t"] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        fmlbm.fmlbm_server_submit(servers[r["n"]], r["mix"], fmlbm.make_lattice(r["side"], r["side"], 1.0,
+                                                                                 "isotropic", prec), r["rho"], tag=r["k"])
+        for s in servers.values():
+            results += fmlbm.fmlbm_server_poll(s)
+    while len(results) < R:
+        for s in servers.values():
+            results += fmlbm.fmlbm_server_poll(s)
+        time.sleep(0.002)
+    wall = time.perf_counter() - t0
+    busy = {nc: fmlbm.fmlbm_server_stats(s)["busy"] for nc, s in servers.items()}
+    for s in servers.values():
+        fmlbm.fmlbm_server_destroy(s)
+    lat_s = [r["t_done"] - r["t_submit"] for r in results]
+    units = sum(reqs[r["tag"]]["n"] * reqs[r["tag"]]["side"] ** 2 * r["steps"] for r in results)
+
+    # FIFO baseline: the same arrivals, one request at a time through a single-lattice handle
+    seq_lat = []
+    t0 = time.perf_counter()
+    for r in reqs:
+        wait = r["t"] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        lat = fmlbm.Lattice(r["mix"], r["side"], r["side"], 1.0, "isotropic", prec, "lagged")
+        lat.init(r["rho"])
+        lat.diagnostics()
+        done = 0
+        try:
+            while done < args.max_steps:
+                lat.step(args.check_every)
+                done += args.check_every
+                if lat.diagnostics()[1] < args.tol:
+                    break
+        except fmlbm.FmlbmError:
+            pass
+        lat.close()
+        seq_lat.append(time.perf_counter() - t0 - r["t"])
+    seq_wall = time.perf_counter() - t0
+    counts = {}
+    for r in results:
+        counts[fmlbm.STATUS[r["status"]]] = counts.get(fmlbm.STATUS[r["status"]], 0) + 1
+    line = dict(
+        metric="served VLE solves/sec", value=R / wall, unit="solves/s", n_gpus=world, steps=args.max_steps,
+        warmup=0, ms_per_step=None, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+        data="synthetic", config=dict(
+            workload=f"Poisson arrivals ({args.rate}/s) of {R} binary/ternary PR VLE requests, side "
+                     f"U{{64..{args.max_side}}}, T U[0.80,0.92] Tc1 (binary) / U[0.85,0.92] Tc1 (ternary)",
+            slots=args.slots, chunk_steps=args.check_every, tol=args.tol, max_steps=args.max_steps,
+            hbm_budget_gb=args.budget_gb),
+        p50_s=_stats_pct(lat_s, 50), p99_s=_stats_pct(lat_s, 99), aggregate_glups=units / wall / 1e9,
+        gpu_busy_fraction={str(k): v / wall for k, v in busy.items()}, statuses=counts, seconds=wall,
+        fifo_baseline=dict(value=R / seq_wall, unit="solves/s", p50_s=_stats_pct(seq_lat, 50),
+                           p99_s=_stats_pct(seq_lat, 99), seconds=seq_wall),
+    )
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -332,12 +505,27 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--tile-y", type=int, default=0, help="override the fused step's tile height (8 or 16)")
     ap.add_argument("--variant", default=None, choices=["auto", "plain", "tma"], help="step kernel variant")
+    ap.add_argument("--batch-lattices", type=int, default=256)
+    ap.add_argument("--max-steps", type=int, default=4000)
+    ap.add_argument("--check-every", type=int, default=500)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--max-side", type=int, default=1024)
+    ap.add_argument("--slots", type=int, default=256)
+    ap.add_argument("--budget-gb", type=float, default=64.0)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         w = workload(args.workload)
         run_reference(args, w, rank, world)
+        return
+    if args.workload == "batch256":
+        run_batch(args, rank, world)
+        return
+    if args.workload == "serve":
+        run_serve(args, rank, world)
         return
     dist = None
     if world > 1:

@@ -62,6 +62,26 @@ def main():
         except ArithmeticError as e:  # recorded, not hidden
             sweep.append(dict(z=[z1, 1.0 - z1], error=str(e)))
     out["binary_sweep"] = sweep
+    # request templates for the serving workload: random temperature and feed per template
+    # (seeded), flash state at S_V = 0.5
+    rng = np.random.default_rng(5)
+    serve = []
+    for k in range(48):
+        if k % 2 == 0:
+            Tr = float(rng.uniform(0.80, 0.92))
+            z1 = float(rng.uniform(0.35, 0.65))
+            d = mixture_dict(Tr, [1.0, 1.3], [1.0, 0.9], [0.011, 0.2], [0.05, 0.075], 0.0)
+            z = [z1, 1.0 - z1]
+        else:
+            Tr = float(rng.uniform(0.85, 0.92))
+            w = rng.dirichlet([8.0, 6.0, 6.0])
+            d = mixture_dict(Tr, [1.0, 1.3, 1.6], [1.0, 0.85, 0.7], [0.011, 0.1, 0.25], [0.05, 0.10, 0.15], 0.02)
+            z = [float(v) for v in w]
+        try:
+            serve.append(dict(Tr=Tr, mixture=d, slab=state(d, z)))
+        except ArithmeticError as e:
+            serve.append(dict(Tr=Tr, mixture=d, z=z, error=str(e)))
+    out["serve_templates"] = serve
     with open(os.path.join(HERE, "workloads.json"), "w") as f:
         json.dump(out, f, indent=1)
         f.write("\n")
