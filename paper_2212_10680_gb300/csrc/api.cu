@@ -466,8 +466,8 @@ fmlbm_status fmlbm_step(fmlbm_handle* h, int64_t nsteps) {
 }
 
 fmlbm_status fmlbm_set_tile_height(fmlbm_handle* h, int32_t tile_y) {
-    if (!h || (tile_y != kTileYSmall && tile_y != kTileYLarge))
-        return fail(h, FMLBM_E_INVALID_ARG, "tile height must be 8 or 16");
+    if (!h || (tile_y != kTileYSmall && tile_y != kTileYLarge && tile_y != kTileYHuge))
+        return fail(h, FMLBM_E_INVALID_ARG, "tile height must be 8, 16 or 32");
     h->tile_y = tile_y;
     return FMLBM_OK;
 }

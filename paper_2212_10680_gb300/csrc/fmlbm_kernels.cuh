@@ -280,7 +280,7 @@ template <typename E, int NC, int TY>
 struct StepSmem {
     Tile<E, NC, TY, 2> rt;   // rho~ on tile + 2
     Tile<E, NC, TY, 1> lf;   // ln f on tile + 1
-    Tile<E, NC, TY, 1> G;    // sum_j kappa_ij lap rho~_j on tile + 1
+    Tile<E, NC, TY, 1> G;    // Phi_i = sum_j kappa_ij lap rho~_j - RT ln f_i on tile + 1
 };
 
 // Pull offsets: g_a(r, t) = g*_a(r - e_a, t - 1).
@@ -392,7 +392,8 @@ __device__ __forceinline__ void phase1_ring(const MixConstT<Real>& m, StepSmem<R
     }
 }
 
-// Phase 2: G_i = sum_j kappa_ij lap rho~_j on tile + 1 (step 6, mu_I,i = -G_i).
+// Phase 2: G_i = sum_j kappa_ij lap rho~_j on tile + 1 (step 6, mu_I,i = -G_i), stored as
+// the potential Phi_i = G_i - RT ln f_i whose gradient times rho~_i is the force of step 7.
 template <int NC, int TY, typename Real>
 __device__ __forceinline__ void phase2(const MixConstT<Real>& m, StepSmem<Real, NC, TY>& S, int stencil, int tid) {
     constexpr int NT = kTX * TY;
@@ -408,7 +409,7 @@ __device__ __forceinline__ void phase2(const MixConstT<Real>& m, StepSmem<Real, 
             Real Gi = Real(0);
 #pragma unroll
             for (int j = 0; j < NC; ++j) Gi += m.kap[i * kMaxC + j] * L[j];
-            S.G.v[i][cy][cx] = Gi;
+            S.G.v[i][cy][cx] = Gi - m.RT * S.lf.v[i][cy][cx];
         }
     }
 }
@@ -425,17 +426,16 @@ __device__ __forceinline__ void phase3(const StepArgs& A, const MixConstT<typena
     const int cx = tx + 1, cy = ty + 1;  // tile+1 coordinates of this node
     Real Fx[NC], Fy[NC], grx[NC], gry[NC], rhoi[NC];
     Real rho = Real(0), jx = Real(0), jy = Real(0), Ftx = Real(0), Fty = Real(0);
-    const Real RT = m.RT;
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
-        Real lx, ly, Gx, Gy, rx, ry;
-        grad_at<Real>(S.lf, i, cx, cy, A.stencil, lx, ly);
-        grad_at<Real>(S.G, i, cx, cy, A.stencil, Gx, Gy);
+        Real px, py, rx, ry;
+        grad_at<Real>(S.G, i, cx, cy, A.stencil, px, py);
         grad_at<Real>(S.rt, i, cx + 1, cy + 1, A.stencil, rx, ry);
         const Real rti = S.rt.v[i][cy + 1][cx + 1];
         // Eq. eqforcefinal: F_i = -rho~_i RT grad ln f_i + rho~_i grad(sum_j kappa_ij lap rho~_j)
-        Fx[i] = rti * (Gx - RT * lx);
-        Fy[i] = rti * (Gy - RT * ly);
+        //                      = rho~_i grad Phi_i (the stencils are linear)
+        Fx[i] = rti * px;
+        Fy[i] = rti * py;
         Ftx += Fx[i];
         Fty += Fy[i];
         // grad rho_i = M_i grad rho~_i

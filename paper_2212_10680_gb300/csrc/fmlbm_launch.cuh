@@ -10,6 +10,7 @@ namespace fmlbm {
 // lattice (fmlbm_set_tile_height / the batch autotuner).
 constexpr int kTileYSmall = 8;
 constexpr int kTileYLarge = 16;
+constexpr int kTileYHuge = 32;
 
 template <int ST>
 cudaError_t launch_step(const StepArgs& A, int nc, bool moments, int tile_y, cudaStream_t s);
@@ -52,6 +53,7 @@ cudaError_t launch_reduce(const StepArgs& A, int nc, void* rho_prev, int have_pr
         if (tile_y == kTileYLarge)                                                                        \
             return moments ? launch_step_nc_##ST<NC, true, kTileYLarge>(A, s)                             \
                            : launch_step_nc_##ST<NC, false, kTileYLarge>(A, s);                           \
+        if (tile_y == kTileYHuge && !moments) return launch_step_nc_##ST<NC, false, kTileYHuge>(A, s);    \
         return moments ? launch_step_nc_##ST<NC, true, kTileYSmall>(A, s)                                 \
                        : launch_step_nc_##ST<NC, false, kTileYSmall>(A, s);                               \
     }                                                                                                     \
