@@ -233,11 +233,16 @@ def run_ours(args, w, rank, world, dist):
                         stream=stream.cuda_stream)
     if args.tile_y:
         fmlbm.fmlbm_set_tile_height(lat.h, args.tile_y)
-    if args.variant:
-        fmlbm.fmlbm_set_step_variant(lat.h, args.variant)
-    variant = fmlbm.fmlbm_get_step_variant(lat.h)
     rho_dev = torch.from_numpy(w["rho"]).to(dev)
     fmlbm.fmlbm_init_device(lat.h, rho_dev.data_ptr())
+    tuned = None
+    if args.variant:
+        fmlbm.fmlbm_set_step_variant(lat.h, args.variant)
+    else:
+        # the autotuner's trial steps are real (untimed) steps, part of the warm-up
+        v, ty, ms = fmlbm.fmlbm_autotune(lat.h, 5)
+        tuned = dict(variant=v, tile_y=ty, ms_per_step=ms)
+    variant = fmlbm.fmlbm_get_step_variant(lat.h)
     lat.step(args.warmup)
     lat.synchronize()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -269,7 +274,7 @@ def run_ours(args, w, rank, world, dist):
     algo = ALGO_BYTES[prec] * n * nodes
     peak = measured_peaks()
     achieved = algo / per_launch_s / 1e9
-    kernel_name = "fused_step_tma" if variant == "tma" else "fused_step"
+    kernel_name = "fused_step_tma" if variant.startswith("tma") else "fused_step"
     traffic = profile_traffic(kernel_name, args.workload, prec)
 
     # end to end through the public API with host buffers: H2D of the initial field from
@@ -304,7 +309,7 @@ def run_ours(args, w, rank, world, dist):
         vs_baseline=None, dtype="f64" if prec == "fp64" else "f32",
         data="synthetic (seeded droplet/slab initial fields from oracle flash densities)",
         config=dict(workload=w["name"], nx=nx, ny=ny, n_components=n, tau=w["tau"], stencil=w["stencil"],
-                    precision=prec, velocity_force="lagged", step_kernel=variant,
+                    precision=prec, velocity_force="lagged", step_kernel=variant, autotune=tuned,
                     l2="flushed between timed steps (256 MB write)",
                     timing="CUDA events around each fused launch on the launching stream"),
         roofline=dict(bound="hbm", achieved=achieved, peak=peak["hbm_gbs"], unit="GB/s",
@@ -504,7 +509,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--tile-y", type=int, default=0, help="override the fused step's tile height (8 or 16)")
-    ap.add_argument("--variant", default=None, choices=["auto", "plain", "tma"], help="step kernel variant")
+    ap.add_argument("--variant", default=None, choices=["auto", "plain", "tma", "tma_tile"], help="step kernel variant")
     ap.add_argument("--batch-lattices", type=int, default=256)
     ap.add_argument("--max-steps", type=int, default=4000)
     ap.add_argument("--check-every", type=int, default=500)

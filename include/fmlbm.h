@@ -180,14 +180,24 @@ fmlbm_status fmlbm_set_tile_height(fmlbm_handle* h, int32_t tile_y);
  * double-buffered so the next tile's copy overlaps the current tile's arithmetic; tiles
  * on the periodic edges take the plain path.  Both give bit-identical results.  TMA is
  * available for FP32 and 16-bit storage with nx a multiple of 4 (FP32) or 8 (16-bit) and a
- * lattice of at least 38 x 22.  AUTO (default): TMA where available and the lattice has
- * at least 48 tiles of 32 x 16 per multiprocessor (where its pipelining pays), else
- * PLAIN.  Asking for TMA where it is not available returns FMLBM_E_UNSUPPORTED. */
+ * lattice of at least 38 x 22.  TMA_TILE: the same copies with one tile per block, a single
+ * stage and two blocks per multiprocessor (the pulled values wait in shared memory).  AUTO
+ * (default): where the TMA forms are available and the lattice has at least 48 tiles of
+ * 32 x 16 per multiprocessor, TMA for FP32 and TMA_TILE for the 16-bit forms, else PLAIN;
+ * fmlbm_autotune measures instead.  Asking for a TMA form where it is not available
+ * returns FMLBM_E_UNSUPPORTED. */
 typedef enum fmlbm_step_variant {
-    FMLBM_VARIANT_AUTO = 0, FMLBM_VARIANT_PLAIN = 1, FMLBM_VARIANT_TMA = 2
+    FMLBM_VARIANT_AUTO = 0, FMLBM_VARIANT_PLAIN = 1, FMLBM_VARIANT_TMA = 2,
+    FMLBM_VARIANT_TMA_TILE = 3  /* one tile per block, single stage, two blocks per SM */
 } fmlbm_step_variant;
 fmlbm_status fmlbm_set_step_variant(fmlbm_handle* h, int32_t variant);
-/* The kernel fmlbm_step will use (PLAIN or TMA). */
+/* Autotuner: times steps_per_trial steps of every available kernel variant and tile
+ * height on the handle's own lattice and keeps the fastest.  The trial steps are real
+ * steps of the lattice (all variants give bit-identical results); synchronises.
+ * Outputs (may be NULL): chosen variant, tile height, ms per step. */
+fmlbm_status fmlbm_autotune(fmlbm_handle* h, int32_t steps_per_trial, int32_t* variant, int32_t* tile_y,
+                            double* ms_per_step);
+/* The kernel fmlbm_step will use (PLAIN, TMA or TMA_TILE). */
 fmlbm_status fmlbm_get_step_variant(fmlbm_handle* h, int32_t* variant);
 
 /* Waits for the handle's stream and reports latched kernel errors. */

@@ -233,30 +233,34 @@ void setup_tma(fmlbm_handle* h) {
     h->tma_maps = ok;
 }
 
-cudaError_t dispatch_step_tma(const fmlbm_handle* h, const StepArgs& A) {
+cudaError_t dispatch_step_tma(const fmlbm_handle* h, const StepArgs& A, bool single) {
     const CUtensorMap* maps = h->tmap[h->cur];
     switch (h->lattice.precision) {
-        case FMLBM_FP32: return launch_step_tma<ST_F32>(A, h->nc, maps, 1, h->stream);
-        case FMLBM_FP16DEV: return launch_step_tma<ST_F16DEV>(A, h->nc, maps, 1, h->stream);
-        case FMLBM_BF16DEV: return launch_step_tma<ST_BF16DEV>(A, h->nc, maps, 1, h->stream);
+        case FMLBM_FP32: return launch_step_tma<ST_F32>(A, h->nc, maps, 1, single, h->stream);
+        case FMLBM_FP16DEV: return launch_step_tma<ST_F16DEV>(A, h->nc, maps, 1, single, h->stream);
+        case FMLBM_BF16DEV: return launch_step_tma<ST_BF16DEV>(A, h->nc, maps, 1, single, h->stream);
         default: return cudaErrorNotSupported;
     }
 }
 
-// AUTO takes the persistent TMA step only when each SM gets many tiles to pipeline
-// (measured on GB300: slower than the plain step at 1024^2, 13 tiles per SM; faster at
-// 4096^2, 215 tiles per SM).
+// The kernel AUTO resolves to (measured on GB300): the plain step unless each SM gets many
+// tiles (slower TMA at 1024^2, 13 tiles per SM; faster at 4096^2, 215 tiles per SM); there
+// the persistent double-buffered TMA step for float storage and the one-tile-per-block TMA
+// step (two blocks per SM) for the 16-bit forms.
 constexpr int kTmaMinTilesPerSM = 48;
 
-bool use_tma(const fmlbm_handle* h) {
-    if (!h->tma_maps || h->variant == FMLBM_VARIANT_PLAIN) return false;
-    if (h->variant == FMLBM_VARIANT_TMA) return true;
+int resolved_variant(const fmlbm_handle* h) {
+    if (!h->tma_maps || h->variant == FMLBM_VARIANT_PLAIN) return FMLBM_VARIANT_PLAIN;
+    if (h->variant != FMLBM_VARIANT_AUTO) return h->variant;
     const long tiles = (long)((h->lattice.nx + kTX - 1) / kTX) * ((h->lattice.ny + kTmaTileY - 1) / kTmaTileY);
-    return tiles >= (long)kTmaMinTilesPerSM * h->sms;
+    if (tiles < (long)kTmaMinTilesPerSM * h->sms) return FMLBM_VARIANT_PLAIN;
+    return h->lattice.precision == FMLBM_FP32 ? FMLBM_VARIANT_TMA : FMLBM_VARIANT_TMA_TILE;
 }
 
+bool use_tma(const fmlbm_handle* h) { return resolved_variant(h) != FMLBM_VARIANT_PLAIN; }
+
 cudaError_t dispatch_step(const fmlbm_handle* h, const StepArgs& A, bool moments) {
-    if (!moments && use_tma(h)) return dispatch_step_tma(h, A);
+    if (!moments && use_tma(h)) return dispatch_step_tma(h, A, resolved_variant(h) == FMLBM_VARIANT_TMA_TILE);
     switch (h->lattice.precision) {
         case FMLBM_FP64: return launch_step<ST_F64>(A, h->nc, moments, h->tile_y, h->stream);
         case FMLBM_FP32: return launch_step<ST_F32>(A, h->nc, moments, h->tile_y, h->stream);
@@ -465,6 +469,8 @@ fmlbm_status fmlbm_step(fmlbm_handle* h, int64_t nsteps) {
     return FMLBM_OK;
 }
 
+fmlbm_status fmlbm_step(fmlbm_handle* h, int64_t nsteps);
+
 fmlbm_status fmlbm_set_tile_height(fmlbm_handle* h, int32_t tile_y) {
     if (!h || (tile_y != kTileYSmall && tile_y != kTileYLarge && tile_y != kTileYHuge))
         return fail(h, FMLBM_E_INVALID_ARG, "tile height must be 8, 16 or 32");
@@ -473,17 +479,62 @@ fmlbm_status fmlbm_set_tile_height(fmlbm_handle* h, int32_t tile_y) {
 }
 
 fmlbm_status fmlbm_set_step_variant(fmlbm_handle* h, int32_t variant) {
-    if (!h || variant < FMLBM_VARIANT_AUTO || variant > FMLBM_VARIANT_TMA)
+    if (!h || variant < FMLBM_VARIANT_AUTO || variant > FMLBM_VARIANT_TMA_TILE)
         return fail(h, FMLBM_E_INVALID_ARG, "unknown step variant");
-    if (variant == FMLBM_VARIANT_TMA && !h->tma_maps)
+    if ((variant == FMLBM_VARIANT_TMA || variant == FMLBM_VARIANT_TMA_TILE) && !h->tma_maps)
         return fail(h, FMLBM_E_UNSUPPORTED, "no TMA step for this precision, component count or lattice shape");
     h->variant = variant;
     return FMLBM_OK;
 }
 
+fmlbm_status fmlbm_autotune(fmlbm_handle* h, int32_t steps_per_trial, int32_t* variant, int32_t* tile_y,
+                            double* ms_per_step) {
+    if (!h || steps_per_trial < 1) return fail(h, FMLBM_E_INVALID_ARG, "bad argument");
+    struct Cand { int variant, tile_y; };
+    Cand cands[5];
+    int nc = 0;
+    for (int ty : {kTileYSmall, kTileYLarge, kTileYHuge})
+        if (ty <= 16 || h->lattice.ny >= 64) cands[nc++] = Cand{FMLBM_VARIANT_PLAIN, ty};
+    if (h->tma_maps) {
+        cands[nc++] = Cand{FMLBM_VARIANT_TMA, h->tile_y};
+        cands[nc++] = Cand{FMLBM_VARIANT_TMA_TILE, h->tile_y};
+    }
+    cudaEvent_t e0, e1;
+    FM_CUDA(h, cudaEventCreate(&e0));
+    FM_CUDA(h, cudaEventCreate(&e1));
+    float best = 1e30f;
+    Cand pick = cands[0];
+    for (int k = 0; k < nc; ++k) {
+        h->variant = cands[k].variant;
+        h->tile_y = cands[k].tile_y;
+        // every trial step is a real step: the variants give bit-identical results
+        fmlbm_status st = fmlbm_step(h, 1);
+        if (st != FMLBM_OK) return st;
+        FM_CUDA(h, cudaEventRecord(e0, h->stream));
+        st = fmlbm_step(h, steps_per_trial);
+        if (st != FMLBM_OK) return st;
+        FM_CUDA(h, cudaEventRecord(e1, h->stream));
+        FM_CUDA(h, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        FM_CUDA(h, cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+            best = ms;
+            pick = cands[k];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->variant = pick.variant;
+    h->tile_y = pick.tile_y;
+    if (variant) *variant = pick.variant;
+    if (tile_y) *tile_y = pick.tile_y;
+    if (ms_per_step) *ms_per_step = best / steps_per_trial;
+    return sync_and_check(h);
+}
+
 fmlbm_status fmlbm_get_step_variant(fmlbm_handle* h, int32_t* variant) {
     if (!h || !variant) return FMLBM_E_INVALID_ARG;
-    *variant = use_tma(h) ? FMLBM_VARIANT_TMA : FMLBM_VARIANT_PLAIN;
+    *variant = resolved_variant(h);
     return FMLBM_OK;
 }
 

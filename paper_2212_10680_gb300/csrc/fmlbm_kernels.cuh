@@ -326,7 +326,9 @@ __device__ __forceinline__ void domain_check(const StepArgs& A, const Real* rt, 
             bad = true;
         }
     }
-    if (bad && atomicCAS(&A.err->flag, 0, 1) == 0) {
+    // a plain read first: once a lattice has failed, every bad node would otherwise
+    // contend for the same word with an atomic in every step
+    if (bad && *reinterpret_cast<volatile int*>(&A.err->flag) == 0 && atomicCAS(&A.err->flag, 0, 1) == 0) {
         A.err->comp = badc;
         A.err->x = x;
         A.err->y = y;

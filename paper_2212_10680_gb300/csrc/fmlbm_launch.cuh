@@ -16,8 +16,11 @@ template <int ST>
 cudaError_t launch_step(const StepArgs& A, int nc, bool moments, int tile_y, cudaStream_t s);
 // Persistent TMA-fed step (float and 16-bit storage); maps[0]: float planes, maps[1]:
 // 16-bit planes (deviation forms).  tma_ok = 0 sends every tile down the plain pull path.
+// single_stage = false: persistent double-buffered blocks (one per SM);
+// true: one tile per block, single stage, two blocks per SM.
 template <int ST>
-cudaError_t launch_step_tma(const StepArgs& A, int nc, const CUtensorMap* maps, int tma_ok, cudaStream_t s);
+cudaError_t launch_step_tma(const StepArgs& A, int nc, const CUtensorMap* maps, int tma_ok, bool single_stage,
+                            cudaStream_t s);
 // Whether the TMA variant exists for this storage and component count (shared memory).
 template <int ST>
 bool tma_supported(int nc);
@@ -119,41 +122,49 @@ cudaError_t launch_reduce(const StepArgs& A, int nc, void* rho_prev, int have_pr
     }
 
 #define FMLBM_DEFINE_TMA_LAUNCHER(ST)                                                                     \
-    template <int NC>                                                                                     \
+    template <int NC, bool SINGLE>                                                                        \
     static cudaError_t launch_tma_nc_##ST(const StepArgs& A, const CUtensorMap* maps, int tma_ok,         \
                                           cudaStream_t s) {                                               \
         using L = TmaLayout<NC, ST, kTmaTileY>;                                                           \
         if constexpr (!L::fits) {                                                                         \
             return cudaErrorNotSupported;                                                                 \
         } else {                                                                                          \
-            auto k = fused_step_tma<NC, ST, kTmaTileY, L::stages>;                                        \
+            constexpr int NS = SINGLE ? 1 : L::stages;                                                    \
+            constexpr int MINB = SINGLE ? 2 : 1;                                                          \
+            constexpr size_t smem = L::scratch_bytes + NS * L::stage_bytes + 64;                          \
+            auto k = fused_step_tma<NC, ST, kTmaTileY, NS, MINB>;                                         \
             static int per_sm = 0, sms = 0;                                                               \
             if (per_sm == 0) {                                                                            \
                 cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
-                                                     (int)L::smem_bytes);                                 \
+                                                     (int)smem);                                          \
                 if (e != cudaSuccess) return e;                                                           \
                 int dev = 0;                                                                              \
                 cudaGetDevice(&dev);                                                                      \
                 cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);                        \
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTX * kTmaTileY,            \
-                                                                  L::smem_bytes);                         \
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTX * kTmaTileY, smem);     \
                 if (e != cudaSuccess) return e;                                                           \
                 if (per_sm < 1) return cudaErrorInvalidConfiguration;                                     \
             }                                                                                             \
             const int ntiles = ((A.nx + kTX - 1) / kTX) * ((A.ny + kTmaTileY - 1) / kTmaTileY);           \
-            const int grid = ntiles < sms * per_sm ? ntiles : sms * per_sm;                               \
-            k<<<grid, dim3(kTX, kTmaTileY), L::smem_bytes, s>>>(A, maps[0], maps[1], tma_ok);             \
+            const int grid = SINGLE ? ntiles : (ntiles < sms * per_sm ? ntiles : sms * per_sm);           \
+            k<<<grid, dim3(kTX, kTmaTileY), smem, s>>>(A, maps[0], maps[1], tma_ok);                      \
             return cudaGetLastError();                                                                    \
         }                                                                                                 \
     }                                                                                                     \
+    template <int NC>                                                                                     \
+    static cudaError_t launch_tma_mode_##ST(const StepArgs& A, const CUtensorMap* maps, int tma_ok,       \
+                                            bool single, cudaStream_t s) {                                \
+        return single ? launch_tma_nc_##ST<NC, true>(A, maps, tma_ok, s)                                  \
+                      : launch_tma_nc_##ST<NC, false>(A, maps, tma_ok, s);                                \
+    }                                                                                                     \
     template <>                                                                                           \
     cudaError_t launch_step_tma<ST>(const StepArgs& A, int nc, const CUtensorMap* maps, int tma_ok,       \
-                                    cudaStream_t s) {                                                     \
+                                    bool single, cudaStream_t s) {                                        \
         switch (nc) {                                                                                     \
-            case 1: return launch_tma_nc_##ST<1>(A, maps, tma_ok, s);                                     \
-            case 2: return launch_tma_nc_##ST<2>(A, maps, tma_ok, s);                                     \
-            case 3: return launch_tma_nc_##ST<3>(A, maps, tma_ok, s);                                     \
-            case 4: return launch_tma_nc_##ST<4>(A, maps, tma_ok, s);                                     \
+            case 1: return launch_tma_mode_##ST<1>(A, maps, tma_ok, single, s);                           \
+            case 2: return launch_tma_mode_##ST<2>(A, maps, tma_ok, single, s);                           \
+            case 3: return launch_tma_mode_##ST<3>(A, maps, tma_ok, single, s);                           \
+            case 4: return launch_tma_mode_##ST<4>(A, maps, tma_ok, single, s);                           \
         }                                                                                                 \
         return cudaErrorInvalidValue;                                                                     \
     }                                                                                                     \

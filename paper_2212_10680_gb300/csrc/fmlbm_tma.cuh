@@ -103,12 +103,19 @@ __device__ __forceinline__ typename StoreTraits<ST>::Real stage_value(const unsi
     }
 }
 
-template <int NC, int ST, int TY, int NSTAGE>
-__global__ void __launch_bounds__(kTX* TY, 1)
+// NSTAGE = 2: persistent blocks, the next tile's copy overlaps this tile's arithmetic; each
+// thread keeps its node's pulled values in registers between the phases.
+// NSTAGE = 1: one tile per block (grid = tile count), MINB blocks resident per SM; the
+// pulled values stay in shared memory between the phases (the stage for copied tiles, the
+// same bytes as a compact [9N][TY][32] array for edge tiles), which keeps the register
+// count within MINB blocks per SM.
+template <int NC, int ST, int TY, int NSTAGE, int MINB>
+__global__ void __launch_bounds__(kTX* TY, MINB)
     fused_step_tma(const __grid_constant__ StepArgs A, const __grid_constant__ CUtensorMap map_f32,
                    const __grid_constant__ CUtensorMap map_b16, int tma_ok) {
     using Real = typename StoreTraits<ST>::Real;
     using L = TmaLayout<NC, ST, TY>;
+    static_assert((size_t)9 * NC * TY * kTX * sizeof(Real) <= L::stage_bytes, "edge tiles park g in the stage");
     extern __shared__ __align__(128) unsigned char smem_tma[];
     auto& S = *reinterpret_cast<StepSmem<Real, NC, TY>*>(smem_tma);
     unsigned char* stages = smem_tma + L::scratch_bytes;
@@ -169,6 +176,9 @@ __global__ void __launch_bounds__(kTX* TY, 1)
         int x0, y0;
         origin(t, x0, y0);
         const int gxn = x0 + tx, gyn = y0 + ty;
+        unsigned char* st = stages + s * L::stage_bytes;
+        Real* gpark = reinterpret_cast<Real*>(st);  // edge tiles: [9N][TY][32]
+        constexpr bool PARK = NSTAGE == 1;
         Real g[NC][9];
         if (tma_here) {
             const bool ok = mbar_wait_bounded(&bar[s], (parity >> s) & 1u);
@@ -187,7 +197,6 @@ __global__ void __launch_bounds__(kTX* TY, 1)
             }
             parity ^= 1u << s;
             pending &= ~(1u << s);
-            const unsigned char* st = stages + s * L::stage_bytes;
 #pragma unroll
             for (int a = 0; a < 9; ++a)
 #pragma unroll
@@ -209,11 +218,27 @@ __global__ void __launch_bounds__(kTX* TY, 1)
             }
         } else {
             phase1_global<NC, ST, TY>(A, m, S, g, x0, y0, is_inner(x0, y0), tx, ty, tid);
+            if constexpr (PARK) {
+#pragma unroll
+                for (int i = 0; i < NC; ++i)
+#pragma unroll
+                    for (int a = 0; a < 9; ++a) gpark[((i * 9 + a) * TY + ty) * kTX + tx] = g[i][a];
+            }
         }
         __syncthreads();
         phase2<NC, TY, Real>(m, S, A.stencil, tid);
         __syncthreads();
-        if (gxn < nx && gyn < ny) phase3<NC, ST, TY, false>(A, m, S, g, tx, ty, gxn, gyn);
+        if (gxn < nx && gyn < ny) {
+            if constexpr (PARK) {
+#pragma unroll
+                for (int a = 0; a < 9; ++a)
+#pragma unroll
+                    for (int i = 0; i < NC; ++i)
+                        g[i][a] = tma_here ? stage_value<NC, ST, TY>(st, i, a, ty + 3 - ey(a), tx + 4 - ex(a))
+                                           : gpark[((i * 9 + a) * TY + ty) * kTX + tx];
+            }
+            phase3<NC, ST, TY, false>(A, m, S, g, tx, ty, gxn, gyn);
+        }
         __syncthreads();  // shared tiles and the stage are free again
     }
 }

@@ -5,7 +5,7 @@ namespace fmlbm {
 FMLBM_DEFINE_LAUNCHERS(ST_F64)
 // the FP64 path (the parity reference) has no TMA variant
 template <>
-cudaError_t launch_step_tma<ST_F64>(const StepArgs&, int, const CUtensorMap*, int, cudaStream_t) {
+cudaError_t launch_step_tma<ST_F64>(const StepArgs&, int, const CUtensorMap*, int, bool, cudaStream_t) {
     return cudaErrorNotSupported;
 }
 template <>

@@ -284,7 +284,7 @@ def test_tma_step_is_bit_identical_to_plain(fm, precision, n):
     rho = inputs.with_noise(inputs.slab(wl["slab"]["rt_vapour"], wl["slab"]["rt_liquid"], 200, 100, 0.5, 4.0),
                             0.01, 5)
     out = []
-    for variant in ("plain", "tma"):
+    for variant in ("plain", "tma", "tma_tile"):
         lat = fm.Lattice(fm.mixture_from_dict(wl["mixture"]), 200, 100, 1.0, "isotropic", precision, "lagged")
         fm.fmlbm_set_step_variant(lat.h, variant)
         assert fm.fmlbm_get_step_variant(lat.h) == variant
@@ -292,7 +292,8 @@ def test_tma_step_is_bit_identical_to_plain(fm, precision, n):
         lat.step(30)
         out.append(lat.distributions())
         lat.close()
-    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    for k in (1, 2):
+        assert np.array_equal(out[0][0], out[k][0]) and np.array_equal(out[0][1], out[k][1])
 
 
 def test_tma_path_oracle_parity(fm):
@@ -325,3 +326,22 @@ def test_tma_unavailable_is_reported(fm):
     lat = fm.Lattice(fm.mixture_from_dict(mixd), 64, 64, 1.0, "isotropic", "fp64", "lagged")
     assert fm.fmlbm_get_step_variant(lat.h) == "plain"   # the FP64 reference path has no TMA variant
     lat.close()
+
+
+def test_autotune_keeps_results(fm):
+    mixd, rho = slab_state_binary(256, 96, seed=14)
+    a = fm.Lattice(fm.mixture_from_dict(mixd), 256, 96, 1.0, "isotropic", "fp32", "lagged")
+    a.init(rho)
+    variant, ty, ms = fm.fmlbm_autotune(a.h, 2)
+    assert variant in ("plain", "tma", "tma_tile") and ty in (8, 16, 32) and ms > 0
+    done = fm.fmlbm_diagnostics(a.h, 2)[2]
+    a.step(7)
+    g1, F1 = a.distributions()
+    a.close()
+    b = fm.Lattice(fm.mixture_from_dict(mixd), 256, 96, 1.0, "isotropic", "fp32", "lagged")
+    fm.fmlbm_set_step_variant(b.h, "plain")
+    b.init(rho)
+    b.step(done + 7)
+    g2, F2 = b.distributions()
+    b.close()
+    assert np.array_equal(g1, g2) and np.array_equal(F1, F2)
