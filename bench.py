@@ -68,21 +68,23 @@ def profile_traffic(kernel: str, workload_key: str, precision: str):
     return float(m_bytes.group(1))
 
 
-def workload(name: str):
+def workload(name: str, size: int = 0):
+    """A bench workload; size > 0 scales its lattice to size x size (profiling captures)."""
     wl = json.load(open(os.path.join(ROOT, "tests", "golden", "workloads.json")))
     from paper_2212_10680_gb300 import inputs
     if name == "droplet1024":
         b = wl["binary"]
-        n = 1024
-        rho = inputs.with_noise(inputs.droplet(b["slab"]["rt_vapour"], b["slab"]["rt_liquid"], n, n, 200.0, 4.0),
+        n = size or 1024
+        radius = 200.0 * n / 1024
+        rho = inputs.with_noise(inputs.droplet(b["slab"]["rt_vapour"], b["slab"]["rt_liquid"], n, n, radius, 4.0),
                                 0.01, 2)
-        return dict(name="binary PR droplet R=200, 1024x1024 periodic D2Q9", mixture=b["mixture"], rho=rho,
+        return dict(name=f"binary PR droplet R={radius:g}, {n}x{n} periodic D2Q9", mixture=b["mixture"], rho=rho,
                     nx=n, ny=n, tau=1.0, stencil="isotropic", precision="fp32")
     if name == "ternary4096":
         t = wl["ternary"]
-        n = 4096
+        n = size or 4096
         rho = inputs.with_noise(inputs.slab(t["slab"]["rt_vapour"], t["slab"]["rt_liquid"], n, n, 0.5, 4.0), 0.01, 3)
-        return dict(name="ternary PR flat slab, 4096x4096 periodic D2Q9", mixture=t["mixture"], rho=rho,
+        return dict(name=f"ternary PR flat slab, {n}x{n} periodic D2Q9", mixture=t["mixture"], rho=rho,
                     nx=n, ny=n, tau=1.0, stencil="isotropic", precision="fp32")
     raise SystemExit(f"unknown workload {name}")
 
@@ -275,7 +277,8 @@ def run_ours(args, w, rank, world, dist):
     peak = measured_peaks()
     achieved = algo / per_launch_s / 1e9
     kernel_name = "fused_step_tma" if variant.startswith("tma") else "fused_step"
-    traffic = profile_traffic(kernel_name, args.workload, prec)
+    # the committed counters describe the workload at its own size only
+    traffic = None if args.size else profile_traffic(kernel_name, args.workload, prec)
 
     # end to end through the public API with host buffers: H2D of the initial field from
     # pinned memory, then per step one fused update and a D2H read of the step's
@@ -505,6 +508,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="droplet1024")
+    ap.add_argument("--size", type=int, default=0, help="scale the workload's lattice to size x size (profiling)")
     ap.add_argument("--precision", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -523,7 +527,7 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
-        w = workload(args.workload)
+        w = workload(args.workload, args.size)
         run_reference(args, w, rank, world)
         return
     if args.workload == "batch256":
@@ -539,7 +543,7 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         td.init_process_group("nccl")
         dist = td
-    w = workload(args.workload)
+    w = workload(args.workload, args.size)
     run_ours(args, w, rank, world, dist)
     if dist is not None:
         dist.destroy_process_group()

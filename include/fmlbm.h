@@ -220,8 +220,9 @@ fmlbm_status fmlbm_lattice_bytes(int32_t n_components, const fmlbm_lattice* latt
  *                   float; for FP16DEV/BF16DEV the 16-bit planes a = 1..8), read only;
  *   g0_device       FP16DEV/BF16DEV only: the float planes a = 0 ([N][ny][nx]); else NULL;
  *   rho_prev_device [N][ny][nx] values in the arithmetic type of the storage (double for
- *                   FP64, float otherwise): read when have_prev != 0, then overwritten
- *                   with this state's densities;
+ *                   FP64, float otherwise): read on every call (the values are ignored
+ *                   when have_prev == 0, so it may hold anything then), then
+ *                   overwritten with this state's densities;
  *   out_device      N + 2 doubles written: sum rho_i for each i, sum (rho - rho_prev)^2
  *                   (0 when have_prev == 0), sum rho^2; residual = sqrt(out[N] / out[N+1]).
  * Work is enqueued on cuda_stream (NULL: legacy default stream); the call returns

@@ -281,7 +281,34 @@ struct StepSmem {
     Tile<E, NC, TY, 2> rt;   // rho~ on tile + 2
     Tile<E, NC, TY, 1> lf;   // ln f on tile + 1
     Tile<E, NC, TY, 1> G;    // Phi_i = sum_j kappa_ij lap rho~_j - RT ln f_i on tile + 1
+    E Fl[2][TY][kTX];        // stored total force at the tile's nodes (lagged reading)
 };
+
+// The stored force F(t - 1) that the lagged reading puts into u (step 1) is needed only in
+// phase 3; its copy into shared memory starts before phase 1 (cp.async, no registers held)
+// so that its latency hides behind phases 1 and 2 instead of stalling every warp in phase 3.
+// Each thread copies and later reads only its own node's two entries.
+template <typename E>
+__device__ __forceinline__ void cp_async_elem(E* dst_smem, const E* src) {
+    static_assert(sizeof(E) == 4 || sizeof(E) == 8, "cp.async of 4 or 8 bytes");
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    if constexpr (sizeof(E) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+template <typename Real, int NC, int TY>
+__device__ __forceinline__ void prefetch_force(const StepArgs& A, StepSmem<Real, NC, TY>& S, int tx, int ty, int gxn,
+                                               int gyn) {
+    if (A.lagged && gxn < A.nx && gyn < A.ny) {
+        const size_t nxy = (size_t)A.nx * A.ny, node = (size_t)gyn * A.nx + gxn;
+        const Real* Fin = static_cast<const Real*>(A.Fin);
+        cp_async_elem(&S.Fl[0][ty][tx], Fin + node);
+        cp_async_elem(&S.Fl[1][ty][tx], Fin + nxy + node);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
 
 // Pull offsets: g_a(r, t) = g*_a(r - e_a, t - 1).
 __device__ __forceinline__ int pull_src(int a, int wx, int wy, int xm, int xp, int ym, int yp, int nx) {
@@ -455,10 +482,10 @@ __device__ __forceinline__ void phase3(const StepArgs& A, const MixConstT<typena
     }
     const int node = gyn * nx + gxn;
     Real Fux = Ftx, Fuy = Fty;
-    if (A.lagged) {
-        const Real* Fin = static_cast<const Real*>(A.Fin);
-        Fux = __ldg(Fin + node);
-        Fuy = __ldg(Fin + nxy + node);
+    if (A.lagged) {  // F(t - 1), copied by prefetch_force
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        Fux = S.Fl[0][ty][tx];
+        Fuy = S.Fl[1][ty][tx];
     }
     const Real inv_rho = Real(1) / rho;
     const Real ux = (jx + Real(0.5) * Fux) * inv_rho;
@@ -573,12 +600,13 @@ __global__ void __launch_bounds__(kTX* TY) fused_step(StepArgs A) {
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * TY;
     // no periodic wrap anywhere in this block's reach (tile + 2 halo + 1 pull)
     const bool inner = x0 >= 3 && x0 + kTX + 3 <= nx && y0 >= 3 && y0 + TY + 3 <= ny;
+    const int gxn = x0 + tx, gyn = y0 + ty;
+    prefetch_force<Real, NC, TY>(A, S, tx, ty, gxn, gyn);
     Real g[NC][9];
     phase1_global<NC, ST, TY>(A, m, S, g, x0, y0, inner, tx, ty, tid);
     __syncthreads();
     phase2<NC, TY, Real>(m, S, A.stencil, tid);
     __syncthreads();
-    const int gxn = x0 + tx, gyn = y0 + ty;
     if (gxn < nx && gyn < ny) phase3<NC, ST, TY, MOMENTS>(A, m, S, g, tx, ty, gxn, gyn);
 }
 
@@ -655,16 +683,17 @@ __global__ void __launch_bounds__(kTX* kRedTY) reduce_partial(StepArgs A,
         Real r[NC];
         pull_rho<NC, ST>(A, x, y, inner, nx, ny, nxy, r);
         const int node = y * nx + x;
-        // read every snapshot value before the first store (the stores may alias later
-        // reads as far as the compiler can tell, which would serialise them)
+        // The snapshot is read whatever have_prev says (its buffer always holds NC x nx x ny
+        // values) and before the first store: a read guarded by the flag was issued only
+        // after the pulled sums had arrived and made this kernel about three times slower.
         Real prev[NC];
 #pragma unroll
-        for (int i = 0; i < NC; ++i) prev[i] = have_prev ? rho_prev[(size_t)i * nxy + node] : r[i];
+        for (int i = 0; i < NC; ++i) prev[i] = rho_prev[(size_t)i * nxy + node];
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
             acc[i] = r[i];
             acc[NC + 1] += r[i] * r[i];
-            const Real d = r[i] - prev[i];
+            const Real d = have_prev ? r[i] - prev[i] : Real(0);
             acc[NC] += d * d;
         }
 #pragma unroll

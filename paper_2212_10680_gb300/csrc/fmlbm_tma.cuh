@@ -176,6 +176,7 @@ __global__ void __launch_bounds__(kTX* TY, MINB)
         int x0, y0;
         origin(t, x0, y0);
         const int gxn = x0 + tx, gyn = y0 + ty;
+        prefetch_force<Real, NC, TY>(A, S, tx, ty, gxn, gyn);
         unsigned char* st = stages + s * L::stage_bytes;
         Real* gpark = reinterpret_cast<Real*>(st);  // edge tiles: [9N][TY][32]
         constexpr bool PARK = NSTAGE == 1;
@@ -193,6 +194,7 @@ __global__ void __launch_bounds__(kTX* TY, MINB)
 #pragma unroll
                 for (int q = 0; q < NSTAGE; ++q)
                     if (((pending >> q) & 1u) && q != s) mbar_wait_bounded(&bar[q], (parity >> q) & 1u);
+                asm volatile("cp.async.wait_all;\n" ::: "memory");  // the force prefetch
                 return;
             }
             parity ^= 1u << s;
