@@ -171,7 +171,8 @@ fmlbm_status fmlbm_set_state(fmlbm_handle* h, const void* buf, size_t bytes);
 
 /* Tuning: height (8, 16 or 32 rows) of the 32-column tile each thread block of the
  * plain fused step owns (moments always use 8 or 16).  Results do not depend on it
- * (bit-identical).  Default: 16 when ny >= 64, else 8. */
+ * (bit-identical).  Default: 8 (the fastest measured on GB300 for two and three
+ * components; taller tiles recompute less halo but keep fewer blocks per SM). */
 fmlbm_status fmlbm_set_tile_height(fmlbm_handle* h, int32_t tile_y);
 
 /* Which kernel advances the lattice.  PLAIN: the fused step with per-thread pulls from

@@ -387,7 +387,7 @@ fmlbm_status fmlbm_create(const fmlbm_mixture* mixture, const fmlbm_lattice* lat
     h->mixture = *mixture;
     h->lattice = *lattice;
     h->stream = static_cast<cudaStream_t>(cuda_stream);
-    h->tile_y = lattice->ny >= 64 ? kTileYLarge : kTileYSmall;
+    h->tile_y = kTileYSmall;
     if (cudaGetDevice(&h->device) != cudaSuccess) {
         delete h;
         return FMLBM_E_CUDA;
