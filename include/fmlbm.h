@@ -176,20 +176,20 @@ fmlbm_status fmlbm_set_state(fmlbm_handle* h, const void* buf, size_t bytes);
 fmlbm_status fmlbm_set_tile_height(fmlbm_handle* h, int32_t tile_y);
 
 /* Which kernel advances the lattice.  PLAIN: the fused step with per-thread pulls from
- * global memory.  TMA: a persistent fused step whose blocks copy each wrap-free tile
- * (every plane plus a 3-node halo) into shared memory with one bulk tensor copy,
- * double-buffered so the next tile's copy overlaps the current tile's arithmetic; tiles
- * on the periodic edges take the plain path.  Both give bit-identical results.  TMA is
- * available for FP32 and 16-bit storage with nx a multiple of 4 (FP32) or 8 (16-bit) and a
- * lattice of at least 38 x 22.  TMA_TILE: the same copies with one tile per block, a single
- * stage and two blocks per multiprocessor (the pulled values wait in shared memory).  AUTO
- * (default): where the TMA forms are available and the lattice has at least 48 tiles of
- * 32 x 16 per multiprocessor, TMA for FP32 and TMA_TILE for the 16-bit forms, else PLAIN;
- * fmlbm_autotune measures instead.  Asking for a TMA form where it is not available
- * returns FMLBM_E_UNSUPPORTED. */
+ * global memory.  TMA: a persistent fused step whose blocks copy each wrap-free tile of
+ * 32 x 8 nodes (every plane plus a 3-node halo) into shared memory with one bulk tensor
+ * copy, double-buffered so the next tile's copy overlaps the current tile's arithmetic;
+ * tiles on the periodic edges take the plain path.  TMA_TILE: the same copies with one
+ * tile per block and a single stage, as many blocks per multiprocessor as shared memory
+ * admits (the pulled values wait in shared memory).  All give bit-identical results.  The
+ * TMA forms are available for FP32 and 16-bit storage with nx a multiple of 4 (FP32) or 8
+ * (16-bit) and a lattice of at least 38 x 14.  AUTO (default): PLAIN, which matched or beat
+ * the TMA forms on the workloads measured on GB300; fmlbm_autotune measures the lattice at
+ * hand instead.  Asking for a TMA form where it is not available returns
+ * FMLBM_E_UNSUPPORTED. */
 typedef enum fmlbm_step_variant {
     FMLBM_VARIANT_AUTO = 0, FMLBM_VARIANT_PLAIN = 1, FMLBM_VARIANT_TMA = 2,
-    FMLBM_VARIANT_TMA_TILE = 3  /* one tile per block, single stage, two blocks per SM */
+    FMLBM_VARIANT_TMA_TILE = 3  /* one tile per block, single stage */
 } fmlbm_step_variant;
 fmlbm_status fmlbm_set_step_variant(fmlbm_handle* h, int32_t variant);
 /* Autotuner: times steps_per_trial steps of every available kernel variant and tile

@@ -243,18 +243,12 @@ cudaError_t dispatch_step_tma(const fmlbm_handle* h, const StepArgs& A, bool sin
     }
 }
 
-// The kernel AUTO resolves to (measured on GB300): the plain step unless each SM gets many
-// tiles (slower TMA at 1024^2, 13 tiles per SM; faster at 4096^2, 215 tiles per SM); there
-// the persistent double-buffered TMA step for float storage and the one-tile-per-block TMA
-// step (two blocks per SM) for the 16-bit forms.
-constexpr int kTmaMinTilesPerSM = 48;
-
+// AUTO resolves to the plain step: with 8-row tiles and the ring-first phase 1 it matched
+// or beat both TMA forms on every measured workload (GB300: 1024^2 binary FP32, 4096^2
+// ternary FP32 and BF16DEV); fmlbm_autotune can still pick a TMA form where it wins.
 int resolved_variant(const fmlbm_handle* h) {
-    if (!h->tma_maps || h->variant == FMLBM_VARIANT_PLAIN) return FMLBM_VARIANT_PLAIN;
-    if (h->variant != FMLBM_VARIANT_AUTO) return h->variant;
-    const long tiles = (long)((h->lattice.nx + kTX - 1) / kTX) * ((h->lattice.ny + kTmaTileY - 1) / kTmaTileY);
-    if (tiles < (long)kTmaMinTilesPerSM * h->sms) return FMLBM_VARIANT_PLAIN;
-    return h->lattice.precision == FMLBM_FP32 ? FMLBM_VARIANT_TMA : FMLBM_VARIANT_TMA_TILE;
+    if (!h->tma_maps || h->variant == FMLBM_VARIANT_AUTO) return FMLBM_VARIANT_PLAIN;
+    return h->variant;
 }
 
 bool use_tma(const fmlbm_handle* h) { return resolved_variant(h) != FMLBM_VARIANT_PLAIN; }

@@ -392,7 +392,8 @@ __device__ __forceinline__ void phase1_node(const StepArgs& A, const MixConstT<R
 }
 
 // Ring position r (0 <= r < 4 (32 + 4) + 4 TY) -> box coordinates (bx, by) of the 2-node halo
-// ring around the tile (box origin at tile origin - (2, 2)).
+// ring around the tile (box origin at tile origin - (2, 2)), row by row.  (Putting the
+// inner-ring positions, which also need ln f, first measured slower.)
 template <int TY>
 __device__ __forceinline__ void ring_position(int r, int& bx, int& by) {
     constexpr int WB = kTX + 4;
@@ -430,23 +431,29 @@ __device__ __forceinline__ void phase1_ring(const MixConstT<Real>& m, StepSmem<R
 // Phase 2: G_i = sum_j kappa_ij lap rho~_j on tile + 1 (step 6, mu_I,i = -G_i), stored as
 // the potential Phi_i = G_i - RT ln f_i whose gradient times rho~_i is the force of step 7.
 template <int NC, int TY, typename Real>
-__device__ __forceinline__ void phase2(const MixConstT<Real>& m, StepSmem<Real, NC, TY>& S, int stencil, int tid) {
-    constexpr int NT = kTX * TY;
-    constexpr int W1 = kTX + 2;
-    constexpr int N1 = W1 * (TY + 2);
-    for (int q = tid; q < N1; q += NT) {
-        const int cy = q / W1, cx = q % W1;  // tile+1 coordinates
-        Real L[NC];
+__device__ __forceinline__ void phase2_at(const MixConstT<Real>& m, StepSmem<Real, NC, TY>& S, int stencil, int cx,
+                                          int cy) {
+    Real L[NC];
 #pragma unroll
-        for (int j = 0; j < NC; ++j) L[j] = lap_at<Real>(S.rt, j, cx + 1, cy + 1, stencil);
+    for (int j = 0; j < NC; ++j) L[j] = lap_at<Real>(S.rt, j, cx + 1, cy + 1, stencil);
 #pragma unroll
-        for (int i = 0; i < NC; ++i) {
-            Real Gi = Real(0);
+    for (int i = 0; i < NC; ++i) {
+        Real Gi = Real(0);
 #pragma unroll
-            for (int j = 0; j < NC; ++j) Gi += m.kap[i * kMaxC + j] * L[j];
-            S.G.v[i][cy][cx] = Gi - m.RT * S.lf.v[i][cy][cx];
-        }
+        for (int j = 0; j < NC; ++j) Gi += m.kap[i * kMaxC + j] * L[j];
+        S.G.v[i][cy][cx] = Gi - m.RT * S.lf.v[i][cy][cx];
     }
+}
+
+// The tile + 1 box has TY + 2 rows of 32 + 2 columns.  Each warp takes whole rows of the
+// first 32 columns (one shared-memory row per instruction: no bank conflicts, no index
+// division); the last warp, which has one row, also takes the two edge columns.
+template <int NC, int TY, typename Real>
+__device__ __forceinline__ void phase2(const MixConstT<Real>& m, StepSmem<Real, NC, TY>& S, int stencil, int tid) {
+    const int tx = tid & (kTX - 1), ty = tid / kTX;
+    for (int cy = ty; cy < TY + 2; cy += TY) phase2_at<NC, TY, Real>(m, S, stencil, tx, cy);
+    if (ty == TY - 1)
+        for (int e = tx; e < 2 * (TY + 2); e += kTX) phase2_at<NC, TY, Real>(m, S, stencil, kTX + (e & 1), e >> 1);
 }
 
 // Phase 3 at one valid node: force (step 7), velocity (step 1), equilibrium and forcing
@@ -476,13 +483,12 @@ __device__ __forceinline__ void phase3(const StepArgs& A, const MixConstT<typena
         // grad rho_i = M_i grad rho~_i
         grx[i] = rx * m.M[i];
         gry[i] = ry * m.M[i];
-        Real r = Real(0);
-#pragma unroll
-        for (int a = 0; a < 9; ++a) {
-            r += g[i][a];
-            jx += Real(ex(a)) * g[i][a];
-            jy += Real(ey(a)) * g[i][a];
-        }
+        // zeroth and first moments with e_a in {0, +-1} written out: IEEE arithmetic keeps
+        // every 0 * g_a the compiler is given
+        const Real(&h)[9] = g[i];
+        const Real r = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
+        jx += ((h[1] + h[5]) + h[8]) - ((h[3] + h[6]) + h[7]);
+        jy += ((h[2] + h[5]) + h[6]) - ((h[4] + h[7]) + h[8]);
         rhoi[i] = r;
         rho += r;
     }
@@ -513,36 +519,48 @@ __device__ __forceinline__ void phase3(const StepArgs& A, const MixConstT<typena
         // (e_abar = -e_a): the parts even in e are shared, the odd parts change sign.
         //   g^eq_a = w rho [3 eu + 4.5 eu^2 - 1.5 u^2]
         //   F_a    = w [3 eF - 3 uF + 9 eu eF + (c_a - 1) ug + 3 eu eg],  c_a = (3 e^2 - 2)/2
+        // (eu = e_a.u, eF = e_a.F_i, eg = e_a.grad rho_i, uF = u.F_i, ug = u.grad rho_i).  With
+        // rw = omega rho_i, fc = fcoef, base = 1.5 rw u^2 the post-collision value is
+        //   g'_a = (1 - omega) g_a + even_a + odd_a,   g'_abar = (1 - omega) g_abar + even_a - odd_a
+        //   even_a = w_a [eu (e_a.V) + cb_a],  V = 4.5 rw u + fc (9 F_i + 3 grad rho_i),
+        //            cb_a = fc (c_a - 1) ug - 3 fc uF - base
+        //   odd_a  = 3 w_a (rw eu + fc eF) = e_a.O (axes), e_a.O / 4 (diagonals),
+        //            O = (rw u + fc F_i) / 3
+        //   g'_0   = (1 - omega) g_0 + rw + (4/9) (-base - 3 fc uF - 2 fc ug)
+        // and each e_a.X is written out (components 0, +-1): no multiplication by zero.
         const Real omega = m.omega, fc = m.fcoef, keep = Real(1) - omega;
-        const Real usq = ux * ux + uy * uy;
+        const Real usq15 = Real(1.5) * (ux * ux + uy * uy);
+        const Real fc9 = Real(9) * fc, fc3 = Real(3) * fc, fc_3 = fc * Real(1.0 / 3.0);
+        const Real u5 = ux + uy, u6 = uy - ux;  // e_a.u for a = 5 (1,1) and a = 6 (-1,1)
+        const Real w1 = Real(1.0 / 9.0), w5 = Real(1.0 / 36.0);
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
+            const Real(&h)[9] = g[i];
             const Real rw = omega * rhoi[i];
             const Real uF = ux * Fx[i] + uy * Fy[i];
             const Real ug = ux * grx[i] + uy * gry[i];
-            const Real base = rw * Real(1.5) * usq;                    // omega rho 1.5 u^2
-            const Real c_ax = fc * (Real(-3) * uF - Real(0.5) * ug);   // c - 1 = -1/2 on the axes
-            const Real c_dg = fc * (Real(-3) * uF + ug);               // c - 1 = +1 on the diagonals
-            // a = 0: g^eq_0 = rho - (4/9) rho 1.5 u^2, F_0 = (4/9)(-3 uF - 2 ug)
-            const Real g0 = keep * g[i][0] + rw - Real(4.0 / 9.0) * base +
-                            Real(4.0 / 9.0) * fc * (Real(-3) * uF - Real(2) * ug);
-            store_g<ST>(A, i, 0, (size_t)node, (size_t)nxy, g0);
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                // pairs (1,3), (2,4), (5,7), (6,8)
-                const int a = p < 2 ? 1 + p : 5 + (p - 2);
-                const int b = a + 2;
-                const Real w = wgt<Real>(a);
-                const Real cxa = Real(ex(a)), cya = Real(ey(a));
-                const Real eu = cxa * ux + cya * uy;
-                const Real eF = cxa * Fx[i] + cya * Fy[i];
-                const Real eg = cxa * grx[i] + cya * gry[i];
-                const Real even = w * (eu * (Real(4.5) * rw * eu + fc * (Real(9) * eF + Real(3) * eg)) - base +
-                                       (p < 2 ? c_ax : c_dg));
-                const Real odd = Real(3) * w * (rw * eu + fc * eF);
-                store_g<ST>(A, i, a, (size_t)node, (size_t)nxy, keep * g[i][a] + even + odd);
-                store_g<ST>(A, i, b, (size_t)node, (size_t)nxy, keep * g[i][b] + even - odd);
-            }
+            const Real a0 = -(rw * usq15 + fc3 * uF);  // -base - 3 fc uF
+            const Real cb_ax = a0 - Real(0.5) * fc * ug;
+            const Real cb_dg = a0 + fc * ug;
+            const Real rw45 = Real(4.5) * rw, rw3 = rw * Real(1.0 / 3.0);
+            const Real Vx = rw45 * ux + (fc9 * Fx[i] + fc3 * grx[i]);
+            const Real Vy = rw45 * uy + (fc9 * Fy[i] + fc3 * gry[i]);
+            const Real Ox = rw3 * ux + fc_3 * Fx[i];
+            const Real Oy = rw3 * uy + fc_3 * Fy[i];
+            store_g<ST>(A, i, 0, (size_t)node, (size_t)nxy,
+                        keep * h[0] + (rw + Real(4.0 / 9.0) * (a0 - Real(2) * fc * ug)));
+            const Real e1 = w1 * (ux * Vx + cb_ax);
+            store_g<ST>(A, i, 1, (size_t)node, (size_t)nxy, keep * h[1] + (e1 + Ox));
+            store_g<ST>(A, i, 3, (size_t)node, (size_t)nxy, keep * h[3] + (e1 - Ox));
+            const Real e2 = w1 * (uy * Vy + cb_ax);
+            store_g<ST>(A, i, 2, (size_t)node, (size_t)nxy, keep * h[2] + (e2 + Oy));
+            store_g<ST>(A, i, 4, (size_t)node, (size_t)nxy, keep * h[4] + (e2 - Oy));
+            const Real e5 = w5 * (u5 * (Vx + Vy) + cb_dg), o5 = Real(0.25) * (Ox + Oy);
+            store_g<ST>(A, i, 5, (size_t)node, (size_t)nxy, keep * h[5] + (e5 + o5));
+            store_g<ST>(A, i, 7, (size_t)node, (size_t)nxy, keep * h[7] + (e5 - o5));
+            const Real e6 = w5 * (u6 * (Vy - Vx) + cb_dg), o6 = Real(0.25) * (Oy - Ox);
+            store_g<ST>(A, i, 6, (size_t)node, (size_t)nxy, keep * h[6] + (e6 + o6));
+            store_g<ST>(A, i, 8, (size_t)node, (size_t)nxy, keep * h[8] + (e6 - o6));
         }
         Real* Fout = static_cast<Real*>(A.Fout);
         Fout[node] = Ftx;
@@ -562,6 +580,24 @@ __device__ __forceinline__ void phase1_global(const StepArgs& A, const MixConstT
     const int nx = A.nx, ny = A.ny, nxy = nx * ny;
     const int gxn = x0 + tx, gyn = y0 + ty;
     const bool valid = gxn < nx && gyn < ny;
+    // Each thread owns one node and at most one ring node.  Ring first (measured faster
+    // except for three or four components in FP32, where it holds too many registers): the
+    // ring node's pulled sums arrive, then the owned node's loads are issued and the ring
+    // node's ln f is computed while they are in flight.  Otherwise the owned node comes
+    // first and the ring node after it.
+    constexpr int RING = 4 * (kTX + 4) + 4 * TY;
+    static_assert(RING <= NT, "one ring node per thread");
+    constexpr bool RING_FIRST = !(ST == ST_F32 && NC >= 3);
+    const bool has_ring = tid < RING;
+    int bx = 0, by = 0;
+    Real rr[NC];
+    auto pull_ring = [&]() {
+        ring_position<TY>(tid, bx, by);
+        const int wx = inner ? x0 - 2 + bx : wrap(x0 - 2 + bx, nx);
+        const int wy = inner ? y0 - 2 + by : wrap(y0 - 2 + by, ny);
+        pull_rho<NC, ST>(A, wx, wy, inner, nx, ny, nxy, rr);
+    };
+    if (RING_FIRST && has_ring) pull_ring();
     {
         const int wx = inner ? gxn : wrap(gxn, nx), wy = inner ? gyn : wrap(gyn, ny);
         const int node = wy * nx + wx;
@@ -578,24 +614,27 @@ __device__ __forceinline__ void phase1_global(const StepArgs& A, const MixConstT
 #pragma unroll
             for (int i = 0; i < NC; ++i) g[i][a] = load_g<ST>(A, i, a, (size_t)src, (size_t)nxy);
         }
-        phase1_node<NC, TY, Real>(A, m, S, g, tx, ty, valid, gxn, gyn);
     }
-    constexpr int RING = 4 * (kTX + 4) + 4 * TY;
-    for (int r = tid; r < RING; r += NT) {
-        int bx, by;
-        ring_position<TY>(r, bx, by);
-        const int wx = inner ? x0 - 2 + bx : wrap(x0 - 2 + bx, nx);
-        const int wy = inner ? y0 - 2 + by : wrap(y0 - 2 + by, ny);
-        Real rt[NC];
-        pull_rho<NC, ST>(A, wx, wy, inner, nx, ny, nxy, rt);
-        phase1_ring<NC, TY, Real>(m, S, rt, bx, by);
+    if constexpr (RING_FIRST) {
+        if (has_ring) phase1_ring<NC, TY, Real>(m, S, rr, bx, by);
+        phase1_node<NC, TY, Real>(A, m, S, g, tx, ty, valid, gxn, gyn);
+    } else {
+        phase1_node<NC, TY, Real>(A, m, S, g, tx, ty, valid, gxn, gyn);
+        if (has_ring) {
+            pull_ring();
+            phase1_ring<NC, TY, Real>(m, S, rr, bx, by);
+        }
     }
 }
 
 // MOMENTS = true: compute the macroscopic fields of the current state instead of
 // advancing it (no distribution or force store).
 template <int NC, int ST, int TY, bool MOMENTS>
-__global__ void __launch_bounds__(kTX* TY) fused_step(StepArgs A) {
+// Float arithmetic: 1024 resident threads per SM (64 registers a thread), measured faster
+// than trading occupancy for registers (77 registers and three 8-row blocks per SM were 7%
+// slower for three components) or registers for occupancy (48 registers spill).  The FP64
+// reference path keeps what the compiler chooses.
+__global__ void __launch_bounds__(kTX* TY, ST == ST_F64 ? 1 : 1024 / (kTX * TY)) fused_step(StepArgs A) {
     using Real = typename StoreTraits<ST>::Real;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto& S = *reinterpret_cast<StepSmem<Real, NC, TY>*>(smem_raw);

@@ -17,7 +17,7 @@ cudaError_t launch_step(const StepArgs& A, int nc, bool moments, int tile_y, cud
 // Persistent TMA-fed step (float and 16-bit storage); maps[0]: float planes, maps[1]:
 // 16-bit planes (deviation forms).  tma_ok = 0 sends every tile down the plain pull path.
 // single_stage = false: persistent double-buffered blocks (one per SM);
-// true: one tile per block, single stage, two blocks per SM.
+// true: one tile per block, single stage, as many blocks per SM as shared memory admits.
 template <int ST>
 cudaError_t launch_step_tma(const StepArgs& A, int nc, const CUtensorMap* maps, int tma_ok, bool single_stage,
                             cudaStream_t s);
@@ -130,7 +130,11 @@ cudaError_t launch_reduce(const StepArgs& A, int nc, void* rho_prev, int have_pr
             return cudaErrorNotSupported;                                                                 \
         } else {                                                                                          \
             constexpr int NS = SINGLE ? 1 : L::stages;                                                    \
-            constexpr int MINB = SINGLE ? 2 : 1;                                                          \
+            /* single stage: as many blocks as shared memory admits (at most 4), which */             \
+            /* also bounds the registers the compiler may give each thread              */             \
+            constexpr size_t smem1 = L::scratch_bytes + L::stage_bytes + 64 + 1024;                     \
+            constexpr int fit1 = (int)((228 * 1024) / smem1);                                          \
+            constexpr int MINB = SINGLE ? (fit1 > 4 ? 4 : (fit1 < 1 ? 1 : fit1)) : 1;                \
             constexpr size_t smem = L::scratch_bytes + NS * L::stage_bytes + 64;                          \
             auto k = fused_step_tma<NC, ST, kTmaTileY, NS, MINB>;                                         \
             static int per_sm = 0, sms = 0;                                                               \

@@ -21,7 +21,7 @@
 
 namespace fmlbm {
 
-constexpr int kTmaTileY = 16;
+constexpr int kTmaTileY = 8;
 constexpr long long kMaxPolls = 1ll << 24;  // try_wait polls before a wait is declared failed
 
 template <int ST> struct TmaGeom;

@@ -277,15 +277,18 @@ def test_tile_heights_are_bit_identical(fm):
 
 @pytest.mark.parametrize("precision", ["fp32", "fp16dev", "bf16dev"])
 @pytest.mark.parametrize("n", [2, 3])
-def test_tma_step_is_bit_identical_to_plain(fm, precision, n):
-    # 200 x 100: ragged in both directions, wrap-free inner tiles for the bulk-copy path
+@pytest.mark.parametrize("shape", [(200, 100), (96, 24)])
+def test_tma_step_is_bit_identical_to_plain(fm, precision, n, shape):
+    # 200 x 100: ragged in both directions, many wrap-free inner tiles for the bulk-copy
+    # path; 96 x 24: the smallest kind of lattice with one row of inner tiles
     from paper_2212_10680_gb300 import inputs
+    nx, ny = shape
     wl = workloads()["binary" if n == 2 else "ternary"]
-    rho = inputs.with_noise(inputs.slab(wl["slab"]["rt_vapour"], wl["slab"]["rt_liquid"], 200, 100, 0.5, 4.0),
+    rho = inputs.with_noise(inputs.slab(wl["slab"]["rt_vapour"], wl["slab"]["rt_liquid"], nx, ny, 0.5, 4.0),
                             0.01, 5)
     out = []
     for variant in ("plain", "tma", "tma_tile"):
-        lat = fm.Lattice(fm.mixture_from_dict(wl["mixture"]), 200, 100, 1.0, "isotropic", precision, "lagged")
+        lat = fm.Lattice(fm.mixture_from_dict(wl["mixture"]), nx, ny, 1.0, "isotropic", precision, "lagged")
         fm.fmlbm_set_step_variant(lat.h, variant)
         assert fm.fmlbm_get_step_variant(lat.h) == variant
         lat.init(rho)
@@ -297,7 +300,7 @@ def test_tma_step_is_bit_identical_to_plain(fm, precision, n):
 
 
 def test_tma_path_oracle_parity(fm):
-    # a lattice the bulk-copy path serves by default, against the oracle
+    # the persistent bulk-copy step against the oracle
     mixd, rho = slab_state_binary(136, 40, seed=13)
     rec = (1, 10, 30)
     ora = run_oracle(mixd, rho, 1.0, "isotropic", "lagged", max(rec), rec)
