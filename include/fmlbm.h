@@ -148,13 +148,32 @@ fmlbm_status fmlbm_get_distributions(fmlbm_handle* h, double* g, double* force);
  * Resets the step counter to 0 and clears the residual snapshot. */
 fmlbm_status fmlbm_set_distributions(fmlbm_handle* h, const double* g, const double* force);
 
-/* Reductions over the lattice (deterministic, fixed-order, FP64 accumulation):
+/* Reductions over the lattice (deterministic, fixed-order, FP64 accumulation per block):
  * mass[N] = sum_x rho_i; residual = ||rho(t) - rho(t_prev)||_2 / ||rho(t)||_2
- * where t_prev is the state at the previous fmlbm_diagnostics call (+inf on the
- * first call after init); step = steps taken since init.  Then snapshots rho(t).
- * Any pointer may be NULL.  Host outputs; synchronises; reports a latched
+ * where t_prev is the state of the previous diagnostics request (+inf on the first
+ * request after init); step = steps taken since init.  Then snapshots rho(t).
+ * Any pointer may be NULL.  Host outputs; waits for the result (equivalent to
+ * fmlbm_diagnostics_async followed by fmlbm_diagnostics_wait); reports a latched
  * FMLBM_E_NONPHYSICAL. */
 fmlbm_status fmlbm_diagnostics(fmlbm_handle* h, double* mass, double* residual, int64_t* step);
+
+/* Asynchronous diagnostics (the paper has none; a convergence monitor for the time
+ * loop).  fmlbm_diagnostics_async asks for the diagnostics above of the current state
+ * and returns at once with a ticket (requests repeated before the next step share
+ * one).  Nothing is computed yet: the next fmlbm_step computes them inside its first
+ * time step, from the distributions that step reads anyway (plain step kernel; the
+ * TMA forms run the separate reduction before stepping), so a loop that steps and asks
+ * every step adds no extra pass over the lattice; if no step follows,
+ * fmlbm_diagnostics_wait runs the separate reduction.  Results are bit-identical either
+ * way.  fmlbm_diagnostics_wait blocks until the ticket's results have reached the host
+ * (it does not wait for work enqueued after them) and returns them with the state's
+ * step count; it reports a latched FMLBM_E_NONPHYSICAL or FMLBM_E_TIMEOUT as of that
+ * point.  Four results are kept: a ticket older than the four most recent requests
+ * has expired (FMLBM_E_INVALID_ARG), as has a request whose state fmlbm_init,
+ * fmlbm_set_distributions or fmlbm_set_state replaced before it was computed. */
+fmlbm_status fmlbm_diagnostics_async(fmlbm_handle* h, int64_t* ticket);
+fmlbm_status fmlbm_diagnostics_wait(fmlbm_handle* h, int64_t ticket, double* mass, double* residual,
+                                    int64_t* step);
 
 /* First node that left the EOS domain since the last init (after a call returned
  * FMLBM_E_NONPHYSICAL): component, x, y. */

@@ -15,6 +15,22 @@
 
 using namespace fmlbm;
 
+namespace {
+
+// Asynchronous diagnostics: a ring of result slots, each filled by one reduction (fused
+// into the next plain step, or standalone) and read back with its own event.
+constexpr int kDiagSlots = 4;
+constexpr int kDiagWords = kMaxC + 2 + (int)(sizeof(ErrorLatch) + 7) / 8;
+
+struct DiagSlot {
+    int64_t ticket = -1;  // which request owns the slot (-1: none)
+    int64_t step = 0;     // the state (steps taken) the request describes
+    int have_prev = 0;    // whether a snapshot existed when it was computed
+    bool enqueued = false;
+};
+
+}  // namespace
+
 struct fmlbm_handle {
     int nc = 0;
     fmlbm_mixture mixture{};
@@ -28,9 +44,13 @@ struct fmlbm_handle {
     int cur = 0;
     void* rho_prev = nullptr;     // storage arithmetic type
     int have_prev = 0;
-    double* partial = nullptr;
+    void* partial = nullptr;         // per-strip sums, storage arithmetic type (8 bytes reserved each)
     double* diag_dev = nullptr;
-    double* diag_host = nullptr;     // pinned
+    double* diag_host = nullptr;     // pinned: kDiagSlots x kDiagWords doubles (results + error latch)
+    cudaEvent_t diag_ev[kDiagSlots] = {};
+    DiagSlot slot[kDiagSlots];
+    int64_t next_ticket = 0;
+    int64_t pending = -1;            // ticket asked for the current state, not yet enqueued
     ErrorLatch* err_dev = nullptr;
     ErrorLatch* err_host = nullptr;  // pinned
     int64_t step = 0;
@@ -315,8 +335,9 @@ void release(fmlbm_handle* h) {
     if (h->rho_prev) cudaFree(h->rho_prev);
     if (h->partial) cudaFree(h->partial);
     if (h->diag_dev) cudaFree(h->diag_dev);
-    if (h->err_dev) cudaFree(h->err_dev);
     if (h->diag_host) cudaFreeHost(h->diag_host);
+    for (int k = 0; k < kDiagSlots; ++k)
+        if (h->diag_ev[k]) cudaEventDestroy(h->diag_ev[k]);
     if (h->err_host) cudaFreeHost(h->err_host);
 }
 
@@ -325,7 +346,33 @@ fmlbm_status reset_state_flags(fmlbm_handle* h) {
     h->have_prev = 0;
     h->step = 0;
     h->cur = 0;
+    h->pending = -1;  // a request for the replaced state can no longer be served
+    for (int k = 0; k < kDiagSlots; ++k)
+        if (!h->slot[k].enqueued) h->slot[k].ticket = -1;
     return FMLBM_OK;
+}
+
+// Finish the enqueueing of request `ticket` (the current state): final sum, copy of the
+// results and of the error latch into its host slot, event.  The partial sums are
+// already enqueued (fused step or reduce_partial).
+fmlbm_status enqueue_diag_tail(fmlbm_handle* h, int64_t ticket) {
+    DiagSlot& sl = h->slot[ticket % kDiagSlots];
+    double* host = h->diag_host + (size_t)(ticket % kDiagSlots) * kDiagWords;
+    FM_CUDA(h, cudaMemcpyAsync(host, h->diag_dev, kDiagWords * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    FM_CUDA(h, cudaEventRecord(h->diag_ev[ticket % kDiagSlots], h->stream));
+    sl.have_prev = h->have_prev;
+    sl.enqueued = true;
+    h->have_prev = 1;
+    h->pending = -1;
+    return FMLBM_OK;
+}
+
+// The pending request served by a standalone reduction of the current state.
+fmlbm_status enqueue_pending_standalone(fmlbm_handle* h) {
+    if (h->pending < 0) return FMLBM_OK;
+    StepArgs A = make_args(h, h->cur);
+    FM_CUDA(h, dispatch_reduce(h, A));
+    return enqueue_diag_tail(h, h->pending);
 }
 
 }  // namespace
@@ -396,11 +443,14 @@ fmlbm_status fmlbm_create(const fmlbm_mixture* mixture, const fmlbm_lattice* lat
         ok = ok && cudaMalloc(&h->F[k], fb) == cudaSuccess;
     }
     ok = ok && cudaMalloc(&h->rho_prev, (size_t)h->nc * nxy * real_size(lattice->precision)) == cudaSuccess;
-    ok = ok && cudaMalloc((void**)&h->partial,
+    ok = ok && cudaMalloc(&h->partial,
                           (size_t)reduce_blocks(lattice->nx, lattice->ny) * (kMaxC + 2) * sizeof(double)) == cudaSuccess;
-    ok = ok && cudaMalloc((void**)&h->diag_dev, (kMaxC + 2) * sizeof(double)) == cudaSuccess;
-    ok = ok && cudaMalloc((void**)&h->err_dev, sizeof(ErrorLatch)) == cudaSuccess;
-    ok = ok && cudaMallocHost((void**)&h->diag_host, (kMaxC + 2) * sizeof(double)) == cudaSuccess;
+    // the diagnostics results and the error latch share one block, so one copy brings both
+    ok = ok && cudaMalloc((void**)&h->diag_dev, kDiagWords * sizeof(double)) == cudaSuccess;
+    if (ok) h->err_dev = reinterpret_cast<ErrorLatch*>(h->diag_dev + kMaxC + 2);
+    ok = ok && cudaMallocHost((void**)&h->diag_host, (size_t)kDiagSlots * kDiagWords * sizeof(double)) == cudaSuccess;
+    for (int k = 0; k < kDiagSlots; ++k)
+        ok = ok && cudaEventCreateWithFlags(&h->diag_ev[k], cudaEventDisableTiming) == cudaSuccess;
     ok = ok && cudaMallocHost((void**)&h->err_host, sizeof(ErrorLatch)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -454,9 +504,25 @@ fmlbm_status fmlbm_init(fmlbm_handle* h, const double* rho_host) {
 
 fmlbm_status fmlbm_step(fmlbm_handle* h, int64_t nsteps) {
     if (!h || nsteps < 0) return fail(h, FMLBM_E_INVALID_ARG, "bad argument");
+    if (nsteps > 0 && h->pending >= 0 && use_tma(h)) {
+        fmlbm_status s = enqueue_pending_standalone(h);  // the TMA forms have no fused reduction
+        if (s != FMLBM_OK) return s;
+    }
     for (int64_t k = 0; k < nsteps; ++k) {
         StepArgs A = make_args(h, h->cur);
+        const int64_t fused = h->pending;
+        if (fused >= 0) {  // this step also reduces the state it reads
+            A.diag_partial = h->partial;
+            A.rho_prev = h->rho_prev;
+            A.have_prev = h->have_prev;
+        }
         FM_CUDA(h, dispatch_step(h, A, false));
+        if (fused >= 0) {
+            FM_CUDA(h, launch_reduce_final(h->nc, h->lattice.precision == FMLBM_FP64, h->partial, h->lattice.nx,
+                                           h->lattice.ny, h->diag_dev, h->stream));
+            fmlbm_status s = enqueue_diag_tail(h, fused);
+            if (s != FMLBM_OK) return s;
+        }
         h->cur ^= 1;
         ++h->step;
     }
@@ -622,20 +688,52 @@ fmlbm_status fmlbm_set_distributions(fmlbm_handle* h, const double* g, const dou
     return sync_and_check(h);
 }
 
-fmlbm_status fmlbm_diagnostics(fmlbm_handle* h, double* mass, double* residual, int64_t* step) {
-    if (!h) return FMLBM_E_INVALID_ARG;
-    StepArgs A = make_args(h, h->cur);
-    FM_CUDA(h, dispatch_reduce(h, A));
-    FM_CUDA(h, cudaMemcpyAsync(h->diag_host, h->diag_dev, (h->nc + 2) * sizeof(double), cudaMemcpyDeviceToHost,
-                               h->stream));
-    fmlbm_status s = sync_and_check(h);
-    const double* d = h->diag_host;
+fmlbm_status fmlbm_diagnostics_async(fmlbm_handle* h, int64_t* ticket) {
+    if (!h || !ticket) return fail(h, FMLBM_E_INVALID_ARG, "null argument");
+    if (h->pending < 0) {
+        const int64_t t = h->next_ticket++;
+        DiagSlot& sl = h->slot[t % kDiagSlots];
+        sl.ticket = t;
+        sl.step = h->step;
+        sl.enqueued = false;
+        h->pending = t;
+    }
+    *ticket = h->pending;  // repeated requests for one state share a ticket
+    return FMLBM_OK;
+}
+
+fmlbm_status fmlbm_diagnostics_wait(fmlbm_handle* h, int64_t ticket, double* mass, double* residual, int64_t* step) {
+    if (!h || ticket < 0) return fail(h, FMLBM_E_INVALID_ARG, "bad argument");
+    DiagSlot& sl = h->slot[ticket % kDiagSlots];
+    if (sl.ticket != ticket) return fail(h, FMLBM_E_INVALID_ARG, "unknown or expired diagnostics ticket");
+    if (!sl.enqueued) {
+        fmlbm_status s = enqueue_pending_standalone(h);  // no step has served it yet
+        if (s != FMLBM_OK) return s;
+    }
+    FM_CUDA(h, cudaEventSynchronize(h->diag_ev[ticket % kDiagSlots]));
+    const double* d = h->diag_host + (size_t)(ticket % kDiagSlots) * kDiagWords;
+    ErrorLatch latch;
+    std::memcpy(&latch, d + kMaxC + 2, sizeof latch);
     if (mass)
         for (int i = 0; i < h->nc; ++i) mass[i] = d[i];
-    if (residual) *residual = h->have_prev ? std::sqrt(d[h->nc]) / std::sqrt(d[h->nc + 1]) : INFINITY;
-    if (step) *step = h->step;
-    h->have_prev = 1;
-    return s;
+    if (residual) *residual = sl.have_prev ? std::sqrt(d[h->nc]) / std::sqrt(d[h->nc + 1]) : INFINITY;
+    if (step) *step = sl.step;
+    if (latch.flag == 2) return fail(h, FMLBM_E_TIMEOUT, "a bounded wait for a tile copy ran out");
+    if (latch.flag) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "node left the EOS domain: component %d at (x=%d, y=%d)", latch.comp, latch.x,
+                      latch.y);
+        return fail(h, FMLBM_E_NONPHYSICAL, buf);
+    }
+    return FMLBM_OK;
+}
+
+fmlbm_status fmlbm_diagnostics(fmlbm_handle* h, double* mass, double* residual, int64_t* step) {
+    if (!h) return FMLBM_E_INVALID_ARG;
+    int64_t t = -1;
+    fmlbm_status s = fmlbm_diagnostics_async(h, &t);
+    if (s != FMLBM_OK) return s;
+    return fmlbm_diagnostics_wait(h, t, mass, residual, step);
 }
 
 fmlbm_status fmlbm_error_node(fmlbm_handle* h, int32_t* comp, int32_t* x, int32_t* y) {
@@ -696,6 +794,9 @@ fmlbm_status fmlbm_set_state(fmlbm_handle* h, const void* buf, size_t bytes) {
     h->cur = 0;
     h->step = hd.step;
     h->have_prev = 0;
+    h->pending = -1;  // a request for the replaced state can no longer be served
+    for (int k = 0; k < kDiagSlots; ++k)
+        if (!h->slot[k].enqueued) h->slot[k].ticket = -1;
     return sync_and_check(h);
 }
 

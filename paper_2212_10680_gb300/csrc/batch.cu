@@ -126,10 +126,12 @@ cudaError_t launch_batch_step(const fmlbm_batch* b, int ty, int grid) {
 
 template <int ST, int NC>
 cudaError_t launch_batch_reduce_nc(const fmlbm_batch* b) {
+    using Real = typename StoreTraits<ST>::Real;
     batch_reduce<NC, ST><<<b->nwork, dim3(kTX, 8), 0, b->stream>>>(b->d_lat, b->d_work, b->nwork, b->d_prev,
-                                                                   b->d_partial);
+                                                                   reinterpret_cast<Real*>(b->d_partial));
     const int total = b->capacity * (NC + 2);
-    batch_reduce_final<NC><<<(total + 127) / 128, 128, 0, b->stream>>>(b->d_lat, b->capacity, b->d_partial, b->d_out);
+    batch_reduce_final<NC, Real><<<(total + 127) / 128, 128, 0, b->stream>>>(
+        b->d_lat, b->capacity, reinterpret_cast<const Real*>(b->d_partial), b->d_out);
     return cudaGetLastError();
 }
 template <int ST>

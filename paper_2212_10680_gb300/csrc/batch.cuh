@@ -77,7 +77,7 @@ __global__ void batch_advance(BatchLattice* __restrict__ lat, int n) {
 template <int NC, int ST>
 __global__ void __launch_bounds__(kTX* 8) batch_reduce(BatchLattice* __restrict__ lat, const WorkItem* __restrict__ work,
                                                        int nwork, void* const* __restrict__ rho_prev,
-                                                       double* __restrict__ partial) {
+                                                       typename StoreTraits<ST>::Real* __restrict__ partial) {
     using Real = typename StoreTraits<ST>::Real;
     const int w = blockIdx.x;
     if (w >= nwork) return;
@@ -112,32 +112,21 @@ __global__ void __launch_bounds__(kTX* 8) batch_reduce(BatchLattice* __restrict_
             }
         }
     }
-    __shared__ double red[8][NC + 2];
-#pragma unroll
-    for (int k = 0; k < NC + 2; ++k) {
-        Real v = acc[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (threadIdx.x == 0) red[threadIdx.y][k] = (double)v;
-    }
+    __shared__ Real red[8][NC + 2];
+    diag_warp<NC, Real>(acc, red[threadIdx.y]);
     __syncthreads();
     const int tid = threadIdx.y * kTX + threadIdx.x;
-    if (tid < NC + 2) {
-        double v = 0.0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) v += red[q][tid];
-        partial[(size_t)w * (NC + 2) + tid] = v;
-    }
+    if (tid < NC + 2) partial[(size_t)w * (NC + 2) + tid] = diag_strip<NC, Real>(red, 0, tid);
 }
 
-template <int NC>
-__global__ void batch_reduce_final(const BatchLattice* __restrict__ lat, int n, const double* __restrict__ partial,
+template <int NC, typename Real>
+__global__ void batch_reduce_final(const BatchLattice* __restrict__ lat, int n, const Real* __restrict__ partial,
                                    double* __restrict__ out) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n * (NC + 2)) return;
     const int l = k / (NC + 2), q = k % (NC + 2);
     double v = 0.0;
-    for (int w = lat[l].item0; w < lat[l].item0 + lat[l].nitems; ++w) v += partial[(size_t)w * (NC + 2) + q];
+    for (int w = lat[l].item0; w < lat[l].item0 + lat[l].nitems; ++w) v += (double)partial[(size_t)w * (NC + 2) + q];
     out[k] = v;
 }
 

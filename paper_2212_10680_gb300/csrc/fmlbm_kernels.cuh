@@ -113,6 +113,12 @@ struct StepArgs {
     ErrorLatch* err;
     MixConstT<double> mixd;
     MixConstT<float> mixf;
+    // diagnostics of the input state fused into a plain step (diag_partial null: none):
+    // N + 2 sums per 32 x 8 strip in reduce_partial's layout (storage arithmetic type),
+    // and the density snapshot
+    void* diag_partial;
+    void* rho_prev;  // [N][ny][nx] in the storage arithmetic type
+    int have_prev;
 };
 
 template <typename E> __device__ __forceinline__ const MixConstT<E>& mixc(const StepArgs& A);
@@ -627,6 +633,49 @@ __device__ __forceinline__ void phase1_global(const StepArgs& A, const MixConstT
     }
 }
 
+// Diagnostics sums at one node, shared by reduce_partial and the fused step so that both
+// give the same bits: rho_i, (rho_i - pv_i)^2 (0 without a snapshot) and rho_i^2 into acc,
+// then the snapshot refresh (prev <- rho).  The callers read the snapshot pv whatever
+// have_prev says (its buffer always holds N x nx x ny values) and early: a read guarded by
+// the flag was issued only after the pulled sums had arrived and made the reduction about
+// three times slower.
+template <int NC, typename Real>
+__device__ __forceinline__ void diag_node(const Real (&r)[NC], const Real (&pv)[NC], Real* __restrict__ prev,
+                                          int have_prev, size_t node, size_t nxy, Real (&acc)[NC + 2]) {
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+        acc[i] = r[i];
+        acc[NC + 1] += r[i] * r[i];
+        const Real d = have_prev ? r[i] - pv[i] : Real(0);
+        acc[NC] += d * d;
+    }
+#pragma unroll
+    for (int i = 0; i < NC; ++i) prev[(size_t)i * nxy + node] = r[i];
+}
+
+// Warp sums of acc (a fixed shuffle tree in the arithmetic type) into one row of a
+// per-block table.  No FP64 instruction for float storage: on GB300 a handful of FP64
+// conversions per warp made the fused step three times slower.
+template <int NC, typename Real>
+__device__ __forceinline__ void diag_warp(const Real (&acc)[NC + 2], Real* row) {
+#pragma unroll
+    for (int k = 0; k < NC + 2; ++k) {
+        Real v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) row[k] = v;
+    }
+}
+
+// Sum of eight consecutive rows of that table, in row order (one 32 x 8 strip).
+template <int NC, typename Real>
+__device__ __forceinline__ Real diag_strip(const Real (*red)[NC + 2], int row0, int k) {
+    Real v = Real(0);
+#pragma unroll
+    for (int w = 0; w < 8; ++w) v += red[row0 + w][k];
+    return v;
+}
+
 // MOMENTS = true: compute the macroscopic fields of the current state instead of
 // advancing it (no distribution or force store).
 template <int NC, int ST, int TY, bool MOMENTS>
@@ -646,6 +695,17 @@ __global__ void __launch_bounds__(kTX* TY, ST == ST_F64 ? 1 : 1024 / (kTX * TY))
     // no periodic wrap anywhere in this block's reach (tile + 2 halo + 1 pull)
     const bool inner = x0 >= 3 && x0 + kTX + 3 <= nx && y0 >= 3 && y0 + TY + 3 <= ny;
     const int gxn = x0 + tx, gyn = y0 + ty;
+    // diagnostics: the density snapshot of this thread's node, copied like the force (a load
+    // issued after phase 3 stalled the whole step about 2x)
+    Real* pv_s = reinterpret_cast<Real*>(smem_raw + sizeof(StepSmem<Real, NC, TY>));
+    if constexpr (!MOMENTS) {
+        if (A.diag_partial != nullptr && gxn < nx && gyn < ny) {
+            const Real* prev = static_cast<const Real*>(A.rho_prev);
+            const size_t nxy = (size_t)nx * ny, node = (size_t)gyn * nx + gxn;
+#pragma unroll
+            for (int i = 0; i < NC; ++i) cp_async_elem(&pv_s[(i * TY + ty) * kTX + tx], prev + i * nxy + node);
+        }
+    }
     prefetch_force<Real, NC, TY>(A, S, tx, ty, gxn, gyn);
     Real g[NC][9];
     phase1_global<NC, ST, TY>(A, m, S, g, x0, y0, inner, tx, ty, tid);
@@ -653,6 +713,39 @@ __global__ void __launch_bounds__(kTX* TY, ST == ST_F64 ? 1 : 1024 / (kTX * TY))
     phase2<NC, TY, Real>(m, S, A.stencil, tid);
     __syncthreads();
     if (gxn < nx && gyn < ny) phase3<NC, ST, TY, MOMENTS>(A, m, S, g, tx, ty, gxn, gyn);
+    if constexpr (!MOMENTS) {
+        if (A.diag_partial != nullptr) {  // uniform: diagnostics of the state this step read
+            static_assert(TY % 8 == 0, "diagnostics strips of 8 rows");
+            __shared__ Real dred[TY][NC + 2];
+            Real acc[NC + 2];
+#pragma unroll
+            for (int k = 0; k < NC + 2; ++k) acc[k] = Real(0);
+            if (gxn < nx && gyn < ny) {
+                Real r[NC];
+#pragma unroll
+                for (int i = 0; i < NC; ++i) {
+                    r[i] = Real(0);
+#pragma unroll
+                    for (int a = 0; a < 9; ++a) r[i] += g[i][a];  // the order of pull_rho
+                }
+                asm volatile("cp.async.wait_all;\n" ::: "memory");
+                Real pv[NC];
+#pragma unroll
+                for (int i = 0; i < NC; ++i) pv[i] = pv_s[(i * TY + ty) * kTX + tx];
+                diag_node<NC, Real>(r, pv, static_cast<Real*>(A.rho_prev), A.have_prev, (size_t)gyn * nx + gxn,
+                                    (size_t)nx * ny, acc);
+            }
+            diag_warp<NC, Real>(acc, dred[ty]);
+            __syncthreads();
+            constexpr int STRIPS = TY / 8;
+            if (tid < STRIPS * (NC + 2)) {
+                const int sub = tid / (NC + 2), k = tid % (NC + 2);
+                if (y0 + 8 * sub < ny)
+                    static_cast<Real*>(A.diag_partial)[((size_t)(blockIdx.y * STRIPS + sub) * gridDim.x + blockIdx.x) *
+                                                           (NC + 2) + k] = diag_strip<NC, Real>(dred, 8 * sub, k);
+            }
+        }
+    }
 }
 
 // g = g^eq(rho, u = 0): rho_i in a = 0, zero elsewhere; stored force zero.
@@ -708,15 +801,19 @@ __global__ void convert_g(StepArgs A, const double* __restrict__ gin_d, double* 
 // as the step (so the block count, and with it the summation order, depends only on
 // the lattice shape).  Each block writes NC + 2 doubles: sum rho_i, sum (rho - rho_prev)^2,
 // sum rho^2; then rho_prev <- rho.  reduce_final adds the block rows in a fixed order.
-// Per node and within a warp the sums run in the storage arithmetic type (a pairwise
-// shuffle tree); block sums are promoted to double, so FP32 lattices pay no FP64
-// arithmetic per node.  rho_prev holds values of that same type.
+// A plain fused step asked for the diagnostics of the state it reads writes the same
+// partial sums, bit for bit (same node sums, same shuffle tree, same strips).
+// Per node, within a warp (a pairwise shuffle tree) and over the eight warps of a strip the
+// sums run in the storage arithmetic type; reduce_final promotes the strip sums to double,
+// so FP32 lattices pay no FP64 arithmetic in the per-node kernels.  rho_prev and the
+// partial sums hold values of that same type.
 constexpr int kRedTY = 8;
 
 template <int NC, int ST>
 __global__ void __launch_bounds__(kTX* kRedTY) reduce_partial(StepArgs A,
                                                                typename StoreTraits<ST>::Real* __restrict__ rho_prev,
-                                                               int have_prev, double* __restrict__ partial) {
+                                                               int have_prev,
+                                                               typename StoreTraits<ST>::Real* __restrict__ partial) {
     using Real = typename StoreTraits<ST>::Real;
     const int nx = A.nx, ny = A.ny, nxy = nx * ny;
     const int x = blockIdx.x * kTX + threadIdx.x, y = blockIdx.y * kRedTY + threadIdx.y;
@@ -725,53 +822,30 @@ __global__ void __launch_bounds__(kTX* kRedTY) reduce_partial(StepArgs A,
     for (int k = 0; k < NC + 2; ++k) acc[k] = Real(0);
     if (x < nx && y < ny) {
         const bool inner = x >= 1 && x + 1 < nx && y >= 1 && y + 1 < ny;
+        Real pv[NC];
+#pragma unroll
+        for (int i = 0; i < NC; ++i) pv[i] = rho_prev[(size_t)i * nxy + (size_t)y * nx + x];
         Real r[NC];
         pull_rho<NC, ST>(A, x, y, inner, nx, ny, nxy, r);
-        const int node = y * nx + x;
-        // The snapshot is read whatever have_prev says (its buffer always holds NC x nx x ny
-        // values) and before the first store: a read guarded by the flag was issued only
-        // after the pulled sums had arrived and made this kernel about three times slower.
-        Real prev[NC];
-#pragma unroll
-        for (int i = 0; i < NC; ++i) prev[i] = rho_prev[(size_t)i * nxy + node];
-#pragma unroll
-        for (int i = 0; i < NC; ++i) {
-            acc[i] = r[i];
-            acc[NC + 1] += r[i] * r[i];
-            const Real d = have_prev ? r[i] - prev[i] : Real(0);
-            acc[NC] += d * d;
-        }
-#pragma unroll
-        for (int i = 0; i < NC; ++i) rho_prev[(size_t)i * nxy + node] = r[i];
+        diag_node<NC, Real>(r, pv, rho_prev, have_prev, (size_t)y * nx + x, (size_t)nxy, acc);
     }
-    __shared__ double red[kRedTY][NC + 2];
-    const int lane = threadIdx.x;
-#pragma unroll
-    for (int k = 0; k < NC + 2; ++k) {
-        Real v = acc[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[threadIdx.y][k] = (double)v;
-    }
+    __shared__ Real red[kRedTY][NC + 2];
+    diag_warp<NC, Real>(acc, red[threadIdx.y]);
     __syncthreads();
     const int tid = threadIdx.y * kTX + threadIdx.x;
-    if (tid < NC + 2) {
-        double v = 0.0;
-#pragma unroll
-        for (int w = 0; w < kRedTY; ++w) v += red[w][tid];
-        partial[(size_t)(blockIdx.y * gridDim.x + blockIdx.x) * (NC + 2) + tid] = v;
-    }
+    if (tid < NC + 2)
+        partial[(size_t)(blockIdx.y * gridDim.x + blockIdx.x) * (NC + 2) + tid] = diag_strip<NC, Real>(red, 0, tid);
 }
 
 constexpr int kFinalThreads = 256;
 
-template <int NC>
-__global__ void __launch_bounds__(kFinalThreads) reduce_final(const double* __restrict__ partial, int nblocks,
+template <int NC, typename Real>
+__global__ void __launch_bounds__(kFinalThreads) reduce_final(const Real* __restrict__ partial, int nblocks,
                                                                double* __restrict__ out) {
-    // block k sums quantity k over all block rows: fixed strided order, then a fixed tree
+    // block k sums quantity k over all strips in double: fixed strided order, then a fixed tree
     const int k = blockIdx.x;
     double v = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += kFinalThreads) v += partial[(size_t)b * (NC + 2) + k];
+    for (int b = threadIdx.x; b < nblocks; b += kFinalThreads) v += (double)partial[(size_t)b * (NC + 2) + k];
     __shared__ double red[kFinalThreads / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);

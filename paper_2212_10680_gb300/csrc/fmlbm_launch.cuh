@@ -30,16 +30,38 @@ cudaError_t launch_init(const StepArgs& A, int nc, const double* rho, cudaStream
 template <int ST>
 cudaError_t launch_convert(const StepArgs& A, int nc, const double* gin_d, double* gout_d, bool to_storage,
                            cudaStream_t s);
-// rho_prev: NC * nx * ny values of the storage arithmetic type (double for FP64, else float)
+// rho_prev and partial: values of the storage arithmetic type (double for FP64, else
+// float); rho_prev NC * nx * ny of them, partial (NC + 2) * reduce_blocks(nx, ny).
 template <int ST>
-cudaError_t launch_reduce(const StepArgs& A, int nc, void* rho_prev, int have_prev, double* partial,
+cudaError_t launch_reduce(const StepArgs& A, int nc, void* rho_prev, int have_prev, void* partial,
                           double* out, cudaStream_t s);
+
+// The fixed-order final sum alone, for partial sums a fused step wrote (A.diag_partial).
+template <typename Real>
+inline cudaError_t launch_reduce_final_t(int nc, const void* partial, int nb, double* out, cudaStream_t s) {
+    const Real* p = static_cast<const Real*>(partial);
+    switch (nc) {
+        case 1: reduce_final<1, Real><<<1 + 2, kFinalThreads, 0, s>>>(p, nb, out); break;
+        case 2: reduce_final<2, Real><<<2 + 2, kFinalThreads, 0, s>>>(p, nb, out); break;
+        case 3: reduce_final<3, Real><<<3 + 2, kFinalThreads, 0, s>>>(p, nb, out); break;
+        case 4: reduce_final<4, Real><<<4 + 2, kFinalThreads, 0, s>>>(p, nb, out); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+inline cudaError_t launch_reduce_final(int nc, bool fp64, const void* partial, int nx, int ny, double* out,
+                                       cudaStream_t s) {
+    const int nb = reduce_blocks(nx, ny);
+    return fp64 ? launch_reduce_final_t<double>(nc, partial, nb, out, s)
+                : launch_reduce_final_t<float>(nc, partial, nb, out, s);
+}
 
 #define FMLBM_DEFINE_LAUNCHERS(ST)                                                                        \
     template <int NC, bool MOM, int TY>                                                                   \
     static cudaError_t launch_step_nc_##ST(const StepArgs& A, cudaStream_t s) {                           \
         using Real = typename StoreTraits<ST>::Real;                                                      \
-        constexpr size_t smem = sizeof(StepSmem<Real, NC, TY>);                                           \
+        /* + the diagnostics snapshot copy of the tile's nodes */                                       \
+        constexpr size_t smem = sizeof(StepSmem<Real, NC, TY>) + (MOM ? 0 : (size_t)NC * TY * kTX * sizeof(Real)); \
         auto k = fused_step<NC, ST, TY, MOM>;                                                             \
         static bool attr_done = false;                                                                    \
         if (!attr_done) {                                                                                 \
@@ -101,17 +123,18 @@ cudaError_t launch_reduce(const StepArgs& A, int nc, void* rho_prev, int have_pr
     }                                                                                                     \
     template <int NC>                                                                                     \
     static cudaError_t launch_reduce_nc_##ST(const StepArgs& A, void* rho_prev, int have_prev,            \
-                                             double* partial, double* out, cudaStream_t s) {              \
+                                             void* partial, double* out, cudaStream_t s) {                \
         using Real = typename StoreTraits<ST>::Real;                                                      \
         dim3 grid((A.nx + kTX - 1) / kTX, (A.ny + kRedTY - 1) / kRedTY);                                  \
         reduce_partial<NC, ST><<<grid, dim3(kTX, kRedTY), 0, s>>>(A, static_cast<Real*>(rho_prev),        \
-                                                                   have_prev, partial);                   \
-        reduce_final<NC><<<NC + 2, kFinalThreads, 0, s>>>(partial, reduce_blocks(A.nx, A.ny), out);       \
+                                                                   have_prev, static_cast<Real*>(partial)); \
+        reduce_final<NC, Real><<<NC + 2, kFinalThreads, 0, s>>>(static_cast<const Real*>(partial),        \
+                                                                 reduce_blocks(A.nx, A.ny), out);         \
         return cudaGetLastError();                                                                        \
     }                                                                                                     \
     template <>                                                                                           \
     cudaError_t launch_reduce<ST>(const StepArgs& A, int nc, void* rho_prev, int have_prev,               \
-                                  double* partial, double* out, cudaStream_t s) {                         \
+                                  void* partial, double* out, cudaStream_t s) {                           \
         switch (nc) {                                                                                     \
             case 1: return launch_reduce_nc_##ST<1>(A, rho_prev, have_prev, partial, out, s);             \
             case 2: return launch_reduce_nc_##ST<2>(A, rho_prev, have_prev, partial, out, s);             \

@@ -103,6 +103,8 @@ def _load() -> ctypes.CDLL:
         "fmlbm_diagnostics_noalloc": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                        ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+        "fmlbm_diagnostics_async": ([H, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "fmlbm_diagnostics_wait": ([H, ctypes.c_int64, dp, dp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
         "fmlbm_destroy": ([H], None),
         "fmlbm_batch_create": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(H)],
                                ctypes.c_int),
@@ -232,6 +234,22 @@ def fmlbm_diagnostics(h, n_components: int):
     step = ctypes.c_int64()
     st = LIB.fmlbm_diagnostics(h, _ptr(mass), ctypes.byref(res), ctypes.byref(step))
     _check(st, "fmlbm_diagnostics", h)
+    return mass, res.value, step.value
+
+
+def fmlbm_diagnostics_async(h) -> int:
+    """Ticket for the diagnostics of the current state (computed inside the next step)."""
+    t = ctypes.c_int64()
+    _check(LIB.fmlbm_diagnostics_async(h, ctypes.byref(t)), "fmlbm_diagnostics_async", h)
+    return t.value
+
+
+def fmlbm_diagnostics_wait(h, ticket: int, n_components: int):
+    mass = np.empty(n_components)
+    res = ctypes.c_double()
+    step = ctypes.c_int64()
+    st = LIB.fmlbm_diagnostics_wait(h, ticket, _ptr(mass), ctypes.byref(res), ctypes.byref(step))
+    _check(st, "fmlbm_diagnostics_wait", h)
     return mass, res.value, step.value
 
 
