@@ -11,6 +11,8 @@ from paper_2212_10680_gb300 import inputs
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 WORKLOADS = os.path.join(HERE, "golden", "workloads.json")
+PAPER_CASES = os.path.join(HERE, "golden", "paper_cases.json")
+R_BAR = 83.14462618  # bar cm^3 / (mol K)
 
 OA, OB = OMEGA["pr"]
 TC1 = (2.0 / 49.0) / (2.0 / 21.0) * OB / OA
@@ -70,3 +72,36 @@ def normwise(a, b):
     den = np.max(np.abs(b))
     num = np.max(np.abs(a - b))
     return num / den if den > 0 else num
+
+
+def paper_cases() -> dict:
+    with open(PAPER_CASES) as f:
+        return json.load(f)
+
+
+def paper_mixture(names, T_K, eos="pr", kappa=None, physical=False):
+    """A mixture of the components of Table tabCompProp at T_K.
+
+    physical=True: bar, K, cm^3/mol (R = 83.14462618).  Otherwise the lattice units of
+    Section V: R = 1 and, for the most volatile component (the first listed), a = 2/49,
+    b = 2/21, M = 1; since a = Omega_a R^2 Tc^2 / Pc and b = Omega_b R Tc / Pc this fixes
+    that component's Tc and Pc, and every temperature and pressure scales by the same
+    factors (reduced temperatures and pressures, and so alpha(T) and every phase
+    equilibrium, are unchanged); molar masses scale by the first one's.
+    Returns (mixture dict, scale) with scale = dict(T=..., p=...) lattice per physical."""
+    comp = paper_cases()["components"]
+    c = [comp[n] for n in names]
+    n = len(names)
+    kappa = [0.0] * n if kappa is None else list(kappa)
+    if physical:
+        d = dict(eos=eos, R=R_BAR, T=T_K, Tc=[q["Tc_K"] for q in c], Pc=[q["Pc_bar"] for q in c],
+                 omega=[q["omega"] for q in c], M=[q["M"] for q in c], kappa=kappa, kij=[0.0] * (n * n))
+        return d, dict(T=1.0, p=1.0)
+    oa, ob = OMEGA[eos]
+    a1, b1 = 2.0 / 49.0, 2.0 / 21.0
+    tc1 = (a1 / b1) * ob / oa
+    pc1 = ob * tc1 / b1
+    sT, sp = tc1 / c[0]["Tc_K"], pc1 / c[0]["Pc_bar"]
+    d = dict(eos=eos, R=1.0, T=T_K * sT, Tc=[q["Tc_K"] * sT for q in c], Pc=[q["Pc_bar"] * sp for q in c],
+             omega=[q["omega"] for q in c], M=[q["M"] / c[0]["M"] for q in c], kappa=kappa, kij=[0.0] * (n * n))
+    return d, dict(T=sT, p=sp)

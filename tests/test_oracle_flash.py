@@ -122,3 +122,36 @@ def test_table_tabfug_c2_c5_physical_units():
     pL, pV = pressure(mix, np.exp(sL)), pressure(mix, np.exp(sV))
     assert np.exp(sL).sum() > 1.5 * np.exp(sV).sum()
     assert 0 < (pL - pV) / pV < 1e-2
+
+
+def test_section_v_e_density_ratio_c3_c5_340K_5bar():
+    # Section V.E: the PR flash of propane / n-pentane at 340 K and 5 bar gives a density
+    # ratio of 50.97 (the paper prints four figures); the phase compositions of a binary
+    # flash do not depend on the feed
+    from cases import paper_mixture, oracle_mixture
+    mixd, _ = paper_mixture(["C3", "C5"], 340.0, "pr", physical=True)
+    mix = oracle_mixture(mixd)
+    M = np.array(mixd["M"])
+    for z in ([0.4, 0.6], [0.3, 0.7]):
+        r = flash(mix, 5.0, z)
+        ratio = (r["rtL"] * M).sum() / (r["rtV"] * M).sum()
+        assert abs(ratio - 50.97) < 0.006
+
+
+def test_section_v_lattice_units_leave_phase_equilibria_unchanged():
+    # R = 1, a = 2/49, b = 2/21, M = 1 for the most volatile component: temperatures and
+    # pressures scale by fixed factors, so compositions and density ratios are unchanged
+    from cases import paper_mixture, oracle_mixture
+    for names, T, p, z, eos in ((["C3", "C5"], 370.03, 16.547, [0.4, 0.6], "pr"),
+                                (["C3", "C5"], 370.03, 16.547, [0.4, 0.6], "srk"),
+                                (["C1", "C2", "C3"], 216.483, 20.684, [0.4, 0.3, 0.3], "pr")):
+        dl, sc = paper_mixture(names, T, eos)
+        dp, _ = paper_mixture(names, T, eos, physical=True)
+        oa, ob = OMEGA[eos]
+        assert abs(oa * dl["Tc"][0] ** 2 / dl["Pc"][0] - 2.0 / 49.0) < 1e-15  # a_1 (R = 1)
+        assert abs(ob * dl["Tc"][0] / dl["Pc"][0] - 2.0 / 21.0) < 1e-15       # b_1
+        fl = flash(oracle_mixture(dl), p * sc["p"], z)
+        fp = flash(oracle_mixture(dp), p, z)
+        assert np.allclose(fl["x"], fp["x"], atol=1e-12) and np.allclose(fl["y"], fp["y"], atol=1e-12)
+        ML, MP = np.array(dl["M"]), np.array(dp["M"])
+        assert abs((fl["rtL"] * ML).sum() / (fl["rtV"] * ML).sum() / ((fp["rtL"] * MP).sum() / (fp["rtV"] * MP).sum()) - 1) < 1e-10
