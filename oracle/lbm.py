@@ -36,6 +36,12 @@ document of this repository):
   any field that is uniform along y (every flat-slab case).
 * The (1 - 1/(2 tau)) prefactor multiplies the whole F_{a,i} of Eq. eqLBEMCfinal3.
 * rho_0 and rho_{0,i} of Eq. eqLBEMCb are one constant, 0.
+* ``formulation="standard"`` is the variant Section VI (Discussion) allows: the
+  standard LBE of Eq. eqLBE per component (equilibrium rho_i w_a [1 + ...], i.e.
+  Eq. eqLBEMCb with rho_{0,i} = rho_i; forcing term of Eq. eqLBEfinal3, i.e.
+  Eq. eqLBEMCfinal3 without its grad rho_i part) with the force of Eq. eqForceGen,
+  which adds c_s^2 grad rho_i (mass density) to Eq. eqforcefinal.  Its flat-interface
+  equilibria deviate slightly from the flash, as the paper says.
 * The direction order below is a convention of this code, not of the paper.
 
 Parity: the step-by-step transient is "parity unpinned" beyond the invariants
@@ -73,6 +79,7 @@ class Lattice:
     stencil: str = "isotropic"     # or "central"
     velocity_force: str = "lagged"  # or "current"
     rho0: float = 0.0
+    formulation: str = "well_balanced"  # or "standard" (Eq. eqLBE with Eq. eqForceGen)
 
 
 def neighbour(h: np.ndarray, dx: int, dy: int) -> np.ndarray:
@@ -106,8 +113,10 @@ def laplacian(h: np.ndarray, stencil: str) -> np.ndarray:
     return 2.0 * out / CS2
 
 
-def equilibrium(rho_i: np.ndarray, ux: np.ndarray, uy: np.ndarray, rho0: float = 0.0) -> np.ndarray:
-    """Well-balanced equilibrium of Eq. eqLBEMCb for every component and direction.
+def equilibrium(rho_i: np.ndarray, ux: np.ndarray, uy: np.ndarray, rho0: float = 0.0,
+                standard: bool = False) -> np.ndarray:
+    """Well-balanced equilibrium of Eq. eqLBEMCb for every component and direction
+    (standard=True: the equilibrium of Eq. eqLBE, rho_i w_a [1 + S]).
 
     rho_i has shape (N, ny, nx); the result has shape (N, 9, ny, nx).
     """
@@ -117,7 +126,9 @@ def equilibrium(rho_i: np.ndarray, ux: np.ndarray, uy: np.ndarray, rho0: float =
     for a in range(9):
         eu = E[a, 0] * ux + E[a, 1] * uy
         S = eu / CS2 + eu * eu / (2.0 * CS2 * CS2) - usq / (2.0 * CS2)
-        if a == 0:
+        if standard:
+            geq[:, a] = W[a] * rho_i * (1.0 + S)
+        elif a == 0:
             geq[:, 0] = rho_i - (1.0 - W[0]) * rho0 + W[0] * rho_i * S
         else:
             geq[:, a] = W[a] * rho0 + W[a] * rho_i * S
@@ -181,14 +192,21 @@ def macroscopic(g: np.ndarray, mix: Mixture, lat: Lattice, F_prev: np.ndarray = 
     kappa_ij = np.sqrt(np.outer(mix.kappa, mix.kappa))
     lap_rt = np.stack([laplacian(rt[j], lat.stencil) for j in range(mix.n)])
     muI = -np.tensordot(kappa_ij, lap_rt, axes=(1, 0))
-    # step 7: F_i = -rho~_i RT grad ln f_i - rho~_i grad mu_I,i
+    # step 7: F_i = -rho~_i RT grad ln f_i - rho~_i grad mu_I,i (+ c_s^2 grad rho_i in the
+    # standard formulation, Eq. eqForceGen)
     Fx = np.empty_like(rho)
     Fy = np.empty_like(rho)
+    grx = np.empty_like(rho)
+    gry = np.empty_like(rho)
     for i in range(mix.n):
         glx, gly = gradient(lnf[i], lat.stencil)
         gmx, gmy = gradient(muI[i], lat.stencil)
+        grx[i], gry[i] = gradient(rho[i], lat.stencil)
         Fx[i] = -rt[i] * mix.RT * glx - rt[i] * gmx
         Fy[i] = -rt[i] * mix.RT * gly - rt[i] * gmy
+        if lat.formulation == "standard":
+            Fx[i] = Fx[i] + CS2 * grx[i]
+            Fy[i] = Fy[i] + CS2 * gry[i]
     # velocity of step 1: u = (1/rho) sum_i [sum_a g_{a,i} e_a + F_i / 2]
     if lat.velocity_force == "current":
         Fu_x, Fu_y = Fx.sum(axis=0), Fy.sum(axis=0)
@@ -199,7 +217,7 @@ def macroscopic(g: np.ndarray, mix: Mixture, lat: Lattice, F_prev: np.ndarray = 
     ux = (jx.sum(axis=0) + 0.5 * Fu_x) / rho_tot
     uy = (jy.sum(axis=0) + 0.5 * Fu_y) / rho_tot
     F_tot = np.stack([Fx.sum(axis=0), Fy.sum(axis=0)])
-    return dict(rho=rho, rt=rt, p=p, lnf=lnf, muI=muI, Fx=Fx, Fy=Fy, ux=ux, uy=uy, F_tot=F_tot)
+    return dict(rho=rho, rt=rt, p=p, lnf=lnf, muI=muI, Fx=Fx, Fy=Fy, grx=grx, gry=gry, ux=ux, uy=uy, F_tot=F_tot)
 
 
 def step(g: np.ndarray, mix: Mixture, lat: Lattice, F_prev: np.ndarray = None,
@@ -211,12 +229,14 @@ def step(g: np.ndarray, mix: Mixture, lat: Lattice, F_prev: np.ndarray = None,
     the "lagged" reading.  With return_macro, also the dict of ``macroscopic``."""
     m = macroscopic(g, mix, lat, F_prev)
     # step 8
-    geq = equilibrium(m["rho"], m["ux"], m["uy"], lat.rho0)
-    grx = np.empty_like(m["rho"])
-    gry = np.empty_like(m["rho"])
-    for i in range(mix.n):
-        grx[i], gry[i] = gradient(m["rho"][i], lat.stencil)
-    Fa = forcing_term(m["Fx"], m["Fy"], grx, gry, m["ux"], m["uy"])
+    if lat.formulation == "standard":
+        # Eq. eqLBE per component: rho_{0,i} = rho_i, forcing without the grad rho_i part
+        geq = equilibrium(m["rho"], m["ux"], m["uy"], standard=True)
+        zero = np.zeros_like(m["rho"])
+        Fa = forcing_term(m["Fx"], m["Fy"], zero, zero, m["ux"], m["uy"])
+    else:
+        geq = equilibrium(m["rho"], m["ux"], m["uy"], lat.rho0)
+        Fa = forcing_term(m["Fx"], m["Fy"], m["grx"], m["gry"], m["ux"], m["uy"])
     # step 9: collision (Eq. eqLBEMCa), then streaming to r + e_a
     gstar = g - (g - geq) / lat.tau + (1.0 - 1.0 / (2.0 * lat.tau)) * Fa
     out = np.empty_like(g)
@@ -227,12 +247,14 @@ def step(g: np.ndarray, mix: Mixture, lat: Lattice, F_prev: np.ndarray = None,
     return out, m["F_tot"]
 
 
-def init_at_rest(rho: np.ndarray, rho0: float = 0.0):
-    """State of a fluid at rest: g = g^eq(rho_i, u = 0) of Eq. eqLBEMCb and a zero stored
-    force (there is no previous step whose force the first velocity could use)."""
+def init_at_rest(rho: np.ndarray, rho0: float = 0.0, formulation: str = "well_balanced"):
+    """State of a fluid at rest: g = g^eq(rho_i, u = 0) of Eq. eqLBEMCb (Eq. eqLBE in the
+    standard formulation: rho_i w_a) and a zero stored force (there is no previous step
+    whose force the first velocity could use)."""
     rho = np.asarray(rho, dtype=np.float64)
     z = np.zeros(rho.shape[1:], dtype=np.float64)
-    return equilibrium(rho, z, z, rho0), np.zeros((2,) + rho.shape[1:], dtype=np.float64)
+    geq = equilibrium(rho, z, z, rho0, standard=formulation == "standard")
+    return geq, np.zeros((2,) + rho.shape[1:], dtype=np.float64)
 
 
 def run(g: np.ndarray, F_prev: np.ndarray, mix: Mixture, lat: Lattice, nsteps: int):

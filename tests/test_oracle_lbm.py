@@ -11,6 +11,10 @@
   swapped indices and mis-assigned directions); the isotropic stencils equal the
   central ones on y-uniform fields.
 * The single-component limit settles on the Maxwell pair of the PR EOS.
+* The standard formulation of Section VI (Eq. eqLBE, force of Eq. eqForceGen): its
+  equilibrium carries c_s^2 rho_i I, Guo's forcing term has the plain moments, mass is
+  conserved, a uniform state is invariant, and a flat slab settles slightly off the
+  Maxwell pair (close enough to catch a wrong sign of the c_s^2 grad rho_i term).
 """
 import numpy as np
 import pytest
@@ -185,3 +189,66 @@ def test_single_component_limit_reaches_maxwell_pair():
     assert abs(r[0] / s["rtV"] - 1) < 2e-4
     # and the slab did move away from the tanh start (the test is not vacuous)
     assert np.max(np.abs(r - rho[0, 0])) > 1e-3
+
+
+# --- the standard formulation of Section VI (Eq. eqLBE with the force of Eq. eqForceGen) ---
+
+def test_standard_equilibrium_and_forcing_moments():
+    # Eq. eqLBE's equilibrium carries the ideal-gas flux c_s^2 rho_i I that the well-balanced
+    # form removes, and Guo's forcing term (Eq. eqLBEfinal3) has second moment u F + F u
+    rng = np.random.default_rng(3)
+    rho = rng.uniform(0.1, 3.0, (2, 3, 4))
+    ux = rng.uniform(-0.1, 0.1, (3, 4))
+    uy = rng.uniform(-0.1, 0.1, (3, 4))
+    geq, _ = lbm.init_at_rest(rho, formulation="standard")
+    assert np.allclose(geq, lbm.W[None, :, None, None] * rho[:, None], atol=1e-15)   # rho_i w_a at rest
+    geq = lbm.equilibrium(rho, ux, uy, standard=True)
+    assert np.allclose(geq, lbm.equilibrium(rho, ux, uy, rho), atol=1e-15)   # Eq. eqLBEMCb, rho_0,i = rho_i
+    E = lbm.E.astype(float)
+    for a in range(9):
+        eu = E[a, 0] * ux + E[a, 1] * uy
+        expect = lbm.W[a] * rho * (1 + eu / CS2 + eu * eu / (2 * CS2 ** 2) - (ux * ux + uy * uy) / (2 * CS2))
+        assert np.allclose(geq[:, a], expect, atol=1e-15)
+    Pxx = np.tensordot(E[:, 0] ** 2, geq, axes=(0, 1))
+    assert np.allclose(Pxx, rho * ux * ux + CS2 * rho, atol=1e-14)
+    Fx, Fy = rng.normal(size=(2,) + rho.shape)
+    z = np.zeros_like(Fx)
+    Fa = lbm.forcing_term(Fx, Fy, z, z, ux, uy)
+    assert np.allclose(Fa.sum(axis=1), 0.0, atol=1e-14)
+    assert np.allclose(np.tensordot(E[:, 0], Fa, axes=(0, 1)), Fx, atol=1e-14)
+    assert np.allclose(np.tensordot(E[:, 0] * E[:, 1], Fa, axes=(0, 1)), ux * Fy + uy * Fx, atol=1e-13)
+
+
+def test_standard_form_conserves_mass_and_keeps_a_uniform_state():
+    mix = binary_mixture(Tr=1.1)
+    lat = lbm.Lattice(tau=0.9, stencil="isotropic", formulation="standard")
+    g, F = lbm.init_at_rest(_smooth_binary_state(), formulation="standard")
+    m0 = lbm.component_mass(g)
+    g, F = lbm.run(g, F, mix, lat, 200)
+    assert np.max(np.abs(lbm.component_mass(g) / m0 - 1)) < 1e-13
+    rho = np.stack([np.full((6, 7), 2.0), np.full((6, 7), 1.5)])
+    g0, F0 = lbm.init_at_rest(rho, formulation="standard")
+    g, F = lbm.run(g0, F0, mix, lat, 50)
+    # invariant up to the rounding of sum_a w_a rho_i (the well-balanced rest state puts
+    # all of rho_i in a = 0 and is invariant bit for bit)
+    assert np.allclose(g, g0, rtol=1e-14, atol=0) and np.max(np.abs(F)) < 1e-14
+
+
+def test_standard_form_single_component_slab_deviates_slightly_from_maxwell():
+    # Section VI: the standard formulation works with "slight deviations" from
+    # thermodynamics.  The c_s^2 grad rho of Eq. eqForceGen cancels the LBE's own ideal-gas
+    # pressure gradient only up to discretisation, which shows most in the vapour: at
+    # T = 0.95 Tc the slab settles 0.7% (liquid) and 3.7% (vapour) off the Maxwell pair,
+    # where the well-balanced form is within 7e-4 (at 0.85 Tc the vapour is 30% off, so
+    # "slight" holds for moderate density ratios only).  A wrong sign of that term drives
+    # the vapour negative within a few thousand steps.
+    Tc1, Pc1 = lattice_units()
+    mix = Mixture("pr", 1.0, 0.95 * Tc1, Tc=[Tc1], Pc=[Pc1], omega=[0.011], kappa=[0.1])
+    s = pure_coexistence(mix)
+    nx = 128
+    rho = inputs.slab([s["rtV"]], [s["rtL"]], nx, 1, 0.5, 4.0)
+    g, F = lbm.init_at_rest(rho, formulation="standard")
+    g, F = lbm.run(g, F, mix, lbm.Lattice(tau=1.0, stencil="central", formulation="standard"), 8000)
+    r = g.sum(axis=1)[0, 0]
+    dL, dV = abs(r[nx // 2] / s["rtL"] - 1), abs(r[0] / s["rtV"] - 1)
+    assert 3e-3 < dL < 0.012 and 0.02 < dV < 0.05, (dL, dV)
