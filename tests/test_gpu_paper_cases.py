@@ -1,0 +1,189 @@
+"""The paper's validation cases (Section V) on the GPU, in the paper's lattice units.
+
+Mixtures come from Table tabCompProp with the mapping of Section V (R = 1; a = 2/49,
+b = 2/21, M = 1 for the most volatile component; tests/cases.py: paper_mixture), the
+set-ups from tests/golden/paper_cases.json.  Each case compares the lattice with the
+FP64 flash oracle the way the paper does, and checks the result against a bound; the
+numbers the paper prints (Tables tabcase1error, tabcase3, tabFug; the oscillation
+periods of Section V.E) are the context for those bounds:
+
+* V.A  propane / n-pentane flat interface, PR and SRK: bulk densities and compositions
+       against the flash at the lattice's own pressure;
+* V.C  methane / ethane / propane flat interface (PR): the same for three components;
+* V.D  spinodal decomposition of ethane / n-pentane: equal fugacities in the two
+       phases (iso-fugacity) and their values in bar against Table tabFug;
+* V.E  oscillating propane / n-pentane droplet: the oscillation period against the
+       paper's and against Lamb's period with the interfacial tension of Eq. eqMCsigma
+       measured on a flat interface at the same conditions.
+
+Step counts are shorter than the paper's (which ran 5e5 - 1e6 steps) where the bulk
+values have settled well inside the bounds; the bounds and what was measured are
+recorded with each case.
+"""
+import numpy as np
+import pytest
+from scipy.optimize import curve_fit
+
+from cases import oracle_mixture, paper_cases, paper_mixture
+from oracle.eos import lnf_density_form, pressure
+from oracle.flash import flash, vapour_volume_fraction, volume_roots
+from oracle.interface import crossing_radius, interfacial_tension, lamb_period
+from paper_2212_10680_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+CASES = paper_cases()
+
+
+@pytest.fixture(scope="module")
+def fm():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2212_10680_gb300 import fmlbm
+    return fmlbm
+
+
+def _relax(fm, mixd, rho, tau, steps, precision="fp64", stencil="central"):
+    n, ny, nx = rho.shape
+    lat = fm.Lattice(fm.mixture_from_dict(mixd), nx, ny, tau, stencil, precision, "lagged")
+    lat.init(rho)
+    lat.step(steps)
+    r, u, lnf = lat.moments()  # raises on a latched non-physical state
+    lat.close()
+    return r, u, lnf
+
+
+def _bulk_phases(r, M):
+    """Molar densities at the middle of the liquid run and of the vapour run of a 1-D
+    periodic profile (the slab may sit anywhere: a flat slab can translate)."""
+    tot = r[:, 0, :].sum(axis=0)
+    nx = tot.size
+    liquid = tot > 0.5 * (tot.max() + tot.min())
+    start = int(np.argmin(tot))           # a vapour node: the liquid run is contiguous after it
+    idx = np.nonzero(np.roll(liquid, -start))[0]
+    iL = (start + (idx[0] + idx[-1]) // 2) % nx
+    iV = (iL + nx // 2) % nx
+    return r[:, 0, iL] / M, r[:, 0, iV] / M
+
+
+def _errors_percent(mix, M, L, V, z):
+    """Relative errors (%) of Eq. eqerror against the flash at the vapour's pressure."""
+    f = flash(mix, float(pressure(mix, V)), z)
+    pct = lambda a, b: 100.0 * np.abs(a - b) / np.abs(b)
+    dens = [pct((L * M).sum(), (f["rtL"] * M).sum()), pct((V * M).sum(), (f["rtV"] * M).sum())]
+    comp = [pct(L / L.sum(), f["x"]), pct(V / V.sum(), f["y"])]
+    return np.array(dens), np.array(comp)
+
+
+def _flat_case(c, eos):
+    mixd, sc = paper_mixture(c["components"], c["T_K"], eos, c["kappa"])
+    mix = oracle_mixture(mixd)
+    M = np.array(mixd["M"])
+    f = flash(mix, c["p_bar"] * sc["p"], c["z"])
+    rho = inputs.slab(f["rtV"] * M, f["rtL"] * M, c["nx"], c["ny"], vapour_volume_fraction(f), c["W"])
+    return mixd, mix, M, rho
+
+
+@pytest.mark.parametrize("eos", ["pr", "srk"])
+def test_v_a_propane_pentane_flat_interface(fm, eos):
+    # paper (Table tabcase1error): every relative error below 3e-4 %, after 1e6 steps.
+    # Here, after the same 1e6 FP64 steps: up to about 3e-3 % (GB300; after 5e5 steps the
+    # bulk is still relaxing, up to 0.04 %); bound 0.01 %.
+    c = CASES["c3c5_flat"]
+    mixd, mix, M, rho = _flat_case(c, eos)
+    r, u, _ = _relax(fm, mixd, rho, c["tau"], c["steps"])
+    L, V = _bulk_phases(r, M)
+    dens, comp = _errors_percent(mix, M, L, V, c["z"])
+    print(eos, "density error %", dens, "composition error %", comp)
+    assert np.max(dens) < 0.01 and np.max(comp) < 0.01, (dens, comp)
+    assert np.max(np.abs(lnf_density_form(mix, L) - lnf_density_form(mix, V))) < 1e-4
+
+
+def test_v_c_methane_ethane_propane_flat_interface(fm):
+    # paper (Table tabcase3): density errors 0.07 %, composition errors up to 0.92 %.
+    # Here, after 3e5 FP64 steps: density 0.07-0.16 %, compositions up to about 1 % (the
+    # same pattern: ethane and propane carry the largest errors); bounds 0.3 % and 1.5 %.
+    # The thin liquid slab (vapour fraction 0.78) translates slowly, so the bulk phases
+    # are located on the profile rather than at fixed nodes.
+    # The overall composition for the flash is the lattice's own (three components: the
+    # phase compositions depend on it).
+    c = CASES["c1c2c3_flat"]
+    mixd, mix, M, rho = _flat_case(c, "pr")
+    r, u, _ = _relax(fm, mixd, rho, c["tau"], 300000)
+    L, V = _bulk_phases(r, M)
+    z = (r / M[:, None, None]).sum(axis=(1, 2))
+    dens, comp = _errors_percent(mix, M, L, V, z / z.sum())
+    print("ternary density error %", dens, "composition error %", comp)
+    assert np.max(dens) < 0.3, dens
+    assert np.max(comp) < 1.5, comp
+
+
+def test_v_d_spinodal_decomposition_iso_fugacity(fm):
+    # paper (Table tabFug): liquid 35.1276 / 4.4563 bar, vapour 35.1262 / 4.4567 bar.
+    # A uniform C2/C5 state at 50 bar (the single volume root at x = 0.62 / 0.38) with a
+    # seeded 1% fluctuation of the total density separates within 5e5 steps (the paper's
+    # count).  FP64: at the densest and the least dense node the fugacities agree to 1e-3
+    # (4e-4 measured) and lie within 1% of the table's (0.35% measured; the final pressure
+    # depends on the curvature the separation ends with, which depends on the
+    # fluctuation).  FP32 storage separates the same way but its fugacities agree only to
+    # about 4e-3 (the force balance is computed in single precision).
+    c = CASES["spinodal"]
+    mixd, sc = paper_mixture(c["components"], c["T_K"], "pr", c["kappa"])
+    mix = oracle_mixture(mixd)
+    M = np.array(mixd["M"])
+    x = np.array(c["x"])
+    v = np.sort(volume_roots(mix, c["p_bar"] * sc["p"], x))
+    rt = x / v[len(v) // 2]
+    xi = inputs.uniform_noise(7, 0, 0, c["nx"] * c["ny"]).reshape(c["ny"], c["nx"])
+    rho = (rt * M)[:, None, None] * (1.0 + 0.01 * xi)[None]
+    r, u, _ = _relax(fm, mixd, rho, c["tau"], c["steps"], precision="fp64", stencil="isotropic")
+    tot = r.sum(axis=0)
+    assert tot.max() / tot.min() > 2.5  # two phases
+    a = np.unravel_index(np.argmax(tot), tot.shape)
+    b = np.unravel_index(np.argmin(tot), tot.shape)
+    fL = np.exp(lnf_density_form(mix, r[:, a[0], a[1]] / M)) / sc["p"]   # bar
+    fV = np.exp(lnf_density_form(mix, r[:, b[0], b[1]] / M)) / sc["p"]
+    print("fugacities (bar) liquid", fL, "vapour", fV)
+    assert np.max(np.abs(fL / fV - 1)) < 1e-3, (fL, fV)
+    paper = 0.5 * (np.array(c["fugacity_liquid_bar"]) + np.array(c["fugacity_vapor_bar"]))
+    assert np.max(np.abs(fL / paper - 1)) < 0.01, (fL, paper)
+
+
+def test_v_e_oscillating_droplet_period(fm):
+    # paper: period 1787.5 steps from the lattice, 1717.5 from Eq. eqPeriod (its sigma
+    # is not printed).  Exploratory run here: about 1765 steps from the lattice and about
+    # 1753 from Eq. eqPeriod with sigma of Eq. eqMCsigma on a flat interface at the same
+    # state; bounds 3% against each.
+    c = CASES["oscillating_droplet"]
+    mixd, sc = paper_mixture(c["components"], c["T_K"], "pr", c["kappa"])
+    mix = oracle_mixture(mixd)
+    M = np.array(mixd["M"])
+    f = flash(mix, c["p_bar"] * sc["p"], [0.4, 0.6])
+    rhoL, rhoV = (f["rtL"] * M).sum(), (f["rtV"] * M).sum()
+    assert abs(rhoL / rhoV - c["mass_density_ratio"]) < 0.006
+    nx, ny = c["nx"], c["ny"]
+    rho = inputs.droplet(f["rtV"] * M, f["rtL"] * M, nx, ny, c["R0"], c["W"], c["h"])
+    lat = fm.Lattice(fm.mixture_from_dict(mixd), nx, ny, c["tau"], "isotropic", "fp64", "lagged")
+    lat.init(rho)
+    level = 0.5 * (rhoL + rhoV)
+    t, rx = [], []
+    for k in range(0, c["steps"] + 1, 10):
+        if k:
+            lat.step(10)
+        tot = lat.moments()[0].sum(axis=0)
+        t.append(k)
+        rx.append(crossing_radius(tot[ny // 2, :], nx / 2, level))   # along the major (x) axis
+    lat.close()
+    t, rx = np.array(t, dtype=np.float64), np.array(rx)
+    assert np.all(np.isfinite(rx))
+    model = lambda s, A, T, ph, td, c0, c1: c0 + c1 * s + A * np.cos(2 * np.pi * s / T + ph) * np.exp(-s / td)
+    p, _ = curve_fit(model, t, rx, p0=[rx[0] - rx[-1], 1750.0, 0.0, 2000.0, rx[-1], 0.0], maxfev=20000)
+    period = abs(p[1])
+    # sigma from a relaxed flat interface at the same state
+    slab = inputs.slab(f["rtV"] * M, f["rtL"] * M, 200, 2, 0.5, c["W"])
+    r1, _, _ = _relax(fm, mixd, slab, c["tau"], 100000, stencil="isotropic")
+    sigma = interfacial_tension(r1[:, 0, :] / M[:, None], mixd["kappa"], n_interfaces=2)
+    rho_liquid = float(r1[:, 0, 100].sum())
+    Ta = lamb_period(sigma, rho_liquid, c["R0"] * np.sqrt(c["h"]), c["mode"])
+    print("period", period, "Lamb", Ta, "sigma", sigma)
+    assert abs(period / c["period_lbm_steps"] - 1) < 0.03, period
+    assert abs(period / Ta - 1) < 0.03, (period, Ta)
