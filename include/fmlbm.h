@@ -83,6 +83,17 @@ typedef enum fmlbm_precision {
  * always uses the current force. */
 typedef enum fmlbm_velocity_force { FMLBM_FORCE_LAGGED = 0, FMLBM_FORCE_CURRENT = 1 } fmlbm_velocity_force;
 
+/* Which lattice Boltzmann formulation carries the fugacity force.  WELL_BALANCED
+ * (default, the method of Section III): equilibrium of Eq. eqLBEMCb with rho_0 = 0,
+ * forcing term of Eq. eqLBEMCfinal3, force of Eq. eqforcefinal.  STANDARD (Section VI):
+ * the standard equilibrium rho_i w_a [1 + ...] and Guo forcing term of Eq. eqLBE per
+ * component, with the force of Eq. eqForceGen (Eq. eqforcefinal + c_s^2 grad rho_i);
+ * its equilibria deviate slightly from thermodynamics, more for larger density ratios.
+ * STANDARD needs FP64 or FP32 storage (the 16-bit forms store deviations from the
+ * well-balanced rest state), runs the plain step with 8-row tiles (no TMA form,
+ * fmlbm_set_tile_height does not apply) and is not accepted by batches or servers. */
+typedef enum fmlbm_formulation { FMLBM_WELL_BALANCED = 0, FMLBM_STANDARD = 1 } fmlbm_formulation;
+
 /* A mixture at fixed temperature in consistent units (the paper's lattice units:
  * R = 1 and a = 2/49, b = 2/21 for the most volatile component, Section V).
  * a_i, b_i, alpha_i follow from Tc, Pc, omega and T by Appendix C. kij is the
@@ -106,7 +117,7 @@ typedef struct fmlbm_lattice {
     int32_t stencil;                      /* fmlbm_stencil                           */
     int32_t precision;                    /* fmlbm_precision                         */
     int32_t velocity_force;               /* fmlbm_velocity_force                    */
-    int32_t reserved;                     /* must be 0                               */
+    int32_t formulation;                  /* fmlbm_formulation                       */
 } fmlbm_lattice;
 
 typedef struct fmlbm_handle fmlbm_handle;

@@ -161,7 +161,16 @@ bool lattice_ok(const fmlbm_lattice& L, int nc, std::string* why) {
         *why = "unknown velocity_force";
         return false;
     }
-    if (L.reserved != 0) { *why = "reserved must be 0"; return false; }
+    if (L.formulation != FMLBM_WELL_BALANCED && L.formulation != FMLBM_STANDARD) {
+        *why = "unknown formulation";
+        return false;
+    }
+    if (L.formulation == FMLBM_STANDARD && L.precision != FMLBM_FP64 && L.precision != FMLBM_FP32) {
+        // the 16-bit forms store g_a (a != 0) as deviations from the well-balanced rest
+        // state, 0; the standard rest state w_a rho_i would not fit their range
+        *why = "the standard formulation needs FP64 or FP32 storage";
+        return false;
+    }
     return true;
 }
 
@@ -172,6 +181,7 @@ StepArgs make_args(const fmlbm_handle* h, int src) {
     A.ny = h->lattice.ny;
     A.stencil = h->lattice.stencil;
     A.lagged = h->lattice.velocity_force == FMLBM_FORCE_LAGGED;
+    A.standard = h->lattice.formulation == FMLBM_STANDARD;
     A.gin = h->g[src];
     A.g0in = h->g0[src];
     A.gout = h->g[src ^ 1];
@@ -235,6 +245,7 @@ void setup_tma(fmlbm_handle* h) {
     h->tma_maps = false;
     const int p = h->lattice.precision, nc = h->nc, nx = h->lattice.nx, ny = h->lattice.ny;
     if (!tma_supported_for(p, nc) || nx < kTX + 6 || ny < kTmaTileY + 6) return;
+    if (h->lattice.formulation != FMLBM_WELL_BALANCED) return;  // the TMA forms are well-balanced only
     const int H = kTmaTileY + 6;
     bool ok = true;
     for (int b = 0; b < 2 && ok; ++b) {

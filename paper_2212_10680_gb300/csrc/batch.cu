@@ -381,6 +381,8 @@ fmlbm_status fmlbm_batch_add(fmlbm_batch* b, const fmlbm_mixture* mixture, const
     if (!b || !mixture || !lattice || !rho_host || !slot_out) return bfail(b, FMLBM_E_INVALID_ARG, "null argument");
     if (mixture->n_components != b->nc) return bfail(b, FMLBM_E_INVALID_ARG, "component count differs from the batch");
     if (lattice->precision != b->precision) return bfail(b, FMLBM_E_INVALID_ARG, "precision differs from the batch");
+    if (lattice->formulation != FMLBM_WELL_BALANCED)
+        return bfail(b, FMLBM_E_INVALID_ARG, "batches run the well-balanced formulation only");
     std::string why;
     MixConst mc;
     if (!fmlbm_internal_mixture_constants(*mixture, &mc, &why) ||

@@ -100,6 +100,7 @@ struct StepArgs {
     int nx, ny;
     int stencil;      // 0 isotropic, 1 central
     int lagged;       // 1: u uses the stored force of the previous step
+    int standard;     // 1: standard formulation (Eq. eqLBE, force of Eq. eqForceGen)
     const void* gin;  // F64/F32: all planes; DEV: 16-bit planes a = 1..8
     const float* g0in;  // DEV: float planes a = 0
     void* gout;
@@ -464,7 +465,10 @@ __device__ __forceinline__ void phase2(const MixConstT<Real>& m, StepSmem<Real, 
 
 // Phase 3 at one valid node: force (step 7), velocity (step 1), equilibrium and forcing
 // (step 8), collision (step 9), coalesced stores at the node.
-template <int NC, int ST, int TY, bool MOMENTS>
+// STD: the standard formulation of Section VI -- equilibrium rho_i w_a [1 + ...] of
+// Eq. eqLBE, Guo's forcing term of Eq. eqLBEfinal3 (no grad rho_i part) and
+// F_i + c_s^2 grad rho_i of Eq. eqForceGen.
+template <int NC, int ST, int TY, bool MOMENTS, bool STD = false>
 __device__ __forceinline__ void phase3(const StepArgs& A, const MixConstT<typename StoreTraits<ST>::Real>& m,
                                        StepSmem<typename StoreTraits<ST>::Real, NC, TY>& S,
                                        const typename StoreTraits<ST>::Real (&g)[NC][9], int tx, int ty, int gxn,
@@ -480,15 +484,19 @@ __device__ __forceinline__ void phase3(const StepArgs& A, const MixConstT<typena
         grad_at<Real>(S.G, i, cx, cy, A.stencil, px, py);
         grad_at<Real>(S.rt, i, cx + 1, cy + 1, A.stencil, rx, ry);
         const Real rti = S.rt.v[i][cy + 1][cx + 1];
+        // grad rho_i = M_i grad rho~_i
+        grx[i] = rx * m.M[i];
+        gry[i] = ry * m.M[i];
         // Eq. eqforcefinal: F_i = -rho~_i RT grad ln f_i + rho~_i grad(sum_j kappa_ij lap rho~_j)
         //                      = rho~_i grad Phi_i (the stencils are linear)
         Fx[i] = rti * px;
         Fy[i] = rti * py;
+        if constexpr (STD) {  // Eq. eqForceGen: + c_s^2 grad rho_i
+            Fx[i] += Real(1.0 / 3.0) * grx[i];
+            Fy[i] += Real(1.0 / 3.0) * gry[i];
+        }
         Ftx += Fx[i];
         Fty += Fy[i];
-        // grad rho_i = M_i grad rho~_i
-        grx[i] = rx * m.M[i];
-        gry[i] = ry * m.M[i];
         // zeroth and first moments with e_a in {0, +-1} written out: IEEE arithmetic keeps
         // every 0 * g_a the compiler is given
         const Real(&h)[9] = g[i];
@@ -543,28 +551,34 @@ __device__ __forceinline__ void phase3(const StepArgs& A, const MixConstT<typena
         for (int i = 0; i < NC; ++i) {
             const Real(&h)[9] = g[i];
             const Real rw = omega * rhoi[i];
+            // the forcing term's grad rho_i part belongs to the well-balanced scheme only
+            const Real gX = STD ? Real(0) : grx[i], gY = STD ? Real(0) : gry[i];
+            // the standard equilibrium adds w_a rho_i (a != 0) and (w_0 - 1) rho_i (a = 0);
+            // -0 in the well-balanced case: x + (-0) is x exactly, so the compiler drops it
+            const Real rwS = STD ? rw : Real(-0.0);
             const Real uF = ux * Fx[i] + uy * Fy[i];
-            const Real ug = ux * grx[i] + uy * gry[i];
+            const Real ug = ux * gX + uy * gY;
             const Real a0 = -(rw * usq15 + fc3 * uF);  // -base - 3 fc uF
             const Real cb_ax = a0 - Real(0.5) * fc * ug;
             const Real cb_dg = a0 + fc * ug;
             const Real rw45 = Real(4.5) * rw, rw3 = rw * Real(1.0 / 3.0);
-            const Real Vx = rw45 * ux + (fc9 * Fx[i] + fc3 * grx[i]);
-            const Real Vy = rw45 * uy + (fc9 * Fy[i] + fc3 * gry[i]);
+            const Real Vx = rw45 * ux + (fc9 * Fx[i] + fc3 * gX);
+            const Real Vy = rw45 * uy + (fc9 * Fy[i] + fc3 * gY);
             const Real Ox = rw3 * ux + fc_3 * Fx[i];
             const Real Oy = rw3 * uy + fc_3 * Fy[i];
+            const Real rest0 = STD ? Real(4.0 / 9.0) * rw : rw;
             store_g<ST>(A, i, 0, (size_t)node, (size_t)nxy,
-                        keep * h[0] + (rw + Real(4.0 / 9.0) * (a0 - Real(2) * fc * ug)));
-            const Real e1 = w1 * (ux * Vx + cb_ax);
+                        keep * h[0] + (rest0 + Real(4.0 / 9.0) * (a0 - Real(2) * fc * ug)));
+            const Real e1 = w1 * (ux * Vx + cb_ax + rwS);
             store_g<ST>(A, i, 1, (size_t)node, (size_t)nxy, keep * h[1] + (e1 + Ox));
             store_g<ST>(A, i, 3, (size_t)node, (size_t)nxy, keep * h[3] + (e1 - Ox));
-            const Real e2 = w1 * (uy * Vy + cb_ax);
+            const Real e2 = w1 * (uy * Vy + cb_ax + rwS);
             store_g<ST>(A, i, 2, (size_t)node, (size_t)nxy, keep * h[2] + (e2 + Oy));
             store_g<ST>(A, i, 4, (size_t)node, (size_t)nxy, keep * h[4] + (e2 - Oy));
-            const Real e5 = w5 * (u5 * (Vx + Vy) + cb_dg), o5 = Real(0.25) * (Ox + Oy);
+            const Real e5 = w5 * (u5 * (Vx + Vy) + cb_dg + rwS), o5 = Real(0.25) * (Ox + Oy);
             store_g<ST>(A, i, 5, (size_t)node, (size_t)nxy, keep * h[5] + (e5 + o5));
             store_g<ST>(A, i, 7, (size_t)node, (size_t)nxy, keep * h[7] + (e5 - o5));
-            const Real e6 = w5 * (u6 * (Vy - Vx) + cb_dg), o6 = Real(0.25) * (Oy - Ox);
+            const Real e6 = w5 * (u6 * (Vy - Vx) + cb_dg + rwS), o6 = Real(0.25) * (Oy - Ox);
             store_g<ST>(A, i, 6, (size_t)node, (size_t)nxy, keep * h[6] + (e6 + o6));
             store_g<ST>(A, i, 8, (size_t)node, (size_t)nxy, keep * h[8] + (e6 - o6));
         }
@@ -678,7 +692,7 @@ __device__ __forceinline__ Real diag_strip(const Real (*red)[NC + 2], int row0, 
 
 // MOMENTS = true: compute the macroscopic fields of the current state instead of
 // advancing it (no distribution or force store).
-template <int NC, int ST, int TY, bool MOMENTS>
+template <int NC, int ST, int TY, bool MOMENTS, bool STD = false>
 // Float arithmetic: 1024 resident threads per SM (64 registers a thread), measured faster
 // than trading occupancy for registers (77 registers and three 8-row blocks per SM were 7%
 // slower for three components) or registers for occupancy (48 registers spill).  The FP64
@@ -712,7 +726,7 @@ __global__ void __launch_bounds__(kTX* TY, ST == ST_F64 ? 1 : 1024 / (kTX * TY))
     __syncthreads();
     phase2<NC, TY, Real>(m, S, A.stencil, tid);
     __syncthreads();
-    if (gxn < nx && gyn < ny) phase3<NC, ST, TY, MOMENTS>(A, m, S, g, tx, ty, gxn, gyn);
+    if (gxn < nx && gyn < ny) phase3<NC, ST, TY, MOMENTS, STD>(A, m, S, g, tx, ty, gxn, gyn);
     if constexpr (!MOMENTS) {
         if (A.diag_partial != nullptr) {  // uniform: diagnostics of the state this step read
             static_assert(TY % 8 == 0, "diagnostics strips of 8 rows");
@@ -748,7 +762,8 @@ __global__ void __launch_bounds__(kTX* TY, ST == ST_F64 ? 1 : 1024 / (kTX * TY))
     }
 }
 
-// g = g^eq(rho, u = 0): rho_i in a = 0, zero elsewhere; stored force zero.
+// g = g^eq(rho, u = 0): rho_i in a = 0, zero elsewhere (well-balanced); w_a rho_i in every
+// direction (standard formulation, stored where the next pull reads it); stored force zero.
 template <int NC, int ST>
 __global__ void init_rest(StepArgs A, const double* __restrict__ rho) {
     using Real = typename StoreTraits<ST>::Real;
@@ -758,8 +773,20 @@ __global__ void init_rest(StepArgs A, const double* __restrict__ rho) {
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
             const Real r = (Real)rho[(size_t)i * nxy + node];
+            if (!A.standard) {
 #pragma unroll
-            for (int a = 0; a < 9; ++a) store_g<ST>(A, i, a, node, nxy, a == 0 ? r : Real(0));
+                for (int a = 0; a < 9; ++a) store_g<ST>(A, i, a, node, nxy, a == 0 ? r : Real(0));
+            } else {
+                // the buffer holds what the next pull reads: g_a(s + e_a) is stored at s, so
+                // direction a takes w_a rho at the node s + e_a (periodic)
+                const int x = (int)(node % A.nx), y = (int)(node / A.nx);
+#pragma unroll
+                for (int a = 0; a < 9; ++a) {
+                    const int xs = wrap(x + ex(a), A.nx), ys = wrap(y + ey(a), A.ny);
+                    const Real ra = (Real)rho[(size_t)i * nxy + (size_t)ys * A.nx + xs];
+                    store_g<ST>(A, i, a, node, nxy, wgt<Real>(a) * ra);
+                }
+            }
         }
         Real* F = static_cast<Real*>(A.Fout);
         F[node] = Real(0);

@@ -57,12 +57,12 @@ inline cudaError_t launch_reduce_final(int nc, bool fp64, const void* partial, i
 }
 
 #define FMLBM_DEFINE_LAUNCHERS(ST)                                                                        \
-    template <int NC, bool MOM, int TY>                                                                   \
+    template <int NC, bool MOM, int TY, bool STD = false>                                                 \
     static cudaError_t launch_step_nc_##ST(const StepArgs& A, cudaStream_t s) {                           \
         using Real = typename StoreTraits<ST>::Real;                                                      \
         /* + the diagnostics snapshot copy of the tile's nodes */                                       \
         constexpr size_t smem = sizeof(StepSmem<Real, NC, TY>) + (MOM ? 0 : (size_t)NC * TY * kTX * sizeof(Real)); \
-        auto k = fused_step<NC, ST, TY, MOM>;                                                             \
+        auto k = fused_step<NC, ST, TY, MOM, STD>;                                                        \
         static bool attr_done = false;                                                                    \
         if (!attr_done) {                                                                                 \
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
@@ -75,6 +75,14 @@ inline cudaError_t launch_reduce_final(int nc, bool fp64, const void* partial, i
     }                                                                                                     \
     template <int NC>                                                                                     \
     static cudaError_t launch_step_ty_##ST(const StepArgs& A, bool moments, int tile_y, cudaStream_t s) { \
+        /* the standard formulation: FP64 and FP32 storage, 8-row tiles */                              \
+        if constexpr (ST == ST_F64 || ST == ST_F32) {                                                     \
+            if (A.standard)                                                                               \
+                return moments ? launch_step_nc_##ST<NC, true, kTileYSmall, true>(A, s)                   \
+                               : launch_step_nc_##ST<NC, false, kTileYSmall, true>(A, s);                 \
+        } else {                                                                                          \
+            if (A.standard) return cudaErrorNotSupported;                                                 \
+        }                                                                                                 \
         if (tile_y == kTileYLarge)                                                                        \
             return moments ? launch_step_nc_##ST<NC, true, kTileYLarge>(A, s)                             \
                            : launch_step_nc_##ST<NC, false, kTileYLarge>(A, s);                           \

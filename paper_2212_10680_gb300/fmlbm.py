@@ -23,6 +23,7 @@ EOS = {"pr": 0, "srk": 1, "vdw": 2}
 STENCIL = {"isotropic": 0, "central": 1}
 PRECISION = {"fp64": 0, "fp32": 1, "fp16dev": 2, "bf16dev": 3}
 VELOCITY_FORCE = {"lagged": 0, "current": 1}
+FORMULATION = {"well_balanced": 0, "standard": 1}
 STATUS = {0: "FMLBM_OK", 1: "FMLBM_E_INVALID_ARG", 2: "FMLBM_E_OOM", 3: "FMLBM_E_CUDA",
           4: "FMLBM_E_NONPHYSICAL", 5: "FMLBM_E_TIMEOUT", 6: "FMLBM_E_BUSY", 7: "FMLBM_E_NOT_CONVERGED",
           8: "FMLBM_E_UNSUPPORTED"}
@@ -49,7 +50,7 @@ class fmlbm_mixture(ctypes.Structure):
 class fmlbm_lattice(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("tau", ctypes.c_double),
                 ("stencil", ctypes.c_int32), ("precision", ctypes.c_int32), ("velocity_force", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("formulation", ctypes.c_int32)]
 
 
 class fmlbm_server_config(ctypes.Structure):
@@ -182,13 +183,13 @@ def mixture_from_dict(d: dict) -> fmlbm_mixture:
 
 
 def make_lattice(nx: int, ny: int, tau: float, stencil: str = "isotropic", precision: str = "fp32",
-                 velocity_force: str = "lagged") -> fmlbm_lattice:
+                 velocity_force: str = "lagged", formulation: str = "well_balanced") -> fmlbm_lattice:
     L = fmlbm_lattice()
     L.nx, L.ny, L.tau = nx, ny, tau
     L.stencil = STENCIL[stencil]
     L.precision = PRECISION[precision]
     L.velocity_force = VELOCITY_FORCE[velocity_force]
-    L.reserved = 0
+    L.formulation = FORMULATION[formulation]
     return L
 
 
@@ -455,10 +456,12 @@ class Lattice:
     """One lattice on the current CUDA device; a convenience owner of a handle."""
 
     def __init__(self, mixture: fmlbm_mixture, nx: int, ny: int, tau: float, stencil: str = "isotropic",
-                 precision: str = "fp32", velocity_force: str = "lagged", stream: int = 0):
+                 precision: str = "fp32", velocity_force: str = "lagged", stream: int = 0,
+                 formulation: str = "well_balanced"):
         self.n = mixture.n_components
         self.nx, self.ny = nx, ny
-        self.h = fmlbm_create(mixture, make_lattice(nx, ny, tau, stencil, precision, velocity_force), stream)
+        self.h = fmlbm_create(mixture, make_lattice(nx, ny, tau, stencil, precision, velocity_force, formulation),
+                              stream)
 
     def init(self, rho: np.ndarray):
         fmlbm_init(self.h, rho)

@@ -54,10 +54,10 @@ def slab_state_binary(nx, ny, seed=1, W=4.0):
     return wl["mixture"], inputs.with_noise(rho, 0.01, seed)
 
 
-def run_oracle(mixd, rho, tau, stencil, velocity_force, steps, record=()):
+def run_oracle(mixd, rho, tau, stencil, velocity_force, steps, record=(), formulation="well_balanced"):
     mix = oracle_mixture(mixd)
-    lat = lbm.Lattice(tau=tau, stencil=stencil, velocity_force=velocity_force)
-    g, F = lbm.init_at_rest(rho)
+    lat = lbm.Lattice(tau=tau, stencil=stencil, velocity_force=velocity_force, formulation=formulation)
+    g, F = lbm.init_at_rest(rho, formulation=formulation)
     out = {}
     for k in range(1, steps + 1):
         g, F = lbm.step(g, mix, lat, F)

@@ -24,8 +24,9 @@ def fm():
     return fmlbm
 
 
-def _gpu_run(fm, mixd, rho, tau, stencil, precision, velocity_force, steps, record):
-    lat = fm.Lattice(fm.mixture_from_dict(mixd), rho.shape[2], rho.shape[1], tau, stencil, precision, velocity_force)
+def _gpu_run(fm, mixd, rho, tau, stencil, precision, velocity_force, steps, record, formulation="well_balanced"):
+    lat = fm.Lattice(fm.mixture_from_dict(mixd), rho.shape[2], rho.shape[1], tau, stencil, precision, velocity_force,
+                     formulation=formulation)
     lat.init(rho)
     out = {}
     done = 0
@@ -348,3 +349,42 @@ def test_autotune_keeps_results(fm):
     g2, F2 = b.distributions()
     b.close()
     assert np.array_equal(g1, g2) and np.array_equal(F1, F2)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("stencil,velocity_force", [("isotropic", "lagged"), ("central", "current")])
+def test_standard_formulation_parity(fm, precision, stencil, velocity_force):
+    # Section VI: Eq. eqLBE per component with the force of Eq. eqForceGen, against the
+    # oracle's standard formulation (70 x 37: ragged tiles in both directions).  A smooth
+    # near-critical field: the standard form drives the vapour of the benchmark slab at
+    # 0.8 Tc negative within a few steps (its errors grow with the density ratio).
+    mixd = mixture_dict(n=2, Tr=1.05 if velocity_force == "lagged" else 1.1, kappa_scale=0.5 if velocity_force ==
+                        "lagged" else 0.2, M=[1.0, 1.6])
+    rho = smooth_state(2, 70, 37, seed=18)
+    rec = (1, 3, 12)
+    ora = run_oracle(mixd, rho, 0.9, stencil, velocity_force, max(rec), rec, formulation="standard")
+    gpu = _gpu_run(fm, mixd, rho, 0.9, stencil, precision, velocity_force, max(rec), rec, formulation="standard")
+    _compare(gpu, ora, TOL[precision], mixd)
+
+
+def test_standard_formulation_limits(fm):
+    mixd, rho = slab_state_binary(64, 16, seed=19)
+    # the 16-bit forms hold deviations from the well-balanced rest state only
+    with pytest.raises(fm.FmlbmError) as ei:
+        fm.Lattice(fm.mixture_from_dict(mixd), 64, 16, 1.0, "isotropic", "bf16dev", "lagged", formulation="standard")
+    assert ei.value.status == 1
+    lat = fm.Lattice(fm.mixture_from_dict(mixd), 64, 64, 1.0, "isotropic", "fp32", "lagged", formulation="standard")
+    with pytest.raises(fm.FmlbmError) as ei:
+        fm.fmlbm_set_step_variant(lat.h, "tma_tile")
+    assert ei.value.status == 8
+    lat.close()
+    # the rest state is w_a rho_i(r) in every direction, as the oracle's
+    from oracle import lbm
+    for precision, tol in (("fp64", 1e-15), ("fp32", 1e-7)):
+        lat = fm.Lattice(fm.mixture_from_dict(mixd), 64, 16, 1.0, "isotropic", precision, "lagged",
+                         formulation="standard")
+        lat.init(rho)
+        g, F = lat.distributions()
+        lat.close()
+        g_ref, _ = lbm.init_at_rest(rho, formulation="standard")
+        assert np.max(np.abs(g - g_ref)) <= tol * np.max(np.abs(g_ref)) and not F.any()
