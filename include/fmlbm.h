@@ -124,8 +124,8 @@ typedef struct fmlbm_handle fmlbm_handle;
 
 /* Creates a lattice: validates the mixture (Appendix C parameters) and lattice,
  * allocates its device buffers (two distribution buffers, two force buffers,
- * a density snapshot for the residual and reduction scratch) on the current
- * device, and leaves it uninitialised.  cuda_stream: a cudaStream_t (may be
+ * a density snapshot for the residual and reduction scratch) and a second stream for
+ * diagnostics on the current device, and leaves it uninitialised.  cuda_stream: a cudaStream_t (may be
  * NULL), owned by the caller, must outlive the handle. */
 fmlbm_status fmlbm_create(const fmlbm_mixture* mixture, const fmlbm_lattice* lattice,
                           void* cuda_stream, fmlbm_handle** out);
@@ -176,7 +176,9 @@ fmlbm_status fmlbm_diagnostics(fmlbm_handle* h, double* mass, double* residual, 
  * TMA forms run the separate reduction before stepping), so a loop that steps and asks
  * every step adds no extra pass over the lattice; if no step follows,
  * fmlbm_diagnostics_wait runs the separate reduction.  Results are bit-identical either
- * way.  fmlbm_diagnostics_wait blocks until the ticket's results have reached the host
+ * way.  The final sum and the copies to the host of a request served inside a step run
+ * on a second, non-blocking stream of the handle, ordered by events, so the next step
+ * does not wait for them (while the handle's stream is being captured they stay on it).  fmlbm_diagnostics_wait blocks until the ticket's results have reached the host
  * (it does not wait for work enqueued after them) and returns them with the state's
  * step count; it reports a latched FMLBM_E_NONPHYSICAL or FMLBM_E_TIMEOUT as of that
  * point.  Four results are kept: a ticket older than the four most recent requests
@@ -231,7 +233,8 @@ fmlbm_status fmlbm_autotune(fmlbm_handle* h, int32_t steps_per_trial, int32_t* v
 /* The kernel fmlbm_step will use (PLAIN, TMA or TMA_TILE). */
 fmlbm_status fmlbm_get_step_variant(fmlbm_handle* h, int32_t* variant);
 
-/* Waits for the handle's stream and reports latched kernel errors. */
+/* Waits for the handle's streams (including its diagnostics stream) and reports latched
+ * kernel errors. */
 fmlbm_status fmlbm_synchronize(fmlbm_handle* h);
 
 /* Device bytes one lattice of this shape and precision holds (for admission

@@ -44,8 +44,11 @@ struct fmlbm_handle {
     int cur = 0;
     void* rho_prev = nullptr;     // storage arithmetic type
     int have_prev = 0;
-    void* partial = nullptr;         // per-strip sums, storage arithmetic type (8 bytes reserved each)
-    double* diag_dev = nullptr;
+    void* partial = nullptr;         // two sets of per-strip sums (storage type, 8 bytes reserved each)
+    double* diag_dev = nullptr;      // kDiagSlots x kDiagWords results, then the error latch
+    cudaStream_t tail = nullptr;     // final sums and copies of fused requests (non-blocking)
+    cudaEvent_t part_ev[2] = {};     // [parity]: partial sums of a fused request written
+    cudaEvent_t tail_done[2] = {};   // [parity]: the tail that read them has finished
     double* diag_host = nullptr;     // pinned: kDiagSlots x kDiagWords doubles (results + error latch)
     cudaEvent_t diag_ev[kDiagSlots] = {};
     DiagSlot slot[kDiagSlots];
@@ -309,12 +312,12 @@ cudaError_t dispatch_convert(const fmlbm_handle* h, const StepArgs& A, const dou
         default: return launch_convert<ST_BF16DEV>(A, h->nc, gi, go, to, h->stream);
     }
 }
-cudaError_t dispatch_reduce(fmlbm_handle* h, const StepArgs& A) {
+cudaError_t dispatch_reduce(fmlbm_handle* h, const StepArgs& A, void* partial, double* out) {
     switch (h->lattice.precision) {
-        case FMLBM_FP64: return launch_reduce<ST_F64>(A, h->nc, h->rho_prev, h->have_prev, h->partial, h->diag_dev, h->stream);
-        case FMLBM_FP32: return launch_reduce<ST_F32>(A, h->nc, h->rho_prev, h->have_prev, h->partial, h->diag_dev, h->stream);
-        case FMLBM_FP16DEV: return launch_reduce<ST_F16DEV>(A, h->nc, h->rho_prev, h->have_prev, h->partial, h->diag_dev, h->stream);
-        default: return launch_reduce<ST_BF16DEV>(A, h->nc, h->rho_prev, h->have_prev, h->partial, h->diag_dev, h->stream);
+        case FMLBM_FP64: return launch_reduce<ST_F64>(A, h->nc, h->rho_prev, h->have_prev, partial, out, h->stream);
+        case FMLBM_FP32: return launch_reduce<ST_F32>(A, h->nc, h->rho_prev, h->have_prev, partial, out, h->stream);
+        case FMLBM_FP16DEV: return launch_reduce<ST_F16DEV>(A, h->nc, h->rho_prev, h->have_prev, partial, out, h->stream);
+        default: return launch_reduce<ST_BF16DEV>(A, h->nc, h->rho_prev, h->have_prev, partial, out, h->stream);
     }
 }
 
@@ -349,6 +352,11 @@ void release(fmlbm_handle* h) {
     if (h->diag_host) cudaFreeHost(h->diag_host);
     for (int k = 0; k < kDiagSlots; ++k)
         if (h->diag_ev[k]) cudaEventDestroy(h->diag_ev[k]);
+    for (int k = 0; k < 2; ++k) {
+        if (h->part_ev[k]) cudaEventDestroy(h->part_ev[k]);
+        if (h->tail_done[k]) cudaEventDestroy(h->tail_done[k]);
+    }
+    if (h->tail) cudaStreamDestroy(h->tail);
     if (h->err_host) cudaFreeHost(h->err_host);
 }
 
@@ -363,14 +371,25 @@ fmlbm_status reset_state_flags(fmlbm_handle* h) {
     return FMLBM_OK;
 }
 
-// Finish the enqueueing of request `ticket` (the current state): final sum, copy of the
-// results and of the error latch into its host slot, event.  The partial sums are
-// already enqueued (fused step or reduce_partial).
-fmlbm_status enqueue_diag_tail(fmlbm_handle* h, int64_t ticket) {
+// Partial sums of request `ticket`: two sets alternate by ticket parity, so a request's
+// final sum can still read its set while the next step writes the other one.
+void* partial_set(const fmlbm_handle* h, int64_t ticket) {
+    return static_cast<char*>(h->partial) +
+           (size_t)(ticket & 1) * reduce_blocks(h->lattice.nx, h->lattice.ny) * (kMaxC + 2) * sizeof(double);
+}
+double* result_slot(const fmlbm_handle* h, int64_t ticket) { return h->diag_dev + (ticket % kDiagSlots) * kDiagWords; }
+
+// Final sum of request `ticket` (unless already done; its partial sums are enqueued ahead
+// on stream s), copy of the results and of the error latch into its host slot, event.
+fmlbm_status enqueue_diag_tail(fmlbm_handle* h, int64_t ticket, cudaStream_t s, bool final_sum) {
     DiagSlot& sl = h->slot[ticket % kDiagSlots];
     double* host = h->diag_host + (size_t)(ticket % kDiagSlots) * kDiagWords;
-    FM_CUDA(h, cudaMemcpyAsync(host, h->diag_dev, kDiagWords * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    FM_CUDA(h, cudaEventRecord(h->diag_ev[ticket % kDiagSlots], h->stream));
+    if (final_sum)
+        FM_CUDA(h, launch_reduce_final(h->nc, h->lattice.precision == FMLBM_FP64, partial_set(h, ticket),
+                                       h->lattice.nx, h->lattice.ny, result_slot(h, ticket), s));
+    FM_CUDA(h, cudaMemcpyAsync(host, result_slot(h, ticket), (kMaxC + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    FM_CUDA(h, cudaMemcpyAsync(host + kMaxC + 2, h->err_dev, sizeof(ErrorLatch), cudaMemcpyDeviceToHost, s));
+    FM_CUDA(h, cudaEventRecord(h->diag_ev[ticket % kDiagSlots], s));
     sl.have_prev = h->have_prev;
     sl.enqueued = true;
     h->have_prev = 1;
@@ -378,12 +397,15 @@ fmlbm_status enqueue_diag_tail(fmlbm_handle* h, int64_t ticket) {
     return FMLBM_OK;
 }
 
-// The pending request served by a standalone reduction of the current state.
+// The pending request served by a standalone reduction of the current state (all on the
+// handle's stream, after any tail still reading the same set of partial sums).
 fmlbm_status enqueue_pending_standalone(fmlbm_handle* h) {
     if (h->pending < 0) return FMLBM_OK;
+    const int64_t t = h->pending;
     StepArgs A = make_args(h, h->cur);
-    FM_CUDA(h, dispatch_reduce(h, A));
-    return enqueue_diag_tail(h, h->pending);
+    FM_CUDA(h, cudaStreamWaitEvent(h->stream, h->tail_done[t & 1], 0));
+    FM_CUDA(h, dispatch_reduce(h, A, partial_set(h, t), result_slot(h, t)));
+    return enqueue_diag_tail(h, t, h->stream, false);
 }
 
 }  // namespace
@@ -420,7 +442,7 @@ fmlbm_status fmlbm_lattice_bytes(int32_t n_components, const fmlbm_lattice* latt
     buffer_bytes(n_components, *lattice, &gb, &g0b, &fb);
     const size_t nxy = (size_t)lattice->nx * lattice->ny;
     *bytes = 2 * (gb + g0b + fb) + (size_t)n_components * nxy * real_size(lattice->precision) +
-             (size_t)reduce_blocks(lattice->nx, lattice->ny) * (FMLBM_MAX_COMPONENTS + 2) * 8 + 256;
+             2 * (size_t)reduce_blocks(lattice->nx, lattice->ny) * (FMLBM_MAX_COMPONENTS + 2) * 8 + 512;
     return FMLBM_OK;
 }
 
@@ -455,10 +477,14 @@ fmlbm_status fmlbm_create(const fmlbm_mixture* mixture, const fmlbm_lattice* lat
     }
     ok = ok && cudaMalloc(&h->rho_prev, (size_t)h->nc * nxy * real_size(lattice->precision)) == cudaSuccess;
     ok = ok && cudaMalloc(&h->partial,
-                          (size_t)reduce_blocks(lattice->nx, lattice->ny) * (kMaxC + 2) * sizeof(double)) == cudaSuccess;
-    // the diagnostics results and the error latch share one block, so one copy brings both
-    ok = ok && cudaMalloc((void**)&h->diag_dev, kDiagWords * sizeof(double)) == cudaSuccess;
-    if (ok) h->err_dev = reinterpret_cast<ErrorLatch*>(h->diag_dev + kMaxC + 2);
+                          2 * (size_t)reduce_blocks(lattice->nx, lattice->ny) * (kMaxC + 2) * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&h->diag_dev, (kDiagSlots * kDiagWords + 2) * sizeof(double)) == cudaSuccess;
+    if (ok) h->err_dev = reinterpret_cast<ErrorLatch*>(h->diag_dev + kDiagSlots * kDiagWords);
+    ok = ok && cudaStreamCreateWithFlags(&h->tail, cudaStreamNonBlocking) == cudaSuccess;
+    for (int k = 0; k < 2; ++k) {
+        ok = ok && cudaEventCreateWithFlags(&h->part_ev[k], cudaEventDisableTiming) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&h->tail_done[k], cudaEventDisableTiming) == cudaSuccess;
+    }
     ok = ok && cudaMallocHost((void**)&h->diag_host, (size_t)kDiagSlots * kDiagWords * sizeof(double)) == cudaSuccess;
     for (int k = 0; k < kDiagSlots; ++k)
         ok = ok && cudaEventCreateWithFlags(&h->diag_ev[k], cudaEventDisableTiming) == cudaSuccess;
@@ -484,6 +510,7 @@ void fmlbm_destroy(fmlbm_handle* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
+    if (h->tail) cudaStreamSynchronize(h->tail);
     release(h);
     delete h;
 }
@@ -523,16 +550,27 @@ fmlbm_status fmlbm_step(fmlbm_handle* h, int64_t nsteps) {
         StepArgs A = make_args(h, h->cur);
         const int64_t fused = h->pending;
         if (fused >= 0) {  // this step also reduces the state it reads
-            A.diag_partial = h->partial;
+            A.diag_partial = partial_set(h, fused);
             A.rho_prev = h->rho_prev;
             A.have_prev = h->have_prev;
+            // the tail of request fused - 2 may still read this set of partial sums
+            FM_CUDA(h, cudaStreamWaitEvent(h->stream, h->tail_done[fused & 1], 0));
         }
         FM_CUDA(h, dispatch_step(h, A, false));
         if (fused >= 0) {
-            FM_CUDA(h, launch_reduce_final(h->nc, h->lattice.precision == FMLBM_FP64, h->partial, h->lattice.nx,
-                                           h->lattice.ny, h->diag_dev, h->stream));
-            fmlbm_status s = enqueue_diag_tail(h, fused);
+            // final sum and copies on the tail stream, so the next step need not wait for them;
+            // during a stream capture everything stays on the captured stream
+            cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+            FM_CUDA(h, cudaStreamIsCapturing(h->stream, &cap));
+            cudaStream_t ts = h->stream;
+            if (cap == cudaStreamCaptureStatusNone) {
+                FM_CUDA(h, cudaEventRecord(h->part_ev[fused & 1], h->stream));
+                FM_CUDA(h, cudaStreamWaitEvent(h->tail, h->part_ev[fused & 1], 0));
+                ts = h->tail;
+            }
+            fmlbm_status s = enqueue_diag_tail(h, fused, ts, true);
             if (s != FMLBM_OK) return s;
+            FM_CUDA(h, cudaEventRecord(h->tail_done[fused & 1], ts));
         }
         h->cur ^= 1;
         ++h->step;
@@ -611,6 +649,7 @@ fmlbm_status fmlbm_get_step_variant(fmlbm_handle* h, int32_t* variant) {
 
 fmlbm_status fmlbm_synchronize(fmlbm_handle* h) {
     if (!h) return FMLBM_E_INVALID_ARG;
+    FM_CUDA(h, cudaStreamSynchronize(h->tail));
     return sync_and_check(h);
 }
 
