@@ -178,7 +178,10 @@ fmlbm_status fmlbm_diagnostics(fmlbm_handle* h, double* mass, double* residual, 
  * fmlbm_diagnostics_wait runs the separate reduction.  Results are bit-identical either
  * way.  The final sum and the copies to the host of a request served inside a step run
  * on a second, non-blocking stream of the handle, ordered by events, so the next step
- * does not wait for them (while the handle's stream is being captured they stay on it).  fmlbm_diagnostics_wait blocks until the ticket's results have reached the host
+ * does not wait for them.  While the handle's stream is being captured into a CUDA graph
+ * they stay on that stream and are not ordered after diagnostics work still running on
+ * the second stream: call fmlbm_synchronize before capturing if requests were made.
+ * fmlbm_diagnostics_wait blocks until the ticket's results have reached the host
  * (it does not wait for work enqueued after them) and returns them with the state's
  * step count; it reports a latched FMLBM_E_NONPHYSICAL or FMLBM_E_TIMEOUT as of that
  * point.  Four results are kept: a ticket older than the four most recent requests

@@ -381,7 +381,7 @@ double* result_slot(const fmlbm_handle* h, int64_t ticket) { return h->diag_dev 
 
 // Final sum of request `ticket` (unless already done; its partial sums are enqueued ahead
 // on stream s), copy of the results and of the error latch into its host slot, event.
-fmlbm_status enqueue_diag_tail(fmlbm_handle* h, int64_t ticket, cudaStream_t s, bool final_sum) {
+fmlbm_status enqueue_diag_tail(fmlbm_handle* h, int64_t ticket, cudaStream_t s, bool final_sum, bool capturing) {
     DiagSlot& sl = h->slot[ticket % kDiagSlots];
     double* host = h->diag_host + (size_t)(ticket % kDiagSlots) * kDiagWords;
     if (final_sum)
@@ -389,7 +389,12 @@ fmlbm_status enqueue_diag_tail(fmlbm_handle* h, int64_t ticket, cudaStream_t s, 
                                        h->lattice.nx, h->lattice.ny, result_slot(h, ticket), s));
     FM_CUDA(h, cudaMemcpyAsync(host, result_slot(h, ticket), (kMaxC + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
     FM_CUDA(h, cudaMemcpyAsync(host + kMaxC + 2, h->err_dev, sizeof(ErrorLatch), cudaMemcpyDeviceToHost, s));
-    FM_CUDA(h, cudaEventRecord(h->diag_ev[ticket % kDiagSlots], s));
+    // inside a stream capture the record becomes a node of the graph (an external event),
+    // so fmlbm_diagnostics_wait can wait for it after the graph is launched
+    if (capturing)
+        FM_CUDA(h, cudaEventRecordWithFlags(h->diag_ev[ticket % kDiagSlots], s, cudaEventRecordExternal));
+    else
+        FM_CUDA(h, cudaEventRecord(h->diag_ev[ticket % kDiagSlots], s));
     sl.have_prev = h->have_prev;
     sl.enqueued = true;
     h->have_prev = 1;
@@ -403,9 +408,12 @@ fmlbm_status enqueue_pending_standalone(fmlbm_handle* h) {
     if (h->pending < 0) return FMLBM_OK;
     const int64_t t = h->pending;
     StepArgs A = make_args(h, h->cur);
-    FM_CUDA(h, cudaStreamWaitEvent(h->stream, h->tail_done[t & 1], 0));
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    FM_CUDA(h, cudaStreamIsCapturing(h->stream, &cap));
+    const bool capturing = cap != cudaStreamCaptureStatusNone;
+    if (!capturing) FM_CUDA(h, cudaStreamWaitEvent(h->stream, h->tail_done[t & 1], 0));
     FM_CUDA(h, dispatch_reduce(h, A, partial_set(h, t), result_slot(h, t)));
-    return enqueue_diag_tail(h, t, h->stream, false);
+    return enqueue_diag_tail(h, t, h->stream, false, capturing);
 }
 
 }  // namespace
@@ -546,6 +554,15 @@ fmlbm_status fmlbm_step(fmlbm_handle* h, int64_t nsteps) {
         fmlbm_status s = enqueue_pending_standalone(h);  // the TMA forms have no fused reduction
         if (s != FMLBM_OK) return s;
     }
+    // During a stream capture nothing crosses to the diagnostics stream (a captured stream
+    // may not wait on work outside the capture): a request is then served entirely on the
+    // captured stream.
+    bool capturing = false;
+    if (nsteps > 0 && h->pending >= 0) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        FM_CUDA(h, cudaStreamIsCapturing(h->stream, &cap));
+        capturing = cap != cudaStreamCaptureStatusNone;
+    }
     for (int64_t k = 0; k < nsteps; ++k) {
         StepArgs A = make_args(h, h->cur);
         const int64_t fused = h->pending;
@@ -554,23 +571,20 @@ fmlbm_status fmlbm_step(fmlbm_handle* h, int64_t nsteps) {
             A.rho_prev = h->rho_prev;
             A.have_prev = h->have_prev;
             // the tail of request fused - 2 may still read this set of partial sums
-            FM_CUDA(h, cudaStreamWaitEvent(h->stream, h->tail_done[fused & 1], 0));
+            if (!capturing) FM_CUDA(h, cudaStreamWaitEvent(h->stream, h->tail_done[fused & 1], 0));
         }
         FM_CUDA(h, dispatch_step(h, A, false));
         if (fused >= 0) {
-            // final sum and copies on the tail stream, so the next step need not wait for them;
-            // during a stream capture everything stays on the captured stream
-            cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-            FM_CUDA(h, cudaStreamIsCapturing(h->stream, &cap));
+            // final sum and copies on the diagnostics stream, so the next step need not wait
             cudaStream_t ts = h->stream;
-            if (cap == cudaStreamCaptureStatusNone) {
+            if (!capturing) {
                 FM_CUDA(h, cudaEventRecord(h->part_ev[fused & 1], h->stream));
                 FM_CUDA(h, cudaStreamWaitEvent(h->tail, h->part_ev[fused & 1], 0));
                 ts = h->tail;
             }
-            fmlbm_status s = enqueue_diag_tail(h, fused, ts, true);
+            fmlbm_status s = enqueue_diag_tail(h, fused, ts, true, capturing);
             if (s != FMLBM_OK) return s;
-            FM_CUDA(h, cudaEventRecord(h->tail_done[fused & 1], ts));
+            if (!capturing) FM_CUDA(h, cudaEventRecord(h->tail_done[fused & 1], ts));
         }
         h->cur ^= 1;
         ++h->step;

@@ -129,3 +129,32 @@ def test_tma_variant_serves_requests_with_the_separate_kernel(fm):
         lat.close()
     for a, b in zip(*outs):
         _same(a, b)
+
+
+def test_request_served_inside_a_captured_graph(fm):
+    # A request pending while the handle's stream is captured is served on that stream
+    # (no cross-stream events): the graph's first step computes it, and replaying the graph
+    # gives the same state and diagnostics as stepping directly.
+    import torch
+    ref, lat = None, None
+    mixd, rho = slab_state_binary(96, 40, seed=35)
+    ref = fm.Lattice(fm.mixture_from_dict(mixd), 96, 40, 1.0, "isotropic", "fp32", "lagged")
+    ref.init(rho)
+    expect = ref.diagnostics()
+    ref.step(2)
+    g_ref, F_ref = ref.distributions()
+    ref.close()
+    s = torch.cuda.Stream()
+    lat = fm.Lattice(fm.mixture_from_dict(mixd), 96, 40, 1.0, "isotropic", "fp32", "lagged", stream=s.cuda_stream)
+    lat.init(rho)
+    fm.fmlbm_synchronize(lat.h)
+    t = fm.fmlbm_diagnostics_async(lat.h)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        fm.fmlbm_step(lat.h, 2)
+    graph.replay()
+    torch.cuda.synchronize()
+    _same(expect, fm.fmlbm_diagnostics_wait(lat.h, t, 2))
+    g, F = lat.distributions()
+    assert np.array_equal(g, g_ref) and np.array_equal(F, F_ref)
+    lat.close()
