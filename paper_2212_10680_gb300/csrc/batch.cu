@@ -53,8 +53,8 @@ struct fmlbm_batch {
     WorkItem* d_work = nullptr;
     int work_cap = 0, nwork = 0;
     bool work_dirty = true;
-    int tile_y = kTileYLarge;
-    int grid_mult = 2;          // blocks = grid_mult * SMs (capped by the work count)
+    int tile_y = kTileYSmall;   // 8-row tiles, 4 blocks per SM: as the single-lattice step
+    int grid_mult = 4;          // blocks = grid_mult * SMs (capped by the work count)
     void** d_prev = nullptr;
     double* d_partial = nullptr;
     int partial_cap = 0;

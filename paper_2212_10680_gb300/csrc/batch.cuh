@@ -29,8 +29,9 @@ struct WorkItem {
 };
 
 // One step of every active lattice.
+// Float storage capped at 64 registers (1024 threads per SM), as the single-lattice step.
 template <int NC, int ST, int TY>
-__global__ void __launch_bounds__(kTX* TY) batch_step(BatchLattice* __restrict__ lat,
+__global__ void __launch_bounds__(kTX* TY, ST == ST_F64 ? 1 : 1024 / (kTX * TY)) batch_step(BatchLattice* __restrict__ lat,
                                                       const WorkItem* __restrict__ work, int nwork) {
     using Real = typename StoreTraits<ST>::Real;
     extern __shared__ __align__(16) unsigned char smem_batch[];
