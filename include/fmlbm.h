@@ -172,8 +172,8 @@ fmlbm_status fmlbm_diagnostics(fmlbm_handle* h, double* mass, double* residual, 
  * loop).  fmlbm_diagnostics_async asks for the diagnostics above of the current state
  * and returns at once with a ticket (requests repeated before the next step share
  * one).  Nothing is computed yet: the next fmlbm_step computes them inside its first
- * time step, from the distributions that step reads anyway (plain step kernel; the
- * TMA forms run the separate reduction before stepping), so a loop that steps and asks
+ * time step, from the distributions that step reads anyway (every step variant), so a
+ * loop that steps and asks
  * every step adds no extra pass over the lattice; if no step follows,
  * fmlbm_diagnostics_wait runs the separate reduction.  Results are bit-identical either
  * way.  The final sum and the copies to the host of a request served inside a step run
@@ -329,7 +329,7 @@ fmlbm_status fmlbm_batch_moments(fmlbm_batch* b, int32_t slot, double* rho, doub
 fmlbm_status fmlbm_batch_get_distributions(fmlbm_batch* b, int32_t slot, double* g, double* force);
 /* Autotuner: times steps_per_trial steps of the current active slots for each tile
  * height (8, 16) and grid size (1, 2, 4, 8 blocks per multiprocessor) and keeps the
- * fastest.  The trial steps are real steps of the lattices (the tiling does not change
+ * fastest (without it a batch runs 8-row tiles, 4 blocks per multiprocessor).  The trial steps are real steps of the lattices (the tiling does not change
  * results).  Outputs (may be NULL): chosen tile height, blocks, ms per step. */
 fmlbm_status fmlbm_batch_autotune(fmlbm_batch* b, int32_t steps_per_trial, int32_t* tile_y, int32_t* blocks,
                                   double* ms_per_step);

@@ -550,10 +550,6 @@ fmlbm_status fmlbm_init(fmlbm_handle* h, const double* rho_host) {
 
 fmlbm_status fmlbm_step(fmlbm_handle* h, int64_t nsteps) {
     if (!h || nsteps < 0) return fail(h, FMLBM_E_INVALID_ARG, "bad argument");
-    if (nsteps > 0 && h->pending >= 0 && use_tma(h)) {
-        fmlbm_status s = enqueue_pending_standalone(h);  // the TMA forms have no fused reduction
-        if (s != FMLBM_OK) return s;
-    }
     // During a stream capture nothing crosses to the diagnostics stream (a captured stream
     // may not wait on work outside the capture): a request is then served entirely on the
     // captured stream.

@@ -690,6 +690,56 @@ __device__ __forceinline__ Real diag_strip(const Real (*red)[NC + 2], int row0, 
     return v;
 }
 
+// Diagnostics of the state a step reads, fused into the step (A.diag_partial set): the
+// snapshot value of each owned node is copied into shared memory before phase 1, and after
+// phase 3 each 32 x 8 strip of the tile writes its N + 2 partial sums at the index
+// reduce_partial would use ((strip row) * tiles_x + tile column).
+template <int NC, typename Real, int TY>
+__device__ __forceinline__ void diag_prefetch(const StepArgs& A, Real* pv_s, int tx, int ty, int gxn, int gyn) {
+    if (A.diag_partial != nullptr && gxn < A.nx && gyn < A.ny) {
+        const Real* prev = static_cast<const Real*>(A.rho_prev);
+        const size_t nxy = (size_t)A.nx * A.ny, node = (size_t)gyn * A.nx + gxn;
+#pragma unroll
+        for (int i = 0; i < NC; ++i) cp_async_elem(&pv_s[(i * TY + ty) * kTX + tx], prev + i * nxy + node);
+    }
+}
+
+// Called by every thread of the block (it synchronises); uniform in A.diag_partial.
+template <int NC, typename Real, int TY>
+__device__ __forceinline__ void diag_tile(const StepArgs& A, const Real (&g)[NC][9], const Real* pv_s, int tx, int ty,
+                                          int gxn, int gyn, int y0, int tile_row, int tile_col, int tiles_x) {
+    static_assert(TY % 8 == 0, "diagnostics strips of 8 rows");
+    __shared__ Real dred[TY][NC + 2];
+    const int nx = A.nx, ny = A.ny, tid = ty * kTX + tx;
+    Real acc[NC + 2];
+#pragma unroll
+    for (int k = 0; k < NC + 2; ++k) acc[k] = Real(0);
+    if (gxn < nx && gyn < ny) {
+        Real r[NC];
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+            r[i] = Real(0);
+#pragma unroll
+            for (int a = 0; a < 9; ++a) r[i] += g[i][a];  // the order of pull_rho
+        }
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        Real pv[NC];
+#pragma unroll
+        for (int i = 0; i < NC; ++i) pv[i] = pv_s[(i * TY + ty) * kTX + tx];
+        diag_node<NC, Real>(r, pv, static_cast<Real*>(A.rho_prev), A.have_prev, (size_t)gyn * nx + gxn,
+                            (size_t)nx * ny, acc);
+    }
+    diag_warp<NC, Real>(acc, dred[ty]);
+    __syncthreads();
+    constexpr int STRIPS = TY / 8;
+    if (tid < STRIPS * (NC + 2)) {
+        const int sub = tid / (NC + 2), k = tid % (NC + 2);
+        if (y0 + 8 * sub < ny)
+            static_cast<Real*>(A.diag_partial)[((size_t)(tile_row * STRIPS + sub) * tiles_x + tile_col) * (NC + 2) + k] =
+                diag_strip<NC, Real>(dred, 8 * sub, k);
+    }
+}
+
 // MOMENTS = true: compute the macroscopic fields of the current state instead of
 // advancing it (no distribution or force store).
 template <int NC, int ST, int TY, bool MOMENTS, bool STD = false>
@@ -712,14 +762,7 @@ __global__ void __launch_bounds__(kTX* TY, ST == ST_F64 ? 1 : 1024 / (kTX * TY))
     // diagnostics: the density snapshot of this thread's node, copied like the force (a load
     // issued after phase 3 stalled the whole step about 2x)
     Real* pv_s = reinterpret_cast<Real*>(smem_raw + sizeof(StepSmem<Real, NC, TY>));
-    if constexpr (!MOMENTS) {
-        if (A.diag_partial != nullptr && gxn < nx && gyn < ny) {
-            const Real* prev = static_cast<const Real*>(A.rho_prev);
-            const size_t nxy = (size_t)nx * ny, node = (size_t)gyn * nx + gxn;
-#pragma unroll
-            for (int i = 0; i < NC; ++i) cp_async_elem(&pv_s[(i * TY + ty) * kTX + tx], prev + i * nxy + node);
-        }
-    }
+    if constexpr (!MOMENTS) diag_prefetch<NC, Real, TY>(A, pv_s, tx, ty, gxn, gyn);
     prefetch_force<Real, NC, TY>(A, S, tx, ty, gxn, gyn);
     Real g[NC][9];
     phase1_global<NC, ST, TY>(A, m, S, g, x0, y0, inner, tx, ty, tid);
@@ -728,37 +771,8 @@ __global__ void __launch_bounds__(kTX* TY, ST == ST_F64 ? 1 : 1024 / (kTX * TY))
     __syncthreads();
     if (gxn < nx && gyn < ny) phase3<NC, ST, TY, MOMENTS, STD>(A, m, S, g, tx, ty, gxn, gyn);
     if constexpr (!MOMENTS) {
-        if (A.diag_partial != nullptr) {  // uniform: diagnostics of the state this step read
-            static_assert(TY % 8 == 0, "diagnostics strips of 8 rows");
-            __shared__ Real dred[TY][NC + 2];
-            Real acc[NC + 2];
-#pragma unroll
-            for (int k = 0; k < NC + 2; ++k) acc[k] = Real(0);
-            if (gxn < nx && gyn < ny) {
-                Real r[NC];
-#pragma unroll
-                for (int i = 0; i < NC; ++i) {
-                    r[i] = Real(0);
-#pragma unroll
-                    for (int a = 0; a < 9; ++a) r[i] += g[i][a];  // the order of pull_rho
-                }
-                asm volatile("cp.async.wait_all;\n" ::: "memory");
-                Real pv[NC];
-#pragma unroll
-                for (int i = 0; i < NC; ++i) pv[i] = pv_s[(i * TY + ty) * kTX + tx];
-                diag_node<NC, Real>(r, pv, static_cast<Real*>(A.rho_prev), A.have_prev, (size_t)gyn * nx + gxn,
-                                    (size_t)nx * ny, acc);
-            }
-            diag_warp<NC, Real>(acc, dred[ty]);
-            __syncthreads();
-            constexpr int STRIPS = TY / 8;
-            if (tid < STRIPS * (NC + 2)) {
-                const int sub = tid / (NC + 2), k = tid % (NC + 2);
-                if (y0 + 8 * sub < ny)
-                    static_cast<Real*>(A.diag_partial)[((size_t)(blockIdx.y * STRIPS + sub) * gridDim.x + blockIdx.x) *
-                                                           (NC + 2) + k] = diag_strip<NC, Real>(dred, 8 * sub, k);
-            }
-        }
+        if (A.diag_partial != nullptr)  // uniform: diagnostics of the state this step read
+            diag_tile<NC, Real, TY>(A, g, pv_s, tx, ty, gxn, gyn, y0, blockIdx.y, blockIdx.x, gridDim.x);
     }
 }
 

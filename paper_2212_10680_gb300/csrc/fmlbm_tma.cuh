@@ -46,7 +46,8 @@ struct TmaLayout {
     static constexpr size_t b16_bytes = dev ? (size_t)8 * NC * H * W16 * 2 : 0;
     static constexpr size_t align128(size_t v) { return (v + 127) & ~size_t(127); }
     static constexpr size_t stage_bytes = align128(f32_bytes) + align128(b16_bytes);
-    static constexpr size_t scratch_bytes = align128(sizeof(StepSmem<float, NC, TY>));
+    // the step's shared tiles, then the diagnostics snapshot copy of the tile's nodes
+    static constexpr size_t scratch_bytes = align128(sizeof(StepSmem<float, NC, TY>) + (size_t)NC * TY * kTX * 4);
     static constexpr int stages = (scratch_bytes + 2 * stage_bytes + 64 <= 220 * 1024) ? 2 : 1;
     static constexpr size_t smem_bytes = scratch_bytes + stages * stage_bytes + 64;
     static constexpr bool fits = smem_bytes <= 227 * 1024;
@@ -119,6 +120,7 @@ __global__ void __launch_bounds__(kTX* TY, MINB)
     extern __shared__ __align__(128) unsigned char smem_tma[];
     auto& S = *reinterpret_cast<StepSmem<Real, NC, TY>*>(smem_tma);
     unsigned char* stages = smem_tma + L::scratch_bytes;
+    Real* pv_s = reinterpret_cast<Real*>(smem_tma + sizeof(StepSmem<Real, NC, TY>));
     uint64_t* bar = reinterpret_cast<uint64_t*>(stages + NSTAGE * L::stage_bytes);
     const MixConstT<Real>& m = mixc<Real>(A);
 
@@ -177,6 +179,7 @@ __global__ void __launch_bounds__(kTX* TY, MINB)
         origin(t, x0, y0);
         const int gxn = x0 + tx, gyn = y0 + ty;
         prefetch_force<Real, NC, TY>(A, S, tx, ty, gxn, gyn);
+        diag_prefetch<NC, Real, TY>(A, pv_s, tx, ty, gxn, gyn);
         unsigned char* st = stages + s * L::stage_bytes;
         Real* gpark = reinterpret_cast<Real*>(st);  // edge tiles: [9N][TY][32]
         constexpr bool PARK = NSTAGE == 1;
@@ -241,6 +244,8 @@ __global__ void __launch_bounds__(kTX* TY, MINB)
             }
             phase3<NC, ST, TY, false>(A, m, S, g, tx, ty, gxn, gyn);
         }
+        if (A.diag_partial != nullptr)  // uniform: diagnostics of the state this step read
+            diag_tile<NC, Real, TY>(A, g, pv_s, tx, ty, gxn, gyn, y0, t / tiles_x, t % tiles_x, tiles_x);
         __syncthreads();  // shared tiles and the stage are free again
     }
 }
