@@ -297,6 +297,26 @@ struct StepSmem {
     E Fl[2][TY][kTX];        // stored total force at the tile's nodes (lagged reading)
 };
 
+// Occupancy for two components in float storage (8-row tiles): the second component's
+// nine pulled values wait in shared memory from the end of phase 1 to phase 3 instead of
+// in registers, which lets the step fit 48 registers without spilling, i.e. five blocks
+// of 256 threads per SM instead of four (1024^2 binary FP32: 2.5% faster on GB300).  With
+// three or four components the step spills at 48 registers even with values parked, and
+// parking every value of a node was slower.
+template <int NC, int ST, int TY>
+constexpr bool kParkLast = ST != ST_F64 && NC == 2 && TY == 8;
+template <int NC, int ST, int TY>
+constexpr size_t park_bytes() {
+    return kParkLast<NC, ST, TY> ? (size_t)9 * TY * kTX * sizeof(typename StoreTraits<ST>::Real) : 0;
+}
+
+// The pulled value g_a of component i at this thread's node: from the parked copy
+// (park[a][thread]) for the last component when the step parks it.
+template <int NC, int TY, bool PARK, typename Real>
+__device__ __forceinline__ Real pulled(const Real (&g)[NC][9], const Real* park, int i, int a, int tid) {
+    return (PARK && i == NC - 1) ? park[a * kTX * TY + tid] : g[i][a];
+}
+
 // The stored force F(t - 1) that the lagged reading puts into u (step 1) is needed only in
 // phase 3; its copy into shared memory starts before phase 1 (cp.async, no registers held)
 // so that its latency hides behind phases 1 and 2 instead of stalling every warp in phase 3.
@@ -468,11 +488,11 @@ __device__ __forceinline__ void phase2(const MixConstT<Real>& m, StepSmem<Real, 
 // STD: the standard formulation of Section VI -- equilibrium rho_i w_a [1 + ...] of
 // Eq. eqLBE, Guo's forcing term of Eq. eqLBEfinal3 (no grad rho_i part) and
 // F_i + c_s^2 grad rho_i of Eq. eqForceGen.
-template <int NC, int ST, int TY, bool MOMENTS, bool STD = false>
+template <int NC, int ST, int TY, bool MOMENTS, bool STD = false, bool PARK = false>
 __device__ __forceinline__ void phase3(const StepArgs& A, const MixConstT<typename StoreTraits<ST>::Real>& m,
                                        StepSmem<typename StoreTraits<ST>::Real, NC, TY>& S,
                                        const typename StoreTraits<ST>::Real (&g)[NC][9], int tx, int ty, int gxn,
-                                       int gyn) {
+                                       int gyn, const typename StoreTraits<ST>::Real* park = nullptr) {
     using Real = typename StoreTraits<ST>::Real;
     const int nx = A.nx, nxy = A.nx * A.ny;
     const int cx = tx + 1, cy = ty + 1;  // tile+1 coordinates of this node
@@ -499,7 +519,9 @@ __device__ __forceinline__ void phase3(const StepArgs& A, const MixConstT<typena
         Fty += Fy[i];
         // zeroth and first moments with e_a in {0, +-1} written out: IEEE arithmetic keeps
         // every 0 * g_a the compiler is given
-        const Real(&h)[9] = g[i];
+        Real h[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) h[a] = pulled<NC, TY, PARK, Real>(g, park, i, a, ty * kTX + tx);
         const Real r = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
         jx += ((h[1] + h[5]) + h[8]) - ((h[3] + h[6]) + h[7]);
         jy += ((h[2] + h[5]) + h[6]) - ((h[4] + h[7]) + h[8]);
@@ -549,7 +571,9 @@ __device__ __forceinline__ void phase3(const StepArgs& A, const MixConstT<typena
         const Real w1 = Real(1.0 / 9.0), w5 = Real(1.0 / 36.0);
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
-            const Real(&h)[9] = g[i];
+            Real h[9];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) h[a] = pulled<NC, TY, PARK, Real>(g, park, i, a, ty * kTX + tx);
             const Real rw = omega * rhoi[i];
             // the forcing term's grad rho_i part belongs to the well-balanced scheme only
             const Real gX = STD ? Real(0) : grx[i], gY = STD ? Real(0) : gry[i];
@@ -747,10 +771,14 @@ template <int NC, int ST, int TY, bool MOMENTS, bool STD = false>
 // than trading occupancy for registers (77 registers and three 8-row blocks per SM were 7%
 // slower for three components) or registers for occupancy (48 registers spill).  The FP64
 // reference path keeps what the compiler chooses.
-__global__ void __launch_bounds__(kTX* TY, ST == ST_F64 ? 1 : 1024 / (kTX * TY)) fused_step(StepArgs A) {
+__global__ void __launch_bounds__(kTX* TY, ST == ST_F64 ? 1 : (kParkLast<NC, ST, TY> ? 5 : 1024 / (kTX * TY)))
+    fused_step(StepArgs A) {
     using Real = typename StoreTraits<ST>::Real;
+    constexpr bool PARK = kParkLast<NC, ST, TY>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto& S = *reinterpret_cast<StepSmem<Real, NC, TY>*>(smem_raw);
+    // dynamic shared memory: StepSmem, the parked values (PARK), the diagnostics snapshot
+    Real* park = reinterpret_cast<Real*>(smem_raw + sizeof(StepSmem<Real, NC, TY>));
     const MixConstT<Real>& m = mixc<Real>(A);
     const int nx = A.nx, ny = A.ny;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -761,18 +789,27 @@ __global__ void __launch_bounds__(kTX* TY, ST == ST_F64 ? 1 : 1024 / (kTX * TY))
     const int gxn = x0 + tx, gyn = y0 + ty;
     // diagnostics: the density snapshot of this thread's node, copied like the force (a load
     // issued after phase 3 stalled the whole step about 2x)
-    Real* pv_s = reinterpret_cast<Real*>(smem_raw + sizeof(StepSmem<Real, NC, TY>));
+    Real* pv_s = reinterpret_cast<Real*>(smem_raw + sizeof(StepSmem<Real, NC, TY>) + park_bytes<NC, ST, TY>());
     if constexpr (!MOMENTS) diag_prefetch<NC, Real, TY>(A, pv_s, tx, ty, gxn, gyn);
     prefetch_force<Real, NC, TY>(A, S, tx, ty, gxn, gyn);
     Real g[NC][9];
     phase1_global<NC, ST, TY>(A, m, S, g, x0, y0, inner, tx, ty, tid);
+    if constexpr (PARK) {
+#pragma unroll
+        for (int a = 0; a < 9; ++a) park[a * kTX * TY + tid] = g[NC - 1][a];
+    }
     __syncthreads();
     phase2<NC, TY, Real>(m, S, A.stencil, tid);
     __syncthreads();
-    if (gxn < nx && gyn < ny) phase3<NC, ST, TY, MOMENTS, STD>(A, m, S, g, tx, ty, gxn, gyn);
+    if (gxn < nx && gyn < ny) phase3<NC, ST, TY, MOMENTS, STD, PARK>(A, m, S, g, tx, ty, gxn, gyn, park);
     if constexpr (!MOMENTS) {
-        if (A.diag_partial != nullptr)  // uniform: diagnostics of the state this step read
+        if (A.diag_partial != nullptr) {  // uniform: diagnostics of the state this step read
+            if constexpr (PARK) {
+#pragma unroll
+                for (int a = 0; a < 9; ++a) g[NC - 1][a] = park[a * kTX * TY + tid];
+            }
             diag_tile<NC, Real, TY>(A, g, pv_s, tx, ty, gxn, gyn, y0, blockIdx.y, blockIdx.x, gridDim.x);
+        }
     }
 }
 

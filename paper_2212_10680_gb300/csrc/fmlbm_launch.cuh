@@ -60,8 +60,9 @@ inline cudaError_t launch_reduce_final(int nc, bool fp64, const void* partial, i
     template <int NC, bool MOM, int TY, bool STD = false>                                                 \
     static cudaError_t launch_step_nc_##ST(const StepArgs& A, cudaStream_t s) {                           \
         using Real = typename StoreTraits<ST>::Real;                                                      \
-        /* + the diagnostics snapshot copy of the tile's nodes */                                       \
-        constexpr size_t smem = sizeof(StepSmem<Real, NC, TY>) + (MOM ? 0 : (size_t)NC * TY * kTX * sizeof(Real)); \
+        /* + the parked values and the diagnostics snapshot copy of the tile's nodes */                 \
+        constexpr size_t smem = sizeof(StepSmem<Real, NC, TY>) + park_bytes<NC, ST, TY>() +                \
+                                (MOM ? 0 : (size_t)NC * TY * kTX * sizeof(Real));                         \
         auto k = fused_step<NC, ST, TY, MOM, STD>;                                                        \
         static bool attr_done = false;                                                                    \
         if (!attr_done) {                                                                                 \
