@@ -313,8 +313,25 @@ constexpr size_t park_bytes() {
 // The pulled value g_a of component i at this thread's node: from the parked copy
 // (park[a][thread]) for the last component when the step parks it.
 template <int NC, int TY, bool PARK, typename Real>
-__device__ __forceinline__ Real pulled(const Real (&g)[NC][9], const Real* park, int i, int a, int tid) {
-    return (PARK && i == NC - 1) ? park[a * kTX * TY + tid] : g[i][a];
+__device__ __forceinline__ void pulled_all(const Real (&g)[NC][9], const Real* park, int i, int tid, Real (&h)[9]) {
+    if constexpr (PARK) {
+        if (i == NC - 1) {
+            const float4 a = reinterpret_cast<const float4*>(park)[tid];
+            const float4 b = reinterpret_cast<const float4*>(park)[kTX * TY + tid];
+            h[0] = a.x; h[1] = a.y; h[2] = a.z; h[3] = a.w;
+            h[4] = b.x; h[5] = b.y; h[6] = b.z; h[7] = b.w;
+            h[8] = park[8 * kTX * TY + tid];
+            return;
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 9; ++a) h[a] = g[i][a];
+}
+template <int TY, typename Real>
+__device__ __forceinline__ void park_store(const Real (&v)[9], Real* park, int tid) {
+    reinterpret_cast<float4*>(park)[tid] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float4*>(park)[kTX * TY + tid] = make_float4(v[4], v[5], v[6], v[7]);
+    park[8 * kTX * TY + tid] = v[8];
 }
 
 // The stored force F(t - 1) that the lagged reading puts into u (step 1) is needed only in
@@ -520,8 +537,7 @@ __device__ __forceinline__ void phase3(const StepArgs& A, const MixConstT<typena
         // zeroth and first moments with e_a in {0, +-1} written out: IEEE arithmetic keeps
         // every 0 * g_a the compiler is given
         Real h[9];
-#pragma unroll
-        for (int a = 0; a < 9; ++a) h[a] = pulled<NC, TY, PARK, Real>(g, park, i, a, ty * kTX + tx);
+        pulled_all<NC, TY, PARK, Real>(g, park, i, ty * kTX + tx, h);
         const Real r = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
         jx += ((h[1] + h[5]) + h[8]) - ((h[3] + h[6]) + h[7]);
         jy += ((h[2] + h[5]) + h[6]) - ((h[4] + h[7]) + h[8]);
@@ -572,8 +588,7 @@ __device__ __forceinline__ void phase3(const StepArgs& A, const MixConstT<typena
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
             Real h[9];
-#pragma unroll
-            for (int a = 0; a < 9; ++a) h[a] = pulled<NC, TY, PARK, Real>(g, park, i, a, ty * kTX + tx);
+            pulled_all<NC, TY, PARK, Real>(g, park, i, ty * kTX + tx, h);
             const Real rw = omega * rhoi[i];
             // the forcing term's grad rho_i part belongs to the well-balanced scheme only
             const Real gX = STD ? Real(0) : grx[i], gY = STD ? Real(0) : gry[i];
@@ -794,20 +809,14 @@ __global__ void __launch_bounds__(kTX* TY, ST == ST_F64 ? 1 : (kParkLast<NC, ST,
     prefetch_force<Real, NC, TY>(A, S, tx, ty, gxn, gyn);
     Real g[NC][9];
     phase1_global<NC, ST, TY>(A, m, S, g, x0, y0, inner, tx, ty, tid);
-    if constexpr (PARK) {
-#pragma unroll
-        for (int a = 0; a < 9; ++a) park[a * kTX * TY + tid] = g[NC - 1][a];
-    }
+    if constexpr (PARK) park_store<TY, Real>(g[NC - 1], park, tid);
     __syncthreads();
     phase2<NC, TY, Real>(m, S, A.stencil, tid);
     __syncthreads();
     if (gxn < nx && gyn < ny) phase3<NC, ST, TY, MOMENTS, STD, PARK>(A, m, S, g, tx, ty, gxn, gyn, park);
     if constexpr (!MOMENTS) {
         if (A.diag_partial != nullptr) {  // uniform: diagnostics of the state this step read
-            if constexpr (PARK) {
-#pragma unroll
-                for (int a = 0; a < 9; ++a) g[NC - 1][a] = park[a * kTX * TY + tid];
-            }
+            if constexpr (PARK) pulled_all<NC, TY, PARK, Real>(g, park, NC - 1, tid, g[NC - 1]);
             diag_tile<NC, Real, TY>(A, g, pv_s, tx, ty, gxn, gyn, y0, blockIdx.y, blockIdx.x, gridDim.x);
         }
     }
