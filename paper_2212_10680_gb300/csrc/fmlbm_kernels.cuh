@@ -120,7 +120,27 @@ struct StepArgs {
     void* diag_partial;
     void* rho_prev;  // [N][ny][nx] in the storage arithmetic type
     int have_prev;
+    // the base address of every distribution plane of gin / gout (set_planes): F64/F32 plane
+    // i*9+a; 16-bit storage plane i*8+a-1 (a >= 1) and float plane i (a = 0)
+    const void* gin_p[kMaxC * 9];
+    void* gout_p[kMaxC * 9];
+    const float* g0in_p[kMaxC];
+    float* g0out_p[kMaxC];
 };
+
+// elem: bytes per element of the planes gin / gout point to (8, 4 or 2).
+inline void set_planes(StepArgs& A, int nc, bool dev16, size_t elem) {
+    const size_t nxy = (size_t)A.nx * A.ny;
+    const int per = dev16 ? 8 : 9;
+    for (int k = 0; k < nc * per; ++k) {
+        A.gin_p[k] = A.gin ? static_cast<const char*>(A.gin) + k * nxy * elem : nullptr;
+        A.gout_p[k] = A.gout ? static_cast<char*>(A.gout) + k * nxy * elem : nullptr;
+    }
+    for (int i = 0; i < nc && dev16; ++i) {
+        A.g0in_p[i] = A.g0in ? A.g0in + i * nxy : nullptr;
+        A.g0out_p[i] = A.g0out ? A.g0out + i * nxy : nullptr;
+    }
+}
 
 template <typename E> __device__ __forceinline__ const MixConstT<E>& mixc(const StepArgs& A);
 template <> __device__ __forceinline__ const MixConstT<double>& mixc<double>(const StepArgs& A) { return A.mixd; }
@@ -160,6 +180,34 @@ __device__ __forceinline__ typename StoreTraits<ST>::Real load_g(const StepArgs&
     }
 }
 
+// The same through the plane base addresses of the launch's parameters and a 32-bit node
+// index: each access address is then a single multiply-add onto a parameter, where the
+// forms above compute a 64-bit plane offset (two-component step: +1.5% on GB300; with
+// three components it cost registers and spilled).
+template <int ST>
+__device__ __forceinline__ typename StoreTraits<ST>::Real load_gp(const StepArgs& A, int i, int a, int node) {
+    using Elem = typename StoreTraits<ST>::Elem;
+    if constexpr (ST == ST_F64 || ST == ST_F32) {
+        return to_real(ldg(static_cast<const Elem*>(A.gin_p[i * 9 + a]) + node));
+    } else {
+        if (a == 0) return ldg(A.g0in_p[i] + node);
+        return to_real(ldg(static_cast<const Elem*>(A.gin_p[i * 8 + a - 1]) + node));
+    }
+}
+template <int ST>
+__device__ __forceinline__ void store_gp(const StepArgs& A, int i, int a, int node,
+                                         typename StoreTraits<ST>::Real v) {
+    using Elem = typename StoreTraits<ST>::Elem;
+    if constexpr (ST == ST_F64 || ST == ST_F32) {
+        static_cast<Elem*>(A.gout_p[i * 9 + a])[node] = v;
+    } else {
+        if (a == 0)
+            A.g0out_p[i][node] = v;
+        else
+            static_cast<Elem*>(A.gout_p[i * 8 + a - 1])[node] = from_real<Elem>(v);
+    }
+}
+
 template <int ST>
 __device__ __forceinline__ void store_g(const StepArgs& A, int i, int a, size_t node, size_t nxy,
                                         typename StoreTraits<ST>::Real v) {
@@ -174,6 +222,13 @@ __device__ __forceinline__ void store_g(const StepArgs& A, int i, int a, size_t 
         else
             static_cast<Elem*>(A.gout)[(size_t)(i * 8 + a - 1) * nxy + node] = from_real<Elem>(v);
     }
+}
+
+template <int ST, bool PP>
+__device__ __forceinline__ void store_gsel(const StepArgs& A, int i, int a, int node, int nxy,
+                                           typename StoreTraits<ST>::Real v) {
+    if constexpr (PP) store_gp<ST>(A, i, a, node, v);
+    else store_g<ST>(A, i, a, (size_t)node, (size_t)nxy, v);
 }
 
 // Reciprocal and natural logarithm: exact library forms in double (the FP64 path is the
@@ -302,7 +357,8 @@ struct StepSmem {
 // in registers, which lets the step fit 48 registers without spilling, i.e. five blocks
 // of 256 threads per SM instead of four (1024^2 binary FP32: 2.5% faster on GB300).  With
 // three or four components the step spills at 48 registers even with values parked, and
-// parking every value of a node was slower.
+// parking every value of a node was slower.  The same step also addresses the distribution
+// planes through the launch's plane pointers (load_gp / store_gp).
 template <int NC, int ST, int TY>
 constexpr bool kParkLast = ST != ST_F64 && NC == 2 && TY == 8;
 template <int NC, int ST, int TY>
@@ -368,7 +424,7 @@ __device__ __forceinline__ int pull_src(int a, int wx, int wy, int xm, int xp, i
 }
 
 // Sum of the pulled distributions of component i at node (wx, wy) (wrapped coordinates).
-template <int NC, int ST>
+template <int NC, int ST, bool PP = false>
 __device__ __forceinline__ void pull_rho(const StepArgs& A, int wx, int wy, bool inner, int nx, int ny, int nxy,
                                          typename StoreTraits<ST>::Real* rs) {
     using Real = typename StoreTraits<ST>::Real;
@@ -386,7 +442,8 @@ __device__ __forceinline__ void pull_rho(const StepArgs& A, int wx, int wy, bool
     for (int a = 0; a < 9; ++a) {
         const int src = inner ? node - ey(a) * nx - ex(a) : pull_src(a, wx, wy, xm, xp, ym, yp, nx);
 #pragma unroll
-        for (int i = 0; i < NC; ++i) rs[i] += load_g<ST>(A, i, a, (size_t)src, (size_t)nxy);
+        for (int i = 0; i < NC; ++i)
+            rs[i] += PP ? load_gp<ST>(A, i, a, src) : load_g<ST>(A, i, a, (size_t)src, (size_t)nxy);
     }
 }
 
@@ -505,7 +562,7 @@ __device__ __forceinline__ void phase2(const MixConstT<Real>& m, StepSmem<Real, 
 // STD: the standard formulation of Section VI -- equilibrium rho_i w_a [1 + ...] of
 // Eq. eqLBE, Guo's forcing term of Eq. eqLBEfinal3 (no grad rho_i part) and
 // F_i + c_s^2 grad rho_i of Eq. eqForceGen.
-template <int NC, int ST, int TY, bool MOMENTS, bool STD = false, bool PARK = false>
+template <int NC, int ST, int TY, bool MOMENTS, bool STD = false, bool PARK = false, bool PP = false>
 __device__ __forceinline__ void phase3(const StepArgs& A, const MixConstT<typename StoreTraits<ST>::Real>& m,
                                        StepSmem<typename StoreTraits<ST>::Real, NC, TY>& S,
                                        const typename StoreTraits<ST>::Real (&g)[NC][9], int tx, int ty, int gxn,
@@ -606,20 +663,20 @@ __device__ __forceinline__ void phase3(const StepArgs& A, const MixConstT<typena
             const Real Ox = rw3 * ux + fc_3 * Fx[i];
             const Real Oy = rw3 * uy + fc_3 * Fy[i];
             const Real rest0 = STD ? Real(4.0 / 9.0) * rw : rw;
-            store_g<ST>(A, i, 0, (size_t)node, (size_t)nxy,
+            store_gsel<ST, PP>(A, i, 0, node, nxy,
                         keep * h[0] + (rest0 + Real(4.0 / 9.0) * (a0 - Real(2) * fc * ug)));
             const Real e1 = w1 * (ux * Vx + cb_ax + rwS);
-            store_g<ST>(A, i, 1, (size_t)node, (size_t)nxy, keep * h[1] + (e1 + Ox));
-            store_g<ST>(A, i, 3, (size_t)node, (size_t)nxy, keep * h[3] + (e1 - Ox));
+            store_gsel<ST, PP>(A, i, 1, node, nxy, keep * h[1] + (e1 + Ox));
+            store_gsel<ST, PP>(A, i, 3, node, nxy, keep * h[3] + (e1 - Ox));
             const Real e2 = w1 * (uy * Vy + cb_ax + rwS);
-            store_g<ST>(A, i, 2, (size_t)node, (size_t)nxy, keep * h[2] + (e2 + Oy));
-            store_g<ST>(A, i, 4, (size_t)node, (size_t)nxy, keep * h[4] + (e2 - Oy));
+            store_gsel<ST, PP>(A, i, 2, node, nxy, keep * h[2] + (e2 + Oy));
+            store_gsel<ST, PP>(A, i, 4, node, nxy, keep * h[4] + (e2 - Oy));
             const Real e5 = w5 * (u5 * (Vx + Vy) + cb_dg + rwS), o5 = Real(0.25) * (Ox + Oy);
-            store_g<ST>(A, i, 5, (size_t)node, (size_t)nxy, keep * h[5] + (e5 + o5));
-            store_g<ST>(A, i, 7, (size_t)node, (size_t)nxy, keep * h[7] + (e5 - o5));
+            store_gsel<ST, PP>(A, i, 5, node, nxy, keep * h[5] + (e5 + o5));
+            store_gsel<ST, PP>(A, i, 7, node, nxy, keep * h[7] + (e5 - o5));
             const Real e6 = w5 * (u6 * (Vy - Vx) + cb_dg + rwS), o6 = Real(0.25) * (Oy - Ox);
-            store_g<ST>(A, i, 6, (size_t)node, (size_t)nxy, keep * h[6] + (e6 + o6));
-            store_g<ST>(A, i, 8, (size_t)node, (size_t)nxy, keep * h[8] + (e6 - o6));
+            store_gsel<ST, PP>(A, i, 6, node, nxy, keep * h[6] + (e6 + o6));
+            store_gsel<ST, PP>(A, i, 8, node, nxy, keep * h[8] + (e6 - o6));
         }
         Real* Fout = static_cast<Real*>(A.Fout);
         Fout[node] = Ftx;
@@ -629,7 +686,7 @@ __device__ __forceinline__ void phase3(const StepArgs& A, const MixConstT<typena
 
 // Phase 1 from global memory for one tile: pull of the owned node (into g) and of the halo
 // ring (rho~ only), with periodic wrap unless the tile is inner.
-template <int NC, int ST, int TY>
+template <int NC, int ST, int TY, bool PP = false>
 __device__ __forceinline__ void phase1_global(const StepArgs& A, const MixConstT<typename StoreTraits<ST>::Real>& m,
                                               StepSmem<typename StoreTraits<ST>::Real, NC, TY>& S,
                                               typename StoreTraits<ST>::Real (&g)[NC][9], int x0, int y0,
@@ -654,7 +711,7 @@ __device__ __forceinline__ void phase1_global(const StepArgs& A, const MixConstT
         ring_position<TY>(tid, bx, by);
         const int wx = inner ? x0 - 2 + bx : wrap(x0 - 2 + bx, nx);
         const int wy = inner ? y0 - 2 + by : wrap(y0 - 2 + by, ny);
-        pull_rho<NC, ST>(A, wx, wy, inner, nx, ny, nxy, rr);
+        pull_rho<NC, ST, PP>(A, wx, wy, inner, nx, ny, nxy, rr);
     };
     if (RING_FIRST && has_ring) pull_ring();
     {
@@ -671,7 +728,8 @@ __device__ __forceinline__ void phase1_global(const StepArgs& A, const MixConstT
         for (int a = 0; a < 9; ++a) {
             const int src = inner ? node - ey(a) * nx - ex(a) : pull_src(a, wx, wy, xm, xp, ym, yp, nx);
 #pragma unroll
-            for (int i = 0; i < NC; ++i) g[i][a] = load_g<ST>(A, i, a, (size_t)src, (size_t)nxy);
+            for (int i = 0; i < NC; ++i)
+                g[i][a] = PP ? load_gp<ST>(A, i, a, src) : load_g<ST>(A, i, a, (size_t)src, (size_t)nxy);
         }
     }
     if constexpr (RING_FIRST) {
@@ -808,12 +866,12 @@ __global__ void __launch_bounds__(kTX* TY, ST == ST_F64 ? 1 : (kParkLast<NC, ST,
     if constexpr (!MOMENTS) diag_prefetch<NC, Real, TY>(A, pv_s, tx, ty, gxn, gyn);
     prefetch_force<Real, NC, TY>(A, S, tx, ty, gxn, gyn);
     Real g[NC][9];
-    phase1_global<NC, ST, TY>(A, m, S, g, x0, y0, inner, tx, ty, tid);
+    phase1_global<NC, ST, TY, PARK>(A, m, S, g, x0, y0, inner, tx, ty, tid);
     if constexpr (PARK) park_store<TY, Real>(g[NC - 1], park, tid);
     __syncthreads();
     phase2<NC, TY, Real>(m, S, A.stencil, tid);
     __syncthreads();
-    if (gxn < nx && gyn < ny) phase3<NC, ST, TY, MOMENTS, STD, PARK>(A, m, S, g, tx, ty, gxn, gyn, park);
+    if (gxn < nx && gyn < ny) phase3<NC, ST, TY, MOMENTS, STD, PARK, PARK>(A, m, S, g, tx, ty, gxn, gyn, park);
     if constexpr (!MOMENTS) {
         if (A.diag_partial != nullptr) {  // uniform: diagnostics of the state this step read
             if constexpr (PARK) pulled_all<NC, TY, PARK, Real>(g, park, NC - 1, tid, g[NC - 1]);
