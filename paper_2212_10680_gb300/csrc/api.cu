@@ -44,11 +44,11 @@ struct fmlbm_handle {
     int cur = 0;
     void* rho_prev = nullptr;     // storage arithmetic type
     int have_prev = 0;
-    void* partial = nullptr;         // two sets of per-strip sums (storage type, 8 bytes reserved each)
+    void* partial = nullptr;         // kDiagSlots sets of per-strip sums (storage type, 8 bytes reserved each)
     double* diag_dev = nullptr;      // kDiagSlots x kDiagWords results, then the error latch
     cudaStream_t tail = nullptr;     // final sums and copies of fused requests (non-blocking)
-    cudaEvent_t part_ev[2] = {};     // [parity]: partial sums of a fused request written
-    cudaEvent_t tail_done[2] = {};   // [parity]: the tail that read them has finished
+    cudaEvent_t part_ev[kDiagSlots] = {};    // [ticket % kDiagSlots]: partial sums of a fused request written
+    cudaEvent_t tail_done[kDiagSlots] = {};  // [ticket % kDiagSlots]: the tail that read them has finished
     double* diag_host = nullptr;     // pinned: kDiagSlots x kDiagWords doubles (results + error latch)
     cudaEvent_t diag_ev[kDiagSlots] = {};
     DiagSlot slot[kDiagSlots];
@@ -354,7 +354,7 @@ void release(fmlbm_handle* h) {
     if (h->diag_host) cudaFreeHost(h->diag_host);
     for (int k = 0; k < kDiagSlots; ++k)
         if (h->diag_ev[k]) cudaEventDestroy(h->diag_ev[k]);
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < kDiagSlots; ++k) {
         if (h->part_ev[k]) cudaEventDestroy(h->part_ev[k]);
         if (h->tail_done[k]) cudaEventDestroy(h->tail_done[k]);
     }
@@ -373,11 +373,13 @@ fmlbm_status reset_state_flags(fmlbm_handle* h) {
     return FMLBM_OK;
 }
 
-// Partial sums of request `ticket`: two sets alternate by ticket parity, so a request's
-// final sum can still read its set while the next step writes the other one.
+// Partial sums of request `ticket`: one set per result slot, so a step that fuses a request
+// waits only for the final sum of the request kDiagSlots tickets earlier (with two sets,
+// alternating, the 1024^2 binary's end-to-end loop stalled for the previous request's
+// final sum, which gets SMs only as the running step drains).
 void* partial_set(const fmlbm_handle* h, int64_t ticket) {
     return static_cast<char*>(h->partial) +
-           (size_t)(ticket & 1) * reduce_blocks(h->lattice.nx, h->lattice.ny) * (kMaxC + 2) * sizeof(double);
+           (size_t)(ticket % kDiagSlots) * reduce_blocks(h->lattice.nx, h->lattice.ny) * (kMaxC + 2) * sizeof(double);
 }
 double* result_slot(const fmlbm_handle* h, int64_t ticket) { return h->diag_dev + (ticket % kDiagSlots) * kDiagWords; }
 
@@ -413,7 +415,7 @@ fmlbm_status enqueue_pending_standalone(fmlbm_handle* h) {
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     FM_CUDA(h, cudaStreamIsCapturing(h->stream, &cap));
     const bool capturing = cap != cudaStreamCaptureStatusNone;
-    if (!capturing) FM_CUDA(h, cudaStreamWaitEvent(h->stream, h->tail_done[t & 1], 0));
+    if (!capturing) FM_CUDA(h, cudaStreamWaitEvent(h->stream, h->tail_done[t % kDiagSlots], 0));
     FM_CUDA(h, dispatch_reduce(h, A, partial_set(h, t), result_slot(h, t)));
     return enqueue_diag_tail(h, t, h->stream, false, capturing);
 }
@@ -452,7 +454,7 @@ fmlbm_status fmlbm_lattice_bytes(int32_t n_components, const fmlbm_lattice* latt
     buffer_bytes(n_components, *lattice, &gb, &g0b, &fb);
     const size_t nxy = (size_t)lattice->nx * lattice->ny;
     *bytes = 2 * (gb + g0b + fb) + (size_t)n_components * nxy * real_size(lattice->precision) +
-             2 * (size_t)reduce_blocks(lattice->nx, lattice->ny) * (FMLBM_MAX_COMPONENTS + 2) * 8 + 512;
+             kDiagSlots * (size_t)reduce_blocks(lattice->nx, lattice->ny) * (FMLBM_MAX_COMPONENTS + 2) * 8 + 512;
     return FMLBM_OK;
 }
 
@@ -486,12 +488,16 @@ fmlbm_status fmlbm_create(const fmlbm_mixture* mixture, const fmlbm_lattice* lat
         ok = ok && cudaMalloc(&h->F[k], fb) == cudaSuccess;
     }
     ok = ok && cudaMalloc(&h->rho_prev, (size_t)h->nc * nxy * real_size(lattice->precision)) == cudaSuccess;
-    ok = ok && cudaMalloc(&h->partial,
-                          2 * (size_t)reduce_blocks(lattice->nx, lattice->ny) * (kMaxC + 2) * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->partial, kDiagSlots * (size_t)reduce_blocks(lattice->nx, lattice->ny) * (kMaxC + 2) *
+                                           sizeof(double)) == cudaSuccess;
     ok = ok && cudaMalloc((void**)&h->diag_dev, (kDiagSlots * kDiagWords + 2) * sizeof(double)) == cudaSuccess;
     if (ok) h->err_dev = reinterpret_cast<ErrorLatch*>(h->diag_dev + kDiagSlots * kDiagWords);
-    ok = ok && cudaStreamCreateWithFlags(&h->tail, cudaStreamNonBlocking) == cudaSuccess;
-    for (int k = 0; k < 2; ++k) {
+    // the diagnostics stream at the highest priority: its small final sums are dispatched as
+    // soon as the running step frees a block slot, instead of after the step's last block
+    int prio_least = 0, prio_greatest = 0;
+    ok = ok && cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithPriority(&h->tail, cudaStreamNonBlocking, prio_greatest) == cudaSuccess;
+    for (int k = 0; k < kDiagSlots; ++k) {
         ok = ok && cudaEventCreateWithFlags(&h->part_ev[k], cudaEventDisableTiming) == cudaSuccess;
         ok = ok && cudaEventCreateWithFlags(&h->tail_done[k], cudaEventDisableTiming) == cudaSuccess;
     }
@@ -568,21 +574,21 @@ fmlbm_status fmlbm_step(fmlbm_handle* h, int64_t nsteps) {
             A.diag_partial = partial_set(h, fused);
             A.rho_prev = h->rho_prev;
             A.have_prev = h->have_prev;
-            // the tail of request fused - 2 may still read this set of partial sums
-            if (!capturing) FM_CUDA(h, cudaStreamWaitEvent(h->stream, h->tail_done[fused & 1], 0));
+            // the tail of request fused - kDiagSlots may still read this set of partial sums
+            if (!capturing) FM_CUDA(h, cudaStreamWaitEvent(h->stream, h->tail_done[fused % kDiagSlots], 0));
         }
         FM_CUDA(h, dispatch_step(h, A, false));
         if (fused >= 0) {
             // final sum and copies on the diagnostics stream, so the next step need not wait
             cudaStream_t ts = h->stream;
             if (!capturing) {
-                FM_CUDA(h, cudaEventRecord(h->part_ev[fused & 1], h->stream));
-                FM_CUDA(h, cudaStreamWaitEvent(h->tail, h->part_ev[fused & 1], 0));
+                FM_CUDA(h, cudaEventRecord(h->part_ev[fused % kDiagSlots], h->stream));
+                FM_CUDA(h, cudaStreamWaitEvent(h->tail, h->part_ev[fused % kDiagSlots], 0));
                 ts = h->tail;
             }
             fmlbm_status s = enqueue_diag_tail(h, fused, ts, true, capturing);
             if (s != FMLBM_OK) return s;
-            if (!capturing) FM_CUDA(h, cudaEventRecord(h->tail_done[fused & 1], ts));
+            if (!capturing) FM_CUDA(h, cudaEventRecord(h->tail_done[fused % kDiagSlots], ts));
         }
         h->cur ^= 1;
         ++h->step;
