@@ -9,7 +9,8 @@ launch).  Prints ONE JSON line (rank 0).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Under torchrun each rank advances its own independent lattice (weak scaling, no
-data-path collective; a barrier and a max-reduction of the timings only).
+data-path collective; a barrier and a max-reduction of the timings only); the batched
+sweep splits its lattices and the serving run its requests between the ranks.
 ``--impl reference`` times the FP64 CPU oracle on the same workload.
 """
 from __future__ import annotations
@@ -34,6 +35,49 @@ ALGO_BYTES = {"fp64": 144.0, "fp32": 72.0, "fp16dev": 40.0, "bf16dev": 40.0}  # 
 L2_FLUSH_BYTES = 256 << 20
 KERNEL_SOURCES = ["paper_2212_10680_gb300/csrc/fmlbm_kernels.cuh", "paper_2212_10680_gb300/csrc/fmlbm_launch.cuh",
                   "paper_2212_10680_gb300/csrc/fmlbm_tma.cuh"]
+
+
+# ---- ranks (torchrun): independent problems are split, timings reduced; no data exchange ----
+
+def shard(n_items: int, rank: int, world: int) -> range:
+    """This rank's contiguous share of n_items independent problems (shares differ by at
+    most one; together they cover every item once)."""
+    return range(n_items * rank // world, n_items * (rank + 1) // world)
+
+
+def round_robin(n_items: int, rank: int, world: int) -> list:
+    """Items rank, rank + world, ...: an arrival stream thinned per rank (each share of a
+    Poisson stream is again Poisson, at rate / world)."""
+    return list(range(rank, n_items, world))
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over the ranks (every rank gets it); x itself without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, dist, device) -> float:
+    """The sum of x over the ranks (every rank gets it)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def gather_lists(xs: list, dist) -> list:
+    """Every rank's list, concatenated in rank order (every rank gets it)."""
+    if dist is None:
+        return list(xs)
+    parts = [None] * dist.get_world_size()
+    dist.all_gather_object(parts, list(xs))
+    return [x for p in parts for x in p]
 
 
 def kernel_hash() -> str:
@@ -265,11 +309,7 @@ def run_ours(args, w, rank, world, dist):
         barrier()
     ms = [a.elapsed_time(b) for a, b in ev]
     lat.synchronize()
-    total_s = sum(ms) / 1e3
-    if dist is not None:
-        t = torch.tensor([total_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(sum(ms) / 1e3, dist, dev)
     units = n * nodes * args.steps * world
     value = units / total_s / 1e9
     per_launch_s = total_s / args.steps
@@ -302,11 +342,7 @@ def run_ours(args, w, rank, world, dist):
     for t in tickets[max(0, e2e_steps - 3):]:
         fmlbm.fmlbm_diagnostics_wait(lat.h, t, n)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
     e2e_value = n * nodes * e2e_steps * world / e2e_s / 1e9
     lat.close()
 
@@ -344,11 +380,12 @@ def _stats_pct(values, q):
     return float(np.percentile(np.asarray(values), q)) if len(values) else None
 
 
-def run_batch(args, rank, world):
+def run_batch(args, rank, world, dist=None):
     """Batched P-x sweep: 256 independent binary lattices (side ~ U{64..512}, feeds z1 swept
     0.05..0.95 at fixed T), one persistent multi-lattice step per time step, graph-captured
     chunks, per-lattice retirement; against the same lattices run one after another with
-    single-lattice handles and the same retirement rule."""
+    single-lattice handles and the same retirement rule.  Under torchrun each rank takes a
+    contiguous share of the 256 lattices (the total is fixed: strong scaling)."""
     import torch
     from paper_2212_10680_gb300 import fmlbm, inputs
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
@@ -359,33 +396,51 @@ def run_batch(args, rank, world):
     nlat = args.batch_lattices
     rng = np.random.default_rng(4)
     sides = rng.integers(64, 513, nlat)
-    fields = []
-    for k in range(nlat):
+    mine = list(shard(nlat, rank, world))
+    fields = {}
+    for k in mine:
         st = wl["binary_sweep"][int(round(k * 255 / max(nlat - 1, 1)))]
         L = int(sides[k])
-        fields.append(inputs.with_noise(inputs.slab(st["rt_vapour"], st["rt_liquid"], L, L, 0.5, 4.0), 0.01, 4,
-                                        lattice=k))
+        fields[k] = inputs.with_noise(inputs.slab(st["rt_vapour"], st["rt_liquid"], L, L, 0.5, 4.0), 0.01, 4,
+                                      lattice=k)
     mix = fmlbm.mixture_from_dict(mixd)
     prec = args.precision or "fp32"
-    b = fmlbm.fmlbm_batch_create(n, prec, nlat)
-    for k in range(nlat):
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ty = blocks = None
+    units, status_mine = 0, []
+    b = fmlbm.fmlbm_batch_create(n, prec, max(len(mine), 1))
+    for k in mine:
         L = int(sides[k])
         fmlbm.fmlbm_batch_add(b, mix, fmlbm.make_lattice(L, L, 1.0, "isotropic", prec), fields[k])
-    ty, blocks, ms_tune = fmlbm.fmlbm_batch_autotune(b, 3)
-    # the autotuner's trial steps are real steps; count them in the work
-    tuned_steps = [fmlbm.fmlbm_batch_slot_info(b, k)[0] for k in range(nlat)]
-    torch.cuda.synchronize()
+    if mine:
+        ty, blocks, ms_tune = fmlbm.fmlbm_batch_autotune(b, 3)
+        # the autotuner's trial steps are real steps; count them in the work
+        tuned_steps = [fmlbm.fmlbm_batch_slot_info(b, j)[0] for j in range(len(mine))]
+    barrier()
     t0 = time.perf_counter()
-    steps, res, st = fmlbm.fmlbm_batch_run(b, nlat, args.max_steps, args.check_every, args.tol)
-    torch.cuda.synchronize()
+    if mine:
+        steps, res, st = fmlbm.fmlbm_batch_run(b, len(mine), args.max_steps, args.check_every, args.tol)
+        torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
     fmlbm.fmlbm_batch_destroy(b)
-    units = sum(n * int(sides[k]) ** 2 * (int(steps[k]) - tuned_steps[k]) for k in range(nlat))
+    if mine:
+        units = sum(n * int(sides[k]) ** 2 * (int(steps[j]) - tuned_steps[j]) for j, k in enumerate(mine))
+        status_mine = [int(v) for v in st]
+    t_batch = max_over_ranks(t_batch, dist, dev)
+    units = sum_over_ranks(units, dist, dev)
+    statuses = np.array(gather_lists(status_mine, dist), dtype=np.int64)
+    max_steps_done = int(max_over_ranks(int(np.max(steps)) if mine else 0, dist, dev))
 
     # the plain per-lattice loop: one handle at a time, same chunking and retirement rule
     seq_units, seq_status = 0, []
+    barrier()
     t0 = time.perf_counter()
-    for k in range(nlat):
+    for k in mine:
         L = int(sides[k])
         lat = fmlbm.Lattice(mix, L, L, 1.0, "isotropic", prec, "lagged")
         lat.init(fields[k])
@@ -406,11 +461,12 @@ def run_batch(args, rank, world):
         seq_status.append(status)
         lat.close()
     torch.cuda.synchronize()
-    t_seq = time.perf_counter() - t0
-    counts = {fmlbm.STATUS[int(v)]: int((st == v).sum()) for v in np.unique(st)}
+    t_seq = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    seq_units = sum_over_ranks(seq_units, dist, dev)
+    counts = {fmlbm.STATUS[int(v)]: int((statuses == v).sum()) for v in np.unique(statuses)}
     line = dict(
         metric="batched VLE solves/sec", value=nlat / t_batch, unit="solves/s", n_gpus=world,
-        steps=int(np.max(steps)), warmup=3, ms_per_step=None, higher_is_better=True, scaling="weak",
+        steps=max_steps_done, warmup=3, ms_per_step=None, higher_is_better=True, scaling="strong",
         vs_baseline=None, dtype="f64" if prec == "fp64" else "f32", data="synthetic",
         config=dict(workload=f"batched P-x sweep: {nlat} binary PR lattices, side U{{64..512}}, z1 0.05..0.95, "
                              f"flat slab, tau 1.0", precision=prec, max_steps=args.max_steps,
@@ -424,10 +480,11 @@ def run_batch(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
-def run_serve(args, rank, world):
+def run_serve(args, rank, world, dist=None):
     """Serving: Poisson arrivals of binary and ternary VLE requests (templates with random T
     and feed, side ~ U{64..1024}); continuous batching servers, one per component count;
-    against a FIFO loop that runs one request at a time with a single-lattice handle."""
+    against a FIFO loop that runs one request at a time with a single-lattice handle.  Under
+    torchrun rank r serves requests r, r + N, ... (the same arrival stream, thinned)."""
     import threading as th
     import torch
     from paper_2212_10680_gb300 import fmlbm, inputs
@@ -439,20 +496,25 @@ def run_serve(args, rank, world):
     R = args.requests
     gaps = rng.exponential(1.0 / args.rate, R)
     arrive = np.cumsum(gaps) - gaps[0]
-    reqs = []
+    mine = set(round_robin(R, rank, world))
+    reqs = {}
     for k in range(R):
         t = temps[int(rng.integers(0, len(temps)))]
         side = int(rng.integers(64, args.max_side + 1))
+        if k not in mine:
+            continue
         rho = inputs.with_noise(inputs.slab(t["slab"]["rt_vapour"], t["slab"]["rt_liquid"], side, side, 0.5, 4.0),
                                 0.01, 5, lattice=k)
-        reqs.append(dict(k=k, n=len(t["mixture"]["Tc"]), mix=fmlbm.mixture_from_dict(t["mixture"]), side=side,
-                         rho=rho, t=float(arrive[k])))
+        reqs[k] = dict(k=k, n=len(t["mixture"]["Tc"]), mix=fmlbm.mixture_from_dict(t["mixture"]), side=side,
+                       rho=rho, t=float(arrive[k]))
+    if dist is not None:
+        dist.barrier()
     prec = "fp32"
     servers = {nc: fmlbm.fmlbm_server_create(nc, prec, args.slots, args.check_every, args.tol, args.max_steps,
                                              int(args.budget_gb * (1 << 30))) for nc in (2, 3)}
     results = []
     t0 = time.perf_counter()
-    for r in reqs:
+    for r in reqs.values():
         wait = r["t"] - (time.perf_counter() - t0)
         if wait > 0:
             time.sleep(wait)
@@ -460,21 +522,25 @@ def run_serve(args, rank, world):
                                                                                  "isotropic", prec), r["rho"], tag=r["k"])
         for s in servers.values():
             results += fmlbm.fmlbm_server_poll(s)
-    while len(results) < R:
+    while len(results) < len(reqs):
         for s in servers.values():
             results += fmlbm.fmlbm_server_poll(s)
         time.sleep(0.002)
-    wall = time.perf_counter() - t0
-    busy = {nc: fmlbm.fmlbm_server_stats(s)["busy"] for nc, s in servers.items()}
+    wall = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    busy = {nc: sum_over_ranks(fmlbm.fmlbm_server_stats(s)["busy"], dist, dev) / world for nc, s in servers.items()}
     for s in servers.values():
         fmlbm.fmlbm_server_destroy(s)
-    lat_s = [r["t_done"] - r["t_submit"] for r in results]
-    units = sum(reqs[r["tag"]]["n"] * reqs[r["tag"]]["side"] ** 2 * r["steps"] for r in results)
+    lat_s = gather_lists([r["t_done"] - r["t_submit"] for r in results], dist)
+    units = sum_over_ranks(sum(reqs[r["tag"]]["n"] * reqs[r["tag"]]["side"] ** 2 * r["steps"] for r in results),
+                           dist, dev)
+    status_all = gather_lists([r["status"] for r in results], dist)
 
     # FIFO baseline: the same arrivals, one request at a time through a single-lattice handle
     seq_lat = []
+    if dist is not None:
+        dist.barrier()
     t0 = time.perf_counter()
-    for r in reqs:
+    for r in reqs.values():
         wait = r["t"] - (time.perf_counter() - t0)
         if wait > 0:
             time.sleep(wait)
@@ -492,10 +558,11 @@ def run_serve(args, rank, world):
             pass
         lat.close()
         seq_lat.append(time.perf_counter() - t0 - r["t"])
-    seq_wall = time.perf_counter() - t0
+    seq_wall = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    seq_lat = gather_lists(seq_lat, dist)
     counts = {}
-    for r in results:
-        counts[fmlbm.STATUS[r["status"]]] = counts.get(fmlbm.STATUS[r["status"]], 0) + 1
+    for s_ in status_all:
+        counts[fmlbm.STATUS[s_]] = counts.get(fmlbm.STATUS[s_], 0) + 1
     line = dict(
         metric="served VLE solves/sec", value=R / wall, unit="solves/s", n_gpus=world, steps=args.max_steps,
         warmup=0, ms_per_step=None, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
@@ -542,12 +609,6 @@ def main():
         w = workload(args.workload, args.size)
         run_reference(args, w, rank, world)
         return
-    if args.workload == "batch256":
-        run_batch(args, rank, world)
-        return
-    if args.workload == "serve":
-        run_serve(args, rank, world)
-        return
     dist = None
     if world > 1:
         import torch
@@ -555,8 +616,13 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         td.init_process_group("nccl")
         dist = td
-    w = workload(args.workload, args.size)
-    run_ours(args, w, rank, world, dist)
+    if args.workload == "batch256":
+        run_batch(args, rank, world, dist)
+    elif args.workload == "serve":
+        run_serve(args, rank, world, dist)
+    else:
+        w = workload(args.workload, args.size)
+        run_ours(args, w, rank, world, dist)
     if dist is not None:
         dist.destroy_process_group()
 

@@ -1,0 +1,83 @@
+"""The multi-rank host paths of bench.py on the CPU: how independent problems are split
+between ranks, the reductions of timings and counts over a gloo process group of two
+ranks, and a two-rank torchrun launch of the reference arm (only rank 0 reports)."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+@pytest.mark.parametrize("n", [0, 1, 7, 256, 257])
+@pytest.mark.parametrize("world", [1, 2, 3, 8])
+def test_shards_cover_every_item_once(n, world):
+    parts = [list(bench.shard(n, r, world)) for r in range(world)]
+    assert sorted(x for p in parts for x in p) == list(range(n))
+    sizes = [len(p) for p in parts]
+    assert max(sizes) - min(sizes) <= 1
+    for p in parts:  # contiguous
+        if p:
+            assert p == list(range(p[0], p[0] + len(p)))
+    rr = [bench.round_robin(n, r, world) for r in range(world)]
+    assert sorted(x for p in rr for x in p) == list(range(n))
+    assert all(x % world == r for r, p in enumerate(rr) for x in p)
+
+
+def test_reductions_without_a_process_group():
+    assert bench.max_over_ranks(3.5, None, None) == 3.5
+    assert bench.sum_over_ranks(2, None, None) == 2.0
+    assert bench.gather_lists([1, 2], None) == [1, 2]
+
+
+def _rank_main(rank, world, port, out_dir):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        res = dict(
+            mx=bench.max_over_ranks(1.5 + rank, dist, "cpu"),
+            sm=bench.sum_over_ranks(10 * (rank + 1), dist, "cpu"),
+            gl=bench.gather_lists([rank] * (rank + 1), dist),
+            mine=list(bench.shard(5, rank, world)),
+        )
+        with open(os.path.join(out_dir, f"rank{rank}.json"), "w") as f:
+            json.dump(res, f)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_reductions_over_two_gloo_ranks(tmp_path):
+    import torch.multiprocessing as mp
+    mp.start_processes(_rank_main, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    got = [json.load(open(tmp_path / f"rank{r}.json")) for r in range(2)]
+    for r, g in enumerate(got):
+        assert g["mx"] == 2.5                 # the slowest rank's time, on every rank
+        assert g["sm"] == 30.0                # units summed over the ranks
+        assert g["gl"] == [0, 1, 1]           # per-request values, rank order
+    assert got[0]["mine"] + got[1]["mine"] == [0, 1, 2, 3, 4]
+
+
+def test_reference_arm_under_torchrun_reports_once():
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
+           os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0"]
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    p = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT, env=env)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [json.loads(line) for line in p.stdout.splitlines() if line.startswith("{")]
+    assert len(lines) == 1
+    d = lines[0]
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
