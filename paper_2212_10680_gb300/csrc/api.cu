@@ -189,8 +189,6 @@ StepArgs make_args(const fmlbm_handle* h, int src) {
     A.g0in = h->g0[src];
     A.gout = h->g[src ^ 1];
     A.g0out = h->g0[src ^ 1];
-    set_planes(A, h->nc, h->lattice.precision == FMLBM_FP16DEV || h->lattice.precision == FMLBM_BF16DEV,
-               h->lattice.precision == FMLBM_FP64 ? 8 : (h->lattice.precision == FMLBM_FP32 ? 4 : 2));
     A.Fin = h->F[src];
     A.Fout = h->F[src ^ 1];
     A.err = h->err_dev;

@@ -120,26 +120,35 @@ struct StepArgs {
     void* diag_partial;
     void* rho_prev;  // [N][ny][nx] in the storage arithmetic type
     int have_prev;
-    // the base address of every distribution plane of gin / gout (set_planes): F64/F32 plane
-    // i*9+a; 16-bit storage plane i*8+a-1 (a >= 1) and float plane i (a = 0)
-    const void* gin_p[kMaxC * 9];
-    void* gout_p[kMaxC * 9];
-    const float* g0in_p[kMaxC];
-    float* g0out_p[kMaxC];
 };
 
-// elem: bytes per element of the planes gin / gout point to (8, 4 or 2).
-inline void set_planes(StepArgs& A, int nc, bool dev16, size_t elem) {
+// The base address of every distribution plane of A.gin / A.gout, a second launch
+// parameter of the single-lattice step only (in StepArgs it made the batch kernel, which
+// copies each lattice's StepArgs into shared memory per tile, 7% slower on the serving
+// workload).  F64/F32 storage: plane i*9+a; 16-bit storage: plane i*8+a-1 (a >= 1) and
+// float plane i (a = 0).  The launcher fills it from A (make_planes).
+struct Planes {
+    const void* in[kMaxC * 9];
+    void* out[kMaxC * 9];
+    const float* g0in[kMaxC];
+    float* g0out[kMaxC];
+};
+
+// elem: bytes per element of the planes A.gin / A.gout point to (8, 4 or 2); unused entries
+// and those of null buffers stay null.
+inline Planes make_planes(const StepArgs& A, int nc, bool dev16, size_t elem) {
+    Planes P = {};
     const size_t nxy = (size_t)A.nx * A.ny;
     const int per = dev16 ? 8 : 9;
     for (int k = 0; k < nc * per; ++k) {
-        A.gin_p[k] = A.gin ? static_cast<const char*>(A.gin) + k * nxy * elem : nullptr;
-        A.gout_p[k] = A.gout ? static_cast<char*>(A.gout) + k * nxy * elem : nullptr;
+        P.in[k] = A.gin ? static_cast<const char*>(A.gin) + k * nxy * elem : nullptr;
+        P.out[k] = A.gout ? static_cast<char*>(A.gout) + k * nxy * elem : nullptr;
     }
     for (int i = 0; i < nc && dev16; ++i) {
-        A.g0in_p[i] = A.g0in ? A.g0in + i * nxy : nullptr;
-        A.g0out_p[i] = A.g0out ? A.g0out + i * nxy : nullptr;
+        P.g0in[i] = A.g0in ? A.g0in + i * nxy : nullptr;
+        P.g0out[i] = A.g0out ? A.g0out + i * nxy : nullptr;
     }
+    return P;
 }
 
 template <typename E> __device__ __forceinline__ const MixConstT<E>& mixc(const StepArgs& A);
@@ -185,26 +194,25 @@ __device__ __forceinline__ typename StoreTraits<ST>::Real load_g(const StepArgs&
 // forms above compute a 64-bit plane offset (two-component step: +1.5% on GB300; with
 // three components it cost registers and spilled).
 template <int ST>
-__device__ __forceinline__ typename StoreTraits<ST>::Real load_gp(const StepArgs& A, int i, int a, int node) {
+__device__ __forceinline__ typename StoreTraits<ST>::Real load_gp(const Planes& P, int i, int a, int node) {
     using Elem = typename StoreTraits<ST>::Elem;
     if constexpr (ST == ST_F64 || ST == ST_F32) {
-        return to_real(ldg(static_cast<const Elem*>(A.gin_p[i * 9 + a]) + node));
+        return to_real(ldg(static_cast<const Elem*>(P.in[i * 9 + a]) + node));
     } else {
-        if (a == 0) return ldg(A.g0in_p[i] + node);
-        return to_real(ldg(static_cast<const Elem*>(A.gin_p[i * 8 + a - 1]) + node));
+        if (a == 0) return ldg(P.g0in[i] + node);
+        return to_real(ldg(static_cast<const Elem*>(P.in[i * 8 + a - 1]) + node));
     }
 }
 template <int ST>
-__device__ __forceinline__ void store_gp(const StepArgs& A, int i, int a, int node,
-                                         typename StoreTraits<ST>::Real v) {
+__device__ __forceinline__ void store_gp(const Planes& P, int i, int a, int node, typename StoreTraits<ST>::Real v) {
     using Elem = typename StoreTraits<ST>::Elem;
     if constexpr (ST == ST_F64 || ST == ST_F32) {
-        static_cast<Elem*>(A.gout_p[i * 9 + a])[node] = v;
+        static_cast<Elem*>(P.out[i * 9 + a])[node] = v;
     } else {
         if (a == 0)
-            A.g0out_p[i][node] = v;
+            P.g0out[i][node] = v;
         else
-            static_cast<Elem*>(A.gout_p[i * 8 + a - 1])[node] = from_real<Elem>(v);
+            static_cast<Elem*>(P.out[i * 8 + a - 1])[node] = from_real<Elem>(v);
     }
 }
 
@@ -225,9 +233,9 @@ __device__ __forceinline__ void store_g(const StepArgs& A, int i, int a, size_t 
 }
 
 template <int ST, bool PP>
-__device__ __forceinline__ void store_gsel(const StepArgs& A, int i, int a, int node, int nxy,
+__device__ __forceinline__ void store_gsel(const StepArgs& A, const Planes* P, int i, int a, int node, int nxy,
                                            typename StoreTraits<ST>::Real v) {
-    if constexpr (PP) store_gp<ST>(A, i, a, node, v);
+    if constexpr (PP) store_gp<ST>(*P, i, a, node, v);
     else store_g<ST>(A, i, a, (size_t)node, (size_t)nxy, v);
 }
 
@@ -358,7 +366,7 @@ struct StepSmem {
 // of 256 threads per SM instead of four (1024^2 binary FP32: 2.5% faster on GB300).  With
 // three or four components the step spills at 48 registers even with values parked, and
 // parking every value of a node was slower.  The same step also addresses the distribution
-// planes through the launch's plane pointers (load_gp / store_gp).
+// planes through the launch's plane pointers (Planes, load_gp / store_gp).
 template <int NC, int ST, int TY>
 constexpr bool kParkLast = ST != ST_F64 && NC == 2 && TY == 8;
 template <int NC, int ST, int TY>
@@ -426,7 +434,7 @@ __device__ __forceinline__ int pull_src(int a, int wx, int wy, int xm, int xp, i
 // Sum of the pulled distributions of component i at node (wx, wy) (wrapped coordinates).
 template <int NC, int ST, bool PP = false>
 __device__ __forceinline__ void pull_rho(const StepArgs& A, int wx, int wy, bool inner, int nx, int ny, int nxy,
-                                         typename StoreTraits<ST>::Real* rs) {
+                                         typename StoreTraits<ST>::Real* rs, const Planes* P = nullptr) {
     using Real = typename StoreTraits<ST>::Real;
     const int node = wy * nx + wx;
     int xm = wx - 1, xp = wx + 1, ym = wy - 1, yp = wy + 1;
@@ -443,7 +451,7 @@ __device__ __forceinline__ void pull_rho(const StepArgs& A, int wx, int wy, bool
         const int src = inner ? node - ey(a) * nx - ex(a) : pull_src(a, wx, wy, xm, xp, ym, yp, nx);
 #pragma unroll
         for (int i = 0; i < NC; ++i)
-            rs[i] += PP ? load_gp<ST>(A, i, a, src) : load_g<ST>(A, i, a, (size_t)src, (size_t)nxy);
+            rs[i] += PP ? load_gp<ST>(*P, i, a, src) : load_g<ST>(A, i, a, (size_t)src, (size_t)nxy);
     }
 }
 
@@ -566,7 +574,8 @@ template <int NC, int ST, int TY, bool MOMENTS, bool STD = false, bool PARK = fa
 __device__ __forceinline__ void phase3(const StepArgs& A, const MixConstT<typename StoreTraits<ST>::Real>& m,
                                        StepSmem<typename StoreTraits<ST>::Real, NC, TY>& S,
                                        const typename StoreTraits<ST>::Real (&g)[NC][9], int tx, int ty, int gxn,
-                                       int gyn, const typename StoreTraits<ST>::Real* park = nullptr) {
+                                       int gyn, const typename StoreTraits<ST>::Real* park = nullptr,
+                                       const Planes* P = nullptr) {
     using Real = typename StoreTraits<ST>::Real;
     const int nx = A.nx, nxy = A.nx * A.ny;
     const int cx = tx + 1, cy = ty + 1;  // tile+1 coordinates of this node
@@ -663,20 +672,20 @@ __device__ __forceinline__ void phase3(const StepArgs& A, const MixConstT<typena
             const Real Ox = rw3 * ux + fc_3 * Fx[i];
             const Real Oy = rw3 * uy + fc_3 * Fy[i];
             const Real rest0 = STD ? Real(4.0 / 9.0) * rw : rw;
-            store_gsel<ST, PP>(A, i, 0, node, nxy,
+            store_gsel<ST, PP>(A, P, i, 0, node, nxy,
                         keep * h[0] + (rest0 + Real(4.0 / 9.0) * (a0 - Real(2) * fc * ug)));
             const Real e1 = w1 * (ux * Vx + cb_ax + rwS);
-            store_gsel<ST, PP>(A, i, 1, node, nxy, keep * h[1] + (e1 + Ox));
-            store_gsel<ST, PP>(A, i, 3, node, nxy, keep * h[3] + (e1 - Ox));
+            store_gsel<ST, PP>(A, P, i, 1, node, nxy, keep * h[1] + (e1 + Ox));
+            store_gsel<ST, PP>(A, P, i, 3, node, nxy, keep * h[3] + (e1 - Ox));
             const Real e2 = w1 * (uy * Vy + cb_ax + rwS);
-            store_gsel<ST, PP>(A, i, 2, node, nxy, keep * h[2] + (e2 + Oy));
-            store_gsel<ST, PP>(A, i, 4, node, nxy, keep * h[4] + (e2 - Oy));
+            store_gsel<ST, PP>(A, P, i, 2, node, nxy, keep * h[2] + (e2 + Oy));
+            store_gsel<ST, PP>(A, P, i, 4, node, nxy, keep * h[4] + (e2 - Oy));
             const Real e5 = w5 * (u5 * (Vx + Vy) + cb_dg + rwS), o5 = Real(0.25) * (Ox + Oy);
-            store_gsel<ST, PP>(A, i, 5, node, nxy, keep * h[5] + (e5 + o5));
-            store_gsel<ST, PP>(A, i, 7, node, nxy, keep * h[7] + (e5 - o5));
+            store_gsel<ST, PP>(A, P, i, 5, node, nxy, keep * h[5] + (e5 + o5));
+            store_gsel<ST, PP>(A, P, i, 7, node, nxy, keep * h[7] + (e5 - o5));
             const Real e6 = w5 * (u6 * (Vy - Vx) + cb_dg + rwS), o6 = Real(0.25) * (Oy - Ox);
-            store_gsel<ST, PP>(A, i, 6, node, nxy, keep * h[6] + (e6 + o6));
-            store_gsel<ST, PP>(A, i, 8, node, nxy, keep * h[8] + (e6 - o6));
+            store_gsel<ST, PP>(A, P, i, 6, node, nxy, keep * h[6] + (e6 + o6));
+            store_gsel<ST, PP>(A, P, i, 8, node, nxy, keep * h[8] + (e6 - o6));
         }
         Real* Fout = static_cast<Real*>(A.Fout);
         Fout[node] = Ftx;
@@ -690,7 +699,7 @@ template <int NC, int ST, int TY, bool PP = false>
 __device__ __forceinline__ void phase1_global(const StepArgs& A, const MixConstT<typename StoreTraits<ST>::Real>& m,
                                               StepSmem<typename StoreTraits<ST>::Real, NC, TY>& S,
                                               typename StoreTraits<ST>::Real (&g)[NC][9], int x0, int y0,
-                                              bool inner, int tx, int ty, int tid) {
+                                              bool inner, int tx, int ty, int tid, const Planes* P = nullptr) {
     using Real = typename StoreTraits<ST>::Real;
     constexpr int NT = kTX * TY;
     const int nx = A.nx, ny = A.ny, nxy = nx * ny;
@@ -711,7 +720,7 @@ __device__ __forceinline__ void phase1_global(const StepArgs& A, const MixConstT
         ring_position<TY>(tid, bx, by);
         const int wx = inner ? x0 - 2 + bx : wrap(x0 - 2 + bx, nx);
         const int wy = inner ? y0 - 2 + by : wrap(y0 - 2 + by, ny);
-        pull_rho<NC, ST, PP>(A, wx, wy, inner, nx, ny, nxy, rr);
+        pull_rho<NC, ST, PP>(A, wx, wy, inner, nx, ny, nxy, rr, P);
     };
     if (RING_FIRST && has_ring) pull_ring();
     {
@@ -729,7 +738,7 @@ __device__ __forceinline__ void phase1_global(const StepArgs& A, const MixConstT
             const int src = inner ? node - ey(a) * nx - ex(a) : pull_src(a, wx, wy, xm, xp, ym, yp, nx);
 #pragma unroll
             for (int i = 0; i < NC; ++i)
-                g[i][a] = PP ? load_gp<ST>(A, i, a, src) : load_g<ST>(A, i, a, (size_t)src, (size_t)nxy);
+                g[i][a] = PP ? load_gp<ST>(*P, i, a, src) : load_g<ST>(A, i, a, (size_t)src, (size_t)nxy);
         }
     }
     if constexpr (RING_FIRST) {
@@ -845,7 +854,7 @@ template <int NC, int ST, int TY, bool MOMENTS, bool STD = false>
 // slower for three components) or registers for occupancy (48 registers spill).  The FP64
 // reference path keeps what the compiler chooses.
 __global__ void __launch_bounds__(kTX* TY, ST == ST_F64 ? 1 : (kParkLast<NC, ST, TY> ? 5 : 1024 / (kTX * TY)))
-    fused_step(StepArgs A) {
+    fused_step(StepArgs A, Planes P) {
     using Real = typename StoreTraits<ST>::Real;
     constexpr bool PARK = kParkLast<NC, ST, TY>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -866,12 +875,12 @@ __global__ void __launch_bounds__(kTX* TY, ST == ST_F64 ? 1 : (kParkLast<NC, ST,
     if constexpr (!MOMENTS) diag_prefetch<NC, Real, TY>(A, pv_s, tx, ty, gxn, gyn);
     prefetch_force<Real, NC, TY>(A, S, tx, ty, gxn, gyn);
     Real g[NC][9];
-    phase1_global<NC, ST, TY, PARK>(A, m, S, g, x0, y0, inner, tx, ty, tid);
+    phase1_global<NC, ST, TY, PARK>(A, m, S, g, x0, y0, inner, tx, ty, tid, &P);
     if constexpr (PARK) park_store<TY, Real>(g[NC - 1], park, tid);
     __syncthreads();
     phase2<NC, TY, Real>(m, S, A.stencil, tid);
     __syncthreads();
-    if (gxn < nx && gyn < ny) phase3<NC, ST, TY, MOMENTS, STD, PARK, PARK>(A, m, S, g, tx, ty, gxn, gyn, park);
+    if (gxn < nx && gyn < ny) phase3<NC, ST, TY, MOMENTS, STD, PARK, PARK>(A, m, S, g, tx, ty, gxn, gyn, park, &P);
     if constexpr (!MOMENTS) {
         if (A.diag_partial != nullptr) {  // uniform: diagnostics of the state this step read
             if constexpr (PARK) pulled_all<NC, TY, PARK, Real>(g, park, NC - 1, tid, g[NC - 1]);

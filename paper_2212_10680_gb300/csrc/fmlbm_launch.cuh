@@ -71,7 +71,9 @@ inline cudaError_t launch_reduce_final(int nc, bool fp64, const void* partial, i
             attr_done = true;                                                                             \
         }                                                                                                 \
         dim3 grid((A.nx + kTX - 1) / kTX, (A.ny + TY - 1) / TY);                                          \
-        k<<<grid, dim3(kTX, TY), smem, s>>>(A);                                                           \
+        const Planes P = make_planes(A, NC, ST == ST_F16DEV || ST == ST_BF16DEV,                          \
+                                     ST == ST_F64 ? 8 : (ST == ST_F32 ? 4 : 2));                          \
+        k<<<grid, dim3(kTX, TY), smem, s>>>(A, P);                                                        \
         return cudaGetLastError();                                                                        \
     }                                                                                                     \
     template <int NC>                                                                                     \

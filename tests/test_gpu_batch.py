@@ -56,6 +56,35 @@ def test_batch_equals_single_lattices_bitwise(fm, precision):
     fm.fmlbm_batch_destroy(b)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16dev"])
+def test_batch_moments_equal_single_lattice_moments(fm, precision):
+    # a lattice below 64 rows takes the 8-row moments kernel (for two components in float
+    # storage the form that parks values and addresses planes through launch parameters),
+    # a taller one the 16-row kernel; both against the single-lattice handle, bitwise
+    from paper_2212_10680_gb300 import inputs
+    wl = workloads()
+    mixd = wl["binary"]["mixture"]
+    b = fm.fmlbm_batch_create(2, precision, 4)
+    cases = []
+    for k, (nx, ny) in enumerate([(70, 37), (40, 96)]):
+        st = wl["binary_sweep"][100 + 30 * k]
+        rho = inputs.with_noise(inputs.slab(st["rt_vapour"], st["rt_liquid"], nx, ny, 0.5, 4.0), 0.01, 20 + k)
+        L = fm.make_lattice(nx, ny, 1.0, "isotropic", precision, "lagged")
+        cases.append((fm.fmlbm_batch_add(b, fm.mixture_from_dict(mixd), L, rho), rho))
+    fm.fmlbm_batch_step(b, 10)
+    for slot, rho in cases:
+        ny, nx = rho.shape[1:]
+        r, u, lnf = np.empty((2, ny, nx)), np.empty((2, ny, nx)), np.empty((2, ny, nx))
+        fm.fmlbm_batch_moments(b, slot, r, u, lnf)
+        lat = fm.Lattice(fm.mixture_from_dict(mixd), nx, ny, 1.0, "isotropic", precision, "lagged")
+        lat.init(rho)
+        lat.step(10)
+        rs, us, ls = lat.moments()
+        lat.close()
+        assert np.array_equal(r, rs) and np.array_equal(u, us) and np.array_equal(lnf, ls), (nx, ny)
+    fm.fmlbm_batch_destroy(b)
+
+
 def test_batch_alone_equals_in_the_mix_and_after_retirements(fm):
     mixd, rho = slab_state_binary(64, 48, seed=3)
     alone = _single(fm, mixd, rho, 60, "fp32", 16)
