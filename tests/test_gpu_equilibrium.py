@@ -7,6 +7,8 @@ steps and its bulk liquid (strip centre) and vapour (strip edge) are compared wi
 * the PT flash of the binary at the pressure of the lattice's bulk vapour (tolerance 3e-4,
   the accuracy the method reaches at this interface resolution; it degrades for sharper
   interfaces) and equal fugacities between the bulk phases.
+The 1024 x 1024 droplet of the throughput benchmark is checked against the flash at its
+vapour's pressure, for equal fugacities across the curved interface, and for Laplace's law.
 """
 import numpy as np
 import pytest
@@ -14,6 +16,7 @@ import pytest
 from cases import PC1, TC1, oracle_mixture
 from oracle.eos import lnf_density_form, pressure
 from oracle.flash import flash, pure_coexistence, slab_state
+from oracle.interface import crossing_radius, interfacial_tension
 
 pytestmark = pytest.mark.gpu
 
@@ -69,3 +72,47 @@ def test_binary_slab_matches_the_flash_at_its_pressure(fm):
     assert np.max(np.abs(L / L.sum() - f["x"]) / f["x"]) < 3e-4
     assert np.max(np.abs(V / V.sum() - f["y"]) / f["y"]) < 3e-4
     assert np.max(np.abs(lnf_density_form(mix, L) - lnf_density_form(mix, V))) < 1e-4
+
+
+def test_droplet_1024_fp32_against_the_flash(fm):
+    # The throughput configuration's physics: the 1024 x 1024 binary droplet (radius 200,
+    # FP32, tau 1, 1% noise) after 50,000 steps.  The curved interface compresses the liquid,
+    # so the flat flash is not the liquid's reference: the vapour far from the droplet is
+    # compared with the flash at its own pressure, and the droplet centre with the far vapour
+    # (equal fugacities across the interface).  Tolerances: the method's discretisation error
+    # at this sharp interface (the flat slab of the same mixture at 0.8 Tc1 is off by 2-3 % in
+    # density and 1e-2 in ln f); FP32 cannot reach a 1e-8 residual and the droplet still
+    # carries spurious currents of about 1e-4.  The droplet keeps its size (crossing radius),
+    # and Eq. eqMCsigma over its own profile gives the sigma of a flat interface of the same
+    # mixture (a strip run alongside) to 2 %: at R / W ~ 50 the tension does not depend on
+    # the curvature.
+    import bench
+    w = bench.workload("droplet1024")
+    mixd = w["mixture"]
+    mix = oracle_mixture(mixd)
+    n = w["nx"]
+    lat = fm.Lattice(fm.mixture_from_dict(mixd), n, n, w["tau"], w["stencil"], "fp32", "lagged")
+    lat.init(w["rho"])
+    lat.step(50000)
+    r, u, lnf = lat.moments()
+    lat.close()
+    c = n // 2
+    L = r[:, c - 2:c + 3, c - 2:c + 3].mean(axis=(1, 2))      # droplet centre (M = 1: molar)
+    V = r[:, 0:5, 0:5].mean(axis=(1, 2))                      # farthest from the droplet
+    f = flash(mix, float(pressure(mix, V)), [0.5, 0.5])
+    assert np.max(np.abs(V / f["rtV"] - 1)) < 2e-2
+    assert np.max(np.abs((V / V.sum() - f["y"]) / f["y"])) < 2e-2
+    assert np.max(np.abs(lnf_density_form(mix, L) - lnf_density_form(mix, V))) < 2e-2
+    row = r[:, c, :].astype(np.float64)                        # crosses two interfaces
+    R = crossing_radius(row.sum(axis=0), c, 0.5 * (L.sum() + V.sum()))
+    assert 190 < R < 210
+    from paper_2212_10680_gb300 import inputs
+    strip = inputs.slab(V, L, n, 4, 0.5, 4.0)
+    lat = fm.Lattice(fm.mixture_from_dict(mixd), n, 4, w["tau"], w["stencil"], "fp32", "lagged")
+    lat.init(strip)
+    lat.step(50000)
+    rs, _, _ = lat.moments()
+    lat.close()
+    sigma_flat = interfacial_tension(rs[:, 2, :].astype(np.float64), mixd["kappa"], n_interfaces=2)
+    sigma_drop = interfacial_tension(row, mixd["kappa"], n_interfaces=2)
+    assert abs(sigma_drop / sigma_flat - 1) < 2e-2, (sigma_drop, sigma_flat)

@@ -86,6 +86,33 @@ def test_binary_slab_parity(fm, precision, stencil):
     _compare(gpu, ora, TOL[precision], mixd)
 
 
+def test_small_binary_fp64_two_thousand_steps(fm):
+    # The small parity configuration: the binary slab on 64 x 64 in FP64 for 2000 steps
+    # (tau 1, isotropic stencils, lagged force, 1% noise), compared at steps 1, 2, 10, 100,
+    # 1000 and 2000.  rho, g and ln f: 1e-12 of their largest value.  F and u decay towards
+    # zero as the slab equilibrates while the terms that cancel in them stay O(1), so their
+    # rounding differences are bounded relative to those terms: 1e-12 RT max(rho~) max|ln f|
+    # for F (the size of rho~ RT grad ln f) and half of that over the smallest total density
+    # for u = (j + F/2) / rho.  (Perturbing the oracle's input by 1e-15 moves F by 3e-15 and u
+    # by 3e-16 at every one of these steps.)  Component masses: conserved to 1e-13.
+    mixd, rho = slab_state_binary(64, 64, seed=1)
+    rec = (1, 2, 10, 100, 1000, 2000)
+    ora = run_oracle(mixd, rho, 1.0, "isotropic", "lagged", max(rec), rec)
+    gpu = _gpu_run(fm, mixd, rho, 1.0, "isotropic", "fp64", "lagged", max(rec), rec)
+    RT = mixd["R"] * mixd["T"]
+    for k in rec:
+        o, gk = ora[k], gpu[k]
+        for f in ("rho", "g", "lnf"):
+            assert normwise(gk[f], o[f]) <= 1e-12, (k, f, normwise(gk[f], o[f]))
+        f_scale = RT * float(np.max(o["rho"])) * float(np.max(np.abs(o["lnf"])))
+        dF = float(np.max(np.abs(gk["F"] - o["F"])))
+        du = float(np.max(np.abs(gk["u"] - o["u"])))
+        assert dF <= 1e-12 * f_scale, (k, dF, f_scale)
+        assert du <= 1e-12 * (float(np.max(np.abs(o["u"]))) + 0.5 * f_scale / float(np.min(o["rho"].sum(axis=0)))), (k, du)
+    mass0 = rho.sum(axis=(1, 2))
+    assert np.max(np.abs(gpu[2000]["rho"].sum(axis=(1, 2)) / mass0 - 1)) <= 1e-13
+
+
 @pytest.mark.parametrize("n", [1, 2, 3, 4])
 @pytest.mark.parametrize("eos", ["pr", "srk", "vdw"])
 def test_components_and_eos_parity(fm, n, eos):
