@@ -177,8 +177,9 @@ fmlbm_status fmlbm_diagnostics(fmlbm_handle* h, double* mass, double* residual, 
  * every step adds no extra pass over the lattice; if no step follows,
  * fmlbm_diagnostics_wait runs the separate reduction.  Results are bit-identical either
  * way.  The final sum and the copies to the host of a request served inside a step run
- * on a second, non-blocking stream of the handle, ordered by events, so the next step
- * does not wait for them.  While the handle's stream is being captured into a CUDA graph
+ * on a second, non-blocking stream of the handle at the highest stream priority, ordered
+ * by events, with one set of partial sums per kept result, so the next steps do not wait
+ * for them.  While the handle's stream is being captured into a CUDA graph
  * they stay on that stream and are not ordered after diagnostics work still running on
  * the second stream: call fmlbm_synchronize before capturing if requests were made.
  * fmlbm_diagnostics_wait blocks until the ticket's results have reached the host
