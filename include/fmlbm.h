@@ -130,6 +130,29 @@ typedef struct fmlbm_handle fmlbm_handle;
 fmlbm_status fmlbm_create(const fmlbm_mixture* mixture, const fmlbm_lattice* lattice,
                           void* cuda_stream, fmlbm_handle** out);
 
+/* Bytes of each caller-provided buffer of fmlbm_create_with_buffers for this component
+ * count and lattice (no GPU needed): g_bytes per distribution buffer (N x 9 x ny x nx
+ * values of the storage type for FP64/FP32; N x 8 x ny x nx 16-bit values for the
+ * deviation forms), g0_bytes per a = 0 buffer (N x ny x nx floats; 0 unless a deviation
+ * form), force_bytes per stored-force buffer (2 x ny x nx doubles for FP64, floats
+ * otherwise).  FMLBM_E_INVALID_ARG for an invalid lattice or component count. */
+fmlbm_status fmlbm_buffer_sizes(int32_t n_components, const fmlbm_lattice* lattice, size_t* g_bytes,
+                                size_t* g0_bytes, size_t* force_bytes);
+
+/* As fmlbm_create, but the two distribution buffers g[0], g[1], the two a = 0 buffers
+ * g0[0], g0[1] of the deviation forms (g0 may be NULL otherwise) and the two stored-force
+ * buffers force[0], force[1] are device memory the caller owns (for example the storage of
+ * framework tensors), at least as large as fmlbm_buffer_sizes gives and 16-byte aligned.
+ * The handle uses them in place, in its own layout (the ping-pong buffers of the storage
+ * form, not the layout fmlbm_get_distributions returns), and never frees them: they must
+ * outlive the handle, and the caller must not write them while the handle's work is in
+ * flight.  Everything else (snapshot, reduction scratch, diagnostics stream) the handle
+ * allocates itself, as fmlbm_create does.  FMLBM_E_INVALID_ARG for a NULL, host, unaligned
+ * or (for non-deviation forms) superfluous g0 pointer. */
+fmlbm_status fmlbm_create_with_buffers(const fmlbm_mixture* mixture, const fmlbm_lattice* lattice,
+                                       void* cuda_stream, void* const g[2], float* const g0[2],
+                                       void* const force[2], fmlbm_handle** out);
+
 /* Fluid at rest: g_{a,i} = g^eq_{a,i}(rho_i, u = 0) (Eq. eqLBEMCb with rho_0 = 0,
  * i.e. rho_i in a = 0 and 0 elsewhere), stored force 0, step counter 0.
  * rho_host: [N][ny][nx] component MASS densities on the host, copied. */

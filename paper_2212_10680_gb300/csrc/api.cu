@@ -61,6 +61,7 @@ struct fmlbm_handle {
     int variant = FMLBM_VARIANT_AUTO;
     int sms = 1;                     // multiprocessors of the handle's device
     bool tma_maps = false;           // tensor maps of both buffers were encoded
+    bool owns_buffers = true;        // false: g, g0 and F belong to the caller (fmlbm_create_with_buffers)
     CUtensorMap tmap[2][2];          // [buffer][0: float planes, 1: 16-bit planes]
     std::string last_error;
 };
@@ -341,7 +342,7 @@ fmlbm_status sync_and_check(fmlbm_handle* h) {
 }
 
 void release(fmlbm_handle* h) {
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 2 && h->owns_buffers; ++k) {
         if (h->g[k]) cudaFree(h->g[k]);
         if (h->g0[k]) cudaFree(h->g0[k]);
         if (h->F[k]) cudaFree(h->F[k]);
@@ -418,6 +419,101 @@ fmlbm_status enqueue_pending_standalone(fmlbm_handle* h) {
     return enqueue_diag_tail(h, t, h->stream, false, capturing);
 }
 
+// Caller-provided distribution and force buffers (fmlbm_create_with_buffers).
+struct ExternalBuffers {
+    void* g[2];
+    float* g0[2];
+    void* F[2];
+};
+
+// A device (or managed) allocation of this process, 16-byte aligned.
+bool usable_device_pointer(const void* p) {
+    if (!p || (reinterpret_cast<uintptr_t>(p) & 15) != 0) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+fmlbm_status create_handle(const fmlbm_mixture* mixture, const fmlbm_lattice* lattice, void* cuda_stream,
+                           const ExternalBuffers* ext, fmlbm_handle** out) {
+    if (!mixture || !lattice || !out) return FMLBM_E_INVALID_ARG;
+    *out = nullptr;
+    fmlbm_handle* h = new (std::nothrow) fmlbm_handle();
+    if (!h) return FMLBM_E_OOM;
+    std::string why;
+    if (!mixture_constants(*mixture, &h->mc, &why) || !lattice_ok(*lattice, mixture->n_components, &why)) {
+        delete h;
+        return FMLBM_E_INVALID_ARG;
+    }
+    h->nc = mixture->n_components;
+    h->mixture = *mixture;
+    h->lattice = *lattice;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->tile_y = kTileYSmall;
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        delete h;
+        return FMLBM_E_CUDA;
+    }
+    size_t gb, g0b, fb;
+    buffer_bytes(h->nc, h->lattice, &gb, &g0b, &fb);
+    const size_t nxy = (size_t)lattice->nx * lattice->ny;
+    bool ok = true;
+    if (ext) {
+        h->owns_buffers = false;
+        for (int k = 0; k < 2; ++k) {
+            const bool g0_ok = g0b ? usable_device_pointer(ext->g0[k]) : ext->g0[k] == nullptr;
+            if (!usable_device_pointer(ext->g[k]) || !g0_ok || !usable_device_pointer(ext->F[k])) {
+                delete h;
+                return FMLBM_E_INVALID_ARG;
+            }
+            h->g[k] = ext->g[k];
+            h->g0[k] = ext->g0[k];
+            h->F[k] = ext->F[k];
+        }
+    }
+    for (int k = 0; k < 2 && ok && !ext; ++k) {
+        ok = ok && cudaMalloc(&h->g[k], gb) == cudaSuccess;
+        if (g0b) ok = ok && cudaMalloc((void**)&h->g0[k], g0b) == cudaSuccess;
+        ok = ok && cudaMalloc(&h->F[k], fb) == cudaSuccess;
+    }
+    ok = ok && cudaMalloc(&h->rho_prev, (size_t)h->nc * nxy * real_size(lattice->precision)) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->partial, kDiagSlots * (size_t)reduce_blocks(lattice->nx, lattice->ny) * (kMaxC + 2) *
+                                           sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&h->diag_dev, (kDiagSlots * kDiagWords + 2) * sizeof(double)) == cudaSuccess;
+    if (ok) h->err_dev = reinterpret_cast<ErrorLatch*>(h->diag_dev + kDiagSlots * kDiagWords);
+    // the diagnostics stream at the highest priority: its small final sums are dispatched as
+    // soon as the running step frees a block slot, instead of after the step's last block
+    int prio_least = 0, prio_greatest = 0;
+    ok = ok && cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithPriority(&h->tail, cudaStreamNonBlocking, prio_greatest) == cudaSuccess;
+    for (int k = 0; k < kDiagSlots; ++k) {
+        ok = ok && cudaEventCreateWithFlags(&h->part_ev[k], cudaEventDisableTiming) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&h->tail_done[k], cudaEventDisableTiming) == cudaSuccess;
+    }
+    ok = ok && cudaMallocHost((void**)&h->diag_host, (size_t)kDiagSlots * kDiagWords * sizeof(double)) == cudaSuccess;
+    for (int k = 0; k < kDiagSlots; ++k)
+        ok = ok && cudaEventCreateWithFlags(&h->diag_ev[k], cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaMallocHost((void**)&h->err_host, sizeof(ErrorLatch)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        release(h);
+        delete h;
+        return FMLBM_E_OOM;
+    }
+    if (cudaMemsetAsync(h->err_dev, 0, sizeof(ErrorLatch), h->stream) != cudaSuccess) {
+        release(h);
+        delete h;
+        return FMLBM_E_CUDA;
+    }
+    cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+    setup_tma(h);
+    *out = h;
+    return FMLBM_OK;
+}
+
 }  // namespace
 
 bool fmlbm_internal_mixture_constants(const fmlbm_mixture& m, MixConst* mc, std::string* why) {
@@ -456,67 +552,33 @@ fmlbm_status fmlbm_lattice_bytes(int32_t n_components, const fmlbm_lattice* latt
     return FMLBM_OK;
 }
 
+
 fmlbm_status fmlbm_create(const fmlbm_mixture* mixture, const fmlbm_lattice* lattice, void* cuda_stream,
                           fmlbm_handle** out) {
-    if (!mixture || !lattice || !out) return FMLBM_E_INVALID_ARG;
-    *out = nullptr;
-    fmlbm_handle* h = new (std::nothrow) fmlbm_handle();
-    if (!h) return FMLBM_E_OOM;
-    std::string why;
-    if (!mixture_constants(*mixture, &h->mc, &why) || !lattice_ok(*lattice, mixture->n_components, &why)) {
-        delete h;
+    return create_handle(mixture, lattice, cuda_stream, nullptr, out);
+}
+
+fmlbm_status fmlbm_create_with_buffers(const fmlbm_mixture* mixture, const fmlbm_lattice* lattice, void* cuda_stream,
+                                       void* const g[2], float* const g0[2], void* const force[2],
+                                       fmlbm_handle** out) {
+    if (!g || !force) return FMLBM_E_INVALID_ARG;
+    ExternalBuffers ext;
+    for (int k = 0; k < 2; ++k) {
+        ext.g[k] = g[k];
+        ext.g0[k] = g0 ? g0[k] : nullptr;
+        ext.F[k] = force[k];
+    }
+    return create_handle(mixture, lattice, cuda_stream, &ext, out);
+}
+
+fmlbm_status fmlbm_buffer_sizes(int32_t n_components, const fmlbm_lattice* lattice, size_t* g_bytes,
+                                size_t* g0_bytes, size_t* force_bytes) {
+    if (!lattice || !g_bytes || !g0_bytes || !force_bytes || n_components < 1 ||
+        n_components > FMLBM_MAX_COMPONENTS)
         return FMLBM_E_INVALID_ARG;
-    }
-    h->nc = mixture->n_components;
-    h->mixture = *mixture;
-    h->lattice = *lattice;
-    h->stream = static_cast<cudaStream_t>(cuda_stream);
-    h->tile_y = kTileYSmall;
-    if (cudaGetDevice(&h->device) != cudaSuccess) {
-        delete h;
-        return FMLBM_E_CUDA;
-    }
-    size_t gb, g0b, fb;
-    buffer_bytes(h->nc, h->lattice, &gb, &g0b, &fb);
-    const size_t nxy = (size_t)lattice->nx * lattice->ny;
-    bool ok = true;
-    for (int k = 0; k < 2 && ok; ++k) {
-        ok = ok && cudaMalloc(&h->g[k], gb) == cudaSuccess;
-        if (g0b) ok = ok && cudaMalloc((void**)&h->g0[k], g0b) == cudaSuccess;
-        ok = ok && cudaMalloc(&h->F[k], fb) == cudaSuccess;
-    }
-    ok = ok && cudaMalloc(&h->rho_prev, (size_t)h->nc * nxy * real_size(lattice->precision)) == cudaSuccess;
-    ok = ok && cudaMalloc(&h->partial, kDiagSlots * (size_t)reduce_blocks(lattice->nx, lattice->ny) * (kMaxC + 2) *
-                                           sizeof(double)) == cudaSuccess;
-    ok = ok && cudaMalloc((void**)&h->diag_dev, (kDiagSlots * kDiagWords + 2) * sizeof(double)) == cudaSuccess;
-    if (ok) h->err_dev = reinterpret_cast<ErrorLatch*>(h->diag_dev + kDiagSlots * kDiagWords);
-    // the diagnostics stream at the highest priority: its small final sums are dispatched as
-    // soon as the running step frees a block slot, instead of after the step's last block
-    int prio_least = 0, prio_greatest = 0;
-    ok = ok && cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) == cudaSuccess;
-    ok = ok && cudaStreamCreateWithPriority(&h->tail, cudaStreamNonBlocking, prio_greatest) == cudaSuccess;
-    for (int k = 0; k < kDiagSlots; ++k) {
-        ok = ok && cudaEventCreateWithFlags(&h->part_ev[k], cudaEventDisableTiming) == cudaSuccess;
-        ok = ok && cudaEventCreateWithFlags(&h->tail_done[k], cudaEventDisableTiming) == cudaSuccess;
-    }
-    ok = ok && cudaMallocHost((void**)&h->diag_host, (size_t)kDiagSlots * kDiagWords * sizeof(double)) == cudaSuccess;
-    for (int k = 0; k < kDiagSlots; ++k)
-        ok = ok && cudaEventCreateWithFlags(&h->diag_ev[k], cudaEventDisableTiming) == cudaSuccess;
-    ok = ok && cudaMallocHost((void**)&h->err_host, sizeof(ErrorLatch)) == cudaSuccess;
-    if (!ok) {
-        cudaGetLastError();
-        release(h);
-        delete h;
-        return FMLBM_E_OOM;
-    }
-    if (cudaMemsetAsync(h->err_dev, 0, sizeof(ErrorLatch), h->stream) != cudaSuccess) {
-        release(h);
-        delete h;
-        return FMLBM_E_CUDA;
-    }
-    cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
-    setup_tma(h);
-    *out = h;
+    std::string why;
+    if (!lattice_ok(*lattice, n_components, &why)) return FMLBM_E_INVALID_ARG;
+    buffer_bytes(n_components, *lattice, g_bytes, g0_bytes, force_bytes);
     return FMLBM_OK;
 }
 

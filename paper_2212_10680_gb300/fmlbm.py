@@ -81,6 +81,11 @@ def _load() -> ctypes.CDLL:
     sig = {
         "fmlbm_create": ([ctypes.POINTER(fmlbm_mixture), ctypes.POINTER(fmlbm_lattice), ctypes.c_void_p,
                           ctypes.POINTER(H)], ctypes.c_int),
+        "fmlbm_create_with_buffers": ([ctypes.POINTER(fmlbm_mixture), ctypes.POINTER(fmlbm_lattice), ctypes.c_void_p,
+                                       ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                       ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(H)], ctypes.c_int),
+        "fmlbm_buffer_sizes": ([ctypes.c_int32, ctypes.POINTER(fmlbm_lattice), ctypes.POINTER(ctypes.c_size_t),
+                                ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
         "fmlbm_init": ([H, dp], ctypes.c_int),
         "fmlbm_init_device": ([H, ctypes.c_void_p], ctypes.c_int),
         "fmlbm_step": ([H, ctypes.c_int64], ctypes.c_int),
@@ -199,6 +204,26 @@ def fmlbm_create(mixture: fmlbm_mixture, lattice: fmlbm_lattice, stream: int = 0
     h = ctypes.c_void_p()
     _check(LIB.fmlbm_create(ctypes.byref(mixture), ctypes.byref(lattice), ctypes.c_void_p(stream or None),
                             ctypes.byref(h)), "fmlbm_create")
+    return h
+
+
+def fmlbm_buffer_sizes(n_components: int, lattice: fmlbm_lattice):
+    """(g_bytes, g0_bytes, force_bytes) of each caller-provided buffer."""
+    s = [ctypes.c_size_t() for _ in range(3)]
+    _check(LIB.fmlbm_buffer_sizes(n_components, ctypes.byref(lattice), *[ctypes.byref(x) for x in s]),
+           "fmlbm_buffer_sizes")
+    return tuple(x.value for x in s)
+
+
+def fmlbm_create_with_buffers(mixture: fmlbm_mixture, lattice: fmlbm_lattice, g, g0, force,
+                              stream: int = 0) -> ctypes.c_void_p:
+    """g, force: two device addresses each (e.g. tensor.data_ptr()); g0: two addresses for the
+    deviation forms, else None.  The caller keeps ownership of the buffers."""
+    pair = ctypes.c_void_p * 2
+    h = ctypes.c_void_p()
+    _check(LIB.fmlbm_create_with_buffers(ctypes.byref(mixture), ctypes.byref(lattice), ctypes.c_void_p(stream or None),
+                                         pair(*g), pair(*g0) if g0 else None, pair(*force), ctypes.byref(h)),
+           "fmlbm_create_with_buffers")
     return h
 
 
@@ -457,11 +482,16 @@ class Lattice:
 
     def __init__(self, mixture: fmlbm_mixture, nx: int, ny: int, tau: float, stencil: str = "isotropic",
                  precision: str = "fp32", velocity_force: str = "lagged", stream: int = 0,
-                 formulation: str = "well_balanced"):
+                 formulation: str = "well_balanced", buffers: Optional[dict] = None):
+        """buffers: {"g": (a0, a1), "g0": (a0, a1) or None, "force": (a0, a1)}, device addresses of
+        caller-owned storage (fmlbm_create_with_buffers); None: the handle allocates its own."""
         self.n = mixture.n_components
         self.nx, self.ny = nx, ny
-        self.h = fmlbm_create(mixture, make_lattice(nx, ny, tau, stencil, precision, velocity_force, formulation),
-                              stream)
+        lat = make_lattice(nx, ny, tau, stencil, precision, velocity_force, formulation)
+        if buffers is None:
+            self.h = fmlbm_create(mixture, lat, stream)
+        else:
+            self.h = fmlbm_create_with_buffers(mixture, lat, buffers["g"], buffers.get("g0"), buffers["force"], stream)
 
     def init(self, rho: np.ndarray):
         fmlbm_init(self.h, rho)

@@ -59,3 +59,19 @@ def test_lattice_bytes_needs_no_gpu(lib):
     assert n >= 2 * 2 * 9 * 1024 * 1024 * 4
     L16 = fmlbm.make_lattice(1024, 1024, 1.0, precision="bf16dev")
     assert fmlbm.fmlbm_lattice_bytes(2, L16) < n
+
+
+def test_buffer_sizes_need_no_gpu(lib):
+    # the caller-provided buffers of fmlbm_create_with_buffers, per buffer: N x 9 planes of the
+    # storage type (16-bit forms: N x 8 planes of 2 bytes plus N float planes for a = 0), and
+    # the stored force, 2 planes of the storage arithmetic type
+    from paper_2212_10680_gb300 import fmlbm
+    nxy = 64 * 32
+    cases = {"fp64": (2 * 9 * nxy * 8, 0, 2 * nxy * 8), "fp32": (2 * 9 * nxy * 4, 0, 2 * nxy * 4),
+             "bf16dev": (2 * 8 * nxy * 2, 2 * nxy * 4, 2 * nxy * 4), "fp16dev": (2 * 8 * nxy * 2, 2 * nxy * 4, 2 * nxy * 4)}
+    for prec, want in cases.items():
+        assert fmlbm.fmlbm_buffer_sizes(2, fmlbm.make_lattice(64, 32, 1.0, precision=prec)) == want, prec
+    for n, L in ((5, fmlbm.make_lattice(64, 32, 1.0)), (2, fmlbm.make_lattice(0, 32, 1.0))):
+        with pytest.raises(fmlbm.FmlbmError) as ei:
+            fmlbm.fmlbm_buffer_sizes(n, L)
+        assert ei.value.status == 1

@@ -1,0 +1,73 @@
+"""Caller-owned device buffers (fmlbm_create_with_buffers): the same run as with the
+handle's own buffers, bit for bit, and the storage stays the caller's."""
+import numpy as np
+import pytest
+
+from cases import slab_state_binary
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fm():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2212_10680_gb300 import fmlbm
+    return fmlbm
+
+
+def _tensors(fm, precision, nx, ny):
+    import torch
+    gb, g0b, fb = fm.fmlbm_buffer_sizes(2, fm.make_lattice(nx, ny, 1.0, "isotropic", precision, "lagged"))
+    mk = lambda n: [torch.zeros(n, dtype=torch.uint8, device="cuda") for _ in range(2)]  # noqa: E731
+    return mk(gb), (mk(g0b) if g0b else None), mk(fb)
+
+
+def _addr(ts, off=0):
+    return None if ts is None else [t.data_ptr() + off for t in ts]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16dev"])
+def test_caller_buffers_run_bit_identically(fm, precision):
+    import torch
+    nx, ny = 70, 37
+    mixd, rho = slab_state_binary(nx, ny, seed=21)
+    gt, g0t, ft = _tensors(fm, precision, nx, ny)
+    out = []
+    for bufs in (dict(g=_addr(gt), g0=_addr(g0t), force=_addr(ft)), None):
+        lat = fm.Lattice(fm.mixture_from_dict(mixd), nx, ny, 1.0, "isotropic", precision, "lagged", buffers=bufs)
+        lat.init(rho)
+        lat.step(15)
+        t = fm.fmlbm_diagnostics_async(lat.h)
+        lat.step(2)
+        out.append((lat.distributions(), fm.fmlbm_diagnostics_wait(lat.h, t, 2)))
+        lat.close()
+    (g1, F1), d1 = out[0]
+    (g2, F2), d2 = out[1]
+    assert np.array_equal(g1, g2) and np.array_equal(F1, F2)
+    assert np.array_equal(np.asarray(d1[0]), np.asarray(d2[0])) and d1[1] == d2[1]
+    # the handle ran in the caller's storage and freed none of it
+    torch.cuda.synchronize()
+    assert all(bool(t.any()) for t in gt + ft)
+    for t in gt + ft + (g0t or []):
+        t.fill_(1)
+    torch.cuda.synchronize()
+
+
+def test_caller_buffers_are_checked(fm):
+    nx, ny = 64, 32
+    mixd, _ = slab_state_binary(nx, ny)
+    mix = fm.mixture_from_dict(mixd)
+    gt, _, ft = _tensors(fm, "fp32", nx, ny)
+    _, g0t, _ = _tensors(fm, "bf16dev", nx, ny)
+    host = np.zeros(1 << 20, dtype=np.uint8)
+    bad = [
+        ("fp32", dict(g=_addr(gt, 4), g0=None, force=_addr(ft))),                        # unaligned
+        ("fp32", dict(g=[host.ctypes.data] * 2, g0=None, force=_addr(ft))),              # host memory
+        ("fp32", dict(g=_addr(gt), g0=_addr(g0t), force=_addr(ft))),                     # a = 0 planes not used
+        ("bf16dev", dict(g=_addr(gt), g0=None, force=_addr(ft))),                        # a = 0 planes missing
+    ]
+    for prec, bufs in bad:
+        with pytest.raises(fm.FmlbmError) as ei:
+            fm.Lattice(mix, nx, ny, 1.0, "isotropic", prec, "lagged", buffers=bufs)
+        assert ei.value.status == 1, (prec, bufs)
