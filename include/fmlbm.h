@@ -363,6 +363,14 @@ const char* fmlbm_batch_last_error(const fmlbm_batch* b);
 /* Synchronises and frees everything.  NULL-safe. */
 void fmlbm_batch_destroy(fmlbm_batch* b);
 
+/* The two phases of a slot's current state, a vapour-liquid solve's answer: the molar
+ * densities rho~_i = rho_i / M_i at the node of largest total molar density (rho_liquid[N])
+ * and at the node of smallest (rho_vapour[N]); ties go to the lowest node index (row-major).
+ * Either pointer may be NULL.  Host outputs; synchronises the batch's stream.  At an
+ * equilibrated flat or curved interface these are the bulk phases (the node extremes of a
+ * still-noisy field are not). */
+fmlbm_status fmlbm_batch_phases(fmlbm_batch* b, int32_t slot, double* rho_liquid, double* rho_vapour);
+
 /* ------------------------------------------------------------------------------------
  * Serving: vapour-liquid solves submitted as requests and run with continuous batching.
  * A worker thread owns a batch; between chunks of chunk_steps steps it admits queued
@@ -398,10 +406,15 @@ typedef struct fmlbm_request {
 typedef struct fmlbm_result {
     uint64_t id, tag;
     int32_t status;            /* FMLBM_OK (converged), FMLBM_E_NOT_CONVERGED, FMLBM_E_NONPHYSICAL, ... */
-    int32_t reserved;
+    int32_t n_components;
     int64_t steps;
     double residual;
     double t_submit, t_admit, t_done;   /* seconds on the server's steady clock */
+    /* the two phases at retirement (fmlbm_batch_phases; zeros for FMLBM_E_NONPHYSICAL):
+     * molar densities rho~_i at the densest and the least dense node; the compositions
+     * are rho~_i / sum_j rho~_j */
+    double rho_liquid[FMLBM_MAX_COMPONENTS];
+    double rho_vapour[FMLBM_MAX_COMPONENTS];
 } fmlbm_result;
 
 /* Creates the server on the current device (its own stream and worker thread). */

@@ -312,6 +312,27 @@ void free_slot(fmlbm_batch* b, Slot& s) {
     s = Slot();
 }
 
+// The moments of a slot's current state into device buffers (rho_out [N][nxy], u_out [2][nxy],
+// lnf_out [N][nxy] doubles; u_out and lnf_out may be null), on the batch's stream.
+cudaError_t launch_slot_moments(fmlbm_batch* b, int32_t slot, double* rho_out, double* u_out, double* lnf_out) {
+    Slot& s = b->slots[slot];
+    fill_descriptor(b, slot);
+    StepArgs A = b->h_lat[slot].args[s.steps & 1];
+    A.rho_out = rho_out;
+    A.u_out = u_out;
+    A.lnf_out = lnf_out;
+    A.gout = nullptr;
+    A.g0out = nullptr;
+    A.Fout = nullptr;
+    const int ty = s.L.ny >= 64 ? kTileYLarge : kTileYSmall;
+    switch (b->precision) {
+        case FMLBM_FP64: return launch_step<ST_F64>(A, b->nc, true, ty, b->stream);
+        case FMLBM_FP32: return launch_step<ST_F32>(A, b->nc, true, ty, b->stream);
+        case FMLBM_FP16DEV: return launch_step<ST_F16DEV>(A, b->nc, true, ty, b->stream);
+        default: return launch_step<ST_BF16DEV>(A, b->nc, true, ty, b->stream);
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -554,32 +575,48 @@ fmlbm_status fmlbm_batch_check(fmlbm_batch* b) {
 fmlbm_status fmlbm_batch_moments(fmlbm_batch* b, int32_t slot, double* rho, double* u, double* lnf) {
     if (!b || slot < 0 || slot >= b->capacity || !b->slots[slot].used) return bfail(b, FMLBM_E_INVALID_ARG, "bad slot");
     Slot& s = b->slots[slot];
-    fill_descriptor(b, slot);
-    StepArgs A = b->h_lat[slot].args[s.steps & 1];
     const size_t nxy = (size_t)s.L.nx * s.L.ny;
     const size_t fb = (size_t)b->nc * nxy * sizeof(double);
     double* d = nullptr;
     BCUDA(b, cudaMallocAsync((void**)&d, 2 * fb + 2 * nxy * sizeof(double), b->stream));
-    A.rho_out = d;
-    A.lnf_out = d + (size_t)b->nc * nxy;
-    A.u_out = d + 2 * (size_t)b->nc * nxy;
-    A.gout = nullptr;
-    A.g0out = nullptr;
-    A.Fout = nullptr;
-    const int ty = s.L.ny >= 64 ? kTileYLarge : kTileYSmall;
-    cudaError_t e;
-    switch (b->precision) {
-        case FMLBM_FP64: e = launch_step<ST_F64>(A, b->nc, true, ty, b->stream); break;
-        case FMLBM_FP32: e = launch_step<ST_F32>(A, b->nc, true, ty, b->stream); break;
-        case FMLBM_FP16DEV: e = launch_step<ST_F16DEV>(A, b->nc, true, ty, b->stream); break;
-        default: e = launch_step<ST_BF16DEV>(A, b->nc, true, ty, b->stream); break;
-    }
-    if (e == cudaSuccess && rho) e = cudaMemcpyAsync(rho, A.rho_out, fb, cudaMemcpyDeviceToHost, b->stream);
-    if (e == cudaSuccess && lnf) e = cudaMemcpyAsync(lnf, A.lnf_out, fb, cudaMemcpyDeviceToHost, b->stream);
-    if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, A.u_out, 2 * nxy * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+    cudaError_t e = launch_slot_moments(b, slot, d, d + 2 * (size_t)b->nc * nxy, d + (size_t)b->nc * nxy);
+    if (e == cudaSuccess && rho) e = cudaMemcpyAsync(rho, d, fb, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess && lnf) e = cudaMemcpyAsync(lnf, d + (size_t)b->nc * nxy, fb, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess && u)
+        e = cudaMemcpyAsync(u, d + 2 * (size_t)b->nc * nxy, 2 * nxy * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
     cudaFreeAsync(d, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bfail(b, FMLBM_E_CUDA, std::string("batch moments: ") + cudaGetErrorString(e));
+    return FMLBM_OK;
+}
+
+fmlbm_status fmlbm_batch_phases(fmlbm_batch* b, int32_t slot, double* rho_liquid, double* rho_vapour) {
+    if (!b || slot < 0 || slot >= b->capacity || !b->slots[slot].used) return bfail(b, FMLBM_E_INVALID_ARG, "bad slot");
+    Slot& s = b->slots[slot];
+    const size_t nxy = (size_t)s.L.nx * s.L.ny;
+    double* d = nullptr;
+    BCUDA(b, cudaMallocAsync((void**)&d, ((size_t)b->nc * nxy + 2 * kMaxC) * sizeof(double), b->stream));
+    double* out = d + (size_t)b->nc * nxy;
+    cudaError_t e = launch_slot_moments(b, slot, d, nullptr, nullptr);
+    if (e == cudaSuccess) {
+        const MixConst& m = b->h_lat[slot].args[0].mixd;
+        switch (b->nc) {
+            case 1: phase_nodes<1><<<1, kPhaseThreads, 0, b->stream>>>(d, (long long)nxy, m, out); break;
+            case 2: phase_nodes<2><<<1, kPhaseThreads, 0, b->stream>>>(d, (long long)nxy, m, out); break;
+            case 3: phase_nodes<3><<<1, kPhaseThreads, 0, b->stream>>>(d, (long long)nxy, m, out); break;
+            default: phase_nodes<4><<<1, kPhaseThreads, 0, b->stream>>>(d, (long long)nxy, m, out); break;
+        }
+        e = cudaGetLastError();
+    }
+    double h[2 * kMaxC];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, out, 2 * b->nc * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+    cudaFreeAsync(d, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, FMLBM_E_CUDA, std::string("batch phases: ") + cudaGetErrorString(e));
+    for (int i = 0; i < b->nc; ++i) {
+        if (rho_liquid) rho_liquid[i] = h[i];
+        if (rho_vapour) rho_vapour[i] = h[b->nc + i];
+    }
     return FMLBM_OK;
 }
 

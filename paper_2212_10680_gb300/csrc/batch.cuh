@@ -131,4 +131,44 @@ __global__ void batch_reduce_final(const BatchLattice* __restrict__ lat, int n, 
     out[k] = v;
 }
 
+// The two phases of a lattice from its densities rho[N][nxy] (mass, double): the node of
+// largest total molar density sum_i rho_i / M_i (liquid) and of smallest (vapour), ties to
+// the lowest node index; out = rho~ at the liquid node [N], then at the vapour node [N].
+// One block, grid-stride over the nodes, a fixed-order tree: deterministic.
+constexpr int kPhaseThreads = 512;
+template <int NC>
+__global__ void __launch_bounds__(kPhaseThreads) phase_nodes(const double* __restrict__ rho, long long nxy,
+                                                             MixConstT<double> m, double* __restrict__ out) {
+    __shared__ double vmax[kPhaseThreads], vmin[kPhaseThreads];
+    __shared__ long long imax[kPhaseThreads], imin[kPhaseThreads];
+    const int t = threadIdx.x;
+    double hi = -1.0, lo = 0.0;
+    long long ih = -1, il = -1;
+    for (long long k = t; k < nxy; k += kPhaseThreads) {
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < NC; ++i) s += rho[i * nxy + k] / m.M[i];
+        if (ih < 0 || s > hi) { hi = s; ih = k; }          // k increases: first maximum kept
+        if (il < 0 || s < lo) { lo = s; il = k; }
+    }
+    vmax[t] = hi; imax[t] = ih; vmin[t] = lo; imin[t] = il;
+    __syncthreads();
+    for (int w = kPhaseThreads / 2; w > 0; w >>= 1) {
+        if (t < w) {
+            const int o = t + w;
+            if (imax[o] >= 0 && (imax[t] < 0 || vmax[o] > vmax[t] || (vmax[o] == vmax[t] && imax[o] < imax[t]))) {
+                vmax[t] = vmax[o]; imax[t] = imax[o];
+            }
+            if (imin[o] >= 0 && (imin[t] < 0 || vmin[o] < vmin[t] || (vmin[o] == vmin[t] && imin[o] < imin[t]))) {
+                vmin[t] = vmin[o]; imin[t] = imin[o];
+            }
+        }
+        __syncthreads();
+    }
+    if (t < NC) {
+        out[t] = rho[t * nxy + imax[0]] / m.M[t];
+        out[NC + t] = rho[t * nxy + imin[0]] / m.M[t];
+    }
+}
+
 }  // namespace fmlbm

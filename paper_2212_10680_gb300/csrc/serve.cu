@@ -68,12 +68,18 @@ struct fmlbm_server {
 
 namespace {
 
-void finish(fmlbm_server* s, Pending& p, int32_t status, int64_t steps, double residual) {
+void finish(fmlbm_server* s, Pending& p, int32_t status, int64_t steps, double residual, const double* liquid,
+            const double* vapour) {
     fmlbm_result r;
     std::memset(&r, 0, sizeof r);
     r.id = p.id;
     r.tag = p.tag;
     r.status = status;
+    r.n_components = p.mix.n_components;
+    for (int i = 0; i < p.mix.n_components && liquid; ++i) {
+        r.rho_liquid[i] = liquid[i];
+        r.rho_vapour[i] = vapour[i];
+    }
     r.steps = steps;
     r.residual = residual;
     r.t_submit = p.t_submit;
@@ -110,7 +116,7 @@ void worker_main(fmlbm_server* s) {
             p.rho.clear();
             p.rho.shrink_to_fit();
             if (st != FMLBM_OK) {
-                finish(s, p, st, 0, NAN);
+                finish(s, p, st, 0, NAN, nullptr, nullptr);
                 continue;
             }
             p.slot = slot;
@@ -146,10 +152,13 @@ void worker_main(fmlbm_server* s) {
             }
             if (!retire) continue;
             Pending& p = kv.second;
+            double liquid[FMLBM_MAX_COMPONENTS] = {}, vapour[FMLBM_MAX_COMPONENTS] = {};
+            const bool phases = status != FMLBM_E_NONPHYSICAL &&
+                                fmlbm_batch_phases(s->batch, kv.first, liquid, vapour) == FMLBM_OK;
             if (p.rho_out && status != FMLBM_E_NONPHYSICAL)
                 fmlbm_batch_moments(s->batch, kv.first, p.rho_out, nullptr, nullptr);
             fmlbm_batch_remove(s->batch, kv.first);
-            finish(s, p, status, steps, res);
+            finish(s, p, status, steps, res, phases ? liquid : nullptr, phases ? vapour : nullptr);
             retired.push_back(kv.first);
         }
         for (int32_t k : retired) s->running.erase(k);

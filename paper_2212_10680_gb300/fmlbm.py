@@ -67,8 +67,9 @@ class fmlbm_request(ctypes.Structure):
 
 class fmlbm_result(ctypes.Structure):
     _fields_ = [("id", ctypes.c_uint64), ("tag", ctypes.c_uint64), ("status", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("steps", ctypes.c_int64), ("residual", ctypes.c_double),
-                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+                ("n_components", ctypes.c_int32), ("steps", ctypes.c_int64), ("residual", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("rho_liquid", ctypes.c_double * MAX_COMPONENTS), ("rho_vapour", ctypes.c_double * MAX_COMPONENTS)]
 
 
 def _load() -> ctypes.CDLL:
@@ -125,6 +126,7 @@ def _load() -> ctypes.CDLL:
         "fmlbm_batch_slot_info": ([H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), dp,
                                    ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "fmlbm_batch_moments": ([H, ctypes.c_int32, dp, dp, dp], ctypes.c_int),
+        "fmlbm_batch_phases": ([H, ctypes.c_int32, dp, dp], ctypes.c_int),
         "fmlbm_batch_get_distributions": ([H, ctypes.c_int32, dp, dp], ctypes.c_int),
         "fmlbm_batch_autotune": ([H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                   dp], ctypes.c_int),
@@ -413,6 +415,13 @@ def fmlbm_batch_moments(b, slot: int, rho=None, u=None, lnf=None):
     _bcheck(LIB.fmlbm_batch_moments(b, slot, _ptr(rho), _ptr(u), _ptr(lnf)), "fmlbm_batch_moments", b)
 
 
+def fmlbm_batch_phases(b, slot: int, n_components: int):
+    """(rho~ at the densest node, rho~ at the least dense node), molar densities."""
+    liq, vap = np.empty(n_components), np.empty(n_components)
+    _bcheck(LIB.fmlbm_batch_phases(b, slot, _ptr(liq), _ptr(vap)), "fmlbm_batch_phases", b)
+    return liq, vap
+
+
 def fmlbm_batch_get_distributions(b, slot: int, g=None, force=None):
     _bcheck(LIB.fmlbm_batch_get_distributions(b, slot, _ptr(g), _ptr(force)), "fmlbm_batch_get_distributions", b)
 
@@ -463,7 +472,8 @@ def fmlbm_server_poll(s, capacity: int = 1024):
     n = ctypes.c_int32()
     _check(LIB.fmlbm_server_poll(s, out, capacity, ctypes.byref(n)), "fmlbm_server_poll")
     return [dict(id=r.id, tag=r.tag, status=r.status, steps=r.steps, residual=r.residual, t_submit=r.t_submit,
-                 t_admit=r.t_admit, t_done=r.t_done) for r in out[:n.value]]
+                 t_admit=r.t_admit, t_done=r.t_done, rho_liquid=list(r.rho_liquid[:r.n_components]),
+                 rho_vapour=list(r.rho_vapour[:r.n_components])) for r in out[:n.value]]
 
 
 def fmlbm_server_stats(s):

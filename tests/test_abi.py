@@ -49,6 +49,8 @@ def test_struct_layout_matches_header():
     # 2 int32 + 2 double + 5 x 4 double + 16 double
     assert ctypes.sizeof(fmlbm.fmlbm_mixture) == 8 + 16 + 5 * 32 + 128
     assert ctypes.sizeof(fmlbm.fmlbm_lattice) == 8 + 8 + 16
+    # 2 uint64 + 2 int32 + int64 + 4 double + 2 x 4 double
+    assert ctypes.sizeof(fmlbm.fmlbm_result) == 16 + 8 + 8 + 32 + 64
 
 
 def test_lattice_bytes_needs_no_gpu(lib):

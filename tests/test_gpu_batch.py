@@ -82,6 +82,16 @@ def test_batch_moments_equal_single_lattice_moments(fm, precision):
         rs, us, ls = lat.moments()
         lat.close()
         assert np.array_equal(r, rs) and np.array_equal(u, us) and np.array_equal(lnf, ls), (nx, ny)
+        # the phases: rho~ (= rho / M) at the nodes of largest and smallest total molar
+        # density, first in row-major order on ties, from the same densities
+        M = np.asarray(mixd["M"], dtype=np.float64)
+        tot = np.zeros(nx * ny)
+        for i in range(2):
+            tot = tot + r[i].ravel() / M[i]
+        liq, vap = fm.fmlbm_batch_phases(b, slot, 2)
+        iL, iV = int(np.argmax(tot)), int(np.argmin(tot))
+        assert np.array_equal(liq, np.array([r[i].ravel()[iL] / M[i] for i in range(2)]))
+        assert np.array_equal(vap, np.array([r[i].ravel()[iV] / M[i] for i in range(2)]))
     fm.fmlbm_batch_destroy(b)
 
 
