@@ -480,6 +480,15 @@ def run_batch(args, rank, world, dist=None):
         print(json.dumps(line), flush=True)
 
 
+def _downsample(points: list, k: int) -> list:
+    """At most k of the (t, value) points, evenly spaced in index, first and last kept;
+    rounded for the JSON line."""
+    if len(points) > k:
+        idx = sorted({round(j * (len(points) - 1) / (k - 1)) for j in range(k)})
+        points = [points[j] for j in idx]
+    return [[round(t, 3), int(v)] for t, v in points]
+
+
 def run_serve(args, rank, world, dist=None):
     """Serving: Poisson arrivals of binary and ternary VLE requests (templates with random T
     and feed, side ~ U{64..1024}); continuous batching servers, one per component count;
@@ -513,6 +522,13 @@ def run_serve(args, rank, world, dist=None):
     servers = {nc: fmlbm.fmlbm_server_create(nc, prec, args.slots, args.check_every, args.tol, args.max_steps,
                                              int(args.budget_gb * (1 << 30))) for nc in (2, 3)}
     results = []
+    timeline = []          # (seconds, device bytes admitted over both servers), every >= 50 ms
+
+    def sample():
+        now = time.perf_counter() - t0
+        if not timeline or now - timeline[-1][0] >= 0.05:
+            timeline.append((now, sum(fmlbm.fmlbm_server_stats(s)["bytes"] for s in servers.values())))
+
     t0 = time.perf_counter()
     for r in reqs.values():
         wait = r["t"] - (time.perf_counter() - t0)
@@ -522,9 +538,11 @@ def run_serve(args, rank, world, dist=None):
                                                                                  "isotropic", prec), r["rho"], tag=r["k"])
         for s in servers.values():
             results += fmlbm.fmlbm_server_poll(s)
+        sample()
     while len(results) < len(reqs):
         for s in servers.values():
             results += fmlbm.fmlbm_server_poll(s)
+        sample()
         time.sleep(0.002)
     wall = max_over_ranks(time.perf_counter() - t0, dist, dev)
     busy = {nc: sum_over_ranks(fmlbm.fmlbm_server_stats(s)["busy"], dist, dev) / world for nc, s in servers.items()}
@@ -573,6 +591,8 @@ def run_serve(args, rank, world, dist=None):
             hbm_budget_gb=args.budget_gb),
         p50_s=_stats_pct(lat_s, 50), p99_s=_stats_pct(lat_s, 99), aggregate_glups=units / wall / 1e9,
         gpu_busy_fraction={str(k): v / wall for k, v in busy.items()}, statuses=counts, seconds=wall,
+        admitted_bytes=dict(max=max((b for _, b in timeline), default=0), budget=int(args.budget_gb * (1 << 30)),
+                            timeline=_downsample(timeline, 40), note="rank 0's servers, sampled every >= 50 ms"),
         fifo_baseline=dict(value=R / seq_wall, unit="solves/s", p50_s=_stats_pct(seq_lat, 50),
                            p99_s=_stats_pct(seq_lat, 99), seconds=seq_wall),
     )

@@ -81,3 +81,11 @@ def test_reference_arm_under_torchrun_reports_once():
     d = lines[0]
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_timeline_downsampling_keeps_the_ends():
+    pts = [(0.01 * i, 10 * i) for i in range(100)]
+    out = bench._downsample(pts, 5)
+    assert len(out) == 5 and out[0] == [0.0, 0] and out[-1] == [0.99, 990]
+    assert bench._downsample(pts[:3], 40) == [[0.0, 0], [0.01, 10], [0.02, 20]]
+    assert bench._downsample([], 40) == []
