@@ -10,6 +10,9 @@
   uniform state; mirror and transpose symmetry of one step (catches wrong signs,
   swapped indices and mis-assigned directions); the isotropic stencils equal the
   central ones on y-uniform fields.
+* Newton's law of the forced collision: with u = (j + F/2) / rho, BGK relaxation plus the
+  (1 - 1/(2 tau)) F_{a,i} of Eq. eqLBEMCa leaves j + F at every node, for any tau (fixes
+  the 1/2 in u and the prefactor, which no equilibrium depends on).
 * The single-component limit settles on the Maxwell pair of the PR EOS.
 * The standard formulation of Section VI (Eq. eqLBE, force of Eq. eqForceGen): its
   equilibrium carries c_s^2 rho_i I, Guo's forcing term has the plain moments, mass is
@@ -109,6 +112,29 @@ def test_mass_conservation(stencil, velocity_force):
     g, F = lbm.run(g, F, mix, lat, 200)
     assert np.max(np.abs(lbm.component_mass(g) / m0 - 1)) < 1e-13
     assert np.abs(g).max() > 0 and np.isfinite(g).all()
+
+
+@pytest.mark.parametrize("tau", [0.6, 1.0, 1.7])
+def test_collision_adds_exactly_the_force_to_the_momentum(tau):
+    # Sum over a and i of g*_{a,i} e_a = J - (J - rho u) / tau + (1 - 1/(2 tau)) F with
+    # rho u = J + F / 2 ("current" reading) is J + F whatever tau is.  Checked node by node
+    # on the post-collision values (the step's streaming undone) of a moving two-phase state.
+    mix = binary_mixture(Tr=1.1)
+    mix.kappa = np.array([0.02, 0.03])
+    lat = lbm.Lattice(tau=tau, stencil="isotropic", velocity_force="current")
+    g, F = lbm.init_at_rest(_smooth_binary_state())
+    g, F = lbm.run(g, F, mix, lat, 3)                   # a state with momentum
+    g_new, F_tot, m = lbm.step(g, mix, lat, F, return_macro=True)
+    gstar = np.empty_like(g_new)
+    for a in range(9):
+        gstar[:, a] = np.roll(g_new[:, a], shift=(-lbm.E[a, 1], -lbm.E[a, 0]), axis=(-2, -1))
+    ex, ey = lbm.E[:, 0].astype(np.float64), lbm.E[:, 1].astype(np.float64)
+    J = [np.einsum("a,iayx->yx", e, g) for e in (ex, ey)]
+    Jstar = [np.einsum("a,iayx->yx", e, gstar) for e in (ex, ey)]
+    scale = max(np.abs(J[0]).max(), np.abs(F_tot).max())
+    assert scale > 1e-4
+    for k in range(2):
+        assert np.max(np.abs(Jstar[k] - (J[k] + F_tot[k]))) <= 1e-14 * max(1.0, np.abs(g).max())
 
 
 @pytest.mark.parametrize("stencil", ["isotropic", "central"])
