@@ -1,0 +1,110 @@
+"""The oracle's pins bind it: a plausible mistake planted in a copy of the oracle (on the
+CPU) -- a dropped term, a wrong sign, factor, weight or index, transposed operands --
+makes at least one of the pin tests fail.  Each case applies one text substitution to
+oracle/eos.py or oracle/lbm.py, loads the result as a separate module, points the pin
+tests at it and counts the pins that fail.  (The unmodified oracle passes every pin: the
+regular runs of these test modules.)"""
+import os
+import sys
+import types
+
+import pytest
+
+import test_oracle_eos as TE
+import test_oracle_lbm as TL
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# the planted mistakes make logarithms of negative numbers and failing quadratures on purpose
+pytestmark = pytest.mark.filterwarnings("ignore")
+
+
+def _mutated(module: str, old: str, new: str):
+    src = open(os.path.join(ROOT, "oracle", module + ".py")).read()
+    assert src.count(old) >= 1, f"{old!r} not in oracle/{module}.py"
+    name = f"oracle._planted_{module}_{abs(hash((old, new)))}"
+    mod = types.ModuleType(name)
+    mod.__package__ = "oracle"
+    mod.__file__ = os.path.join(ROOT, "oracle", module + ".py")
+    sys.modules[name] = mod
+    exec(compile(src.replace(old, new, 1), mod.__file__, "exec"), mod.__dict__)
+    return mod
+
+
+def _failures(pins) -> list:
+    failed = []
+    for pin, args in pins:
+        try:
+            pin(*args)
+        except (AssertionError, FloatingPointError, ValueError, ArithmeticError) as e:
+            failed.append((pin.__name__, args, type(e).__name__))
+    return failed
+
+
+EOS_NAMES = ("Mixture", "alpha_function", "ln_phi_textbook", "lnf_density_form", "pressure",
+             "pressure_from_volume", "volume_roots")
+EOS_PINS = [(TE.test_critical_point_of_each_eos, (e,)) for e in TE.EOSES] + \
+           [(TE.test_ideal_gas_limit, (e,)) for e in TE.EOSES] + \
+           [(TE.test_gibbs_duhem, (e,)) for e in TE.EOSES] + \
+           [(TE.test_lnf_equals_residual_integral, (e,)) for e in TE.EOSES] + \
+           [(TE.test_density_form_equals_textbook_form, (e,)) for e in TE.EOSES] + \
+           [(TE.test_split_identical_component, (e,)) for e in TE.EOSES]
+
+EOS_MISTAKES = {
+    "wrong sign of the PR attraction term of ln f":
+        ("lnx + rep - ln_free + (aam / (2.0 * SQRT2", "lnx + rep - ln_free - (aam / (2.0 * SQRT2"),
+    "dropped b_i / b_m in the repulsion term":
+        ("rep = (b / bm) * (p * v / RT - 1.0)", "rep = (p * v / RT - 1.0)"),
+    "factor 2 lost in the attraction bracket of ln f":
+        ("bracket = b / bm - (2.0 / aam) * S", "bracket = b / bm - (1.0 / aam) * S"),
+    "wrong sign of b_m^2 in the PR denominator":
+        ("return v * v + 2.0 * bm * v - bm * bm", "return v * v + 2.0 * bm * v + bm * bm"),
+    "mole fractions dropped from (a alpha)_m":
+        ("aam = np.sum(x * S, axis=0)", "aam = np.sum(S, axis=0)"),
+    "ln x_i left out of the density form":
+        ("    lnx = np.log(x)\n", "    lnx = 0.0 * np.log(x)\n"),
+}
+
+
+@pytest.mark.parametrize("mistake", sorted(EOS_MISTAKES))
+def test_planted_eos_mistake_fails_a_pin(mistake, monkeypatch):
+    mod = _mutated("eos", *EOS_MISTAKES[mistake])
+    for n in EOS_NAMES:
+        monkeypatch.setattr(TE, n, getattr(mod, n))
+    assert _failures(EOS_PINS), f"no pin caught: {mistake}"
+
+
+LBM_PINS = [(TL.test_d2q9_isotropy, ()), (TL.test_equilibrium_moments, (0.0,)), (TL.test_forcing_term_moments, ()),
+            (TL.test_collision_adds_exactly_the_force_to_the_momentum, (0.8,)),
+            (TL.test_uniform_state_is_stationary, ("isotropic",)),
+            (TL.test_mirror_and_transpose_symmetry, ("isotropic",)),
+            (TL.test_mirror_and_transpose_symmetry, ("central",)),
+            (TL.test_isotropic_equals_central_on_flat_fields, ()),
+            (TL.test_mass_conservation, ("isotropic", "lagged"))]
+
+LBM_MISTAKES = {
+    "wrong diagonal weight":
+        ("[1 / 36] * 4, dtype=np.float64)", "[1 / 18] * 4, dtype=np.float64)"),
+    "forcing prefactor (1 - 1/(2 tau)) dropped":
+        ("(1.0 - 1.0 / (2.0 * lat.tau)) * Fa", "1.0 * Fa"),
+    "full force instead of half in the velocity":
+        ("ux = (jx.sum(axis=0) + 0.5 * Fu_x) / rho_tot", "ux = (jx.sum(axis=0) + 1.0 * Fu_x) / rho_tot"),
+    "wrong sign of the -u . grad rho part of the forcing term":
+        ("tG = (-ux * grx - uy * gry)", "tG = (ux * grx + uy * gry)"),
+    "factor 2 lost in the second-order equilibrium term":
+        ("eu * eu / (2.0 * CS2 * CS2)", "eu * eu / (CS2 * CS2)"),
+    "streaming with x and y swapped":
+        ("shift=(E[a, 1], E[a, 0]), axis=(-2, -1))\n    if return_macro",
+         "shift=(E[a, 0], E[a, 1]), axis=(-2, -1))\n    if return_macro"),
+    "central Laplacian with -2 h":
+        ("+ neighbour(h, 0, -1)\n                - 4.0 * h)", "+ neighbour(h, 0, -1)\n                - 2.0 * h)"),
+    "force on one component with the other's density":
+        ("Fx[i] = -rt[i] * mix.RT * glx - rt[i] * gmx", "Fx[i] = -rt[i - 1] * mix.RT * glx - rt[i] * gmx"),
+}
+
+
+@pytest.mark.parametrize("mistake", sorted(LBM_MISTAKES))
+def test_planted_lbm_mistake_fails_a_pin(mistake, monkeypatch):
+    mod = _mutated("lbm", *LBM_MISTAKES[mistake])
+    monkeypatch.setattr(TL, "lbm", mod)
+    assert _failures(LBM_PINS), f"no pin caught: {mistake}"
