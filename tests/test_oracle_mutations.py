@@ -1,9 +1,10 @@
 """The oracle's pins bind it: a plausible mistake planted in a copy of the oracle (on the
 CPU) -- a dropped term, a wrong sign, factor, weight or index, transposed operands --
 makes at least one of the pin tests fail.  Each case applies one text substitution to
-oracle/eos.py or oracle/lbm.py, loads the result as a separate module, points the pin
+an oracle module, loads the result as a separate module, points the pin
 tests at it and counts the pins that fail.  (The unmodified oracle passes every pin: the
-regular runs of these test modules.)"""
+regular runs of these test modules.)  oracle/eos.py, oracle/flash.py and oracle/lbm.py
+are covered."""
 import os
 import sys
 import types
@@ -11,6 +12,7 @@ import types
 import pytest
 
 import test_oracle_eos as TE
+import test_oracle_flash as TF
 import test_oracle_lbm as TL
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -32,13 +34,13 @@ def _mutated(module: str, old: str, new: str):
 
 
 def _failures(pins) -> list:
-    failed = []
+    """The first pin (in the order given, cheapest first) that fails, or [] if none does."""
     for pin, args in pins:
         try:
             pin(*args)
-        except (AssertionError, FloatingPointError, ValueError, ArithmeticError) as e:
-            failed.append((pin.__name__, args, type(e).__name__))
-    return failed
+        except (AssertionError, FloatingPointError, ValueError, ArithmeticError, RuntimeError) as e:
+            return [(pin.__name__, args, type(e).__name__)]
+    return []
 
 
 EOS_NAMES = ("Mixture", "alpha_function", "ln_phi_textbook", "lnf_density_form", "pressure",
@@ -108,3 +110,35 @@ def test_planted_lbm_mistake_fails_a_pin(mistake, monkeypatch):
     mod = _mutated("lbm", *LBM_MISTAKES[mistake])
     monkeypatch.setattr(TL, "lbm", mod)
     assert _failures(LBM_PINS), f"no pin caught: {mistake}"
+
+
+FLASH_NAMES = ("flash", "pure_coexistence", "slab_state", "bubble_point_from_liquid", "vapour_volume_fraction")
+FLASH_PINS = [(TF.test_pure_coexistence_lattice_units_value, ()),
+              (TF.test_pure_coexistence_obeys_equal_area, ("pr", 0.8)),
+              (TF.test_flash_fugacity_equality_and_balance, (2,)),
+              (TF.test_flash_fugacity_equality_and_balance, (3,)),
+              (TF.test_table_tabfug_c2_c5_physical_units, ()),
+              (TF.test_section_v_e_density_ratio_c3_c5_340K_5bar, ())]
+
+FLASH_MISTAKES = {
+    "K-value update inverted (vapour over liquid)":
+        ("lnK_new = ln_phi_textbook(mix, vL, x) - ln_phi_textbook(mix, vV, y)",
+         "lnK_new = ln_phi_textbook(mix, vV, y) - ln_phi_textbook(mix, vL, x)"),
+    "liquid and vapour roots swapped":
+        ('return float(roots[0] if phase == "liquid" else roots[-1])',
+         'return float(roots[-1] if phase == "liquid" else roots[0])'),
+    "Rachford-Rice liquid composition with K + 1":
+        ("        x = z / (1.0 + beta * (K - 1.0))\n        y = K * x\n        x = x / x.sum()\n        y = y / y.sum()\n        vL",
+         "        x = z / (1.0 + beta * (K + 1.0))\n        y = K * x\n        x = x / x.sum()\n        y = y / y.sum()\n        vL"),
+    "coexistence from the liquid root twice":
+        ('        vV = phase_volume(mix, p, x, "vapor")\n        return float(',
+         '        vV = phase_volume(mix, p, x, "liquid")\n        return float('),
+}
+
+
+@pytest.mark.parametrize("mistake", sorted(FLASH_MISTAKES))
+def test_planted_flash_mistake_fails_a_pin(mistake, monkeypatch):
+    mod = _mutated("flash", *FLASH_MISTAKES[mistake])
+    for n in FLASH_NAMES:
+        monkeypatch.setattr(TF, n, getattr(mod, n))
+    assert _failures(FLASH_PINS), f"no pin caught: {mistake}"
