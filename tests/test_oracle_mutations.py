@@ -3,8 +3,8 @@ CPU) -- a dropped term, a wrong sign, factor, weight or index, transposed operan
 makes at least one of the pin tests fail.  Each case applies one text substitution to
 an oracle module, loads the result as a separate module, points the pin
 tests at it and counts the pins that fail.  (The unmodified oracle passes every pin: the
-regular runs of these test modules.)  oracle/eos.py, oracle/flash.py and oracle/lbm.py
-are covered."""
+regular runs of these test modules.)  oracle/eos.py, oracle/flash.py, oracle/lbm.py and
+oracle/interface.py are covered."""
 import os
 import sys
 import types
@@ -13,6 +13,7 @@ import pytest
 
 import test_oracle_eos as TE
 import test_oracle_flash as TF
+import test_oracle_interface as TI
 import test_oracle_lbm as TL
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -142,3 +143,27 @@ def test_planted_flash_mistake_fails_a_pin(mistake, monkeypatch):
     for n in FLASH_NAMES:
         monkeypatch.setattr(TF, n, getattr(mod, n))
     assert _failures(FLASH_PINS), f"no pin caught: {mistake}"
+
+
+INTERFACE_NAMES = ("crossing_radius", "interfacial_tension", "lamb_period")
+INTERFACE_PINS = [(TI.test_lamb_period_formula, ()), (TI.test_crossing_radius_of_a_sampled_tanh, ()),
+                  (TI.test_tension_of_a_tanh_slab_matches_the_closed_form, ())]
+
+INTERFACE_MISTAKES = {
+    "kappa_ij = kappa_i kappa_j instead of its square root":
+        ("k = np.sqrt(np.outer(kappa, kappa))", "k = np.outer(kappa, kappa)"),
+    "cross terms kappa_ij (i != j) dropped":
+        ("k = np.sqrt(np.outer(kappa, kappa))", "k = np.diag(np.asarray(kappa, dtype=float))"),
+    "n (n^2 + 1) in the Lamb period":
+        ("n * (n * n - 1) * sigma", "n * (n * n + 1) * sigma"),
+    "crossing interpolated from the wrong node":
+        ("return k + (p[k] - level) / (p[k] - p[k + 1]) - centre", "return k + 1 - (p[k] - level) / (p[k] - p[k + 1]) - centre"),
+}
+
+
+@pytest.mark.parametrize("mistake", sorted(INTERFACE_MISTAKES))
+def test_planted_interface_mistake_fails_a_pin(mistake, monkeypatch):
+    mod = _mutated("interface", *INTERFACE_MISTAKES[mistake])
+    for n in INTERFACE_NAMES:
+        monkeypatch.setattr(TI, n, getattr(mod, n))
+    assert _failures(INTERFACE_PINS), f"no pin caught: {mistake}"
