@@ -23,6 +23,9 @@ The package is written to be read against the paper, not to be fast:
 * ``lbm``    -- the nine-step procedure of Section III.B (Implementation) on a
                 periodic D2Q9 lattice, whole-grid numpy array operations in the
                 paper's order, nothing fused or reordered.
+* ``interface`` -- the measures of the dynamic validation (Section V.E): the
+                interfacial tension of Eq. eqMCsigma, the Lamb period of Eq. eqPeriod
+                and the crossing radius of a droplet profile.
 
 Parity status of each function is stated in its module docstring.
 """
