@@ -113,15 +113,18 @@ def test_small_binary_fp64_two_thousand_steps(fm):
     assert np.max(np.abs(gpu[2000]["rho"].sum(axis=(1, 2)) / mass0 - 1)) <= 1e-13
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("n", [1, 2, 3, 4])
 @pytest.mark.parametrize("eos", ["pr", "srk", "vdw"])
-def test_components_and_eos_parity(fm, n, eos):
+def test_components_and_eos_parity(fm, n, eos, precision):
+    # every component count and EOS branch, in FP64 and in FP32 storage (for two components
+    # the FP32 step is the parked, plane-addressed form)
     mixd = mixture_dict(n=n, eos=eos, Tr=1.05, kappa_scale=0.5, M=[1.0, 1.7, 0.8, 2.2][:n], kij=0.03)
     rho = smooth_state(n, 45, 19, seed=5 + n)
     rec = (1, 5, 20)
     ora = run_oracle(mixd, rho, 0.9, "isotropic", "lagged", max(rec), rec)
-    gpu = _gpu_run(fm, mixd, rho, 0.9, "isotropic", "fp64", "lagged", max(rec), rec)
-    _compare(gpu, ora, TOL["fp64"])
+    gpu = _gpu_run(fm, mixd, rho, 0.9, "isotropic", precision, "lagged", max(rec), rec)
+    _compare(gpu, ora, TOL[precision], mixd if precision == "fp32" else None)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
