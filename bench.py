@@ -80,11 +80,20 @@ def gather_lists(xs: list, dist) -> list:
     return [x for p in parts for x in p]
 
 
+def _code_only(src: str) -> str:
+    """C++ source without comments and blank lines: editing a comment keeps the hash."""
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
+
+
 def kernel_hash() -> str:
+    """Identifies the step kernel's code (comments excluded) that a committed profile
+    describes; a profile with another hash gives no traffic figure."""
     h = hashlib.sha256()
     for p in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, p), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, p)) as f:
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

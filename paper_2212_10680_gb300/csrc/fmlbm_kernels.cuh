@@ -5,21 +5,27 @@
 //
 //   phase 1  pull the 9N post-collision values of the previous step into
 //            registers (streaming, step 9 of the previous step), sum them to
-//            rho_i (step 1) and rho~_i = rho_i / M_i (step 2); the same for a
-//            2-node halo ring, whose rho~ goes to shared memory only;
-//   phase 2  on the tile plus a 1-node halo: mixing rules, pressure and ln f_i
-//            (steps 3-5, density-explicit form of Eq. eqfugupdatePR/SRK/VDW) and
-//            G_i = sum_j kappa_ij lap(rho~_j) (step 6, mu_I,i = -G_i);
-//   phase 3  at each node: F_i = -rho~_i RT grad ln f_i + rho~_i grad G_i (step 7,
-//            Eq. eqforcefinal), u from the first moment and half the force
-//            (step 1), g^eq (Eq. eqLBEMCb, rho_0 = 0) and F_{a,i}
+//            rho_i (step 1) and rho~_i = rho_i / M_i (step 2), and evaluate the
+//            mixing rules, pressure and ln f_i (steps 3-5, the density-explicit
+//            form of Eq. eqfugupdatePR/SRK/VDW); the same on a 2-node halo ring
+//            (rho~ to shared memory, ln f on its inner row);
+//   phase 2  on the tile plus a 1-node halo: Phi_i = sum_j kappa_ij lap(rho~_j)
+//            - RT ln f_i (step 6 with mu_I,i = -sum_j kappa_ij lap rho~_j);
+//   phase 3  at each node: F_i = rho~_i grad Phi_i, which is Eq. eqforcefinal
+//            (step 7; the stencils are linear), u from the first moment and half
+//            the force (step 1), g^eq (Eq. eqLBEMCb, rho_0 = 0) and F_{a,i}
 //            (Eq. eqLBEMCfinal3) (step 8), BGK collision (Eq. eqLBEMCa), and a
 //            coalesced store of the post-collision values at the node itself
 //            (the next launch pulls them: streaming happens on the read side).
 //
 // Everything between the one read and the one write of the distributions
 // stays on chip; the only other global traffic is the stored total force
-// sum_i F_i (2 values per node) used by the next step's velocity.
+// sum_i F_i (2 values per node) used by the next step's velocity, and, when a
+// diagnostics request is pending, the density snapshot and per-strip sums of
+// the state the step reads.  With two components in float storage the second
+// component's pulled values wait in shared memory between phases 1 and 3 and
+// the distribution planes are addressed through a second launch parameter
+// (Planes), so that the step fits 48 registers (five blocks per SM).
 //
 // Buffer layout (structure of arrays): plane (i, a) of the distributions is a
 // contiguous nx*ny array in row-major (y, x) order; plane index i*9 + a for
