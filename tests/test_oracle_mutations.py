@@ -167,3 +167,22 @@ def test_planted_interface_mistake_fails_a_pin(mistake, monkeypatch):
     for n in INTERFACE_NAMES:
         monkeypatch.setattr(TI, n, getattr(mod, n))
     assert _failures(INTERFACE_PINS), f"no pin caught: {mistake}"
+
+
+STANDARD_PINS = [(TL.test_standard_equilibrium_and_forcing_moments, ()),
+                 (TL.test_standard_form_conserves_mass_and_keeps_a_uniform_state, ()),
+                 (TL.test_standard_form_single_component_slab_deviates_slightly_from_maxwell, ())]
+
+STANDARD_MISTAKES = {
+    "wrong sign of c_s^2 grad rho_i in the force of Eq. eqForceGen":
+        ("Fx[i] = Fx[i] + CS2 * grx[i]", "Fx[i] = Fx[i] - CS2 * grx[i]"),
+    "the 1 dropped from the standard equilibrium rho_i w_a (1 + S)":
+        ("geq[:, a] = W[a] * rho_i * (1.0 + S)", "geq[:, a] = W[a] * rho_i * S"),
+}
+
+
+@pytest.mark.parametrize("mistake", sorted(STANDARD_MISTAKES))
+def test_planted_standard_form_mistake_fails_a_pin(mistake, monkeypatch):
+    mod = _mutated("lbm", *STANDARD_MISTAKES[mistake])
+    monkeypatch.setattr(TL, "lbm", mod)
+    assert _failures(STANDARD_PINS), f"no pin caught: {mistake}"
