@@ -148,7 +148,9 @@ fmlbm_status fmlbm_buffer_sizes(int32_t n_components, const fmlbm_lattice* latti
  * outlive the handle, and the caller must not write them while the handle's work is in
  * flight.  Everything else (snapshot, reduction scratch, diagnostics stream) the handle
  * allocates itself, as fmlbm_create does.  FMLBM_E_INVALID_ARG for a NULL, host, unaligned
- * or (for non-deviation forms) superfluous g0 pointer. */
+ * or (for non-deviation forms) superfluous g0 pointer, and for a buffer that does not fit
+ * in the device allocation containing it (a buffer carved out of a larger pool allocation
+ * is checked against that allocation only). */
 fmlbm_status fmlbm_create_with_buffers(const fmlbm_mixture* mixture, const fmlbm_lattice* lattice,
                                        void* cuda_stream, void* const g[2], float* const g0[2],
                                        void* const force[2], fmlbm_handle** out);

@@ -426,15 +426,44 @@ struct ExternalBuffers {
     void* F[2];
 };
 
-// A device (or managed) allocation of this process, 16-byte aligned.
-bool usable_device_pointer(const void* p) {
+// cuMemGetAddressRange through the runtime's driver entry point: the base and size of the
+// allocation that contains a device address (null if the driver does not provide it).
+PFN_cuMemGetAddressRange_v3020 address_range_fn() {
+    static PFN_cuMemGetAddressRange_v3020 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &p, 3020, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuMemGetAddressRange_v3020>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// A device (or managed) allocation of this process, 16-byte aligned, with at least `bytes`
+// from p to the end of the allocation that contains it (a buffer carved out of a larger
+// pool allocation is checked against the pool allocation).
+bool usable_device_pointer(const void* p, size_t bytes) {
     if (!p || (reinterpret_cast<uintptr_t>(p) & 15) != 0) return false;
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return false;
+    if (auto range = address_range_fn()) {
+        CUdeviceptr base = 0;
+        size_t size = 0;
+        const CUdeviceptr d = reinterpret_cast<CUdeviceptr>(p);
+        if (range(&base, &size, d) != CUDA_SUCCESS) return false;
+        if (d + bytes > base + size) return false;
+    }
+    return true;
 }
 
 fmlbm_status create_handle(const fmlbm_mixture* mixture, const fmlbm_lattice* lattice, void* cuda_stream,
@@ -464,8 +493,8 @@ fmlbm_status create_handle(const fmlbm_mixture* mixture, const fmlbm_lattice* la
     if (ext) {
         h->owns_buffers = false;
         for (int k = 0; k < 2; ++k) {
-            const bool g0_ok = g0b ? usable_device_pointer(ext->g0[k]) : ext->g0[k] == nullptr;
-            if (!usable_device_pointer(ext->g[k]) || !g0_ok || !usable_device_pointer(ext->F[k])) {
+            const bool g0_ok = g0b ? usable_device_pointer(ext->g0[k], g0b) : ext->g0[k] == nullptr;
+            if (!usable_device_pointer(ext->g[k], gb) || !g0_ok || !usable_device_pointer(ext->F[k], fb)) {
                 delete h;
                 return FMLBM_E_INVALID_ARG;
             }

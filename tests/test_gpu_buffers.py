@@ -71,3 +71,23 @@ def test_caller_buffers_are_checked(fm):
         with pytest.raises(fm.FmlbmError) as ei:
             fm.Lattice(mix, nx, ny, 1.0, "isotropic", prec, "lagged", buffers=bufs)
         assert ei.value.status == 1, (prec, bufs)
+
+
+def test_undersized_caller_buffers_are_rejected(fm):
+    # a buffer whose own allocation is smaller than fmlbm_buffer_sizes asks for is refused
+    # before any kernel could touch it (checked against the allocation that contains the
+    # pointer: the cache is emptied so the half-size tensor gets an allocation of its own)
+    import torch
+    nx, ny = 512, 512
+    mixd, _ = slab_state_binary(nx, ny)
+    mix = fm.mixture_from_dict(mixd)
+    gt, _, ft = _tensors(fm, "fp32", nx, ny)
+    torch.cuda.empty_cache()
+    half = [torch.zeros(gt[0].numel() // 2, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    with pytest.raises(fm.FmlbmError) as ei:
+        fm.Lattice(mix, nx, ny, 1.0, "isotropic", "fp32", "lagged",
+                   buffers=dict(g=_addr(half), g0=None, force=_addr(ft)))
+    assert ei.value.status == 1
+    # the full-size buffers are accepted
+    lat = fm.Lattice(mix, nx, ny, 1.0, "isotropic", "fp32", "lagged", buffers=dict(g=_addr(gt), g0=None, force=_addr(ft)))
+    lat.close()
