@@ -28,7 +28,8 @@
  *   8:(1,-1) (a convention of this library; the paper fixes only the lattice).
  * - The lattice is periodic in x and y.
  * - Device memory of a handle is owned by the library and released by
- *   fmlbm_destroy.  Work is enqueued on the CUDA stream given at creation (NULL:
+ *   fmlbm_destroy, except the distribution and force buffers a caller passes to
+ *   fmlbm_create_with_buffers, which stay the caller's.  Work is enqueued on the CUDA stream given at creation (NULL:
  *   the legacy default stream); calls that return host data synchronise that
  *   stream.  A handle is not thread-safe: one thread at a time.
  * - Errors raised inside kernels (a node leaving the EOS domain: rho_i <= 0,
