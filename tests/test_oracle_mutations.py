@@ -79,6 +79,7 @@ def test_planted_eos_mistake_fails_a_pin(mistake, monkeypatch):
 
 LBM_PINS = [(TL.test_d2q9_isotropy, ()), (TL.test_equilibrium_moments, (0.0,)), (TL.test_forcing_term_moments, ()),
             (TL.test_collision_adds_exactly_the_force_to_the_momentum, (0.8,)),
+            (TL.test_collision_adds_exactly_the_force_to_the_momentum_lagged, (0.8,)),
             (TL.test_uniform_state_is_stationary, ("isotropic",)),
             (TL.test_mirror_and_transpose_symmetry, ("isotropic",)),
             (TL.test_mirror_and_transpose_symmetry, ("central",)),
@@ -103,6 +104,16 @@ LBM_MISTAKES = {
         ("+ neighbour(h, 0, -1)\n                - 4.0 * h)", "+ neighbour(h, 0, -1)\n                - 2.0 * h)"),
     "force on one component with the other's density":
         ("Fx[i] = -rt[i] * mix.RT * glx - rt[i] * gmx", "Fx[i] = -rt[i - 1] * mix.RT * glx - rt[i] * gmx"),
+    # the lagged reading of the velocity (the default on every hot path)
+    "stored force of one component instead of the total":
+        ("F_tot = np.stack([Fx.sum(axis=0), Fy.sum(axis=0)])", "F_tot = np.stack([Fx[0], Fy[0]])"),
+    "stored force not advanced from step to step":
+        ("        g, F_prev = step(g, mix, lat, F_prev)\n", "        g, _ = step(g, mix, lat, F_prev)\n"),
+    "current force used under the lagged reading":
+        ("Fu_x, Fu_y = F_prev[0], F_prev[1]", "Fu_x, Fu_y = Fx.sum(axis=0), Fy.sum(axis=0)"),
+    "lagged force put into the velocity without the half":
+        ("ux = (jx.sum(axis=0) + 0.5 * Fu_x) / rho_tot\n    uy = (jy.sum(axis=0) + 0.5 * Fu_y) / rho_tot",
+         "ux = (jx.sum(axis=0) + Fu_x) / rho_tot\n    uy = (jy.sum(axis=0) + Fu_y) / rho_tot"),
 }
 
 
