@@ -33,7 +33,8 @@ sys.path.insert(0, ROOT)
 
 ALGO_BYTES = {"fp64": 144.0, "fp32": 72.0, "fp16dev": 40.0, "bf16dev": 40.0}  # per component-node update
 L2_FLUSH_BYTES = 256 << 20
-KERNEL_SOURCES = ["paper_2212_10680_gb300/csrc/fmlbm_kernels.cuh", "paper_2212_10680_gb300/csrc/fmlbm_launch.cuh",
+KERNEL_SOURCES = ["paper_2212_10680_gb300/csrc/fmlbm_lanes.cuh", "paper_2212_10680_gb300/csrc/fmlbm_kernels.cuh",
+                  "paper_2212_10680_gb300/csrc/fmlbm_pair.cuh", "paper_2212_10680_gb300/csrc/fmlbm_launch.cuh",
                   "paper_2212_10680_gb300/csrc/fmlbm_tma.cuh"]
 
 
@@ -325,7 +326,8 @@ def run_ours(args, w, rank, world, dist):
     algo = ALGO_BYTES[prec] * n * nodes
     peak = measured_peaks()
     achieved = algo / per_launch_s / 1e9
-    kernel_name = "fused_step_tma" if variant.startswith("tma") else "fused_step"
+    kernel_name = {"tma": "fused_step_tma", "tma_tile": "fused_step_tma", "pair": "fused_step_pair"}.get(variant,
+                                                                                                     "fused_step")
     # the committed counters describe the workload at its own size only
     traffic = None if args.size else profile_traffic(kernel_name, args.workload, prec)
 
@@ -621,7 +623,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--tile-y", type=int, default=0, help="override the fused step's tile height (8 or 16)")
-    ap.add_argument("--variant", default=None, choices=["auto", "plain", "tma", "tma_tile"], help="step kernel variant")
+    ap.add_argument("--variant", default=None, choices=["auto", "plain", "tma", "tma_tile", "pair"], help="step kernel variant")
     ap.add_argument("--batch-lattices", type=int, default=256)
     ap.add_argument("--max-steps", type=int, default=4000)
     ap.add_argument("--check-every", type=int, default=500)

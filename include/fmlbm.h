@@ -238,20 +238,24 @@ fmlbm_status fmlbm_set_state(fmlbm_handle* h, const void* buf, size_t bytes);
 fmlbm_status fmlbm_set_tile_height(fmlbm_handle* h, int32_t tile_y);
 
 /* Which kernel advances the lattice.  PLAIN: the fused step with per-thread pulls from
- * global memory.  TMA: a persistent fused step whose blocks copy each wrap-free tile of
+ * global memory, one node per thread.  PAIR: the same step with two nodes per thread (32
+ * columns apart in a 64-column tile) whose float arithmetic runs as packed two-lane
+ * instructions; float and 16-bit storage, well-balanced formulation, 8-row tiles.  TMA: a persistent fused step whose blocks copy each wrap-free tile of
  * 32 x 8 nodes (every plane plus a 3-node halo) into shared memory with one bulk tensor
  * copy, double-buffered so the next tile's copy overlaps the current tile's arithmetic;
  * tiles on the periodic edges take the plain path.  TMA_TILE: the same copies with one
  * tile per block and a single stage, as many blocks per multiprocessor as shared memory
  * admits (the pulled values wait in shared memory).  All give bit-identical results.  The
  * TMA forms are available for FP32 and 16-bit storage with nx a multiple of 4 (FP32) or 8
- * (16-bit) and a lattice of at least 38 x 14.  AUTO (default): PLAIN, which matched or beat
- * the TMA forms on the workloads measured on GB300; fmlbm_autotune measures the lattice at
- * hand instead.  Asking for a TMA form where it is not available returns
+ * (16-bit) and a lattice of at least 38 x 14.  AUTO (default): PAIR where it exists and the
+ * tile height is the default 8, else PLAIN; fmlbm_autotune measures the lattice at hand
+ * instead.  Every form performs the same operations per node, each rounded once, and gives
+ * the same bits.  Asking for a form where it is not available returns
  * FMLBM_E_UNSUPPORTED. */
 typedef enum fmlbm_step_variant {
     FMLBM_VARIANT_AUTO = 0, FMLBM_VARIANT_PLAIN = 1, FMLBM_VARIANT_TMA = 2,
-    FMLBM_VARIANT_TMA_TILE = 3  /* one tile per block, single stage */
+    FMLBM_VARIANT_TMA_TILE = 3,  /* one tile per block, single stage */
+    FMLBM_VARIANT_PAIR = 4       /* two nodes per thread, packed float arithmetic */
 } fmlbm_step_variant;
 fmlbm_status fmlbm_set_step_variant(fmlbm_handle* h, int32_t variant);
 /* Autotuner: times steps_per_trial steps of every available kernel variant and tile
@@ -260,8 +264,17 @@ fmlbm_status fmlbm_set_step_variant(fmlbm_handle* h, int32_t variant);
  * Outputs (may be NULL): chosen variant, tile height, ms per step. */
 fmlbm_status fmlbm_autotune(fmlbm_handle* h, int32_t steps_per_trial, int32_t* variant, int32_t* tile_y,
                             double* ms_per_step);
-/* The kernel fmlbm_step will use (PLAIN, TMA or TMA_TILE). */
+/* The kernel fmlbm_step will use (PLAIN, TMA, TMA_TILE or PAIR). */
 fmlbm_status fmlbm_get_step_variant(fmlbm_handle* h, int32_t* variant);
+
+/* Bound of the device-side waits of the TMA step forms for a tile's bulk copy, in polls of
+ * the copy's mbarrier (default 2^24, far beyond any copy's completion; the paper has no
+ * counterpart).  A wait that runs out latches FMLBM_E_TIMEOUT, reported by the next
+ * synchronising call; its block then waits, at the default bound, for every copy still in
+ * flight into its shared memory and returns, so the context stays usable (the state of
+ * that step is not computed: re-initialise the lattice).  0 makes the first wait of every
+ * block give up at once (a test of the timeout path).  polls < 0: FMLBM_E_INVALID_ARG. */
+fmlbm_status fmlbm_set_wait_limit(fmlbm_handle* h, int64_t polls);
 
 /* Waits for the handle's streams (including its diagnostics stream) and reports latched
  * kernel errors. */

@@ -62,6 +62,7 @@ struct fmlbm_handle {
     int sms = 1;                     // multiprocessors of the handle's device
     bool tma_maps = false;           // tensor maps of both buffers were encoded
     bool owns_buffers = true;        // false: g, g0 and F belong to the caller (fmlbm_create_with_buffers)
+    long long wait_polls = kMaxPolls;  // bound of a wait for a tile copy (bulk-copy step forms)
     CUtensorMap tmap[2][2];          // [buffer][0: float planes, 1: 16-bit planes]
     std::string last_error;
 };
@@ -193,6 +194,7 @@ StepArgs make_args(const fmlbm_handle* h, int src) {
     A.Fin = h->F[src];
     A.Fout = h->F[src ^ 1];
     A.err = h->err_dev;
+    A.wait_polls = h->wait_polls;
     MixConst mc = h->mc;
     mc.omega = 1.0 / h->lattice.tau;
     mc.fcoef = 1.0 - 0.5 / h->lattice.tau;
@@ -200,6 +202,16 @@ StepArgs make_args(const fmlbm_handle* h, int src) {
     A.mixd = mc;
     A.mixf = cast_mix<float>(mc);
     return A;
+}
+
+bool pair_supported_for(const fmlbm_handle* h) {
+    if (h->lattice.formulation != FMLBM_WELL_BALANCED) return false;  // the paired step is well-balanced only
+    switch (h->lattice.precision) {
+        case FMLBM_FP32: return pair_supported<ST_F32>(h->nc);
+        case FMLBM_FP16DEV: return pair_supported<ST_F16DEV>(h->nc);
+        case FMLBM_BF16DEV: return pair_supported<ST_BF16DEV>(h->nc);
+        default: return false;
+    }
 }
 
 bool tma_supported_for(int precision, int nc) {
@@ -278,18 +290,32 @@ cudaError_t dispatch_step_tma(const fmlbm_handle* h, const StepArgs& A, bool sin
     }
 }
 
-// AUTO resolves to the plain step: with 8-row tiles and the ring-first phase 1 it matched
-// or beat both TMA forms on every measured workload (GB300: 1024^2 binary FP32, 4096^2
-// ternary FP32 and BF16DEV); fmlbm_autotune can still pick a TMA form where it wins.
+// AUTO resolves to the paired step where it exists (float and 16-bit storage, well-balanced
+// formulation) unless a taller tile was asked for (fmlbm_set_tile_height: the plain step's
+// tiles), else to the plain step; fmlbm_autotune can pick another form where it wins.
+// Every form gives the same bits.
 int resolved_variant(const fmlbm_handle* h) {
-    if (!h->tma_maps || h->variant == FMLBM_VARIANT_AUTO) return FMLBM_VARIANT_PLAIN;
+    if (h->variant == FMLBM_VARIANT_AUTO)
+        return pair_supported_for(h) && h->tile_y == kTileYSmall ? FMLBM_VARIANT_PAIR : FMLBM_VARIANT_PLAIN;
     return h->variant;
 }
 
-bool use_tma(const fmlbm_handle* h) { return resolved_variant(h) != FMLBM_VARIANT_PLAIN; }
+cudaError_t dispatch_step_pair(const fmlbm_handle* h, const StepArgs& A) {
+    switch (h->lattice.precision) {
+        case FMLBM_FP32: return launch_step_pair<ST_F32>(A, h->nc, h->stream);
+        case FMLBM_FP16DEV: return launch_step_pair<ST_F16DEV>(A, h->nc, h->stream);
+        case FMLBM_BF16DEV: return launch_step_pair<ST_BF16DEV>(A, h->nc, h->stream);
+        default: return cudaErrorNotSupported;
+    }
+}
 
 cudaError_t dispatch_step(const fmlbm_handle* h, const StepArgs& A, bool moments) {
-    if (!moments && use_tma(h)) return dispatch_step_tma(h, A, resolved_variant(h) == FMLBM_VARIANT_TMA_TILE);
+    if (!moments) {
+        const int v = resolved_variant(h);
+        if (v == FMLBM_VARIANT_PAIR) return dispatch_step_pair(h, A);
+        if (v == FMLBM_VARIANT_TMA || v == FMLBM_VARIANT_TMA_TILE)
+            return dispatch_step_tma(h, A, v == FMLBM_VARIANT_TMA_TILE);
+    }
     switch (h->lattice.precision) {
         case FMLBM_FP64: return launch_step<ST_F64>(A, h->nc, moments, h->tile_y, h->stream);
         case FMLBM_FP32: return launch_step<ST_F32>(A, h->nc, moments, h->tile_y, h->stream);
@@ -695,10 +721,12 @@ fmlbm_status fmlbm_set_tile_height(fmlbm_handle* h, int32_t tile_y) {
 }
 
 fmlbm_status fmlbm_set_step_variant(fmlbm_handle* h, int32_t variant) {
-    if (!h || variant < FMLBM_VARIANT_AUTO || variant > FMLBM_VARIANT_TMA_TILE)
+    if (!h || variant < FMLBM_VARIANT_AUTO || variant > FMLBM_VARIANT_PAIR)
         return fail(h, FMLBM_E_INVALID_ARG, "unknown step variant");
     if ((variant == FMLBM_VARIANT_TMA || variant == FMLBM_VARIANT_TMA_TILE) && !h->tma_maps)
         return fail(h, FMLBM_E_UNSUPPORTED, "no TMA step for this precision, component count or lattice shape");
+    if (variant == FMLBM_VARIANT_PAIR && !pair_supported_for(h))
+        return fail(h, FMLBM_E_UNSUPPORTED, "no paired step for this precision or formulation");
     h->variant = variant;
     return FMLBM_OK;
 }
@@ -707,8 +735,9 @@ fmlbm_status fmlbm_autotune(fmlbm_handle* h, int32_t steps_per_trial, int32_t* v
                             double* ms_per_step) {
     if (!h || steps_per_trial < 1) return fail(h, FMLBM_E_INVALID_ARG, "bad argument");
     struct Cand { int variant, tile_y; };
-    Cand cands[5];
+    Cand cands[6];
     int nc = 0;
+    if (pair_supported_for(h)) cands[nc++] = Cand{FMLBM_VARIANT_PAIR, kTileYSmall};
     for (int ty : {kTileYSmall, kTileYLarge, kTileYHuge})
         if (ty <= 16 || h->lattice.ny >= 64) cands[nc++] = Cand{FMLBM_VARIANT_PLAIN, ty};
     if (h->tma_maps) {
@@ -746,6 +775,12 @@ fmlbm_status fmlbm_autotune(fmlbm_handle* h, int32_t steps_per_trial, int32_t* v
     if (tile_y) *tile_y = pick.tile_y;
     if (ms_per_step) *ms_per_step = best / steps_per_trial;
     return sync_and_check(h);
+}
+
+fmlbm_status fmlbm_set_wait_limit(fmlbm_handle* h, int64_t polls) {
+    if (!h || polls < 0) return fail(h, FMLBM_E_INVALID_ARG, "the wait limit must be >= 0");
+    h->wait_polls = (long long)polls;
+    return FMLBM_OK;
 }
 
 fmlbm_status fmlbm_get_step_variant(fmlbm_handle* h, int32_t* variant) {

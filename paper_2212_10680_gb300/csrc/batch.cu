@@ -87,12 +87,7 @@ cudaError_t launch_batch_step_t(BatchLattice* lat, const WorkItem* work, int nwo
     using Real = typename StoreTraits<ST>::Real;
     constexpr size_t smem = sizeof(StepSmem<Real, NC, TY>);
     auto k = batch_step<NC, ST, TY>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    FMLBM_ENSURE_SMEM(k, smem);
     k<<<grid, dim3(kTX, TY), smem, s>>>(lat, work, nwork);
     return cudaGetLastError();
 }

@@ -57,12 +57,12 @@ __global__ void __launch_bounds__(kTX* TY, ST == ST_F64 ? 1 : 1024 / (kTX * TY))
         const bool inner = x0 >= 3 && x0 + kTX + 3 <= nx && y0 >= 3 && y0 + TY + 3 <= ny;
         const int gxn = x0 + tx, gyn = y0 + ty;
         prefetch_force<Real, NC, TY>(A, S, tx, ty, gxn, gyn);
-        Real g[NC][9];
-        phase1_global<NC, ST, TY>(A, m, S, g, x0, y0, inner, tx, ty, tid);
+        Real g[NC][9], r[NC], jx, jy;
+        phase1_global<NC, ST, TY>(A, m, S, g, r, jx, jy, x0, y0, inner, tx, ty, tid);
         __syncthreads();
         phase2<NC, TY, Real>(m, S, A.stencil, tid);
         __syncthreads();
-        if (gxn < nx && gyn < ny) phase3<NC, ST, TY, false>(A, m, S, g, tx, ty, gxn, gyn);
+        if (gxn < nx && gyn < ny) phase3<NC, ST, TY, false>(A, m, S, g, r, jx, jy, tx, ty, gxn, gyn);
         __syncthreads();  // As and the shared tiles are reused by the next item
     }
 }

@@ -18,6 +18,10 @@
 //            coalesced store of the post-collision values at the node itself
 //            (the next launch pulls them: streaming happens on the read side).
 //
+// The per-node arithmetic is written once over a lane type (fmlbm_lanes.cuh): one node
+// per thread here, two nodes per thread in the paired step (fmlbm_pair.cuh), with every
+// operation rounded once and never contracted, so all kernels give the same bits.
+//
 // Everything between the one read and the one write of the distributions
 // stays on chip; the only other global traffic is the stored total force
 // sum_i F_i (2 values per node) used by the next step's velocity, and, when a
@@ -37,6 +41,8 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include "fmlbm_lanes.cuh"
 
 namespace fmlbm {
 
@@ -126,6 +132,8 @@ struct StepArgs {
     void* diag_partial;
     void* rho_prev;  // [N][ny][nx] in the storage arithmetic type
     int have_prev;
+    int pad0;
+    long long wait_polls;  // polls of a bounded wait for a tile copy (bulk-copy step forms)
 };
 
 // The base address of every distribution plane of A.gin / A.gout, a second launch
@@ -245,17 +253,6 @@ __device__ __forceinline__ void store_gsel(const StepArgs& A, const Planes* P, i
     else store_g<ST>(A, i, a, (size_t)node, (size_t)nxy, v);
 }
 
-// Reciprocal and natural logarithm: exact library forms in double (the FP64 path is the
-// parity reference), the hardware approximations in float, whose documented error
-// bounds (2 ulp for the quotient; for the logarithm 2^-21.41 absolute on [0.5, 2] and
-// 3 ulp elsewhere) lie well inside the FP32 path's error budget.  The logarithm is the
-// costliest step of ln f (N + 1 per node, halo included); the fast form made the
-// three-component step about 10% faster.
-__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
-__device__ __forceinline__ double lnE(double x) { return log(x); }
-__device__ __forceinline__ float lnE(float x) { return __logf(x); }
-
 __device__ __forceinline__ int wrap(int v, int n) {
     int r = v % n;
     return r < 0 ? r + n : r;
@@ -269,93 +266,146 @@ __device__ __forceinline__ int wrap(int v, int n) {
 //   SRK: p v / RT - 1 = beta/(1-beta) - (aa_m rho~ / RT) / (1 + beta),  ln(1 + b_m / v) = log1p(beta)
 //   vdW: b_i / (v - b_m) = b_i rho~ / (1 - beta),  2 S_i / (RT v) = 2 S_i rho~ / RT
 // (each logarithm takes a ratio whose relative rounding is a few ulp, so merging the
-// printed logarithms pairwise costs no accuracy).  Returns beta (for the domain check).
-template <int NC, typename E>
-__device__ __forceinline__ E node_lnf(const MixConstT<E>& m, const E* rt, E* lnf) {
-    E rtot = E(0);
+// printed logarithms pairwise costs no accuracy).  Lane arithmetic: one node per lane.
+// Returns beta (for the domain check).
+template <int NC, typename V, typename E>
+__device__ __forceinline__ V node_lnf(const MixConstT<E>& m, const V* rt, V* lnf) {
+    V rtot = rt[0];
 #pragma unroll
-    for (int i = 0; i < NC; ++i) rtot += rt[i];
-    const E inv = rcp(rtot);
-    E beta = E(0);    // b_m rho~ = sum_i b_i rho~_i (the packing fraction)
+    for (int i = 1; i < NC; ++i) rtot = vadd(rtot, rt[i]);
+    const V inv = vrcp(rtot);
+    V beta = vmul(vbc<V>(m.b[0]), rt[0]);  // b_m rho~ = sum_i b_i rho~_i (the packing fraction)
 #pragma unroll
-    for (int i = 0; i < NC; ++i) beta += m.b[i] * rt[i];
-    E S[NC];          // rho~ S_i = sum_j (a alpha)_ij rho~_j
-    E aam_rt2 = E(0); // (a alpha)_m rho~^2
+    for (int i = 1; i < NC; ++i) beta = vfma(vbc<V>(m.b[i]), rt[i], beta);
+    V S[NC];                               // rho~ S_i = sum_j (a alpha)_ij rho~_j
+    V aam_rt2;                             // (a alpha)_m rho~^2
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
-        E s = E(0);
+        V s = vmul(vbc<V>(m.aij[i * kMaxC]), rt[0]);
 #pragma unroll
-        for (int j = 0; j < NC; ++j) s += m.aij[i * kMaxC + j] * rt[j];
+        for (int j = 1; j < NC; ++j) s = vfma(vbc<V>(m.aij[i * kMaxC + j]), rt[j], s);
         S[i] = s;
-        aam_rt2 += rt[i] * s;
+        aam_rt2 = i == 0 ? vmul(rt[0], s) : vfma(rt[i], s, aam_rt2);
     }
-    const E invomb = rcp(E(1) - beta);
-    const E lead = m.RT * invomb;
+    const V one = vbc<V>(E(1));
+    const V invomb = vrcp(vsub(one, beta));
+    const V lead = vmul(vbc<V>(m.RT), invomb);
     if (m.eos == 2) {
+        const V rb1 = vmul(rtot, invomb);               // rho~ / (1 - beta)
+        const V m2rt = vbc<V>(E(-2) * m.invRT);
 #pragma unroll
         for (int i = 0; i < NC; ++i)
-            lnf[i] = lnE(rt[i] * lead) + m.b[i] * rtot * invomb - E(2) * S[i] * m.invRT;
+            lnf[i] = vfma(S[i], m2rt, vfma(vbc<V>(m.b[i]), rb1, vln(vmul(rt[i], lead))));
         return beta;
     }
-    const E att = aam_rt2 * inv * m.invRT;   // (a alpha)_m rho~ / RT
-    E rep, lr, pref;
+    const V att = vmul(vmul(aam_rt2, inv), vbc<V>(m.invRT));   // (a alpha)_m rho~ / RT
+    V rep, lr;
+    E pref;
     if (m.eos == 0) {
         const E s2 = E(1.4142135623730950488);
-        rep = beta * invomb - att * rcp(E(1) + E(2) * beta - beta * beta);
-        lr = lnE((E(1) + (E(1) + s2) * beta) * rcp(E(1) + (E(1) - s2) * beta));
+        const V den = vfma(beta, vsub(vbc<V>(E(2)), beta), one);   // 1 + 2 beta - beta^2
+        rep = vfma(vneg(att), vrcp(den), vmul(beta, invomb));
+        lr = vln(vmul(vfma(vbc<V>(E(1) + s2), beta, one), vrcp(vfma(vbc<V>(E(1) - s2), beta, one))));
         pref = m.invRT * E(0.35355339059327376220);  // 1 / (2 sqrt2 RT)
     } else {
-        rep = beta * invomb - att * rcp(E(1) + beta);
-        lr = log1p(beta);
+        rep = vfma(vneg(att), vrcp(vadd(one, beta)), vmul(beta, invomb));
+        lr = vlog1p(beta);
         pref = m.invRT;
     }
     // with b_m = beta / rho~ the coefficient of lr, ((a alpha)_m b_i/b_m - 2 sum_j x_j (a alpha)_ij)
     // / (c b_m RT), becomes pref ((a alpha)_m b_i/b_m - 2 S_i / rho~) rho~ / beta
-    const E rb = rtot * rcp(beta);                 // 1 / b_m
-    const E aam = aam_rt2 * inv * inv;             // (a alpha)_m
-    const E plr = pref * rb * lr;
+    const V rb = vmul(rtot, vrcp(beta));                       // 1 / b_m
+    const V aam = vmul(vmul(aam_rt2, inv), inv);               // (a alpha)_m
+    const V plr = vmul(vmul(vbc<V>(pref), rb), lr);
+    const V m2inv = vmul(vbc<V>(E(-2)), inv);
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
-        const E bi = m.b[i] * rb;                  // b_i / b_m
-        lnf[i] = lnE(rt[i] * lead) + bi * rep + plr * (aam * bi - E(2) * S[i] * inv);
+        const V bi = vmul(vbc<V>(m.b[i]), rb);                 // b_i / b_m
+        const V t = vfma(aam, bi, vmul(S[i], m2inv));          // (a alpha)_m b_i/b_m - 2 S_i / rho~
+        lnf[i] = vfma(plr, t, vfma(bi, rep, vln(vmul(rt[i], lead))));
     }
     return beta;
 }
 
-// Shared-memory tile of a field with a halo of H nodes.
-template <typename E, int NC, int TY, int H>
+// Shared-memory tile of a field with a halo of H nodes around TW x TY nodes.
+template <typename E, int NC, int TY, int H, int TW = kTX>
 struct Tile {
-    static constexpr int W = kTX + 2 * H;
+    static constexpr int W = TW + 2 * H;
     static constexpr int Hh = TY + 2 * H;
     E v[NC][Hh][W];
 };
 
-// Finite differences at tile position (cx, cy) of a field tile f (any halo >= 1).
-// stencil 1 = central (Eqs. eq1stder, eq2ndder); 0 = isotropic D2Q9 stencils.
-template <typename E, typename T>
-__device__ __forceinline__ void grad_at(const T& f, int i, int cx, int cy, int stencil, E& gx, E& gy) {
-    const E e = f.v[i][cy][cx + 1], w = f.v[i][cy][cx - 1];
-    const E n = f.v[i][cy + 1][cx], s = f.v[i][cy - 1][cx];
-    if (stencil == 1) {
-        gx = E(0.5) * (e - w);
-        gy = E(0.5) * (n - s);
+// Lane access to a shared tile: lane k of the value sits at column cx + k ds.
+template <typename V, typename T>
+__device__ __forceinline__ V tld(const T& f, int i, int cy, int cx, int ds) {
+    if constexpr (LaneTraits<V>::n == 1) {
+        return f.v[i][cy][cx];
     } else {
-        const E ne = f.v[i][cy + 1][cx + 1], nw = f.v[i][cy + 1][cx - 1];
-        const E sw = f.v[i][cy - 1][cx - 1], se = f.v[i][cy - 1][cx + 1];
-        // 3 sum_a w_a e_a h(r + e_a): 1/3 for the axis neighbours, 1/12 for the diagonals
-        gx = (e - w) * E(1.0 / 3.0) + (ne - nw - sw + se) * E(1.0 / 12.0);
-        gy = (n - s) * E(1.0 / 3.0) + (ne + nw - sw - se) * E(1.0 / 12.0);
+        return make_float2(f.v[i][cy][cx], f.v[i][cy][cx + ds]);
+    }
+}
+template <typename V, typename T>
+__device__ __forceinline__ void tst(T& f, int i, int cy, int cx, int ds, V v) {
+    if constexpr (LaneTraits<V>::n == 1) {
+        f.v[i][cy][cx] = v;
+    } else {
+        f.v[i][cy][cx] = v.x;
+        f.v[i][cy][cx + ds] = v.y;
     }
 }
 
-template <typename E, typename T>
-__device__ __forceinline__ E lap_at(const T& f, int i, int cx, int cy, int stencil) {
-    const E c = f.v[i][cy][cx];
-    const E ax = f.v[i][cy][cx + 1] + f.v[i][cy][cx - 1] + f.v[i][cy + 1][cx] + f.v[i][cy - 1][cx];
-    if (stencil == 1) return ax - E(4) * c;
-    const E dg = f.v[i][cy + 1][cx + 1] + f.v[i][cy + 1][cx - 1] + f.v[i][cy - 1][cx - 1] + f.v[i][cy - 1][cx + 1];
+// Finite differences at tile position (cx, cy) of a field tile f (any halo >= 1).
+// stencil 1 = central (Eqs. eq1stder, eq2ndder); 0 = isotropic D2Q9 stencils.
+template <typename V, typename T>
+__device__ __forceinline__ void grad_at(const T& f, int i, int cx, int cy, int ds, int stencil, V& gx, V& gy) {
+    using E = LaneE<V>;
+    const V e = tld<V>(f, i, cy, cx + 1, ds), w = tld<V>(f, i, cy, cx - 1, ds);
+    const V n = tld<V>(f, i, cy + 1, cx, ds), s = tld<V>(f, i, cy - 1, cx, ds);
+    if (stencil == 1) {
+        gx = vmul(vbc<V>(E(0.5)), vsub(e, w));
+        gy = vmul(vbc<V>(E(0.5)), vsub(n, s));
+    } else {
+        const V ne = tld<V>(f, i, cy + 1, cx + 1, ds), nw = tld<V>(f, i, cy + 1, cx - 1, ds);
+        const V sw = tld<V>(f, i, cy - 1, cx - 1, ds), se = tld<V>(f, i, cy - 1, cx + 1, ds);
+        // 3 sum_a w_a e_a h(r + e_a): 1/3 for the axis neighbours, 1/12 for the diagonals
+        const V third = vbc<V>(E(1.0 / 3.0)), twelfth = vbc<V>(E(1.0 / 12.0));
+        gx = vfma(vsub(e, w), third, vmul(vadd(vsub(ne, nw), vsub(se, sw)), twelfth));
+        gy = vfma(vsub(n, s), third, vmul(vsub(vadd(ne, nw), vadd(sw, se)), twelfth));
+    }
+}
+
+template <typename V, typename T>
+__device__ __forceinline__ V lap_at(const T& f, int i, int cx, int cy, int ds, int stencil) {
+    using E = LaneE<V>;
+    const V c = tld<V>(f, i, cy, cx, ds);
+    const V ax = vadd(vadd(tld<V>(f, i, cy, cx + 1, ds), tld<V>(f, i, cy, cx - 1, ds)),
+                      vadd(tld<V>(f, i, cy + 1, cx, ds), tld<V>(f, i, cy - 1, cx, ds)));
+    const V m4 = vbc<V>(E(-4));
+    if (stencil == 1) return vfma(m4, c, ax);
+    const V dg = vadd(vadd(tld<V>(f, i, cy + 1, cx + 1, ds), tld<V>(f, i, cy + 1, cx - 1, ds)),
+                      vadd(tld<V>(f, i, cy - 1, cx - 1, ds), tld<V>(f, i, cy - 1, cx + 1, ds)));
     // 6 sum_a w_a (h(r+e_a) - h(r)): 2/3 for axis neighbours, 1/6 for diagonals
-    return (ax - E(4) * c) * E(2.0 / 3.0) + (dg - E(4) * c) * E(1.0 / 6.0);
+    return vfma(vfma(m4, c, ax), vbc<V>(E(2.0 / 3.0)), vmul(vfma(m4, c, dg), vbc<V>(E(1.0 / 6.0))));
+}
+
+// Sum of the nine pulled values of one component, in direction order (the order every
+// kernel uses for the density of step 1, and the diagnostics for their sums).
+template <typename V>
+__device__ __forceinline__ V sum9(const V (&h)[9]) {
+    V r = h[0];
+#pragma unroll
+    for (int a = 1; a < 9; ++a) r = vadd(r, h[a]);
+    return r;
+}
+
+// First moment sum_i sum_a g_{a,i} e_a of the pulled values (step 1), e_a in {0, +-1}
+// written out (no multiplications by zero); components in order.
+template <typename V>
+__device__ __forceinline__ void moment_j(const V (&h)[9], bool first, V& jx, V& jy) {
+    const V jxi = vsub(vadd(vadd(h[1], h[5]), h[8]), vadd(vadd(h[3], h[6]), h[7]));
+    const V jyi = vsub(vadd(vadd(h[2], h[5]), h[6]), vadd(vadd(h[4], h[7]), h[8]));
+    jx = first ? jxi : vadd(jx, jxi);
+    jy = first ? jyi : vadd(jy, jyi);
 }
 
 template <typename E, int NC, int TY>
@@ -369,10 +419,10 @@ struct StepSmem {
 // Occupancy for two components in float storage (8-row tiles): the second component's
 // nine pulled values wait in shared memory from the end of phase 1 to phase 3 instead of
 // in registers, which lets the step fit 48 registers without spilling, i.e. five blocks
-// of 256 threads per SM instead of four (1024^2 binary FP32: 2.5% faster on GB300).  With
-// three or four components the step spills at 48 registers even with values parked, and
-// parking every value of a node was slower.  The same step also addresses the distribution
-// planes through the launch's plane pointers (Planes, load_gp / store_gp).
+// of 256 threads per SM instead of four.  With three or four components the step spills
+// at 48 registers even with values parked, and parking every value of a node was slower.
+// The same step also addresses the distribution planes through the launch's plane
+// pointers (Planes, load_gp / store_gp).
 template <int NC, int ST, int TY>
 constexpr bool kParkLast = ST != ST_F64 && NC == 2 && TY == 8;
 template <int NC, int ST, int TY>
@@ -437,11 +487,11 @@ __device__ __forceinline__ int pull_src(int a, int wx, int wy, int xm, int xp, i
     return sy * nx + sx;
 }
 
-// Sum of the pulled distributions of component i at node (wx, wy) (wrapped coordinates).
+// Sum of the pulled distributions of component i at node (wx, wy) (wrapped coordinates),
+// in direction order (sum9).
 template <int NC, int ST, bool PP = false>
 __device__ __forceinline__ void pull_rho(const StepArgs& A, int wx, int wy, bool inner, int nx, int ny, int nxy,
                                          typename StoreTraits<ST>::Real* rs, const Planes* P = nullptr) {
-    using Real = typename StoreTraits<ST>::Real;
     const int node = wy * nx + wx;
     int xm = wx - 1, xp = wx + 1, ym = wy - 1, yp = wy + 1;
     if (!inner) {
@@ -451,67 +501,73 @@ __device__ __forceinline__ void pull_rho(const StepArgs& A, int wx, int wy, bool
         yp = wy == ny - 1 ? 0 : yp;
     }
 #pragma unroll
-    for (int i = 0; i < NC; ++i) rs[i] = Real(0);
-#pragma unroll
     for (int a = 0; a < 9; ++a) {
         const int src = inner ? node - ey(a) * nx - ex(a) : pull_src(a, wx, wy, xm, xp, ym, yp, nx);
 #pragma unroll
-        for (int i = 0; i < NC; ++i)
-            rs[i] += PP ? load_gp<ST>(*P, i, a, src) : load_g<ST>(A, i, a, (size_t)src, (size_t)nxy);
+        for (int i = 0; i < NC; ++i) {
+            const auto v = PP ? load_gp<ST>(*P, i, a, src) : load_g<ST>(A, i, a, (size_t)src, (size_t)nxy);
+            rs[i] = a == 0 ? v : vadd(rs[i], v);
+        }
     }
 }
 
 // Latch the first node that left the EOS domain (rho~_i <= 0, beta >= 1, non-finite ln f).
-template <int NC, typename Real>
-__device__ __forceinline__ void domain_check(const StepArgs& A, const Real* rt, const Real* lnf, Real beta, int x,
-                                             int y) {
-    bool bad = !(beta < Real(1));
-    int badc = 0;
+// Lane k is the node (x + k dx, y); valid_mask bit k says whether it lies in the lattice.
+template <int NC, typename V>
+__device__ __forceinline__ void domain_check(const StepArgs& A, const V* rt, const V* lnf, V beta, int x, int dx,
+                                             int y, unsigned valid_mask) {
+    using E = LaneE<V>;
 #pragma unroll
-    for (int i = NC - 1; i >= 0; --i) {
-        if (!(rt[i] > Real(0)) || !isfinite(lnf[i])) {
-            badc = i;
-            bad = true;
+    for (int k = 0; k < LaneTraits<V>::n; ++k) {
+        if (!((valid_mask >> k) & 1u)) continue;
+        bool bad = !(lane(beta, k) < E(1));
+        int badc = 0;
+#pragma unroll
+        for (int i = NC - 1; i >= 0; --i) {
+            if (!(lane(rt[i], k) > E(0)) || !isfinite(lane(lnf[i], k))) {
+                badc = i;
+                bad = true;
+            }
         }
-    }
-    // a plain read first: once a lattice has failed, every bad node would otherwise
-    // contend for the same word with an atomic in every step
-    if (bad && *reinterpret_cast<volatile int*>(&A.err->flag) == 0 && atomicCAS(&A.err->flag, 0, 1) == 0) {
-        A.err->comp = badc;
-        A.err->x = x;
-        A.err->y = y;
+        // a plain read first: once a lattice has failed, every bad node would otherwise
+        // contend for the same word with an atomic in every step
+        if (bad && *reinterpret_cast<volatile int*>(&A.err->flag) == 0 && atomicCAS(&A.err->flag, 0, 1) == 0) {
+            A.err->comp = badc;
+            A.err->x = x + k * dx;
+            A.err->y = y;
+        }
     }
 }
 
 // ---- the phases of one tile, shared by every variant of the step kernel (so all variants
 //      perform the same arithmetic in the same order and agree bit for bit) ----
 
-// Phase 1, the node owned by this thread: rho~ and ln f from its nine pulled values per
-// component (steps 1-5).
+// Phase 1, the node owned by this thread: rho_i and the first moment (step 1, returned in
+// r, jx, jy) and rho~, ln f (steps 2-5) from its nine pulled values per component.
 template <int NC, int TY, typename Real>
 __device__ __forceinline__ void phase1_node(const StepArgs& A, const MixConstT<Real>& m, StepSmem<Real, NC, TY>& S,
-                                            const Real (&g)[NC][9], int tx, int ty, bool valid, int gx, int gy) {
+                                            const Real (&g)[NC][9], Real (&r)[NC], Real& jx, Real& jy, int tx, int ty,
+                                            bool valid, int gx, int gy) {
     Real rt[NC], lnf[NC];
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
-        Real r = Real(0);
-#pragma unroll
-        for (int a = 0; a < 9; ++a) r += g[i][a];
-        rt[i] = r * m.invM[i];
+        r[i] = sum9(g[i]);
+        moment_j(g[i], i == 0, jx, jy);
+        rt[i] = vmul(r[i], m.invM[i]);
         S.rt.v[i][ty + 2][tx + 2] = rt[i];
     }
     const Real beta = node_lnf<NC, Real>(m, rt, lnf);
 #pragma unroll
     for (int i = 0; i < NC; ++i) S.lf.v[i][ty + 1][tx + 1] = lnf[i];
-    if (valid) domain_check<NC, Real>(A, rt, lnf, beta, gx, gy);
+    domain_check<NC, Real>(A, rt, lnf, beta, gx, 0, gy, valid ? 1u : 0u);
 }
 
-// Ring position r (0 <= r < 4 (32 + 4) + 4 TY) -> box coordinates (bx, by) of the 2-node halo
-// ring around the tile (box origin at tile origin - (2, 2)), row by row.  (Putting the
+// Ring position r (0 <= r < 4 (TW + 4) + 4 TY) -> box coordinates (bx, by) of the 2-node halo
+// ring around a TW x TY tile (box origin at tile origin - (2, 2)), row by row.  (Putting the
 // inner-ring positions, which also need ln f, first measured slower.)
-template <int TY>
+template <int TY, int TW = kTX>
 __device__ __forceinline__ void ring_position(int r, int& bx, int& by) {
-    constexpr int WB = kTX + 4;
+    constexpr int WB = TW + 4;
     if (r < 2 * WB) {
         by = r / WB;
         bx = r % WB;
@@ -522,7 +578,7 @@ __device__ __forceinline__ void ring_position(int r, int& bx, int& by) {
         const int q = r - 4 * WB;
         by = 2 + (q >> 2);
         const int c = q & 3;
-        bx = c < 2 ? c : kTX + c;  // 0, 1, TX+2, TX+3
+        bx = c < 2 ? c : TW + c;  // 0, 1, TW+2, TW+3
     }
 }
 
@@ -532,7 +588,7 @@ __device__ __forceinline__ void phase1_ring(const MixConstT<Real>& m, StepSmem<R
                                             int bx, int by) {
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
-        rt[i] *= m.invM[i];
+        rt[i] = vmul(rt[i], m.invM[i]);
         S.rt.v[i][by][bx] = rt[i];
     }
     if (bx >= 1 && bx <= kTX + 2 && by >= 1 && by <= TY + 2) {
@@ -543,20 +599,22 @@ __device__ __forceinline__ void phase1_ring(const MixConstT<Real>& m, StepSmem<R
     }
 }
 
-// Phase 2: G_i = sum_j kappa_ij lap rho~_j on tile + 1 (step 6, mu_I,i = -G_i), stored as
-// the potential Phi_i = G_i - RT ln f_i whose gradient times rho~_i is the force of step 7.
-template <int NC, int TY, typename Real>
-__device__ __forceinline__ void phase2_at(const MixConstT<Real>& m, StepSmem<Real, NC, TY>& S, int stencil, int cx,
-                                          int cy) {
-    Real L[NC];
+// Phase 2 at box position (cx, cy) of the tile + 1 box (lane k at cx + k ds):
+// G_i = sum_j kappa_ij lap rho~_j (step 6, mu_I,i = -G_i), stored as the potential
+// Phi_i = G_i - RT ln f_i whose gradient times rho~_i is the force of step 7.
+template <int NC, typename V, typename E, typename TR, typename TL, typename TG>
+__device__ __forceinline__ void phase2_core(const MixConstT<E>& m, const TR& rt, const TL& lf, TG& G, int stencil,
+                                            int cx, int cy, int ds) {
+    V L[NC];
 #pragma unroll
-    for (int j = 0; j < NC; ++j) L[j] = lap_at<Real>(S.rt, j, cx + 1, cy + 1, stencil);
+    for (int j = 0; j < NC; ++j) L[j] = lap_at<V>(rt, j, cx + 1, cy + 1, ds, stencil);
+    const V mRT = vbc<V>(-m.RT);
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
-        Real Gi = Real(0);
+        V Gi = vmul(vbc<V>(m.kap[i * kMaxC]), L[0]);
 #pragma unroll
-        for (int j = 0; j < NC; ++j) Gi += m.kap[i * kMaxC + j] * L[j];
-        S.G.v[i][cy][cx] = Gi - m.RT * S.lf.v[i][cy][cx];
+        for (int j = 1; j < NC; ++j) Gi = vfma(vbc<V>(m.kap[i * kMaxC + j]), L[j], Gi);
+        tst<V>(G, i, cy, cx, ds, vfma(mRT, tld<V>(lf, i, cy, cx, ds), Gi));
     }
 }
 
@@ -566,146 +624,189 @@ __device__ __forceinline__ void phase2_at(const MixConstT<Real>& m, StepSmem<Rea
 template <int NC, int TY, typename Real>
 __device__ __forceinline__ void phase2(const MixConstT<Real>& m, StepSmem<Real, NC, TY>& S, int stencil, int tid) {
     const int tx = tid & (kTX - 1), ty = tid / kTX;
-    for (int cy = ty; cy < TY + 2; cy += TY) phase2_at<NC, TY, Real>(m, S, stencil, tx, cy);
+    for (int cy = ty; cy < TY + 2; cy += TY) phase2_core<NC, Real>(m, S.rt, S.lf, S.G, stencil, tx, cy, 0);
     if (ty == TY - 1)
-        for (int e = tx; e < 2 * (TY + 2); e += kTX) phase2_at<NC, TY, Real>(m, S, stencil, kTX + (e & 1), e >> 1);
+        for (int e = tx; e < 2 * (TY + 2); e += kTX)
+            phase2_core<NC, Real>(m, S.rt, S.lf, S.G, stencil, kTX + (e & 1), e >> 1, 0);
 }
 
-// Phase 3 at one valid node: force (step 7), velocity (step 1), equilibrium and forcing
-// (step 8), collision (step 9), coalesced stores at the node.
+// Phase 3 at one lane of nodes: force (step 7), velocity (step 1), equilibrium and
+// forcing (step 8) and collision (step 9).
+//   Gt, Rt: the Phi tile (tile + 1) and the rho~ tile (tile + 2); (cx, cy) the node's
+//           position in the tile + 1 coordinates, lane k at cx + k ds;
+//   rho, jx, jy: the component densities and the total first moment of step 1 (phase 1);
+//   geth(i, h): the nine pulled values of component i;
+//   Fpx, Fpy: the stored total force F(t - 1) (LAG: the lagged reading; ignored otherwise);
+//   COLLIDE = false: velocity only (macroscopic fields); else store(i, a, value) receives
+//           every post-collision value; Ft is the total force of this step.
+// Under the lagged reading u is known before any force of this step, so each component's
+// force goes straight into its collision (no per-component arrays held in registers).
 // STD: the standard formulation of Section VI -- equilibrium rho_i w_a [1 + ...] of
 // Eq. eqLBE, Guo's forcing term of Eq. eqLBEfinal3 (no grad rho_i part) and
 // F_i + c_s^2 grad rho_i of Eq. eqForceGen.
+template <int NC, bool COLLIDE, bool STD, bool LAG, typename V, typename E, typename TG, typename TR, typename GetH,
+          typename Store>
+__device__ __forceinline__ void phase3_core(const MixConstT<E>& m, int stencil, const TG& Gt, const TR& Rt, int cx,
+                                            int cy, int ds, const V (&rho)[NC], V jx, V jy, GetH&& geth, V Fpx,
+                                            V Fpy, Store&& store, V& Ftx, V& Fty, V& ux, V& uy) {
+    // F_i and grad rho_i of component i
+    auto force = [&](int i, V& Fx, V& Fy, V& grx, V& gry) {
+        V px, py, rx, ry;
+        grad_at<V>(Gt, i, cx, cy, ds, stencil, px, py);
+        grad_at<V>(Rt, i, cx + 1, cy + 1, ds, stencil, rx, ry);
+        const V rti = tld<V>(Rt, i, cy + 1, cx + 1, ds);
+        // grad rho_i = M_i grad rho~_i
+        grx = vmul(rx, vbc<V>(m.M[i]));
+        gry = vmul(ry, vbc<V>(m.M[i]));
+        // Eq. eqforcefinal: F_i = -rho~_i RT grad ln f_i + rho~_i grad(sum_j kappa_ij lap rho~_j)
+        //                      = rho~_i grad Phi_i (the stencils are linear)
+        Fx = vmul(rti, px);
+        Fy = vmul(rti, py);
+        if constexpr (STD) {  // Eq. eqForceGen: + c_s^2 grad rho_i
+            Fx = vfma(vbc<V>(E(1.0 / 3.0)), grx, Fx);
+            Fy = vfma(vbc<V>(E(1.0 / 3.0)), gry, Fy);
+        }
+        Ftx = i == 0 ? Fx : vadd(Ftx, Fx);
+        Fty = i == 0 ? Fy : vadd(Fty, Fy);
+    };
+    V rho_t = rho[0];
+#pragma unroll
+    for (int i = 1; i < NC; ++i) rho_t = vadd(rho_t, rho[i]);
+    const V half = vbc<V>(E(0.5));
+    const V inv_rho = vrcp(rho_t);
+    // Collision g' = g - omega (g - g^eq) + fcoef F_a, with g^eq of Eq. eqLBEMCb (rho_0 = 0)
+    // and F_a of Eq. eqLBEMCfinal3, evaluated for each pair of opposite directions
+    // (e_abar = -e_a): the parts even in e are shared, the odd parts change sign.
+    //   g^eq_a = w rho [3 eu + 4.5 eu^2 - 1.5 u^2]
+    //   F_a    = w [3 eF - 3 uF + 9 eu eF + (c_a - 1) ug + 3 eu eg],  c_a = (3 e^2 - 2)/2
+    // (eu = e_a.u, eF = e_a.F_i, eg = e_a.grad rho_i, uF = u.F_i, ug = u.grad rho_i).  With
+    // rw = omega rho_i, fc = fcoef, base = 1.5 rw u^2 the post-collision value is
+    //   g'_a = (1 - omega) g_a + even_a + odd_a,   g'_abar = (1 - omega) g_abar + even_a - odd_a
+    //   even_a = w_a [eu (e_a.V) + cb_a],  V = 4.5 rw u + fc (9 F_i + 3 grad rho_i),
+    //            cb_a = fc (c_a - 1) ug - 3 fc uF - base
+    //   odd_a  = 3 w_a (rw eu + fc eF) = e_a.O (axes), e_a.O / 4 (diagonals),
+    //            O = (rw u + fc F_i) / 3
+    //   g'_0   = (1 - omega) g_0 + rw + (4/9) (-base - 3 fc uF - 2 fc ug)
+    // and each e_a.X is written out (components 0, +-1): no multiplication by zero.
+    auto collide = [&](int i, V Fx, V Fy, V grx, V gry) {
+        const E fc = m.fcoef;
+        const V usq15 = vmul(vbc<V>(E(1.5)), vfma(ux, ux, vmul(uy, uy)));
+        V h[9];
+        geth(i, h);
+        const V rw = vmul(vbc<V>(m.omega), rho[i]);
+        const V uF = vfma(ux, Fx, vmul(uy, Fy));
+        const V a0 = vneg(vfma(rw, usq15, vmul(vbc<V>(E(3) * fc), uF)));  // -base - 3 fc uF
+        V cb_ax, cb_dg, Vx, Vy, g0c;
+        if constexpr (STD) {
+            // the forcing term's grad rho_i part belongs to the well-balanced scheme only;
+            // the standard equilibrium adds w_a rho_i (a != 0) and w_0 rho_i (a = 0)
+            cb_ax = vadd(a0, rw);
+            cb_dg = cb_ax;
+            Vx = vfma(vbc<V>(E(4.5)), vmul(rw, ux), vmul(vbc<V>(E(9) * fc), Fx));
+            Vy = vfma(vbc<V>(E(4.5)), vmul(rw, uy), vmul(vbc<V>(E(9) * fc), Fy));
+            g0c = vmul(vbc<V>(E(4.0 / 9.0)), vadd(rw, a0));
+        } else {
+            const V ug = vfma(ux, grx, vmul(uy, gry));
+            cb_ax = vfma(vbc<V>(E(-0.5) * fc), ug, a0);
+            cb_dg = vfma(vbc<V>(fc), ug, a0);
+            Vx = vfma(vbc<V>(E(4.5)), vmul(rw, ux), vfma(vbc<V>(E(9) * fc), Fx, vmul(vbc<V>(E(3) * fc), grx)));
+            Vy = vfma(vbc<V>(E(4.5)), vmul(rw, uy), vfma(vbc<V>(E(9) * fc), Fy, vmul(vbc<V>(E(3) * fc), gry)));
+            g0c = vfma(vbc<V>(E(4.0 / 9.0)), vfma(vbc<V>(E(-2) * fc), ug, a0), rw);
+        }
+        const V rw3 = vmul(rw, vbc<V>(E(1.0 / 3.0)));
+        const V fc_3 = vbc<V>(fc * E(1.0 / 3.0));
+        const V Ox = vfma(rw3, ux, vmul(fc_3, Fx));
+        const V Oy = vfma(rw3, uy, vmul(fc_3, Fy));
+        const V keep = vbc<V>(E(1) - m.omega);
+        const V w1 = vbc<V>(E(1.0 / 9.0)), w5 = vbc<V>(E(1.0 / 36.0)), quarter = vbc<V>(E(0.25));
+        store(i, 0, vfma(keep, h[0], g0c));
+        const V e1 = vmul(w1, vfma(ux, Vx, cb_ax));
+        store(i, 1, vfma(keep, h[1], vadd(e1, Ox)));
+        store(i, 3, vfma(keep, h[3], vsub(e1, Ox)));
+        const V e2 = vmul(w1, vfma(uy, Vy, cb_ax));
+        store(i, 2, vfma(keep, h[2], vadd(e2, Oy)));
+        store(i, 4, vfma(keep, h[4], vsub(e2, Oy)));
+        const V e5 = vmul(w5, vfma(vadd(ux, uy), vadd(Vx, Vy), cb_dg)), o5 = vmul(quarter, vadd(Ox, Oy));
+        store(i, 5, vfma(keep, h[5], vadd(e5, o5)));
+        store(i, 7, vfma(keep, h[7], vsub(e5, o5)));
+        const V e6 = vmul(w5, vfma(vsub(uy, ux), vsub(Vy, Vx), cb_dg)), o6 = vmul(quarter, vsub(Oy, Ox));
+        store(i, 6, vfma(keep, h[6], vadd(e6, o6)));
+        store(i, 8, vfma(keep, h[8], vsub(e6, o6)));
+    };
+    if constexpr (LAG) {
+        ux = vmul(vfma(half, Fpx, jx), inv_rho);
+        uy = vmul(vfma(half, Fpy, jy), inv_rho);
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+            V Fx, Fy, grx, gry;
+            force(i, Fx, Fy, grx, gry);
+            if constexpr (COLLIDE) collide(i, Fx, Fy, grx, gry);
+        }
+    } else {
+        V Fx[NC], Fy[NC], grx[NC], gry[NC];
+#pragma unroll
+        for (int i = 0; i < NC; ++i) force(i, Fx[i], Fy[i], grx[i], gry[i]);
+        ux = vmul(vfma(half, Ftx, jx), inv_rho);
+        uy = vmul(vfma(half, Fty, jy), inv_rho);
+        if constexpr (COLLIDE) {
+#pragma unroll
+            for (int i = 0; i < NC; ++i) collide(i, Fx[i], Fy[i], grx[i], gry[i]);
+        }
+    }
+}
+
+// Phase 3 of the one-node-per-thread kernels at one valid node.
 template <int NC, int ST, int TY, bool MOMENTS, bool STD = false, bool PARK = false, bool PP = false>
 __device__ __forceinline__ void phase3(const StepArgs& A, const MixConstT<typename StoreTraits<ST>::Real>& m,
                                        StepSmem<typename StoreTraits<ST>::Real, NC, TY>& S,
-                                       const typename StoreTraits<ST>::Real (&g)[NC][9], int tx, int ty, int gxn,
-                                       int gyn, const typename StoreTraits<ST>::Real* park = nullptr,
+                                       const typename StoreTraits<ST>::Real (&g)[NC][9],
+                                       const typename StoreTraits<ST>::Real (&rho)[NC],
+                                       typename StoreTraits<ST>::Real jx, typename StoreTraits<ST>::Real jy, int tx,
+                                       int ty, int gxn, int gyn, const typename StoreTraits<ST>::Real* park = nullptr,
                                        const Planes* P = nullptr) {
     using Real = typename StoreTraits<ST>::Real;
     const int nx = A.nx, nxy = A.nx * A.ny;
-    const int cx = tx + 1, cy = ty + 1;  // tile+1 coordinates of this node
-    Real Fx[NC], Fy[NC], grx[NC], gry[NC], rhoi[NC];
-    Real rho = Real(0), jx = Real(0), jy = Real(0), Ftx = Real(0), Fty = Real(0);
-#pragma unroll
-    for (int i = 0; i < NC; ++i) {
-        Real px, py, rx, ry;
-        grad_at<Real>(S.G, i, cx, cy, A.stencil, px, py);
-        grad_at<Real>(S.rt, i, cx + 1, cy + 1, A.stencil, rx, ry);
-        const Real rti = S.rt.v[i][cy + 1][cx + 1];
-        // grad rho_i = M_i grad rho~_i
-        grx[i] = rx * m.M[i];
-        gry[i] = ry * m.M[i];
-        // Eq. eqforcefinal: F_i = -rho~_i RT grad ln f_i + rho~_i grad(sum_j kappa_ij lap rho~_j)
-        //                      = rho~_i grad Phi_i (the stencils are linear)
-        Fx[i] = rti * px;
-        Fy[i] = rti * py;
-        if constexpr (STD) {  // Eq. eqForceGen: + c_s^2 grad rho_i
-            Fx[i] += Real(1.0 / 3.0) * grx[i];
-            Fy[i] += Real(1.0 / 3.0) * gry[i];
-        }
-        Ftx += Fx[i];
-        Fty += Fy[i];
-        // zeroth and first moments with e_a in {0, +-1} written out: IEEE arithmetic keeps
-        // every 0 * g_a the compiler is given
-        Real h[9];
-        pulled_all<NC, TY, PARK, Real>(g, park, i, ty * kTX + tx, h);
-        const Real r = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
-        jx += ((h[1] + h[5]) + h[8]) - ((h[3] + h[6]) + h[7]);
-        jy += ((h[2] + h[5]) + h[6]) - ((h[4] + h[7]) + h[8]);
-        rhoi[i] = r;
-        rho += r;
-    }
     const int node = gyn * nx + gxn;
-    Real Fux = Ftx, Fuy = Fty;
+    const int tid = ty * kTX + tx;
+    auto geth = [&](int i, Real (&h)[9]) { pulled_all<NC, TY, PARK, Real>(g, park, i, tid, h); };
+    auto store = [&](int i, int a, Real v) { store_gsel<ST, PP>(A, P, i, a, node, nxy, v); };
+    Real Ftx, Fty, ux, uy;
     if (A.lagged) {  // F(t - 1), copied by prefetch_force
         asm volatile("cp.async.wait_all;\n" ::: "memory");
-        Fux = S.Fl[0][ty][tx];
-        Fuy = S.Fl[1][ty][tx];
+        const Real Fpx = S.Fl[0][ty][tx], Fpy = S.Fl[1][ty][tx];
+        phase3_core<NC, !MOMENTS, STD, true, Real>(m, A.stencil, S.G, S.rt, tx + 1, ty + 1, 0, rho, jx, jy, geth, Fpx,
+                                                   Fpy, store, Ftx, Fty, ux, uy);
+    } else {
+        phase3_core<NC, !MOMENTS, STD, false, Real>(m, A.stencil, S.G, S.rt, tx + 1, ty + 1, 0, rho, jx, jy, geth,
+                                                    Real(0), Real(0), store, Ftx, Fty, ux, uy);
     }
-    const Real inv_rho = Real(1) / rho;
-    const Real ux = (jx + Real(0.5) * Fux) * inv_rho;
-    const Real uy = (jy + Real(0.5) * Fuy) * inv_rho;
-
     if constexpr (MOMENTS) {
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
-            if (A.rho_out) A.rho_out[(size_t)i * nxy + node] = (double)rhoi[i];
-            if (A.lnf_out) A.lnf_out[(size_t)i * nxy + node] = (double)S.lf.v[i][cy][cx];
+            if (A.rho_out) A.rho_out[(size_t)i * nxy + node] = (double)rho[i];
+            if (A.lnf_out) A.lnf_out[(size_t)i * nxy + node] = (double)S.lf.v[i][ty + 1][tx + 1];
         }
         if (A.u_out) {
             A.u_out[node] = (double)ux;
             A.u_out[(size_t)nxy + node] = (double)uy;
         }
     } else {
-        // Collision g' = g - omega (g - g^eq) + fcoef F_a, with g^eq of Eq. eqLBEMCb (rho_0 = 0)
-        // and F_a of Eq. eqLBEMCfinal3, evaluated for each pair of opposite directions
-        // (e_abar = -e_a): the parts even in e are shared, the odd parts change sign.
-        //   g^eq_a = w rho [3 eu + 4.5 eu^2 - 1.5 u^2]
-        //   F_a    = w [3 eF - 3 uF + 9 eu eF + (c_a - 1) ug + 3 eu eg],  c_a = (3 e^2 - 2)/2
-        // (eu = e_a.u, eF = e_a.F_i, eg = e_a.grad rho_i, uF = u.F_i, ug = u.grad rho_i).  With
-        // rw = omega rho_i, fc = fcoef, base = 1.5 rw u^2 the post-collision value is
-        //   g'_a = (1 - omega) g_a + even_a + odd_a,   g'_abar = (1 - omega) g_abar + even_a - odd_a
-        //   even_a = w_a [eu (e_a.V) + cb_a],  V = 4.5 rw u + fc (9 F_i + 3 grad rho_i),
-        //            cb_a = fc (c_a - 1) ug - 3 fc uF - base
-        //   odd_a  = 3 w_a (rw eu + fc eF) = e_a.O (axes), e_a.O / 4 (diagonals),
-        //            O = (rw u + fc F_i) / 3
-        //   g'_0   = (1 - omega) g_0 + rw + (4/9) (-base - 3 fc uF - 2 fc ug)
-        // and each e_a.X is written out (components 0, +-1): no multiplication by zero.
-        const Real omega = m.omega, fc = m.fcoef, keep = Real(1) - omega;
-        const Real usq15 = Real(1.5) * (ux * ux + uy * uy);
-        const Real fc9 = Real(9) * fc, fc3 = Real(3) * fc, fc_3 = fc * Real(1.0 / 3.0);
-        const Real u5 = ux + uy, u6 = uy - ux;  // e_a.u for a = 5 (1,1) and a = 6 (-1,1)
-        const Real w1 = Real(1.0 / 9.0), w5 = Real(1.0 / 36.0);
-#pragma unroll
-        for (int i = 0; i < NC; ++i) {
-            Real h[9];
-            pulled_all<NC, TY, PARK, Real>(g, park, i, ty * kTX + tx, h);
-            const Real rw = omega * rhoi[i];
-            // the forcing term's grad rho_i part belongs to the well-balanced scheme only
-            const Real gX = STD ? Real(0) : grx[i], gY = STD ? Real(0) : gry[i];
-            // the standard equilibrium adds w_a rho_i (a != 0) and (w_0 - 1) rho_i (a = 0);
-            // -0 in the well-balanced case: x + (-0) is x exactly, so the compiler drops it
-            const Real rwS = STD ? rw : Real(-0.0);
-            const Real uF = ux * Fx[i] + uy * Fy[i];
-            const Real ug = ux * gX + uy * gY;
-            const Real a0 = -(rw * usq15 + fc3 * uF);  // -base - 3 fc uF
-            const Real cb_ax = a0 - Real(0.5) * fc * ug;
-            const Real cb_dg = a0 + fc * ug;
-            const Real rw45 = Real(4.5) * rw, rw3 = rw * Real(1.0 / 3.0);
-            const Real Vx = rw45 * ux + (fc9 * Fx[i] + fc3 * gX);
-            const Real Vy = rw45 * uy + (fc9 * Fy[i] + fc3 * gY);
-            const Real Ox = rw3 * ux + fc_3 * Fx[i];
-            const Real Oy = rw3 * uy + fc_3 * Fy[i];
-            const Real rest0 = STD ? Real(4.0 / 9.0) * rw : rw;
-            store_gsel<ST, PP>(A, P, i, 0, node, nxy,
-                        keep * h[0] + (rest0 + Real(4.0 / 9.0) * (a0 - Real(2) * fc * ug)));
-            const Real e1 = w1 * (ux * Vx + cb_ax + rwS);
-            store_gsel<ST, PP>(A, P, i, 1, node, nxy, keep * h[1] + (e1 + Ox));
-            store_gsel<ST, PP>(A, P, i, 3, node, nxy, keep * h[3] + (e1 - Ox));
-            const Real e2 = w1 * (uy * Vy + cb_ax + rwS);
-            store_gsel<ST, PP>(A, P, i, 2, node, nxy, keep * h[2] + (e2 + Oy));
-            store_gsel<ST, PP>(A, P, i, 4, node, nxy, keep * h[4] + (e2 - Oy));
-            const Real e5 = w5 * (u5 * (Vx + Vy) + cb_dg + rwS), o5 = Real(0.25) * (Ox + Oy);
-            store_gsel<ST, PP>(A, P, i, 5, node, nxy, keep * h[5] + (e5 + o5));
-            store_gsel<ST, PP>(A, P, i, 7, node, nxy, keep * h[7] + (e5 - o5));
-            const Real e6 = w5 * (u6 * (Vy - Vx) + cb_dg + rwS), o6 = Real(0.25) * (Oy - Ox);
-            store_gsel<ST, PP>(A, P, i, 6, node, nxy, keep * h[6] + (e6 + o6));
-            store_gsel<ST, PP>(A, P, i, 8, node, nxy, keep * h[8] + (e6 - o6));
-        }
         Real* Fout = static_cast<Real*>(A.Fout);
         Fout[node] = Ftx;
         Fout[nxy + node] = Fty;
     }
 }
 
-// Phase 1 from global memory for one tile: pull of the owned node (into g) and of the halo
-// ring (rho~ only), with periodic wrap unless the tile is inner.
+// Phase 1 from global memory for one tile: pull of the owned node (into g, its densities
+// into r) and of the halo ring (rho~ only), with periodic wrap unless the tile is inner.
 template <int NC, int ST, int TY, bool PP = false>
 __device__ __forceinline__ void phase1_global(const StepArgs& A, const MixConstT<typename StoreTraits<ST>::Real>& m,
                                               StepSmem<typename StoreTraits<ST>::Real, NC, TY>& S,
-                                              typename StoreTraits<ST>::Real (&g)[NC][9], int x0, int y0,
-                                              bool inner, int tx, int ty, int tid, const Planes* P = nullptr) {
+                                              typename StoreTraits<ST>::Real (&g)[NC][9],
+                                              typename StoreTraits<ST>::Real (&r)[NC],
+                                              typename StoreTraits<ST>::Real& jx, typename StoreTraits<ST>::Real& jy,
+                                              int x0, int y0, bool inner, int tx, int ty, int tid,
+                                              const Planes* P = nullptr) {
     using Real = typename StoreTraits<ST>::Real;
     constexpr int NT = kTX * TY;
     const int nx = A.nx, ny = A.ny, nxy = nx * ny;
@@ -749,9 +850,9 @@ __device__ __forceinline__ void phase1_global(const StepArgs& A, const MixConstT
     }
     if constexpr (RING_FIRST) {
         if (has_ring) phase1_ring<NC, TY, Real>(m, S, rr, bx, by);
-        phase1_node<NC, TY, Real>(A, m, S, g, tx, ty, valid, gxn, gyn);
+        phase1_node<NC, TY, Real>(A, m, S, g, r, jx, jy, tx, ty, valid, gxn, gyn);
     } else {
-        phase1_node<NC, TY, Real>(A, m, S, g, tx, ty, valid, gxn, gyn);
+        phase1_node<NC, TY, Real>(A, m, S, g, r, jx, jy, tx, ty, valid, gxn, gyn);
         if (has_ring) {
             pull_ring();
             phase1_ring<NC, TY, Real>(m, S, rr, bx, by);
@@ -759,53 +860,57 @@ __device__ __forceinline__ void phase1_global(const StepArgs& A, const MixConstT
     }
 }
 
-// Diagnostics sums at one node, shared by reduce_partial and the fused step so that both
-// give the same bits: rho_i, (rho_i - pv_i)^2 (0 without a snapshot) and rho_i^2 into acc,
-// then the snapshot refresh (prev <- rho).  The callers read the snapshot pv whatever
-// have_prev says (its buffer always holds N x nx x ny values) and early: a read guarded by
-// the flag was issued only after the pulled sums had arrived and made the reduction about
-// three times slower.
-template <int NC, typename Real>
-__device__ __forceinline__ void diag_node(const Real (&r)[NC], const Real (&pv)[NC], Real* __restrict__ prev,
-                                          int have_prev, size_t node, size_t nxy, Real (&acc)[NC + 2]) {
+// Diagnostics sums at one node (lane), shared by reduce_partial and the fused steps so that
+// all give the same bits: rho_i, (rho_i - pv_i)^2 (0 without a snapshot) and rho_i^2 into
+// acc.  The callers read the snapshot pv whatever have_prev says (its buffer always holds
+// N x nx x ny values) and early: a read guarded by the flag was issued only after the
+// pulled sums had arrived and made the reduction about three times slower.
+template <int NC, typename V>
+__device__ __forceinline__ void diag_node(const V (&r)[NC], const V (&pv)[NC], int have_prev, V (&acc)[NC + 2]) {
+    using E = LaneE<V>;
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
         acc[i] = r[i];
-        acc[NC + 1] += r[i] * r[i];
-        const Real d = have_prev ? r[i] - pv[i] : Real(0);
-        acc[NC] += d * d;
+        acc[NC + 1] = i == 0 ? vmul(r[0], r[0]) : vfma(r[i], r[i], acc[NC + 1]);
+        const V d = have_prev ? vsub(r[i], pv[i]) : vbc<V>(E(0));
+        acc[NC] = i == 0 ? vmul(d, d) : vfma(d, d, acc[NC]);
     }
-#pragma unroll
-    for (int i = 0; i < NC; ++i) prev[(size_t)i * nxy + node] = r[i];
+}
+
+__device__ __forceinline__ float shfl_down(float v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double shfl_down(double v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ float2 shfl_down(float2 v, int o) {
+    return make_float2(__shfl_down_sync(0xffffffffu, v.x, o), __shfl_down_sync(0xffffffffu, v.y, o));
 }
 
 // Warp sums of acc (a fixed shuffle tree in the arithmetic type) into one row of a
 // per-block table.  No FP64 instruction for float storage: on GB300 a handful of FP64
 // conversions per warp made the fused step three times slower.
-template <int NC, typename Real>
-__device__ __forceinline__ void diag_warp(const Real (&acc)[NC + 2], Real* row) {
+template <int NC, typename V>
+__device__ __forceinline__ void diag_warp(const V (&acc)[NC + 2], V* row) {
 #pragma unroll
     for (int k = 0; k < NC + 2; ++k) {
-        Real v = acc[k];
+        V v = acc[k];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        for (int o = 16; o > 0; o >>= 1) v = vadd(v, shfl_down(v, o));
         if ((threadIdx.x & 31) == 0) row[k] = v;
     }
 }
 
 // Sum of eight consecutive rows of that table, in row order (one 32 x 8 strip).
-template <int NC, typename Real>
-__device__ __forceinline__ Real diag_strip(const Real (*red)[NC + 2], int row0, int k) {
-    Real v = Real(0);
+template <int NC, typename V>
+__device__ __forceinline__ V diag_strip(const V (*red)[NC + 2], int row0, int k) {
+    V v = red[row0][k];
 #pragma unroll
-    for (int w = 0; w < 8; ++w) v += red[row0 + w][k];
+    for (int w = 1; w < 8; ++w) v = vadd(v, red[row0 + w][k]);
     return v;
 }
 
 // Diagnostics of the state a step reads, fused into the step (A.diag_partial set): the
 // snapshot value of each owned node is copied into shared memory before phase 1, and after
 // phase 3 each 32 x 8 strip of the tile writes its N + 2 partial sums at the index
-// reduce_partial would use ((strip row) * tiles_x + tile column).
+// reduce_partial would use ((strip row) * tiles_x + tile column), and the snapshot takes
+// the densities of this state.
 template <int NC, typename Real, int TY>
 __device__ __forceinline__ void diag_prefetch(const StepArgs& A, Real* pv_s, int tx, int ty, int gxn, int gyn) {
     if (A.diag_partial != nullptr && gxn < A.nx && gyn < A.ny) {
@@ -818,7 +923,7 @@ __device__ __forceinline__ void diag_prefetch(const StepArgs& A, Real* pv_s, int
 
 // Called by every thread of the block (it synchronises); uniform in A.diag_partial.
 template <int NC, typename Real, int TY>
-__device__ __forceinline__ void diag_tile(const StepArgs& A, const Real (&g)[NC][9], const Real* pv_s, int tx, int ty,
+__device__ __forceinline__ void diag_tile(const StepArgs& A, const Real (&r)[NC], const Real* pv_s, int tx, int ty,
                                           int gxn, int gyn, int y0, int tile_row, int tile_col, int tiles_x) {
     static_assert(TY % 8 == 0, "diagnostics strips of 8 rows");
     __shared__ Real dred[TY][NC + 2];
@@ -827,19 +932,15 @@ __device__ __forceinline__ void diag_tile(const StepArgs& A, const Real (&g)[NC]
 #pragma unroll
     for (int k = 0; k < NC + 2; ++k) acc[k] = Real(0);
     if (gxn < nx && gyn < ny) {
-        Real r[NC];
-#pragma unroll
-        for (int i = 0; i < NC; ++i) {
-            r[i] = Real(0);
-#pragma unroll
-            for (int a = 0; a < 9; ++a) r[i] += g[i][a];  // the order of pull_rho
-        }
         asm volatile("cp.async.wait_all;\n" ::: "memory");
         Real pv[NC];
 #pragma unroll
         for (int i = 0; i < NC; ++i) pv[i] = pv_s[(i * TY + ty) * kTX + tx];
-        diag_node<NC, Real>(r, pv, static_cast<Real*>(A.rho_prev), A.have_prev, (size_t)gyn * nx + gxn,
-                            (size_t)nx * ny, acc);
+        diag_node<NC, Real>(r, pv, A.have_prev, acc);
+        Real* prev = static_cast<Real*>(A.rho_prev);
+        const size_t nxy = (size_t)nx * ny, node = (size_t)gyn * nx + gxn;
+#pragma unroll
+        for (int i = 0; i < NC; ++i) prev[i * nxy + node] = r[i];
     }
     diag_warp<NC, Real>(acc, dred[ty]);
     __syncthreads();
@@ -880,18 +981,17 @@ __global__ void __launch_bounds__(kTX* TY, ST == ST_F64 ? 1 : (kParkLast<NC, ST,
     Real* pv_s = reinterpret_cast<Real*>(smem_raw + sizeof(StepSmem<Real, NC, TY>) + park_bytes<NC, ST, TY>());
     if constexpr (!MOMENTS) diag_prefetch<NC, Real, TY>(A, pv_s, tx, ty, gxn, gyn);
     prefetch_force<Real, NC, TY>(A, S, tx, ty, gxn, gyn);
-    Real g[NC][9];
-    phase1_global<NC, ST, TY, PARK>(A, m, S, g, x0, y0, inner, tx, ty, tid, &P);
+    Real g[NC][9], r[NC], jx, jy;
+    phase1_global<NC, ST, TY, PARK>(A, m, S, g, r, jx, jy, x0, y0, inner, tx, ty, tid, &P);
     if constexpr (PARK) park_store<TY, Real>(g[NC - 1], park, tid);
     __syncthreads();
     phase2<NC, TY, Real>(m, S, A.stencil, tid);
     __syncthreads();
-    if (gxn < nx && gyn < ny) phase3<NC, ST, TY, MOMENTS, STD, PARK, PARK>(A, m, S, g, tx, ty, gxn, gyn, park, &P);
+    if (gxn < nx && gyn < ny)
+        phase3<NC, ST, TY, MOMENTS, STD, PARK, PARK>(A, m, S, g, r, jx, jy, tx, ty, gxn, gyn, park, &P);
     if constexpr (!MOMENTS) {
-        if (A.diag_partial != nullptr) {  // uniform: diagnostics of the state this step read
-            if constexpr (PARK) pulled_all<NC, TY, PARK, Real>(g, park, NC - 1, tid, g[NC - 1]);
-            diag_tile<NC, Real, TY>(A, g, pv_s, tx, ty, gxn, gyn, y0, blockIdx.y, blockIdx.x, gridDim.x);
-        }
+        if (A.diag_partial != nullptr)  // uniform: diagnostics of the state this step read
+            diag_tile<NC, Real, TY>(A, r, pv_s, tx, ty, gxn, gyn, y0, blockIdx.y, blockIdx.x, gridDim.x);
     }
 }
 
@@ -959,10 +1059,10 @@ __global__ void convert_g(StepArgs A, const double* __restrict__ gin_d, double* 
 
 // Deterministic reductions over a lattice: one thread per node on the same 32 x 8 tiling
 // as the step (so the block count, and with it the summation order, depends only on
-// the lattice shape).  Each block writes NC + 2 doubles: sum rho_i, sum (rho - rho_prev)^2,
+// the lattice shape).  Each block writes NC + 2 sums: sum rho_i, sum (rho - rho_prev)^2,
 // sum rho^2; then rho_prev <- rho.  reduce_final adds the block rows in a fixed order.
-// A plain fused step asked for the diagnostics of the state it reads writes the same
-// partial sums, bit for bit (same node sums, same shuffle tree, same strips).
+// A fused step asked for the diagnostics of the state it reads writes the same partial
+// sums, bit for bit (same node sums, same shuffle tree, same strips).
 // Per node, within a warp (a pairwise shuffle tree) and over the eight warps of a strip the
 // sums run in the storage arithmetic type; reduce_final promotes the strip sums to double,
 // so FP32 lattices pay no FP64 arithmetic in the per-node kernels.  rho_prev and the
@@ -987,7 +1087,9 @@ __global__ void __launch_bounds__(kTX* kRedTY) reduce_partial(StepArgs A,
         for (int i = 0; i < NC; ++i) pv[i] = rho_prev[(size_t)i * nxy + (size_t)y * nx + x];
         Real r[NC];
         pull_rho<NC, ST>(A, x, y, inner, nx, ny, nxy, r);
-        diag_node<NC, Real>(r, pv, rho_prev, have_prev, (size_t)y * nx + x, (size_t)nxy, acc);
+        diag_node<NC, Real>(r, pv, have_prev, acc);
+#pragma unroll
+        for (int i = 0; i < NC; ++i) rho_prev[(size_t)i * nxy + (size_t)y * nx + x] = r[i];
     }
     __shared__ Real red[kRedTY][NC + 2];
     diag_warp<NC, Real>(acc, red[threadIdx.y]);

@@ -2,9 +2,33 @@
 // storage precision (step_f64.cu, step_f32.cu, step_f16.cu, step_bf16.cu).
 #pragma once
 
+#include <atomic>
+
+#include "fmlbm_pair.cuh"
 #include "fmlbm_tma.cuh"
 
 namespace fmlbm {
+
+// The dynamic shared-memory limit of a kernel is a property of each device, and launches
+// come from any thread (a server's worker and its callers).  Each kernel keeps one atomic
+// bit mask of the devices it has been raised on (bit = device ordinal; ordinals from 64 on
+// raise it at every launch).  Two threads racing both set the same value: harmless.
+inline cudaError_t ensure_smem_attr(std::atomic<unsigned long long>& done, const void* func, size_t bytes) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+    return e;
+}
+#define FMLBM_ENSURE_SMEM(kernel, bytes)                                                     \
+    do {                                                                                   \
+        static std::atomic<unsigned long long> done_{0ull};                                \
+        cudaError_t e_ = ensure_smem_attr(done_, reinterpret_cast<const void*>(kernel), (bytes)); \
+        if (e_ != cudaSuccess) return e_;                                                  \
+    } while (0)
 
 // Tile heights of the fused step (tile width is one warp).  The host picks one per
 // lattice (fmlbm_set_tile_height / the batch autotuner).
@@ -24,6 +48,12 @@ cudaError_t launch_step_tma(const StepArgs& A, int nc, const CUtensorMap* maps, 
 // Whether the TMA variant exists for this storage and component count (shared memory).
 template <int ST>
 bool tma_supported(int nc);
+// The paired step (two nodes per thread, packed float arithmetic; float and 16-bit
+// storage, well-balanced formulation).  cudaErrorNotSupported for FP64 storage.
+template <int ST>
+cudaError_t launch_step_pair(const StepArgs& A, int nc, cudaStream_t s);
+template <int ST>
+bool pair_supported(int nc);
 
 template <int ST>
 cudaError_t launch_init(const StepArgs& A, int nc, const double* rho, cudaStream_t s);
@@ -64,12 +94,7 @@ inline cudaError_t launch_reduce_final(int nc, bool fp64, const void* partial, i
         constexpr size_t smem = sizeof(StepSmem<Real, NC, TY>) + park_bytes<NC, ST, TY>() +                \
                                 (MOM ? 0 : (size_t)NC * TY * kTX * sizeof(Real));                         \
         auto k = fused_step<NC, ST, TY, MOM, STD>;                                                        \
-        static bool attr_done = false;                                                                    \
-        if (!attr_done) {                                                                                 \
-            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-            if (e != cudaSuccess) return e;                                                               \
-            attr_done = true;                                                                             \
-        }                                                                                                 \
+        FMLBM_ENSURE_SMEM(k, smem);                                                                       \
         dim3 grid((A.nx + kTX - 1) / kTX, (A.ny + TY - 1) / TY);                                          \
         const Planes P = make_planes(A, NC, ST == ST_F16DEV || ST == ST_BF16DEV,                          \
                                      ST == ST_F64 ? 8 : (ST == ST_F32 ? 4 : 2));                          \
@@ -171,15 +196,16 @@ inline cudaError_t launch_reduce_final(int nc, bool fp64, const void* partial, i
             constexpr int MINB = SINGLE ? (fit1 > 4 ? 4 : (fit1 < 1 ? 1 : fit1)) : 1;                \
             constexpr size_t smem = L::scratch_bytes + NS * L::stage_bytes + 64;                          \
             auto k = fused_step_tma<NC, ST, kTmaTileY, NS, MINB>;                                         \
-            static int per_sm = 0, sms = 0;                                                               \
-            if (per_sm == 0) {                                                                            \
-                cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
-                                                     (int)smem);                                          \
-                if (e != cudaSuccess) return e;                                                           \
+            FMLBM_ENSURE_SMEM(k, smem);                                                                   \
+            /* blocks per SM and SM count of the current device (per device: a process may */          \
+            /* drive several; computed at each launch of the persistent form only)          */          \
+            int per_sm = 1, sms = 1;                                                                      \
+            if (!SINGLE) {                                                                                \
                 int dev = 0;                                                                              \
-                cudaGetDevice(&dev);                                                                      \
-                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);                        \
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTX * kTmaTileY, smem);     \
+                cudaError_t e = cudaGetDevice(&dev);                                                      \
+                if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev); \
+                if (e == cudaSuccess)                                                                     \
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTX * kTmaTileY, smem); \
                 if (e != cudaSuccess) return e;                                                           \
                 if (per_sm < 1) return cudaErrorInvalidConfiguration;                                     \
             }                                                                                             \
@@ -215,6 +241,42 @@ inline cudaError_t launch_reduce_final(int nc, bool fp64, const void* partial, i
             case 4: return TmaLayout<4, ST, kTmaTileY>::fits;                                             \
         }                                                                                                 \
         return false;                                                                                     \
+    }
+
+
+// Components parked in shared memory by the paired step: registers hold the others'
+// pulled values of both nodes between phases 1 and 3.
+template <int NC> constexpr int kPairPark = NC == 1 ? 0 : (NC == 2 ? 1 : 2);
+
+#define FMLBM_DEFINE_PAIR_LAUNCHER(ST)                                                                    \
+    template <int NC, bool LAG>                                                                           \
+    static cudaError_t launch_pair_lag_##ST(const StepArgs& A, cudaStream_t s) {                          \
+        constexpr int NP = kPairPark<NC>;                                                                 \
+        constexpr size_t smem = pair_smem_bytes<NC, kTileYSmall, NP>();                                   \
+        auto k = fused_step_pair<NC, ST, kTileYSmall, NP, LAG>;                                           \
+        FMLBM_ENSURE_SMEM(k, smem);                                                                       \
+        dim3 grid((A.nx + kPW - 1) / kPW, (A.ny + kTileYSmall - 1) / kTileYSmall);                        \
+        const Planes P = make_planes(A, NC, ST == ST_F16DEV || ST == ST_BF16DEV, ST == ST_F32 ? 4 : 2);   \
+        k<<<grid, dim3(kTX, kTileYSmall), smem, s>>>(A, P);                                               \
+        return cudaGetLastError();                                                                        \
+    }                                                                                                     \
+    template <int NC>                                                                                     \
+    static cudaError_t launch_pair_nc_##ST(const StepArgs& A, cudaStream_t s) {                           \
+        return A.lagged ? launch_pair_lag_##ST<NC, true>(A, s) : launch_pair_lag_##ST<NC, false>(A, s);   \
+    }                                                                                                     \
+    template <>                                                                                           \
+    cudaError_t launch_step_pair<ST>(const StepArgs& A, int nc, cudaStream_t s) {                         \
+        switch (nc) {                                                                                     \
+            case 1: return launch_pair_nc_##ST<1>(A, s);                                                  \
+            case 2: return launch_pair_nc_##ST<2>(A, s);                                                  \
+            case 3: return launch_pair_nc_##ST<3>(A, s);                                                  \
+            case 4: return launch_pair_nc_##ST<4>(A, s);                                                  \
+        }                                                                                                 \
+        return cudaErrorInvalidValue;                                                                     \
+    }                                                                                                     \
+    template <>                                                                                           \
+    bool pair_supported<ST>(int nc) {                                                                     \
+        return nc >= 1 && nc <= 4;                                                                        \
     }
 
 }  // namespace fmlbm

@@ -1,0 +1,307 @@
+// The paired step kernel (sm_103a, float and 16-bit storage): one time step of the method
+// (Section III.B, steps 1-9), each thread advancing two nodes of a 64 x TY tile, 32
+// columns apart.
+//
+// The per-node arithmetic is the lane arithmetic of fmlbm_kernels.cuh with two lanes
+// (float2): every float operation of the two nodes issues as one packed f32x2 instruction,
+// and the two nodes share their address arithmetic (the second node's accesses are the
+// first's plus 32 elements), so the step issues far fewer instructions per node than the
+// one-node kernel, which is bound by instruction issue.  The arithmetic per node is the
+// one-node kernel's, operation for operation, so the two give identical bits (as do the
+// bulk-copy and batch kernels, which run the one-node phases).
+//
+// Phases (as in fused_step):
+//   phase 1  pull the 9N values of both owned nodes (plane base addresses from the launch
+//            parameters), sum rho_i, rho~_i, ln f_i; the 2-node halo ring of the 64-wide
+//            tile (304 nodes for 8 rows) is pulled two ring nodes per thread for rho~ only,
+//            with ln f on its inner row;
+//   phase 2  Phi_i = sum_j kappa_ij lap rho~_j - RT ln f_i on the tile + 1 box, whole warps
+//            on whole shared-memory rows, two columns 32 apart per thread;
+//   phase 3  force, velocity, equilibrium, forcing and collision per node pair, coalesced
+//            stores at the nodes (streaming happens on the next step's read side).
+// The last NPARK components' pulled values wait in shared memory between phases 1 and 3.
+// LAG: the lagged reading of the velocity (a launch with A.lagged set).
+// A pending diagnostics request is served as in fused_step: the partial sums of each 32 x 8
+// strip go where reduce_partial would put them, bit for bit.
+#pragma once
+
+#include "fmlbm_kernels.cuh"
+
+namespace fmlbm {
+
+constexpr int kPW = 2 * kTX;  // width of the paired tile
+
+template <typename E, int NC, int TY>
+struct PairSmem {
+    Tile<E, NC, TY, 2, kPW> rt;  // rho~ on tile + 2
+    Tile<E, NC, TY, 1, kPW> lf;  // ln f on tile + 1
+    Tile<E, NC, TY, 1, kPW> G;   // Phi_i on tile + 1
+    E Fl[2][TY][kPW];            // stored total force at the tile's nodes (lagged reading)
+};
+
+// Shared bytes of the paired step: the tiles, the parked values (five 16-byte slots per
+// parked component and thread), the diagnostics snapshot copy of the tile's nodes.
+template <int NC, int TY, int NPARK>
+constexpr size_t pair_smem_bytes() {
+    return sizeof(PairSmem<float, NC, TY>) + (size_t)NPARK * 5 * 16 * kTX * TY + (size_t)NC * TY * kPW * 4;
+}
+
+// Parked values of one component: slots k = 0..3 hold (h[2k], h[2k+1]) of both lanes as
+// float4 (lane 0, lane 0, lane 1, lane 1 order: x, y of h[2k] then of h[2k+1]); slot 4 holds h[8].
+__device__ __forceinline__ void park_pair_store(const float2 (&h)[9], float4* park, int tid, int NT) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) park[k * NT + tid] = make_float4(h[2 * k].x, h[2 * k].y, h[2 * k + 1].x, h[2 * k + 1].y);
+    reinterpret_cast<float2*>(park + 4 * NT)[2 * tid] = h[8];
+}
+__device__ __forceinline__ void park_pair_load(float2 (&h)[9], const float4* park, int tid, int NT) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float4 v = park[k * NT + tid];
+        h[2 * k] = make_float2(v.x, v.y);
+        h[2 * k + 1] = make_float2(v.z, v.w);
+    }
+    h[8] = reinterpret_cast<const float2*>(park + 4 * NT)[2 * tid];
+}
+
+// Pulled sums of two nodes (wx0, wy0), (wx1, wy1) (wrapped coordinates), in direction order.
+template <int NC, int ST>
+__device__ __forceinline__ void pull_rho_pair(const Planes& P, int wx0, int wy0, int wx1, int wy1, bool inner, int nx,
+                                              int ny, float2* rs) {
+    auto src_of = [&](int a, int wx, int wy) {
+        if (inner) return wy * nx + wx - ey(a) * nx - ex(a);
+        const int xm = wx == 0 ? nx - 1 : wx - 1, xp = wx == nx - 1 ? 0 : wx + 1;
+        const int ym = wy == 0 ? ny - 1 : wy - 1, yp = wy == ny - 1 ? 0 : wy + 1;
+        return pull_src(a, wx, wy, xm, xp, ym, yp, nx);
+    };
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const int s0 = src_of(a, wx0, wy0), s1 = src_of(a, wx1, wy1);
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+            const float2 v = make_float2(load_gp<ST>(P, i, a, s0), load_gp<ST>(P, i, a, s1));
+            rs[i] = a == 0 ? v : vadd(rs[i], v);
+        }
+    }
+}
+
+template <int NC, int ST, int TY, int NPARK, bool LAG>
+__global__ void __launch_bounds__(kTX* TY, NPARK > 0 ? 4 : 3) fused_step_pair(StepArgs A, Planes P) {
+    static_assert(ST != ST_F64, "the paired step packs float arithmetic");
+    static_assert(NPARK >= 0 && NPARK <= NC, "parked components");
+    using V = float2;
+    constexpr int NT = kTX * TY;
+    static_assert(sizeof(PairSmem<float, NC, TY>) % 16 == 0, "the parked values are 16-byte slots");
+    constexpr int NREG = NC - NPARK;  // components whose pulled values stay in registers
+    extern __shared__ __align__(16) unsigned char smem_pair[];
+    auto& S = *reinterpret_cast<PairSmem<float, NC, TY>*>(smem_pair);
+    float4* park = reinterpret_cast<float4*>(smem_pair + sizeof(PairSmem<float, NC, TY>));
+    float* pv_s = reinterpret_cast<float*>(smem_pair + sizeof(PairSmem<float, NC, TY>) + (size_t)NPARK * 5 * 16 * NT);
+    const MixConstT<float>& m = A.mixf;
+    const int nx = A.nx, ny = A.ny, nxy = nx * ny;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTX + tx;
+    const int x0 = blockIdx.x * kPW, y0 = blockIdx.y * TY;
+    const bool inner = x0 >= 3 && x0 + kPW + 3 <= nx && y0 >= 3 && y0 + TY + 3 <= ny;
+    const int gx0 = x0 + tx, gx1 = gx0 + kTX, gy = y0 + ty;
+    const bool valid0 = gx0 < nx && gy < ny, valid1 = gx1 < nx && gy < ny;
+    const unsigned vmask = (valid0 ? 1u : 0u) | (valid1 ? 2u : 0u);
+    const bool diag = A.diag_partial != nullptr;
+
+    // the stored force F(t - 1) and the diagnostics snapshot of the owned nodes, copied into
+    // shared memory while phases 1-2 run (cp.async)
+    {
+        const float* Fin = static_cast<const float*>(A.Fin);
+        const float* prev = static_cast<const float*>(A.rho_prev);
+        if (valid0) {
+            const int node = gy * nx + gx0;
+            if (LAG) {
+                cp_async_elem(&S.Fl[0][ty][tx], Fin + node);
+                cp_async_elem(&S.Fl[1][ty][tx], Fin + nxy + node);
+            }
+            if (diag)
+#pragma unroll
+                for (int i = 0; i < NC; ++i) cp_async_elem(&pv_s[(i * TY + ty) * kPW + tx], prev + i * nxy + node);
+        }
+        if (valid1) {
+            const int node = gy * nx + gx1;
+            if (LAG) {
+                cp_async_elem(&S.Fl[0][ty][tx + kTX], Fin + node);
+                cp_async_elem(&S.Fl[1][ty][tx + kTX], Fin + nxy + node);
+            }
+            if (diag)
+#pragma unroll
+                for (int i = 0; i < NC; ++i)
+                    cp_async_elem(&pv_s[(i * TY + ty) * kPW + tx + kTX], prev + i * nxy + node);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+
+    // ---- phase 1: the ring pair (pull, rho~, ln f on the inner ring), then the owned nodes
+    //      (pull, rho_i and the first moment, the parked components to shared memory, then
+    //      rho~ and ln f), so that only one set of pulled values is live at a time ----
+    constexpr int RING = 4 * (kPW + 4) + 4 * TY;
+    static_assert(RING % 2 == 0 && RING / 2 <= NT, "two ring nodes per thread at most");
+    if (tid < RING / 2) {
+        int bx0, by0, bx1, by1;
+        ring_position<TY, kPW>(tid, bx0, by0);
+        ring_position<TY, kPW>(tid + RING / 2, bx1, by1);
+        const int wx0 = inner ? x0 - 2 + bx0 : wrap(x0 - 2 + bx0, nx);
+        const int wy0 = inner ? y0 - 2 + by0 : wrap(y0 - 2 + by0, ny);
+        const int wx1 = inner ? x0 - 2 + bx1 : wrap(x0 - 2 + bx1, nx);
+        const int wy1 = inner ? y0 - 2 + by1 : wrap(y0 - 2 + by1, ny);
+        V rr[NC];
+        pull_rho_pair<NC, ST>(P, wx0, wy0, wx1, wy1, inner, nx, ny, rr);
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+            rr[i] = vmul(rr[i], vbc<V>(m.invM[i]));
+            S.rt.v[i][by0][bx0] = rr[i].x;
+            S.rt.v[i][by1][bx1] = rr[i].y;
+        }
+        const bool in0 = bx0 >= 1 && bx0 <= kPW + 2 && by0 >= 1 && by0 <= TY + 2;
+        const bool in1 = bx1 >= 1 && bx1 <= kPW + 2 && by1 >= 1 && by1 <= TY + 2;
+        if (in0 || in1) {
+            V lnf[NC];
+            node_lnf<NC, V>(m, rr, lnf);
+#pragma unroll
+            for (int i = 0; i < NC; ++i) {
+                if (in0) S.lf.v[i][by0 - 1][bx0 - 1] = lnf[i].x;
+                if (in1) S.lf.v[i][by1 - 1][bx1 - 1] = lnf[i].y;
+            }
+        }
+    }
+    V g[NREG > 0 ? NREG : 1][9];
+    V r[NC], jx, jy;
+    {
+        V gp[NC][9];
+        const int wx0 = inner ? gx0 : wrap(gx0, nx), wx1 = inner ? gx1 : wrap(gx1, nx);
+        const int wy = inner ? gy : wrap(gy, ny);
+        if (inner) {
+            // both nodes inside: the second node's source is the first's plus 32 elements
+            const int node = wy * nx + wx0;
+#pragma unroll
+            for (int a = 0; a < 9; ++a) {
+                const int src = node - ey(a) * nx - ex(a);
+#pragma unroll
+                for (int i = 0; i < NC; ++i)
+                    gp[i][a] = make_float2(load_gp<ST>(P, i, a, src), load_gp<ST>(P, i, a, src + kTX));
+            }
+        } else {
+            const int ym = wy == 0 ? ny - 1 : wy - 1, yp = wy == ny - 1 ? 0 : wy + 1;
+            const int xm0 = wx0 == 0 ? nx - 1 : wx0 - 1, xp0 = wx0 == nx - 1 ? 0 : wx0 + 1;
+            const int xm1 = wx1 == 0 ? nx - 1 : wx1 - 1, xp1 = wx1 == nx - 1 ? 0 : wx1 + 1;
+#pragma unroll
+            for (int a = 0; a < 9; ++a) {
+                const int s0 = pull_src(a, wx0, wy, xm0, xp0, ym, yp, nx);
+                const int s1 = pull_src(a, wx1, wy, xm1, xp1, ym, yp, nx);
+#pragma unroll
+                for (int i = 0; i < NC; ++i)
+                    gp[i][a] = make_float2(load_gp<ST>(P, i, a, s0), load_gp<ST>(P, i, a, s1));
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+            r[i] = sum9(gp[i]);
+            moment_j(gp[i], i == 0, jx, jy);
+        }
+#pragma unroll
+        for (int c = 0; c < NPARK; ++c) park_pair_store(gp[NREG + c], park + c * 5 * NT, tid, NT);
+#pragma unroll
+        for (int i = 0; i < NREG; ++i)
+#pragma unroll
+            for (int a = 0; a < 9; ++a) g[i][a] = gp[i][a];
+    }
+    {
+        V rt[NC], lnf[NC];
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+            rt[i] = vmul(r[i], vbc<V>(m.invM[i]));
+            tst<V>(S.rt, i, ty + 2, tx + 2, kTX, rt[i]);
+        }
+        const V beta = node_lnf<NC, V>(m, rt, lnf);
+#pragma unroll
+        for (int i = 0; i < NC; ++i) tst<V>(S.lf, i, ty + 1, tx + 1, kTX, lnf[i]);
+        domain_check<NC, V>(A, rt, lnf, beta, gx0, kTX, gy, vmask);
+    }
+    __syncthreads();
+
+    // ---- phase 2 on the tile + 1 box: columns (c, c + 32) for c < 32, then the edge pair (64, 65)
+    for (int cy = ty; cy < TY + 2; cy += TY) phase2_core<NC, V>(m, S.rt, S.lf, S.G, A.stencil, tx, cy, kTX);
+    if (ty == TY - 1)
+        for (int e = tx; e < TY + 2; e += kTX) phase2_core<NC, V>(m, S.rt, S.lf, S.G, A.stencil, kPW, e, 1);
+    __syncthreads();
+
+    // ---- phase 3 ----
+    if (valid0) {  // valid1 implies valid0
+        V Fpx = vbc<V>(0.f), Fpy = vbc<V>(0.f);
+        if constexpr (LAG) {
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
+            Fpx = make_float2(S.Fl[0][ty][tx], S.Fl[0][ty][tx + kTX]);
+            Fpy = make_float2(S.Fl[1][ty][tx], S.Fl[1][ty][tx + kTX]);
+        }
+        auto geth = [&](int i, V (&h)[9]) {
+            if (i >= NREG) {
+                park_pair_load(h, park + (i - NREG) * 5 * NT, tid, NT);
+            } else {
+#pragma unroll
+                for (int a = 0; a < 9; ++a) h[a] = g[i][a];
+            }
+        };
+        const int node0 = gy * nx + gx0;
+        auto store = [&](int i, int a, V v) {
+            store_gp<ST>(P, i, a, node0, v.x);
+            if (valid1) store_gp<ST>(P, i, a, node0 + kTX, v.y);
+        };
+        V Ftx, Fty, ux, uy;
+        phase3_core<NC, true, false, LAG, V>(m, A.stencil, S.G, S.rt, tx + 1, ty + 1, kTX, r, jx, jy, geth, Fpx, Fpy,
+                                             store, Ftx, Fty, ux, uy);
+        float* Fout = static_cast<float*>(A.Fout);
+        Fout[node0] = Ftx.x;
+        Fout[nxy + node0] = Fty.x;
+        if (valid1) {
+            Fout[node0 + kTX] = Ftx.y;
+            Fout[nxy + node0 + kTX] = Fty.y;
+        }
+    }
+
+    // ---- diagnostics of the state this step read (uniform in diag) ----
+    if (diag) {
+        static_assert(TY % 8 == 0, "diagnostics strips of 8 rows");
+        __shared__ V dred[TY][NC + 2];
+        V acc[NC + 2];
+#pragma unroll
+        for (int k = 0; k < NC + 2; ++k) acc[k] = vbc<V>(0.f);
+        if (valid0) {
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
+            V pv[NC];
+#pragma unroll
+            for (int i = 0; i < NC; ++i)
+                pv[i] = make_float2(pv_s[(i * TY + ty) * kPW + tx], pv_s[(i * TY + ty) * kPW + tx + kTX]);
+            diag_node<NC, V>(r, pv, A.have_prev, acc);
+            if (!valid1)
+#pragma unroll
+                for (int k = 0; k < NC + 2; ++k) acc[k].y = 0.f;
+            float* prev = static_cast<float*>(A.rho_prev);
+            const int node0 = gy * nx + gx0;
+#pragma unroll
+            for (int i = 0; i < NC; ++i) {
+                prev[i * nxy + node0] = r[i].x;
+                if (valid1) prev[i * nxy + node0 + kTX] = r[i].y;
+            }
+        }
+        diag_warp<NC, V>(acc, dred[ty]);
+        __syncthreads();
+        constexpr int STRIPS = TY / 8;
+        const int tiles_x = (nx + kTX - 1) / kTX;
+        if (tid < 2 * STRIPS * (NC + 2)) {
+            const int half = tid / (STRIPS * (NC + 2)), q = tid % (STRIPS * (NC + 2));
+            const int sub = q / (NC + 2), k = q % (NC + 2);
+            const int col = 2 * blockIdx.x + half;
+            if (col < tiles_x && y0 + 8 * sub < ny) {
+                const V s = diag_strip<NC, V>(dred, 8 * sub, k);
+                static_cast<float*>(A.diag_partial)[((size_t)(blockIdx.y * STRIPS + sub) * tiles_x + col) * (NC + 2) +
+                                                    k] = half == 0 ? s.x : s.y;
+            }
+        }
+    }
+}
+
+}  // namespace fmlbm

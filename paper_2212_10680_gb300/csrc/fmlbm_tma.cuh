@@ -10,9 +10,9 @@
 //
 // Box of one stage: columns x0 - 4 .. x0 + 35 (x0 - 8 .. x0 + 39 for 16-bit planes, so
 // that the innermost coordinate times the element size is a multiple of 16 bytes), rows
-// y0 - 3 .. y0 + TY + 2, all planes.  Every wait on an mbarrier is bounded; a wait that
-// runs out latches error code 2 and the block waits (bounded) for its copies in flight
-// and returns.
+// y0 - 3 .. y0 + TY + 2, all planes.  Every wait on an mbarrier is bounded (A.wait_polls
+// polls for a tile's copy); a wait that runs out latches error code 2 and the block waits
+// (bounded, at the full limit) for its copies in flight and returns.
 #pragma once
 
 #include <cuda.h>
@@ -74,9 +74,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: true once the phase with this parity has completed, false after kMaxPolls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (long long k = 0; k < kMaxPolls; ++k)
+// Bounded wait: true once the phase with this parity has completed, false after `polls`
+// polls (none at all for polls <= 0).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long polls = kMaxPolls) {
+    for (long long k = 0; k < polls; ++k)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -183,12 +184,13 @@ __global__ void __launch_bounds__(kTX* TY, MINB)
         unsigned char* st = stages + s * L::stage_bytes;
         Real* gpark = reinterpret_cast<Real*>(st);  // edge tiles: [9N][TY][32]
         constexpr bool PARK = NSTAGE == 1;
-        Real g[NC][9];
+        Real g[NC][9], r[NC], jx, jy;
         if (tma_here) {
-            const bool ok = mbar_wait_bounded(&bar[s], (parity >> s) & 1u);
+            const bool ok = mbar_wait_bounded(&bar[s], (parity >> s) & 1u, A.wait_polls);
             if (__syncthreads_or(!ok)) {
-                // a copy never completed: report, give the copies in flight a bounded
-                // chance to land, and leave
+                // a wait ran out: report, wait (at the full limit) for every copy still in
+                // flight into this block's shared memory, the one waited for included, so that
+                // none lands after the block has gone, and leave
                 if (tid == 0 && atomicCAS(&A.err->flag, 0, 2) == 0) {
                     A.err->comp = -1;
                     A.err->x = x0;
@@ -196,7 +198,7 @@ __global__ void __launch_bounds__(kTX* TY, MINB)
                 }
 #pragma unroll
                 for (int q = 0; q < NSTAGE; ++q)
-                    if (((pending >> q) & 1u) && q != s) mbar_wait_bounded(&bar[q], (parity >> q) & 1u);
+                    if ((pending >> q) & 1u) mbar_wait_bounded(&bar[q], (parity >> q) & 1u);
                 asm volatile("cp.async.wait_all;\n" ::: "memory");  // the force prefetch
                 return;
             }
@@ -207,22 +209,23 @@ __global__ void __launch_bounds__(kTX* TY, MINB)
 #pragma unroll
                 for (int i = 0; i < NC; ++i)
                     g[i][a] = stage_value<NC, ST, TY>(st, i, a, ty + 3 - ey(a), tx + 4 - ex(a));
-            phase1_node<NC, TY, Real>(A, m, S, g, tx, ty, gxn < nx && gyn < ny, gxn, gyn);
+            phase1_node<NC, TY, Real>(A, m, S, g, r, jx, jy, tx, ty, gxn < nx && gyn < ny, gxn, gyn);
             constexpr int RING = 4 * (kTX + 4) + 4 * TY;
             for (int r = tid; r < RING; r += kTX * TY) {
                 int bx, by;
                 ring_position<TY>(r, bx, by);
                 Real rt[NC];
 #pragma unroll
-                for (int i = 0; i < NC; ++i) rt[i] = Real(0);
-#pragma unroll
                 for (int a = 0; a < 9; ++a)
 #pragma unroll
-                    for (int i = 0; i < NC; ++i) rt[i] += stage_value<NC, ST, TY>(st, i, a, by + 1 - ey(a), bx + 2 - ex(a));
+                    for (int i = 0; i < NC; ++i) {
+                        const Real v = stage_value<NC, ST, TY>(st, i, a, by + 1 - ey(a), bx + 2 - ex(a));
+                        rt[i] = a == 0 ? v : vadd(rt[i], v);  // the order of pull_rho
+                    }
                 phase1_ring<NC, TY, Real>(m, S, rt, bx, by);
             }
         } else {
-            phase1_global<NC, ST, TY>(A, m, S, g, x0, y0, is_inner(x0, y0), tx, ty, tid);
+            phase1_global<NC, ST, TY>(A, m, S, g, r, jx, jy, x0, y0, is_inner(x0, y0), tx, ty, tid);
             if constexpr (PARK) {
 #pragma unroll
                 for (int i = 0; i < NC; ++i)
@@ -242,10 +245,10 @@ __global__ void __launch_bounds__(kTX* TY, MINB)
                         g[i][a] = tma_here ? stage_value<NC, ST, TY>(st, i, a, ty + 3 - ey(a), tx + 4 - ex(a))
                                            : gpark[((i * 9 + a) * TY + ty) * kTX + tx];
             }
-            phase3<NC, ST, TY, false>(A, m, S, g, tx, ty, gxn, gyn);
+            phase3<NC, ST, TY, false>(A, m, S, g, r, jx, jy, tx, ty, gxn, gyn);
         }
         if (A.diag_partial != nullptr)  // uniform: diagnostics of the state this step read
-            diag_tile<NC, Real, TY>(A, g, pv_s, tx, ty, gxn, gyn, y0, t / tiles_x, t % tiles_x, tiles_x);
+            diag_tile<NC, Real, TY>(A, r, pv_s, tx, ty, gxn, gyn, y0, t / tiles_x, t % tiles_x, tiles_x);
         __syncthreads();  // shared tiles and the stage are free again
     }
 }

@@ -10,4 +10,11 @@ cudaError_t launch_step_tma<ST_F64>(const StepArgs&, int, const CUtensorMap*, in
 }
 template <>
 bool tma_supported<ST_F64>(int) { return false; }
+// nor a paired step (it packs float arithmetic)
+template <>
+cudaError_t launch_step_pair<ST_F64>(const StepArgs&, int, cudaStream_t) {
+    return cudaErrorNotSupported;
+}
+template <>
+bool pair_supported<ST_F64>(int) { return false; }
 }  // namespace fmlbm

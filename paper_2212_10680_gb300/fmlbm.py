@@ -103,6 +103,7 @@ def _load() -> ctypes.CDLL:
         "fmlbm_set_tile_height": ([H, ctypes.c_int32], ctypes.c_int),
         "fmlbm_set_step_variant": ([H, ctypes.c_int32], ctypes.c_int),
         "fmlbm_get_step_variant": ([H, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "fmlbm_set_wait_limit": ([H, ctypes.c_int64], ctypes.c_int),
         "fmlbm_autotune": ([H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), dp],
                            ctypes.c_int),
         "fmlbm_lattice_bytes": ([ctypes.c_int32, ctypes.POINTER(fmlbm_lattice), ctypes.POINTER(ctypes.c_size_t)],
@@ -309,7 +310,7 @@ def fmlbm_set_tile_height(h, tile_y: int):
     _check(LIB.fmlbm_set_tile_height(h, tile_y), "fmlbm_set_tile_height", h)
 
 
-VARIANT = {"auto": 0, "plain": 1, "tma": 2, "tma_tile": 3}
+VARIANT = {"auto": 0, "plain": 1, "tma": 2, "tma_tile": 3, "pair": 4}
 
 
 def fmlbm_set_step_variant(h, variant: str):
@@ -319,14 +320,18 @@ def fmlbm_set_step_variant(h, variant: str):
 def fmlbm_get_step_variant(h) -> str:
     v = ctypes.c_int32()
     _check(LIB.fmlbm_get_step_variant(h, ctypes.byref(v)), "fmlbm_get_step_variant", h)
-    return {1: "plain", 2: "tma", 3: "tma_tile"}[v.value]
+    return {1: "plain", 2: "tma", 3: "tma_tile", 4: "pair"}[v.value]
+
+
+def fmlbm_set_wait_limit(h, polls: int):
+    _check(LIB.fmlbm_set_wait_limit(h, polls), "fmlbm_set_wait_limit", h)
 
 
 def fmlbm_autotune(h, steps_per_trial: int = 5):
     v, ty, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
     _check(LIB.fmlbm_autotune(h, steps_per_trial, ctypes.byref(v), ctypes.byref(ty), ctypes.byref(ms)),
            "fmlbm_autotune", h)
-    return {1: "plain", 2: "tma", 3: "tma_tile"}[v.value], ty.value, ms.value
+    return {1: "plain", 2: "tma", 3: "tma_tile", 4: "pair"}[v.value], ty.value, ms.value
 
 
 def fmlbm_synchronize(h):

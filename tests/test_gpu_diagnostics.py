@@ -119,7 +119,7 @@ def test_tma_variants_fuse_requests_with_the_same_bits(fm):
     # 128 x 48 has wrap-free inner tiles for the copies and edge tiles for the pulls
     mixd, rho = slab_state_binary(128, 48, seed=34)
     outs = []
-    for variant in ("plain", "tma_tile", "tma"):
+    for variant in ("plain", "tma_tile", "tma", "pair"):
         lat = fm.Lattice(fm.mixture_from_dict(mixd), 128, 48, 1.0, "isotropic", "fp32", "lagged")
         fm.fmlbm_set_step_variant(lat.h, variant)
         lat.init(rho)

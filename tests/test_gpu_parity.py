@@ -2,7 +2,8 @@
 element on the same seeded inputs.
 
 Tolerances (normwise, max |gpu - oracle| / max |oracle| per field): FP64 storage
-1e-12, FP32 storage 1e-5.  Grid sizes span several 32 x 8 tiles with ragged tails
+1e-12, FP32 storage 1e-5; densities and distributions also element by element,
+|gpu - oracle| <= tol |oracle| + 16 ulp of the field's maximum.  Grid sizes span several 32 x 8 tiles with ragged tails
 in both directions, plus degenerate lattices (one row, one column, a single node).
 """
 import numpy as np
@@ -41,6 +42,20 @@ def _gpu_run(fm, mixd, rho, tau, stencil, precision, velocity_force, steps, reco
 
 
 EPS32 = float(np.finfo(np.float32).eps)
+EPS64 = float(np.finfo(np.float64).eps)
+# absolute floor of the per-element checks, in units of the storage type's eps times the
+# field's largest value: room for the rounding of the terms that cancel in a small value
+# (a vapour density, a near-zero distribution), far below the normwise budget (1e-5 of the
+# maximum is 84 FP32 ulp of it; 1e-12 is 4500 FP64 ulp)
+FLOOR_ULPS = 16
+
+
+def elementwise_ratio(a, b, tol, eps):
+    """max over elements of |a - b| / (tol |b| + FLOOR_ULPS eps max|b|): <= 1 means every
+    element meets the relative tolerance up to a floor of a few ulp of the field's maximum."""
+    b = np.asarray(b, dtype=np.float64)
+    den = tol * np.abs(b) + FLOOR_ULPS * eps * np.max(np.abs(b))
+    return float(np.max(np.abs(np.asarray(a, dtype=np.float64) - b) / np.maximum(den, 1e-300)))
 
 
 def _compare(gpu, ora, tol, mixd=None, fields=("rho", "u", "lnf", "g", "F")):
@@ -72,6 +87,12 @@ def _compare(gpu, ora, tol, mixd=None, fields=("rho", "u", "lnf", "g", "F")):
                 bound += 0.5 * extra_F / np.min(o["rho"].sum(axis=0))
             worst[f] = max(worst.get(f, 0.0), err / max(bound, 1e-300))
             assert err <= bound, f"step {k} field {f}: max error {err:.3e} > bound {bound:.3e}"
+        # densities and distributions element by element (vapour nodes and small g_a included)
+        eps = EPS64 if tol < 1e-9 else EPS32
+        for f in ("rho", "g"):
+            q = elementwise_ratio(gk[f], o[f], tol, eps)
+            worst[f + "_elem"] = max(worst.get(f + "_elem", 0.0), q)
+            assert q <= 1.0, f"step {k} field {f}: an element exceeds tol |oracle| + {FLOOR_ULPS} ulp of max ({q:.3f})"
     return worst
 
 
@@ -104,6 +125,9 @@ def test_small_binary_fp64_two_thousand_steps(fm):
         o, gk = ora[k], gpu[k]
         for f in ("rho", "g", "lnf"):
             assert normwise(gk[f], o[f]) <= 1e-12, (k, f, normwise(gk[f], o[f]))
+        for f in ("rho", "g"):
+            q = elementwise_ratio(gk[f], o[f], 1e-12, EPS64)
+            assert q <= 1.0, (k, f, q)
         f_scale = RT * float(np.max(o["rho"])) * float(np.max(np.abs(o["lnf"])))
         dF = float(np.max(np.abs(gk["F"] - o["F"])))
         du = float(np.max(np.abs(gk["u"] - o["u"])))
@@ -358,16 +382,18 @@ def test_tile_heights_are_bit_identical(fm):
 @pytest.mark.parametrize("precision", ["fp32", "fp16dev", "bf16dev"])
 @pytest.mark.parametrize("n", [2, 3])
 @pytest.mark.parametrize("shape", [(200, 100), (96, 24)])
-def test_tma_step_is_bit_identical_to_plain(fm, precision, n, shape):
+def test_step_variants_are_bit_identical(fm, precision, n, shape):
     # 200 x 100: ragged in both directions, many wrap-free inner tiles for the bulk-copy
-    # path; 96 x 24: the smallest kind of lattice with one row of inner tiles
+    # path, a last paired tile half outside the lattice; 96 x 24: the smallest kind of
+    # lattice with one row of inner tiles.  The paired step packs two nodes per float
+    # operation; the others run one node per thread: the same bits per node.
     from paper_2212_10680_gb300 import inputs
     nx, ny = shape
     wl = workloads()["binary" if n == 2 else "ternary"]
     rho = inputs.with_noise(inputs.slab(wl["slab"]["rt_vapour"], wl["slab"]["rt_liquid"], nx, ny, 0.5, 4.0),
                             0.01, 5)
     out = []
-    for variant in ("plain", "tma", "tma_tile"):
+    for variant in ("plain", "tma", "tma_tile", "pair"):
         lat = fm.Lattice(fm.mixture_from_dict(wl["mixture"]), nx, ny, 1.0, "isotropic", precision, "lagged")
         fm.fmlbm_set_step_variant(lat.h, variant)
         assert fm.fmlbm_get_step_variant(lat.h) == variant
@@ -375,8 +401,30 @@ def test_tma_step_is_bit_identical_to_plain(fm, precision, n, shape):
         lat.step(30)
         out.append(lat.distributions())
         lat.close()
-    for k in (1, 2):
-        assert np.array_equal(out[0][0], out[k][0]) and np.array_equal(out[0][1], out[k][1])
+    for k in (1, 2, 3):
+        assert np.array_equal(out[0][0], out[k][0]) and np.array_equal(out[0][1], out[k][1]), k
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16dev"])
+@pytest.mark.parametrize("velocity_force", ["lagged", "current"])
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+@pytest.mark.parametrize("shape", [(70, 37), (5, 7), (64, 8), (130, 17), (1, 40)])
+def test_paired_step_is_bit_identical_to_plain(fm, precision, velocity_force, n, shape):
+    # every component count and both readings of the velocity, lattices narrower than one
+    # paired tile, exactly one tile, and ragged ones (the second node of a pair outside)
+    nx, ny = shape
+    mixd = mixture_dict(n=n, Tr=1.05, kappa_scale=0.5 if velocity_force == "lagged" else 0.2,
+                        M=[1.0, 1.7, 0.8, 2.2][:n], kij=0.03)
+    rho = smooth_state(n, nx, ny, seed=31 + n + nx)
+    out = []
+    for variant in ("plain", "pair"):
+        lat = fm.Lattice(fm.mixture_from_dict(mixd), nx, ny, 0.9, "isotropic", precision, velocity_force)
+        fm.fmlbm_set_step_variant(lat.h, variant)
+        lat.init(rho)
+        lat.step(12)
+        out.append(lat.distributions())
+        lat.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
 
 
 def test_tma_path_oracle_parity(fm):
@@ -401,13 +449,16 @@ def test_tma_path_oracle_parity(fm):
 def test_tma_unavailable_is_reported(fm):
     mixd, _ = slab_state_binary(70, 37)
     lat = fm.Lattice(fm.mixture_from_dict(mixd), 70, 37, 1.0, "isotropic", "fp32", "lagged")
-    assert fm.fmlbm_get_step_variant(lat.h) == "plain"   # nx not a multiple of 4
+    assert fm.fmlbm_get_step_variant(lat.h) == "pair"    # the default for float storage
     with pytest.raises(fm.FmlbmError) as ei:
         fm.fmlbm_set_step_variant(lat.h, "tma")
     assert ei.value.status == 8
     lat.close()
     lat = fm.Lattice(fm.mixture_from_dict(mixd), 64, 64, 1.0, "isotropic", "fp64", "lagged")
-    assert fm.fmlbm_get_step_variant(lat.h) == "plain"   # the FP64 reference path has no TMA variant
+    assert fm.fmlbm_get_step_variant(lat.h) == "plain"   # the FP64 reference path has no TMA or paired variant
+    with pytest.raises(fm.FmlbmError) as ei:
+        fm.fmlbm_set_step_variant(lat.h, "pair")
+    assert ei.value.status == 8
     lat.close()
 
 
@@ -416,7 +467,7 @@ def test_autotune_keeps_results(fm):
     a = fm.Lattice(fm.mixture_from_dict(mixd), 256, 96, 1.0, "isotropic", "fp32", "lagged")
     a.init(rho)
     variant, ty, ms = fm.fmlbm_autotune(a.h, 2)
-    assert variant in ("plain", "tma", "tma_tile") and ty in (8, 16, 32) and ms > 0
+    assert variant in ("plain", "tma", "tma_tile", "pair") and ty in (8, 16, 32) and ms > 0
     done = fm.fmlbm_diagnostics(a.h, 2)[2]
     a.step(7)
     g1, F1 = a.distributions()
@@ -467,3 +518,35 @@ def test_standard_formulation_limits(fm):
         lat.close()
         g_ref, _ = lbm.init_at_rest(rho, formulation="standard")
         assert np.max(np.abs(g - g_ref)) <= tol * np.max(np.abs(g_ref)) and not F.any()
+
+
+@pytest.mark.parametrize("variant", ["tma_tile", "tma"])
+def test_a_bounded_wait_that_runs_out_is_reported(fm, variant):
+    # The bulk-copy steps wait for each tile's copy with a bounded number of polls.  With a
+    # bound of zero the first wait of every block gives up at once: the block latches the
+    # timeout, waits (at the default bound) for its copies in flight and leaves, and the next
+    # synchronising call reports FMLBM_E_TIMEOUT.  Nothing faults: a new lattice on the same
+    # context then steps as usual.
+    mixd, rho = slab_state_binary(96, 24, seed=21)
+    lat = fm.Lattice(fm.mixture_from_dict(mixd), 96, 24, 1.0, "isotropic", "fp32", "lagged")
+    fm.fmlbm_set_step_variant(lat.h, variant)
+    with pytest.raises(fm.FmlbmError) as ei:
+        fm.fmlbm_set_wait_limit(lat.h, -1)
+    assert ei.value.status == 1
+    fm.fmlbm_set_wait_limit(lat.h, 0)
+    lat.init(rho)
+    lat.step(1)
+    with pytest.raises(fm.FmlbmError) as ei:
+        lat.synchronize()
+    assert ei.value.status == fm.E_TIMEOUT
+    lat.close()
+    out = []
+    for v in (variant, "plain"):
+        lat = fm.Lattice(fm.mixture_from_dict(mixd), 96, 24, 1.0, "isotropic", "fp32", "lagged")
+        fm.fmlbm_set_step_variant(lat.h, v)
+        lat.init(rho)
+        lat.step(5)
+        lat.synchronize()
+        out.append(lat.distributions())
+        lat.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
