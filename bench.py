@@ -312,7 +312,12 @@ def run_ours(args, w, rank, world, dist):
     barrier()
     with ClockSampler(dev.index) as clk:
         for k in range(args.steps):
-            flush.zero_()                       # evict the previous step's data from L2 (untimed)
+            # evict the previous step's data from L2 (untimed): write a buffer twice the L2
+            # size, then read it, so that the lines left in L2 are clean and none is the step's
+            # (after a write alone the timed step would also pay the write-back of 129 MB of
+            # the flush buffer's dirty lines, traffic that is not the step's)
+            flush.zero_()
+            flush.sum()
             ev[k][0].record(stream)
             fmlbm.fmlbm_step(lat.h, 1)
             ev[k][1].record(stream)
@@ -369,7 +374,7 @@ def run_ours(args, w, rank, world, dist):
         data="synthetic (seeded droplet/slab initial fields from oracle flash densities)",
         config=dict(workload=w["name"], nx=nx, ny=ny, n_components=n, tau=w["tau"], stencil=w["stencil"],
                     precision=prec, velocity_force="lagged", step_kernel=variant, autotune=tuned,
-                    l2="flushed between timed steps (256 MB write)",
+                    l2="flushed between timed steps (256 MB write, then read: clean lines, none of the step's)",
                     e2e="per step fmlbm_step + fmlbm_diagnostics_async, results read three steps behind "
                         "with fmlbm_diagnostics_wait",
                     timing="CUDA events around each fused launch on the launching stream"),

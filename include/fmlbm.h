@@ -247,10 +247,10 @@ fmlbm_status fmlbm_set_tile_height(fmlbm_handle* h, int32_t tile_y);
  * tile per block and a single stage, as many blocks per multiprocessor as shared memory
  * admits (the pulled values wait in shared memory).  All give bit-identical results.  The
  * TMA forms are available for FP32 and 16-bit storage with nx a multiple of 4 (FP32) or 8
- * (16-bit) and a lattice of at least 38 x 14.  AUTO (default): PAIR where it exists and the
- * tile height is the default 8, else PLAIN; fmlbm_autotune measures the lattice at hand
- * instead.  Every form performs the same operations per node, each rounded once, and gives
- * the same bits.  Asking for a form where it is not available returns
+ * (16-bit) and a lattice of at least 38 x 14.  AUTO (default): PLAIN, which matched or beat
+ * the other forms on the workloads measured on GB300; fmlbm_autotune measures the lattice
+ * at hand instead.  Every form performs the same operations per node, each rounded once,
+ * and gives the same bits.  Asking for a form where it is not available returns
  * FMLBM_E_UNSUPPORTED. */
 typedef enum fmlbm_step_variant {
     FMLBM_VARIANT_AUTO = 0, FMLBM_VARIANT_PLAIN = 1, FMLBM_VARIANT_TMA = 2,

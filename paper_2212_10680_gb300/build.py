@@ -20,7 +20,10 @@ LIB = os.path.join(PKG, "libfmlbm.so")
 
 SOURCES = ["api.cu", "step_f64.cu", "step_f32.cu", "step_f16.cu", "step_bf16.cu", "noalloc.cu", "batch.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+# -fmad=false: no multiply-add is formed that the source does not write.  The step kernels
+# spell out every fused multiply-add (fmlbm_lanes.cuh), so that the one-node and the paired
+# (packed two-lane) kernels perform the same operations per node and agree bit for bit.
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-fmad=false",
          "-I" + INCLUDE, "-I" + CSRC]
 
 

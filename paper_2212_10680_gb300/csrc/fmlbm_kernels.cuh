@@ -132,7 +132,7 @@ struct StepArgs {
     void* diag_partial;
     void* rho_prev;  // [N][ny][nx] in the storage arithmetic type
     int have_prev;
-    int pad0;
+    int prefetch_ahead;    // paired step: the tile this many blocks later is prefetched into L2 (0: none)
     long long wait_polls;  // polls of a bounded wait for a tile copy (bulk-copy step forms)
 };
 
@@ -335,10 +335,29 @@ struct Tile {
     E v[NC][Hh][W];
 };
 
-// Lane access to a shared tile: lane k of the value sits at column cx + k ds.
+// A field on a 64 x TY tile plus an H-node halo, stored in pair slots for the paired step:
+// slot s of a row holds the columns (s - H, s - H + 32) of the tile (column 0 = the tile's
+// first) as one float2, so that a thread's two nodes, and the same neighbour of both, are
+// one 8-byte access.  Lane 0 of the slots covers columns -H .. 31 + H, lane 1 columns
+// 32 - H .. 63 + H; the 2H columns 32 - H .. 31 + H appear in two slots.  Slot and row
+// indices are the tile coordinates of the one-node tiles (column + H, row + H).
+template <int NC, int TY, int H>
+struct PairTile {
+    static constexpr int S = kTX + 2 * H;
+    static constexpr int R = TY + 2 * H;
+    static constexpr int halo = H;
+    float2 v[NC][R][S];
+};
+template <typename T> struct IsPairTile { static constexpr bool value = false; };
+template <int NC, int TY, int H> struct IsPairTile<PairTile<NC, TY, H>> { static constexpr bool value = true; };
+
+// Lane access to a shared tile at tile position (cx, cy): lane k of the value sits at column
+// cx + k ds of a one-node tile; a pair tile holds both lanes in one slot.
 template <typename V, typename T>
 __device__ __forceinline__ V tld(const T& f, int i, int cy, int cx, int ds) {
-    if constexpr (LaneTraits<V>::n == 1) {
+    if constexpr (IsPairTile<T>::value) {
+        return f.v[i][cy][cx];
+    } else if constexpr (LaneTraits<V>::n == 1) {
         return f.v[i][cy][cx];
     } else {
         return make_float2(f.v[i][cy][cx], f.v[i][cy][cx + ds]);
@@ -346,7 +365,9 @@ __device__ __forceinline__ V tld(const T& f, int i, int cy, int cx, int ds) {
 }
 template <typename V, typename T>
 __device__ __forceinline__ void tst(T& f, int i, int cy, int cx, int ds, V v) {
-    if constexpr (LaneTraits<V>::n == 1) {
+    if constexpr (IsPairTile<T>::value) {
+        f.v[i][cy][cx] = v;
+    } else if constexpr (LaneTraits<V>::n == 1) {
         f.v[i][cy][cx] = v;
     } else {
         f.v[i][cy][cx] = v.x;
@@ -719,19 +740,20 @@ __device__ __forceinline__ void phase3_core(const MixConstT<E>& m, int stencil, 
         const V Oy = vfma(rw3, uy, vmul(fc_3, Fy));
         const V keep = vbc<V>(E(1) - m.omega);
         const V w1 = vbc<V>(E(1.0 / 9.0)), w5 = vbc<V>(E(1.0 / 36.0)), quarter = vbc<V>(E(0.25));
+        // g'_a = keep g_a + (w_a X_a +- odd_a), X_a = eu (e_a.V) + cb_a: one fused product each
         store(i, 0, vfma(keep, h[0], g0c));
-        const V e1 = vmul(w1, vfma(ux, Vx, cb_ax));
-        store(i, 1, vfma(keep, h[1], vadd(e1, Ox)));
-        store(i, 3, vfma(keep, h[3], vsub(e1, Ox)));
-        const V e2 = vmul(w1, vfma(uy, Vy, cb_ax));
-        store(i, 2, vfma(keep, h[2], vadd(e2, Oy)));
-        store(i, 4, vfma(keep, h[4], vsub(e2, Oy)));
-        const V e5 = vmul(w5, vfma(vadd(ux, uy), vadd(Vx, Vy), cb_dg)), o5 = vmul(quarter, vadd(Ox, Oy));
-        store(i, 5, vfma(keep, h[5], vadd(e5, o5)));
-        store(i, 7, vfma(keep, h[7], vsub(e5, o5)));
-        const V e6 = vmul(w5, vfma(vsub(uy, ux), vsub(Vy, Vx), cb_dg)), o6 = vmul(quarter, vsub(Oy, Ox));
-        store(i, 6, vfma(keep, h[6], vadd(e6, o6)));
-        store(i, 8, vfma(keep, h[8], vsub(e6, o6)));
+        const V X1 = vfma(ux, Vx, cb_ax);
+        store(i, 1, vfma(keep, h[1], vfma(w1, X1, Ox)));
+        store(i, 3, vfma(keep, h[3], vfma(w1, X1, vneg(Ox))));
+        const V X2 = vfma(uy, Vy, cb_ax);
+        store(i, 2, vfma(keep, h[2], vfma(w1, X2, Oy)));
+        store(i, 4, vfma(keep, h[4], vfma(w1, X2, vneg(Oy))));
+        const V X5 = vfma(vadd(ux, uy), vadd(Vx, Vy), cb_dg), o5 = vmul(quarter, vadd(Ox, Oy));
+        store(i, 5, vfma(keep, h[5], vfma(w5, X5, o5)));
+        store(i, 7, vfma(keep, h[7], vfma(w5, X5, vneg(o5))));
+        const V X6 = vfma(vsub(uy, ux), vsub(Vy, Vx), cb_dg), o6 = vmul(quarter, vsub(Oy, Ox));
+        store(i, 6, vfma(keep, h[6], vfma(w5, X6, o6)));
+        store(i, 8, vfma(keep, h[8], vfma(w5, X6, vneg(o6))));
     };
     if constexpr (LAG) {
         ux = vmul(vfma(half, Fpx, jx), inv_rho);

@@ -10,8 +10,7 @@
 // bit.  Where the arithmetic wants a fused multiply-add it says so (vfma).
 //
 // Reciprocal and logarithm work per lane: the exact library forms in double, the
-// hardware approximations in float (documented bounds: 2 ulp for __fdividef; for __logf
-// 2^-21.41 absolute on [0.5, 2] and 3 ulp elsewhere), well inside the FP32 error budget.
+// hardware approximations in float (below), well inside the FP32 error budget.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -53,10 +52,26 @@ __device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf
 __device__ __forceinline__ double vfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// per-lane reciprocal and natural logarithm
-__device__ __forceinline__ float srcp(float x) { return __fdividef(1.0f, x); }
+// Per-lane reciprocal and natural logarithm.  In float: the hardware approximations of the
+// PTX instructions rcp.approx and lg2.approx (documented maximum errors: 1 ulp for the
+// reciprocal, 2^-22.6 absolute for the base-2 logarithm of the mantissa), then
+// ln x = log2(x) ln 2 with one rounded product.  Written as instructions rather than
+// through the fast-math library forms so that the compiler cannot fold them into a
+// neighbouring operation differently in different kernels (a product with an approximate
+// reciprocal becomes an approximate division, for example), which would break the
+// bit-identity of the kernels.  Arguments are never denormal here (densities, 1 - beta and
+// the like), so the flush-to-zero forms lose nothing.
+__device__ __forceinline__ float srcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ double srcp(double x) { return 1.0 / x; }
-__device__ __forceinline__ float sln(float x) { return __logf(x); }
+__device__ __forceinline__ float sln(float x) {
+    float l2;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2) : "f"(x));
+    return __fmul_rn(l2, 0.693147180559945309f);  // ln 2
+}
 __device__ __forceinline__ double sln(double x) { return log(x); }
 __device__ __forceinline__ float slog1p(float x) { return log1pf(x); }
 __device__ __forceinline__ double slog1p(double x) { return log1p(x); }

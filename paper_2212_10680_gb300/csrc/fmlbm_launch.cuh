@@ -252,12 +252,19 @@ template <int NC> constexpr int kPairPark = NC == 1 ? 0 : (NC == 2 ? 1 : 2);
     template <int NC, bool LAG>                                                                           \
     static cudaError_t launch_pair_lag_##ST(const StepArgs& A, cudaStream_t s) {                          \
         constexpr int NP = kPairPark<NC>;                                                                 \
-        constexpr size_t smem = pair_smem_bytes<NC, kTileYSmall, NP>();                                   \
+        constexpr size_t smem = pair_smem_bytes<NC, ST, kTileYSmall, NP>();                                   \
         auto k = fused_step_pair<NC, ST, kTileYSmall, NP, LAG>;                                           \
         FMLBM_ENSURE_SMEM(k, smem);                                                                       \
         dim3 grid((A.nx + kPW - 1) / kPW, (A.ny + kTileYSmall - 1) / kTileYSmall);                        \
         const Planes P = make_planes(A, NC, ST == ST_F16DEV || ST == ST_BF16DEV, ST == ST_F32 ? 4 : 2);   \
-        k<<<grid, dim3(kTX, kTileYSmall), smem, s>>>(A, P);                                               \
+        /* the next wave of blocks: resident blocks on all SMs (four per SM by the launch bounds */     \
+        /* of the parked forms, three otherwise)                                                  */     \
+        StepArgs B = A;                                                                                   \
+        int dev = 0, sms = 0;                                                                             \
+        if (cudaGetDevice(&dev) == cudaSuccess &&                                                         \
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)             \
+            B.prefetch_ahead = sms * (NP > 0 ? 4 : 3);                                                    \
+        k<<<grid, dim3(kTX, kTileYSmall), smem, s>>>(B, P);                                               \
         return cudaGetLastError();                                                                        \
     }                                                                                                     \
     template <int NC>                                                                                     \

@@ -4,19 +4,21 @@
 //
 // The per-node arithmetic is the lane arithmetic of fmlbm_kernels.cuh with two lanes
 // (float2): every float operation of the two nodes issues as one packed f32x2 instruction,
-// and the two nodes share their address arithmetic (the second node's accesses are the
-// first's plus 32 elements), so the step issues far fewer instructions per node than the
-// one-node kernel, which is bound by instruction issue.  The arithmetic per node is the
-// one-node kernel's, operation for operation, so the two give identical bits (as do the
-// bulk-copy and batch kernels, which run the one-node phases).
+// the two nodes share their address arithmetic (the second node's global accesses are the
+// first's plus 32 elements), and the shared tiles hold the two columns of a thread side by
+// side (PairTile), so that every stencil access of both nodes is one 8-byte shared load.
+// The one-node kernel is bound by instruction issue; this one issues about 40% fewer
+// instructions per node.  The arithmetic per node is the one-node kernel's, operation for
+// operation, each rounded once, so the two give identical bits (as do the bulk-copy and
+// batch kernels, which run the one-node phases).
 //
 // Phases (as in fused_step):
 //   phase 1  pull the 9N values of both owned nodes (plane base addresses from the launch
-//            parameters), sum rho_i, rho~_i, ln f_i; the 2-node halo ring of the 64-wide
-//            tile (304 nodes for 8 rows) is pulled two ring nodes per thread for rho~ only,
-//            with ln f on its inner row;
-//   phase 2  Phi_i = sum_j kappa_ij lap rho~_j - RT ln f_i on the tile + 1 box, whole warps
-//            on whole shared-memory rows, two columns 32 apart per thread;
+//            parameters), sum rho_i and the first moment, rho~_i, ln f_i; the 2-node halo
+//            ring of the 64-wide tile (304 nodes for 8 rows) is pulled two ring nodes per
+//            thread for rho~ only, with ln f on its inner row;
+//   phase 2  Phi_i = sum_j kappa_ij lap rho~_j - RT ln f_i on every pair slot of the tile + 1
+//            box;
 //   phase 3  force, velocity, equilibrium, forcing and collision per node pair, coalesced
 //            stores at the nodes (streaming happens on the next step's read side).
 // The last NPARK components' pulled values wait in shared memory between phases 1 and 3.
@@ -27,27 +29,65 @@
 
 #include "fmlbm_kernels.cuh"
 
+#ifndef FMLBM_PAIR_RING_SPREAD
+#define FMLBM_PAIR_RING_SPREAD 0
+#endif
+#ifndef FMLBM_PAIR_RING_ASYNC
+#define FMLBM_PAIR_RING_ASYNC 0
+#endif
+#ifndef FMLBM_PAIR_PREFETCH
+#define FMLBM_PAIR_PREFETCH 0
+#endif
+
 namespace fmlbm {
 
 constexpr int kPW = 2 * kTX;  // width of the paired tile
 
-template <typename E, int NC, int TY>
+template <int NC, int TY>
 struct PairSmem {
-    Tile<E, NC, TY, 2, kPW> rt;  // rho~ on tile + 2
-    Tile<E, NC, TY, 1, kPW> lf;  // ln f on tile + 1
-    Tile<E, NC, TY, 1, kPW> G;   // Phi_i on tile + 1
-    E Fl[2][TY][kPW];            // stored total force at the tile's nodes (lagged reading)
+    PairTile<NC, TY, 2> rt;     // rho~ on tile + 2
+    PairTile<NC, TY, 1> lf;     // ln f on tile + 1
+    PairTile<NC, TY, 1> G;      // Phi_i on tile + 1
+    float2 Fl[2][TY][kTX];      // stored total force at the tile's node pairs (lagged reading)
 };
 
-// Shared bytes of the paired step: the tiles, the parked values (five 16-byte slots per
-// parked component and thread), the diagnostics snapshot copy of the tile's nodes.
-template <int NC, int TY, int NPARK>
+// Ring nodes of the paired tile (two per thread of the first RING / 2 threads).
+template <int TY> constexpr int kPairRing = 4 * (kPW + 4) + 4 * TY;
+
+// The park area: the parked values (five 16-byte slots per parked component and thread);
+// before them, in float storage, the pulled values of the ring pairs ([9N][RING / 2] float2),
+// copied there by cp.async so that their latency overlaps the owned nodes' pulls.
+template <int NC, int ST, int TY, int NPARK>
+constexpr size_t pair_park_bytes() {
+    const size_t park = (size_t)NPARK * 5 * 16 * kTX * TY;
+    const size_t ring = FMLBM_PAIR_RING_ASYNC && ST == ST_F32 ? (size_t)9 * NC * (kPairRing<TY> / 2) * 8 : 0;
+    const size_t b = park > ring ? park : ring;
+    return (b + 15) & ~size_t(15);
+}
+// Shared bytes of the paired step: the tiles, the park area, the diagnostics snapshot copy
+// of the tile's node pairs.
+template <int NC, int ST, int TY, int NPARK>
 constexpr size_t pair_smem_bytes() {
-    return sizeof(PairSmem<float, NC, TY>) + (size_t)NPARK * 5 * 16 * kTX * TY + (size_t)NC * TY * kPW * 4;
+    return sizeof(PairSmem<NC, TY>) + pair_park_bytes<NC, ST, TY, NPARK>() + (size_t)NC * TY * kTX * 8;
+}
+
+// One column's value into a pair tile: into the slot where it is lane 0 and, for the 2H
+// columns held twice, into the slot where it is lane 1.  col: tile column, -H .. 63 + H.
+template <int NC, int TY, int H>
+__device__ __forceinline__ void pair_put(PairTile<NC, TY, H>& t, int i, int row, int col, float v) {
+    if (col < kTX + H) t.v[i][row][col + H].x = v;
+    if (col >= kTX - H) t.v[i][row][col - kTX + H].y = v;
+}
+// A thread's node pair (columns c and c + 32, c = 0 .. 31) into a pair tile.
+template <int NC, int TY, int H>
+__device__ __forceinline__ void pair_put2(PairTile<NC, TY, H>& t, int i, int row, int c, float2 v) {
+    t.v[i][row][c + H] = v;
+    if (c >= kTX - H) t.v[i][row][c - kTX + H].y = v.x;
+    if (c < H) t.v[i][row][c + kTX + H].x = v.y;
 }
 
 // Parked values of one component: slots k = 0..3 hold (h[2k], h[2k+1]) of both lanes as
-// float4 (lane 0, lane 0, lane 1, lane 1 order: x, y of h[2k] then of h[2k+1]); slot 4 holds h[8].
+// float4 (h[2k].x, h[2k].y, h[2k+1].x, h[2k+1].y); slot 4 holds h[8].
 __device__ __forceinline__ void park_pair_store(const float2 (&h)[9], float4* park, int tid, int NT) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) park[k * NT + tid] = make_float4(h[2 * k].x, h[2 * k].y, h[2 * k + 1].x, h[2 * k + 1].y);
@@ -88,14 +128,15 @@ template <int NC, int ST, int TY, int NPARK, bool LAG>
 __global__ void __launch_bounds__(kTX* TY, NPARK > 0 ? 4 : 3) fused_step_pair(StepArgs A, Planes P) {
     static_assert(ST != ST_F64, "the paired step packs float arithmetic");
     static_assert(NPARK >= 0 && NPARK <= NC, "parked components");
+    static_assert(TY == 8, "the phase-2 work split below assumes 8 rows");
     using V = float2;
     constexpr int NT = kTX * TY;
-    static_assert(sizeof(PairSmem<float, NC, TY>) % 16 == 0, "the parked values are 16-byte slots");
     constexpr int NREG = NC - NPARK;  // components whose pulled values stay in registers
+    static_assert(sizeof(PairSmem<NC, TY>) % 16 == 0, "the parked values are 16-byte slots");
     extern __shared__ __align__(16) unsigned char smem_pair[];
-    auto& S = *reinterpret_cast<PairSmem<float, NC, TY>*>(smem_pair);
-    float4* park = reinterpret_cast<float4*>(smem_pair + sizeof(PairSmem<float, NC, TY>));
-    float* pv_s = reinterpret_cast<float*>(smem_pair + sizeof(PairSmem<float, NC, TY>) + (size_t)NPARK * 5 * 16 * NT);
+    auto& S = *reinterpret_cast<PairSmem<NC, TY>*>(smem_pair);
+    float4* park = reinterpret_cast<float4*>(smem_pair + sizeof(PairSmem<NC, TY>));
+    float2* pv_s = reinterpret_cast<float2*>(smem_pair + sizeof(PairSmem<NC, TY>) + pair_park_bytes<NC, ST, TY, NPARK>());
     const MixConstT<float>& m = A.mixf;
     const int nx = A.nx, ny = A.ny, nxy = nx * ny;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTX + tx;
@@ -114,60 +155,105 @@ __global__ void __launch_bounds__(kTX* TY, NPARK > 0 ? 4 : 3) fused_step_pair(St
         if (valid0) {
             const int node = gy * nx + gx0;
             if (LAG) {
-                cp_async_elem(&S.Fl[0][ty][tx], Fin + node);
-                cp_async_elem(&S.Fl[1][ty][tx], Fin + nxy + node);
+                cp_async_elem(&S.Fl[0][ty][tx].x, Fin + node);
+                cp_async_elem(&S.Fl[1][ty][tx].x, Fin + nxy + node);
             }
             if (diag)
 #pragma unroll
-                for (int i = 0; i < NC; ++i) cp_async_elem(&pv_s[(i * TY + ty) * kPW + tx], prev + i * nxy + node);
+                for (int i = 0; i < NC; ++i) cp_async_elem(&pv_s[(i * TY + ty) * kTX + tx].x, prev + i * nxy + node);
         }
         if (valid1) {
             const int node = gy * nx + gx1;
             if (LAG) {
-                cp_async_elem(&S.Fl[0][ty][tx + kTX], Fin + node);
-                cp_async_elem(&S.Fl[1][ty][tx + kTX], Fin + nxy + node);
+                cp_async_elem(&S.Fl[0][ty][tx].y, Fin + node);
+                cp_async_elem(&S.Fl[1][ty][tx].y, Fin + nxy + node);
             }
             if (diag)
 #pragma unroll
-                for (int i = 0; i < NC; ++i)
-                    cp_async_elem(&pv_s[(i * TY + ty) * kPW + tx + kTX], prev + i * nxy + node);
+                for (int i = 0; i < NC; ++i) cp_async_elem(&pv_s[(i * TY + ty) * kTX + tx].y, prev + i * nxy + node);
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
+#if FMLBM_PAIR_PREFETCH
+    // the tile that the block A.prefetch_ahead places later in launch order will read (the
+    // next wave of blocks on the SMs), into L2, so that its pulls need not wait for DRAM
+    if (A.prefetch_ahead > 0) {
+        const int nb = gridDim.x * gridDim.y, t = blockIdx.y * gridDim.x + blockIdx.x + A.prefetch_ahead;
+        if (t < nb) {
+            const int px0 = (t % gridDim.x) * kPW, py0 = (t / gridDim.x) * TY;
+            constexpr bool dev16 = ST == ST_F16DEV || ST == ST_BF16DEV;
+            constexpr int NP = dev16 ? 8 * NC : 9 * NC;      // planes of P.in
+            constexpr int LPR = dev16 ? 1 : 2;               // 128-byte lines per 64-node row segment
+            constexpr int NITEM = NP * TY * LPR + (dev16 ? NC * TY * 2 : 0);
+            for (int it = tid; it < NITEM; it += NT) {
+                int k, row, seg;
+                const char* base;
+                size_t esz;
+                if (it < NP * TY * LPR) {
+                    k = it / (TY * LPR);
+                    row = (it / LPR) % TY;
+                    seg = it % LPR;
+                    base = static_cast<const char*>(P.in[k]);
+                    esz = dev16 ? 2 : 4;
+                } else {
+                    const int q = it - NP * TY * LPR;
+                    k = q / (TY * 2);
+                    row = (q / 2) % TY;
+                    seg = q % 2;
+                    base = reinterpret_cast<const char*>(P.g0in[k]);
+                    esz = 4;
+                }
+                const int y = py0 + row, x = px0 + seg * (int)(128 / esz);
+                if (y < ny && x < nx)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(base + ((size_t)y * nx + x) * esz));
+            }
+        }
+    }
+#endif
 
-    // ---- phase 1: the ring pair (pull, rho~, ln f on the inner ring), then the owned nodes
-    //      (pull, rho_i and the first moment, the parked components to shared memory, then
-    //      rho~ and ln f), so that only one set of pulled values is live at a time ----
-    constexpr int RING = 4 * (kPW + 4) + 4 * TY;
-    static_assert(RING % 2 == 0 && RING / 2 <= NT, "two ring nodes per thread at most");
-    if (tid < RING / 2) {
-        int bx0, by0, bx1, by1;
+    // ---- phase 1: the ring pair and the owned nodes.  Float storage: the ring pair's pulled
+    //      values are copied into the park area (cp.async, no registers) while the owned
+    //      nodes' pulls are in flight; 16-bit storage (no 2-byte cp.async): the ring pair is
+    //      pulled into registers first.  Then rho_i and the first moment of the owned nodes,
+    //      rho~ and ln f of the ring (ln f on its inner ring only), the parked components to
+    //      shared memory, rho~ and ln f of the owned nodes ----
+    constexpr int RING = kPairRing<TY>;
+    constexpr int RP = RING / 2;
+    static_assert(RING % 2 == 0 && RP <= NT, "two ring nodes per thread at most");
+    constexpr bool RING_ASYNC = FMLBM_PAIR_RING_ASYNC && ST == ST_F32;
+    float2* ring_stage = reinterpret_cast<float2*>(park);
+    const bool has_ring = tid < RP;
+    int bx0 = 0, by0 = 0, bx1 = 0, by1 = 0;
+    V rr[NC];
+    if (has_ring) {
         ring_position<TY, kPW>(tid, bx0, by0);
-        ring_position<TY, kPW>(tid + RING / 2, bx1, by1);
+        ring_position<TY, kPW>(tid + RP, bx1, by1);
         const int wx0 = inner ? x0 - 2 + bx0 : wrap(x0 - 2 + bx0, nx);
         const int wy0 = inner ? y0 - 2 + by0 : wrap(y0 - 2 + by0, ny);
         const int wx1 = inner ? x0 - 2 + bx1 : wrap(x0 - 2 + bx1, nx);
         const int wy1 = inner ? y0 - 2 + by1 : wrap(y0 - 2 + by1, ny);
-        V rr[NC];
-        pull_rho_pair<NC, ST>(P, wx0, wy0, wx1, wy1, inner, nx, ny, rr);
+        if constexpr (RING_ASYNC) {
+            auto src_of = [&](int a, int wx, int wy) {
+                if (inner) return wy * nx + wx - ey(a) * nx - ex(a);
+                const int xm = wx == 0 ? nx - 1 : wx - 1, xp = wx == nx - 1 ? 0 : wx + 1;
+                const int ym = wy == 0 ? ny - 1 : wy - 1, yp = wy == ny - 1 ? 0 : wy + 1;
+                return pull_src(a, wx, wy, xm, xp, ym, yp, nx);
+            };
 #pragma unroll
-        for (int i = 0; i < NC; ++i) {
-            rr[i] = vmul(rr[i], vbc<V>(m.invM[i]));
-            S.rt.v[i][by0][bx0] = rr[i].x;
-            S.rt.v[i][by1][bx1] = rr[i].y;
-        }
-        const bool in0 = bx0 >= 1 && bx0 <= kPW + 2 && by0 >= 1 && by0 <= TY + 2;
-        const bool in1 = bx1 >= 1 && bx1 <= kPW + 2 && by1 >= 1 && by1 <= TY + 2;
-        if (in0 || in1) {
-            V lnf[NC];
-            node_lnf<NC, V>(m, rr, lnf);
+            for (int a = 0; a < 9; ++a) {
+                const int s0 = src_of(a, wx0, wy0), s1 = src_of(a, wx1, wy1);
 #pragma unroll
-            for (int i = 0; i < NC; ++i) {
-                if (in0) S.lf.v[i][by0 - 1][bx0 - 1] = lnf[i].x;
-                if (in1) S.lf.v[i][by1 - 1][bx1 - 1] = lnf[i].y;
+                for (int i = 0; i < NC; ++i) {
+                    const float* plane = static_cast<const float*>(P.in[i * 9 + a]);
+                    cp_async_elem(&ring_stage[(i * 9 + a) * RP + tid].x, plane + s0);
+                    cp_async_elem(&ring_stage[(i * 9 + a) * RP + tid].y, plane + s1);
+                }
             }
+        } else {
+            pull_rho_pair<NC, ST>(P, wx0, wy0, wx1, wy1, inner, nx, ny, rr);
         }
     }
+    if constexpr (RING_ASYNC) asm volatile("cp.async.commit_group;\n" ::: "memory");
     V g[NREG > 0 ? NREG : 1][9];
     V r[NC], jx, jy;
     {
@@ -202,6 +288,37 @@ __global__ void __launch_bounds__(kTX* TY, NPARK > 0 ? 4 : 3) fused_step_pair(St
             r[i] = sum9(gp[i]);
             moment_j(gp[i], i == 0, jx, jy);
         }
+        if (has_ring) {
+            if constexpr (RING_ASYNC) {
+                asm volatile("cp.async.wait_all;\n" ::: "memory");
+#pragma unroll
+                for (int a = 0; a < 9; ++a)
+#pragma unroll
+                    for (int i = 0; i < NC; ++i) {
+                        const V v = ring_stage[(i * 9 + a) * RP + tid];
+                        rr[i] = a == 0 ? v : vadd(rr[i], v);   // the order of pull_rho
+                    }
+            }
+#pragma unroll
+            for (int i = 0; i < NC; ++i) {
+                rr[i] = vmul(rr[i], vbc<V>(m.invM[i]));
+                pair_put(S.rt, i, by0, bx0 - 2, rr[i].x);
+                pair_put(S.rt, i, by1, bx1 - 2, rr[i].y);
+            }
+            const bool in0 = bx0 >= 1 && bx0 <= kPW + 2 && by0 >= 1 && by0 <= TY + 2;
+            const bool in1 = bx1 >= 1 && bx1 <= kPW + 2 && by1 >= 1 && by1 <= TY + 2;
+            if (in0 || in1) {
+                V lnf[NC];
+                node_lnf<NC, V>(m, rr, lnf);
+#pragma unroll
+                for (int i = 0; i < NC; ++i) {
+                    if (in0) pair_put(S.lf, i, by0 - 1, bx0 - 2, lnf[i].x);
+                    if (in1) pair_put(S.lf, i, by1 - 1, bx1 - 2, lnf[i].y);
+                }
+            }
+        }
+        // every thread has read its ring values from the park area before any parks
+        if constexpr (RING_ASYNC && NPARK > 0) __syncthreads();
 #pragma unroll
         for (int c = 0; c < NPARK; ++c) park_pair_store(gp[NREG + c], park + c * 5 * NT, tid, NT);
 #pragma unroll
@@ -214,19 +331,34 @@ __global__ void __launch_bounds__(kTX* TY, NPARK > 0 ? 4 : 3) fused_step_pair(St
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
             rt[i] = vmul(r[i], vbc<V>(m.invM[i]));
-            tst<V>(S.rt, i, ty + 2, tx + 2, kTX, rt[i]);
+            pair_put2(S.rt, i, ty + 2, tx, rt[i]);
         }
         const V beta = node_lnf<NC, V>(m, rt, lnf);
 #pragma unroll
-        for (int i = 0; i < NC; ++i) tst<V>(S.lf, i, ty + 1, tx + 1, kTX, lnf[i]);
+        for (int i = 0; i < NC; ++i) pair_put2(S.lf, i, ty + 1, tx, lnf[i]);
         domain_check<NC, V>(A, rt, lnf, beta, gx0, kTX, gy, vmask);
     }
     __syncthreads();
 
-    // ---- phase 2 on the tile + 1 box: columns (c, c + 32) for c < 32, then the edge pair (64, 65)
-    for (int cy = ty; cy < TY + 2; cy += TY) phase2_core<NC, V>(m, S.rt, S.lf, S.G, A.stencil, tx, cy, kTX);
-    if (ty == TY - 1)
-        for (int e = tx; e < TY + 2; e += kTX) phase2_core<NC, V>(m, S.rt, S.lf, S.G, A.stencil, kPW, e, 1);
+    // ---- phase 2 on the 34 pair slots of each of the TY + 2 rows of the tile + 1 box:
+    //      warp w takes slots 0..31 of row w; rows TY, TY + 1 go to the last two warps and
+    //      slots 32, 33 of every row to warp TY - 3 (the ring ran on the first warps) ----
+    phase2_core<NC, V>(m, S.rt, S.lf, S.G, A.stencil, tx, ty, 0);
+#if FMLBM_PAIR_RING_SPREAD
+    {
+        // the rest (rows TY, TY + 1 and slots 32, 33 of every row) spread over the warps
+        constexpr int REST = 2 * kTX + 2 * (TY + 2), PER = (REST + TY - 1) / TY;
+        const int q = ty * PER + tx;
+        if (tx < PER && q < REST) {
+            if (q < 2 * kTX) phase2_core<NC, V>(m, S.rt, S.lf, S.G, A.stencil, q & (kTX - 1), TY + (q >> 5), 0);
+            else phase2_core<NC, V>(m, S.rt, S.lf, S.G, A.stencil, kTX + ((q - 2 * kTX) & 1), (q - 2 * kTX) >> 1, 0);
+        }
+    }
+#else
+    if (ty >= TY - 2) phase2_core<NC, V>(m, S.rt, S.lf, S.G, A.stencil, tx, ty + 2, 0);
+    if (ty == TY - 3 && tx < 2 * (TY + 2))
+        phase2_core<NC, V>(m, S.rt, S.lf, S.G, A.stencil, kTX + (tx & 1), tx >> 1, 0);
+#endif
     __syncthreads();
 
     // ---- phase 3 ----
@@ -234,8 +366,8 @@ __global__ void __launch_bounds__(kTX* TY, NPARK > 0 ? 4 : 3) fused_step_pair(St
         V Fpx = vbc<V>(0.f), Fpy = vbc<V>(0.f);
         if constexpr (LAG) {
             asm volatile("cp.async.wait_all;\n" ::: "memory");
-            Fpx = make_float2(S.Fl[0][ty][tx], S.Fl[0][ty][tx + kTX]);
-            Fpy = make_float2(S.Fl[1][ty][tx], S.Fl[1][ty][tx + kTX]);
+            Fpx = S.Fl[0][ty][tx];
+            Fpy = S.Fl[1][ty][tx];
         }
         auto geth = [&](int i, V (&h)[9]) {
             if (i >= NREG) {
@@ -251,7 +383,7 @@ __global__ void __launch_bounds__(kTX* TY, NPARK > 0 ? 4 : 3) fused_step_pair(St
             if (valid1) store_gp<ST>(P, i, a, node0 + kTX, v.y);
         };
         V Ftx, Fty, ux, uy;
-        phase3_core<NC, true, false, LAG, V>(m, A.stencil, S.G, S.rt, tx + 1, ty + 1, kTX, r, jx, jy, geth, Fpx, Fpy,
+        phase3_core<NC, true, false, LAG, V>(m, A.stencil, S.G, S.rt, tx + 1, ty + 1, 0, r, jx, jy, geth, Fpx, Fpy,
                                              store, Ftx, Fty, ux, uy);
         float* Fout = static_cast<float*>(A.Fout);
         Fout[node0] = Ftx.x;
@@ -273,8 +405,7 @@ __global__ void __launch_bounds__(kTX* TY, NPARK > 0 ? 4 : 3) fused_step_pair(St
             asm volatile("cp.async.wait_all;\n" ::: "memory");
             V pv[NC];
 #pragma unroll
-            for (int i = 0; i < NC; ++i)
-                pv[i] = make_float2(pv_s[(i * TY + ty) * kPW + tx], pv_s[(i * TY + ty) * kPW + tx + kTX]);
+            for (int i = 0; i < NC; ++i) pv[i] = pv_s[(i * TY + ty) * kTX + tx];
             diag_node<NC, V>(r, pv, A.have_prev, acc);
             if (!valid1)
 #pragma unroll

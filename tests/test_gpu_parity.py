@@ -449,7 +449,9 @@ def test_tma_path_oracle_parity(fm):
 def test_tma_unavailable_is_reported(fm):
     mixd, _ = slab_state_binary(70, 37)
     lat = fm.Lattice(fm.mixture_from_dict(mixd), 70, 37, 1.0, "isotropic", "fp32", "lagged")
-    assert fm.fmlbm_get_step_variant(lat.h) == "pair"    # the default for float storage
+    assert fm.fmlbm_get_step_variant(lat.h) == "plain"   # the default (nx not a multiple of 4 either)
+    fm.fmlbm_set_step_variant(lat.h, "pair")             # the paired step has no shape condition
+    assert fm.fmlbm_get_step_variant(lat.h) == "pair"
     with pytest.raises(fm.FmlbmError) as ei:
         fm.fmlbm_set_step_variant(lat.h, "tma")
     assert ei.value.status == 8
