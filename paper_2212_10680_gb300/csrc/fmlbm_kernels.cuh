@@ -132,7 +132,7 @@ struct StepArgs {
     void* diag_partial;
     void* rho_prev;  // [N][ny][nx] in the storage arithmetic type
     int have_prev;
-    int prefetch_ahead;    // paired step: the tile this many blocks later is prefetched into L2 (0: none)
+    int pad0;
     long long wait_polls;  // polls of a bounded wait for a tile copy (bulk-copy step forms)
 };
 

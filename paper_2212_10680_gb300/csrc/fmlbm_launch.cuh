@@ -257,14 +257,7 @@ template <int NC> constexpr int kPairPark = NC == 1 ? 0 : (NC == 2 ? 1 : 2);
         FMLBM_ENSURE_SMEM(k, smem);                                                                       \
         dim3 grid((A.nx + kPW - 1) / kPW, (A.ny + kTileYSmall - 1) / kTileYSmall);                        \
         const Planes P = make_planes(A, NC, ST == ST_F16DEV || ST == ST_BF16DEV, ST == ST_F32 ? 4 : 2);   \
-        /* the next wave of blocks: resident blocks on all SMs (four per SM by the launch bounds */     \
-        /* of the parked forms, three otherwise)                                                  */     \
-        StepArgs B = A;                                                                                   \
-        int dev = 0, sms = 0;                                                                             \
-        if (cudaGetDevice(&dev) == cudaSuccess &&                                                         \
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)             \
-            B.prefetch_ahead = sms * (NP > 0 ? 4 : 3);                                                    \
-        k<<<grid, dim3(kTX, kTileYSmall), smem, s>>>(B, P);                                               \
+        k<<<grid, dim3(kTX, kTileYSmall), smem, s>>>(A, P);                                               \
         return cudaGetLastError();                                                                        \
     }                                                                                                     \
     template <int NC>                                                                                     \

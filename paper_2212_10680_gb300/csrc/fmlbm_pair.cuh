@@ -29,15 +29,6 @@
 
 #include "fmlbm_kernels.cuh"
 
-#ifndef FMLBM_PAIR_RING_SPREAD
-#define FMLBM_PAIR_RING_SPREAD 0
-#endif
-#ifndef FMLBM_PAIR_RING_ASYNC
-#define FMLBM_PAIR_RING_ASYNC 0
-#endif
-#ifndef FMLBM_PAIR_PREFETCH
-#define FMLBM_PAIR_PREFETCH 0
-#endif
 
 namespace fmlbm {
 
@@ -54,15 +45,10 @@ struct PairSmem {
 // Ring nodes of the paired tile (two per thread of the first RING / 2 threads).
 template <int TY> constexpr int kPairRing = 4 * (kPW + 4) + 4 * TY;
 
-// The park area: the parked values (five 16-byte slots per parked component and thread);
-// before them, in float storage, the pulled values of the ring pairs ([9N][RING / 2] float2),
-// copied there by cp.async so that their latency overlaps the owned nodes' pulls.
+// The park area: the parked values, five 16-byte slots per parked component and thread.
 template <int NC, int ST, int TY, int NPARK>
 constexpr size_t pair_park_bytes() {
-    const size_t park = (size_t)NPARK * 5 * 16 * kTX * TY;
-    const size_t ring = FMLBM_PAIR_RING_ASYNC && ST == ST_F32 ? (size_t)9 * NC * (kPairRing<TY> / 2) * 8 : 0;
-    const size_t b = park > ring ? park : ring;
-    return (b + 15) & ~size_t(15);
+    return (size_t)NPARK * 5 * 16 * kTX * TY;
 }
 // Shared bytes of the paired step: the tiles, the park area, the diagnostics snapshot copy
 // of the tile's node pairs.
@@ -174,54 +160,15 @@ __global__ void __launch_bounds__(kTX* TY, NPARK > 0 ? 4 : 3) fused_step_pair(St
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
-#if FMLBM_PAIR_PREFETCH
-    // the tile that the block A.prefetch_ahead places later in launch order will read (the
-    // next wave of blocks on the SMs), into L2, so that its pulls need not wait for DRAM
-    if (A.prefetch_ahead > 0) {
-        const int nb = gridDim.x * gridDim.y, t = blockIdx.y * gridDim.x + blockIdx.x + A.prefetch_ahead;
-        if (t < nb) {
-            const int px0 = (t % gridDim.x) * kPW, py0 = (t / gridDim.x) * TY;
-            constexpr bool dev16 = ST == ST_F16DEV || ST == ST_BF16DEV;
-            constexpr int NP = dev16 ? 8 * NC : 9 * NC;      // planes of P.in
-            constexpr int LPR = dev16 ? 1 : 2;               // 128-byte lines per 64-node row segment
-            constexpr int NITEM = NP * TY * LPR + (dev16 ? NC * TY * 2 : 0);
-            for (int it = tid; it < NITEM; it += NT) {
-                int k, row, seg;
-                const char* base;
-                size_t esz;
-                if (it < NP * TY * LPR) {
-                    k = it / (TY * LPR);
-                    row = (it / LPR) % TY;
-                    seg = it % LPR;
-                    base = static_cast<const char*>(P.in[k]);
-                    esz = dev16 ? 2 : 4;
-                } else {
-                    const int q = it - NP * TY * LPR;
-                    k = q / (TY * 2);
-                    row = (q / 2) % TY;
-                    seg = q % 2;
-                    base = reinterpret_cast<const char*>(P.g0in[k]);
-                    esz = 4;
-                }
-                const int y = py0 + row, x = px0 + seg * (int)(128 / esz);
-                if (y < ny && x < nx)
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(base + ((size_t)y * nx + x) * esz));
-            }
-        }
-    }
-#endif
 
-    // ---- phase 1: the ring pair and the owned nodes.  Float storage: the ring pair's pulled
-    //      values are copied into the park area (cp.async, no registers) while the owned
-    //      nodes' pulls are in flight; 16-bit storage (no 2-byte cp.async): the ring pair is
-    //      pulled into registers first.  Then rho_i and the first moment of the owned nodes,
-    //      rho~ and ln f of the ring (ln f on its inner ring only), the parked components to
-    //      shared memory, rho~ and ln f of the owned nodes ----
+    // ---- phase 1: the ring pair (pull, rho~, ln f on the inner ring), then the owned nodes
+    //      (pull, rho_i and the first moment, the parked components to shared memory, rho~ and
+    //      ln f), so that only one set of pulled values is live at a time.  (The ring's values
+    //      copied into shared memory by cp.async, so that their latency would overlap the
+    //      owned pulls, measured slower: the registers then spill.) ----
     constexpr int RING = kPairRing<TY>;
     constexpr int RP = RING / 2;
     static_assert(RING % 2 == 0 && RP <= NT, "two ring nodes per thread at most");
-    constexpr bool RING_ASYNC = FMLBM_PAIR_RING_ASYNC && ST == ST_F32;
-    float2* ring_stage = reinterpret_cast<float2*>(park);
     const bool has_ring = tid < RP;
     int bx0 = 0, by0 = 0, bx1 = 0, by1 = 0;
     V rr[NC];
@@ -232,28 +179,25 @@ __global__ void __launch_bounds__(kTX* TY, NPARK > 0 ? 4 : 3) fused_step_pair(St
         const int wy0 = inner ? y0 - 2 + by0 : wrap(y0 - 2 + by0, ny);
         const int wx1 = inner ? x0 - 2 + bx1 : wrap(x0 - 2 + bx1, nx);
         const int wy1 = inner ? y0 - 2 + by1 : wrap(y0 - 2 + by1, ny);
-        if constexpr (RING_ASYNC) {
-            auto src_of = [&](int a, int wx, int wy) {
-                if (inner) return wy * nx + wx - ey(a) * nx - ex(a);
-                const int xm = wx == 0 ? nx - 1 : wx - 1, xp = wx == nx - 1 ? 0 : wx + 1;
-                const int ym = wy == 0 ? ny - 1 : wy - 1, yp = wy == ny - 1 ? 0 : wy + 1;
-                return pull_src(a, wx, wy, xm, xp, ym, yp, nx);
-            };
+        pull_rho_pair<NC, ST>(P, wx0, wy0, wx1, wy1, inner, nx, ny, rr);
 #pragma unroll
-            for (int a = 0; a < 9; ++a) {
-                const int s0 = src_of(a, wx0, wy0), s1 = src_of(a, wx1, wy1);
+        for (int i = 0; i < NC; ++i) {
+            rr[i] = vmul(rr[i], vbc<V>(m.invM[i]));
+            pair_put(S.rt, i, by0, bx0 - 2, rr[i].x);
+            pair_put(S.rt, i, by1, bx1 - 2, rr[i].y);
+        }
+        const bool in0 = bx0 >= 1 && bx0 <= kPW + 2 && by0 >= 1 && by0 <= TY + 2;
+        const bool in1 = bx1 >= 1 && bx1 <= kPW + 2 && by1 >= 1 && by1 <= TY + 2;
+        if (in0 || in1) {
+            V lnf[NC];
+            node_lnf<NC, V>(m, rr, lnf);
 #pragma unroll
-                for (int i = 0; i < NC; ++i) {
-                    const float* plane = static_cast<const float*>(P.in[i * 9 + a]);
-                    cp_async_elem(&ring_stage[(i * 9 + a) * RP + tid].x, plane + s0);
-                    cp_async_elem(&ring_stage[(i * 9 + a) * RP + tid].y, plane + s1);
-                }
+            for (int i = 0; i < NC; ++i) {
+                if (in0) pair_put(S.lf, i, by0 - 1, bx0 - 2, lnf[i].x);
+                if (in1) pair_put(S.lf, i, by1 - 1, bx1 - 2, lnf[i].y);
             }
-        } else {
-            pull_rho_pair<NC, ST>(P, wx0, wy0, wx1, wy1, inner, nx, ny, rr);
         }
     }
-    if constexpr (RING_ASYNC) asm volatile("cp.async.commit_group;\n" ::: "memory");
     V g[NREG > 0 ? NREG : 1][9];
     V r[NC], jx, jy;
     {
@@ -288,37 +232,6 @@ __global__ void __launch_bounds__(kTX* TY, NPARK > 0 ? 4 : 3) fused_step_pair(St
             r[i] = sum9(gp[i]);
             moment_j(gp[i], i == 0, jx, jy);
         }
-        if (has_ring) {
-            if constexpr (RING_ASYNC) {
-                asm volatile("cp.async.wait_all;\n" ::: "memory");
-#pragma unroll
-                for (int a = 0; a < 9; ++a)
-#pragma unroll
-                    for (int i = 0; i < NC; ++i) {
-                        const V v = ring_stage[(i * 9 + a) * RP + tid];
-                        rr[i] = a == 0 ? v : vadd(rr[i], v);   // the order of pull_rho
-                    }
-            }
-#pragma unroll
-            for (int i = 0; i < NC; ++i) {
-                rr[i] = vmul(rr[i], vbc<V>(m.invM[i]));
-                pair_put(S.rt, i, by0, bx0 - 2, rr[i].x);
-                pair_put(S.rt, i, by1, bx1 - 2, rr[i].y);
-            }
-            const bool in0 = bx0 >= 1 && bx0 <= kPW + 2 && by0 >= 1 && by0 <= TY + 2;
-            const bool in1 = bx1 >= 1 && bx1 <= kPW + 2 && by1 >= 1 && by1 <= TY + 2;
-            if (in0 || in1) {
-                V lnf[NC];
-                node_lnf<NC, V>(m, rr, lnf);
-#pragma unroll
-                for (int i = 0; i < NC; ++i) {
-                    if (in0) pair_put(S.lf, i, by0 - 1, bx0 - 2, lnf[i].x);
-                    if (in1) pair_put(S.lf, i, by1 - 1, bx1 - 2, lnf[i].y);
-                }
-            }
-        }
-        // every thread has read its ring values from the park area before any parks
-        if constexpr (RING_ASYNC && NPARK > 0) __syncthreads();
 #pragma unroll
         for (int c = 0; c < NPARK; ++c) park_pair_store(gp[NREG + c], park + c * 5 * NT, tid, NT);
 #pragma unroll
@@ -344,21 +257,9 @@ __global__ void __launch_bounds__(kTX* TY, NPARK > 0 ? 4 : 3) fused_step_pair(St
     //      warp w takes slots 0..31 of row w; rows TY, TY + 1 go to the last two warps and
     //      slots 32, 33 of every row to warp TY - 3 (the ring ran on the first warps) ----
     phase2_core<NC, V>(m, S.rt, S.lf, S.G, A.stencil, tx, ty, 0);
-#if FMLBM_PAIR_RING_SPREAD
-    {
-        // the rest (rows TY, TY + 1 and slots 32, 33 of every row) spread over the warps
-        constexpr int REST = 2 * kTX + 2 * (TY + 2), PER = (REST + TY - 1) / TY;
-        const int q = ty * PER + tx;
-        if (tx < PER && q < REST) {
-            if (q < 2 * kTX) phase2_core<NC, V>(m, S.rt, S.lf, S.G, A.stencil, q & (kTX - 1), TY + (q >> 5), 0);
-            else phase2_core<NC, V>(m, S.rt, S.lf, S.G, A.stencil, kTX + ((q - 2 * kTX) & 1), (q - 2 * kTX) >> 1, 0);
-        }
-    }
-#else
     if (ty >= TY - 2) phase2_core<NC, V>(m, S.rt, S.lf, S.G, A.stencil, tx, ty + 2, 0);
     if (ty == TY - 3 && tx < 2 * (TY + 2))
         phase2_core<NC, V>(m, S.rt, S.lf, S.G, A.stencil, kTX + (tx & 1), tx >> 1, 0);
-#endif
     __syncthreads();
 
     // ---- phase 3 ----
