@@ -71,10 +71,18 @@ typedef enum fmlbm_stencil { FMLBM_STENCIL_ISOTROPIC = 0, FMLBM_STENCIL_CENTRAL 
 /* Storage and arithmetic.  FP64: distributions and all arithmetic in double.
  * FP32: float storage and arithmetic.  FP16DEV / BF16DEV: g_0 stored as float,
  * g_a (a != 0) stored as 16-bit deviations from the rest value w_a rho_0 (= 0),
- * collide/stream arithmetic in float, the fugacity-coefficient terms of ln f in
- * double. */
+ * all arithmetic in float (ln f included).  FP16DEV_LNF64 / BF16DEV_LNF64: the same
+ * storage and float collide/stream arithmetic, with ln f (the mixing sums, the repulsion
+ * and attraction terms of the fugacity coefficient and their logarithms; Eq.
+ * eqfugupdatePR/SRK/VDW) evaluated in double from the float densities and rounded to float
+ * once.  GB300 executes FP64 at about 1/64 of its FP32 rate, so the _LNF64 forms are several
+ * times slower per step; they run the plain step only (no TMA or paired form) and are not
+ * accepted by batches or servers (FMLBM_E_UNSUPPORTED).  Every form accumulates the
+ * diagnostics sums (masses, residual) in double from 32 x 8 strips up, and exactly to about
+ * 44 bits within a strip. */
 typedef enum fmlbm_precision {
-    FMLBM_FP64 = 0, FMLBM_FP32 = 1, FMLBM_FP16DEV = 2, FMLBM_BF16DEV = 3
+    FMLBM_FP64 = 0, FMLBM_FP32 = 1, FMLBM_FP16DEV = 2, FMLBM_BF16DEV = 3,
+    FMLBM_FP16DEV_LNF64 = 4, FMLBM_BF16DEV_LNF64 = 5
 } fmlbm_precision;
 
 /* Which body force enters the velocity of step 1 of Section III.B.  LAGGED
@@ -147,11 +155,13 @@ fmlbm_status fmlbm_buffer_sizes(int32_t n_components, const fmlbm_lattice* latti
  * The handle uses them in place, in its own layout (the ping-pong buffers of the storage
  * form, not the layout fmlbm_get_distributions returns), and never frees them: they must
  * outlive the handle, and the caller must not write them while the handle's work is in
- * flight.  Everything else (snapshot, reduction scratch, diagnostics stream) the handle
+ * flight.  The six buffers must not overlap (a step reads one of each pair while it writes
+ * the other).  Everything else (snapshot, reduction scratch, diagnostics stream) the handle
  * allocates itself, as fmlbm_create does.  FMLBM_E_INVALID_ARG for a NULL, host, unaligned
- * or (for non-deviation forms) superfluous g0 pointer, and for a buffer that does not fit
- * in the device allocation containing it (a buffer carved out of a larger pool allocation
- * is checked against that allocation only). */
+ * or (for non-deviation forms) superfluous g0 pointer, for memory of another GPU than the
+ * current one, for overlapping buffers, and for a buffer that does not fit in the device
+ * allocation containing it (a buffer carved out of a larger pool allocation is checked
+ * against that allocation only). */
 fmlbm_status fmlbm_create_with_buffers(const fmlbm_mixture* mixture, const fmlbm_lattice* lattice,
                                        void* cuda_stream, void* const g[2], float* const g0[2],
                                        void* const force[2], fmlbm_handle** out);
@@ -185,7 +195,8 @@ fmlbm_status fmlbm_get_distributions(fmlbm_handle* h, double* g, double* force);
  * Resets the step counter to 0 and clears the residual snapshot. */
 fmlbm_status fmlbm_set_distributions(fmlbm_handle* h, const double* g, const double* force);
 
-/* Reductions over the lattice (deterministic, fixed-order, FP64 accumulation per block):
+/* Reductions over the lattice (deterministic, fixed-order; double accumulation from each
+ * 32 x 8 strip up, exact to about 44 bits within a strip):
  * mass[N] = sum_x rho_i; residual = ||rho(t) - rho(t_prev)||_2 / ||rho(t)||_2
  * where t_prev is the state of the previous diagnostics request (+inf on the first
  * request after init); step = steps taken since init.  Then snapshots rho(t).
@@ -307,9 +318,11 @@ fmlbm_status fmlbm_lattice_bytes(int32_t n_components, const fmlbm_lattice* latt
  * fixed device array of 65536 doubles (512 KiB) that every GPU which loads the
  * library keeps until the process exits, so a lattice may have at most
  * 65536 / (N + 2) tiles of 32 x 8 nodes (about 4.2 million nodes for N = 2);
- * larger lattices are rejected with FMLBM_E_INVALID_ARG, as are NULL buffers or
- * out-of-range sizes.  The first call on each device looks up that array's device
- * address (cudaGetSymbolAddress) with the device current; make that first call
+ * larger lattices are rejected with FMLBM_E_INVALID_ARG, as are out-of-range sizes and
+ * buffers that are NULL, not device memory of the current GPU, misaligned for their
+ * element type or smaller than the lattice needs.  The first call in each CUDA context
+ * (each device, and again after that device's context was reset) looks up that array's
+ * device address (cudaGetSymbolAddress) with the device current; make that first call
  * before capturing work into a CUDA graph.  All calls share the one array and each
  * call overwrites every entry it later reads, so nothing needs clearing; calls that
  * overlap on the GPU (on different streams) race on it and must be serialised by

@@ -44,7 +44,7 @@ struct fmlbm_handle {
     int cur = 0;
     void* rho_prev = nullptr;     // storage arithmetic type
     int have_prev = 0;
-    void* partial = nullptr;         // kDiagSlots sets of per-strip sums (storage type, 8 bytes reserved each)
+    void* partial = nullptr;         // kDiagSlots sets of per-strip sums (doubles)
     double* diag_dev = nullptr;      // kDiagSlots x kDiagWords results, then the error latch
     cudaStream_t tail = nullptr;     // final sums and copies of fused requests (non-blocking)
     cudaEvent_t part_ev[kDiagSlots] = {};    // [ticket % kDiagSlots]: partial sums of a fused request written
@@ -161,7 +161,7 @@ bool lattice_ok(const fmlbm_lattice& L, int nc, std::string* why) {
     if ((double)L.nx * L.ny * nc * 9 >= 2147483647.0) { *why = "lattice too large"; return false; }
     if (!(L.tau > 0.5)) { *why = "tau must exceed 0.5"; return false; }
     if (L.stencil != FMLBM_STENCIL_ISOTROPIC && L.stencil != FMLBM_STENCIL_CENTRAL) { *why = "unknown stencil"; return false; }
-    if (L.precision < FMLBM_FP64 || L.precision > FMLBM_BF16DEV) { *why = "unknown precision"; return false; }
+    if (L.precision < FMLBM_FP64 || L.precision > FMLBM_BF16DEV_LNF64) { *why = "unknown precision"; return false; }
     if (L.velocity_force != FMLBM_FORCE_LAGGED && L.velocity_force != FMLBM_FORCE_CURRENT) {
         *why = "unknown velocity_force";
         return false;
@@ -320,6 +320,8 @@ cudaError_t dispatch_step(const fmlbm_handle* h, const StepArgs& A, bool moments
         case FMLBM_FP64: return launch_step<ST_F64>(A, h->nc, moments, h->tile_y, h->stream);
         case FMLBM_FP32: return launch_step<ST_F32>(A, h->nc, moments, h->tile_y, h->stream);
         case FMLBM_FP16DEV: return launch_step<ST_F16DEV>(A, h->nc, moments, h->tile_y, h->stream);
+        case FMLBM_FP16DEV_LNF64: return launch_step<ST_F16DEV_X>(A, h->nc, moments, h->tile_y, h->stream);
+        case FMLBM_BF16DEV_LNF64: return launch_step<ST_BF16DEV_X>(A, h->nc, moments, h->tile_y, h->stream);
         default: return launch_step<ST_BF16DEV>(A, h->nc, moments, h->tile_y, h->stream);
     }
 }
@@ -327,7 +329,8 @@ cudaError_t dispatch_init(const fmlbm_handle* h, const StepArgs& A, const double
     switch (h->lattice.precision) {
         case FMLBM_FP64: return launch_init<ST_F64>(A, h->nc, rho, h->stream);
         case FMLBM_FP32: return launch_init<ST_F32>(A, h->nc, rho, h->stream);
-        case FMLBM_FP16DEV: return launch_init<ST_F16DEV>(A, h->nc, rho, h->stream);
+        case FMLBM_FP16DEV:
+        case FMLBM_FP16DEV_LNF64: return launch_init<ST_F16DEV>(A, h->nc, rho, h->stream);
         default: return launch_init<ST_BF16DEV>(A, h->nc, rho, h->stream);
     }
 }
@@ -335,7 +338,8 @@ cudaError_t dispatch_convert(const fmlbm_handle* h, const StepArgs& A, const dou
     switch (h->lattice.precision) {
         case FMLBM_FP64: return launch_convert<ST_F64>(A, h->nc, gi, go, to, h->stream);
         case FMLBM_FP32: return launch_convert<ST_F32>(A, h->nc, gi, go, to, h->stream);
-        case FMLBM_FP16DEV: return launch_convert<ST_F16DEV>(A, h->nc, gi, go, to, h->stream);
+        case FMLBM_FP16DEV:
+        case FMLBM_FP16DEV_LNF64: return launch_convert<ST_F16DEV>(A, h->nc, gi, go, to, h->stream);
         default: return launch_convert<ST_BF16DEV>(A, h->nc, gi, go, to, h->stream);
     }
 }
@@ -343,7 +347,8 @@ cudaError_t dispatch_reduce(fmlbm_handle* h, const StepArgs& A, void* partial, d
     switch (h->lattice.precision) {
         case FMLBM_FP64: return launch_reduce<ST_F64>(A, h->nc, h->rho_prev, h->have_prev, partial, out, h->stream);
         case FMLBM_FP32: return launch_reduce<ST_F32>(A, h->nc, h->rho_prev, h->have_prev, partial, out, h->stream);
-        case FMLBM_FP16DEV: return launch_reduce<ST_F16DEV>(A, h->nc, h->rho_prev, h->have_prev, partial, out, h->stream);
+        case FMLBM_FP16DEV:
+        case FMLBM_FP16DEV_LNF64: return launch_reduce<ST_F16DEV>(A, h->nc, h->rho_prev, h->have_prev, partial, out, h->stream);
         default: return launch_reduce<ST_BF16DEV>(A, h->nc, h->rho_prev, h->have_prev, partial, out, h->stream);
     }
 }
@@ -414,8 +419,8 @@ fmlbm_status enqueue_diag_tail(fmlbm_handle* h, int64_t ticket, cudaStream_t s, 
     DiagSlot& sl = h->slot[ticket % kDiagSlots];
     double* host = h->diag_host + (size_t)(ticket % kDiagSlots) * kDiagWords;
     if (final_sum)
-        FM_CUDA(h, launch_reduce_final(h->nc, h->lattice.precision == FMLBM_FP64, partial_set(h, ticket),
-                                       h->lattice.nx, h->lattice.ny, result_slot(h, ticket), s));
+        FM_CUDA(h, launch_reduce_final(h->nc, partial_set(h, ticket), h->lattice.nx, h->lattice.ny,
+                                       result_slot(h, ticket), s));
     FM_CUDA(h, cudaMemcpyAsync(host, result_slot(h, ticket), (kMaxC + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
     FM_CUDA(h, cudaMemcpyAsync(host + kMaxC + 2, h->err_dev, sizeof(ErrorLatch), cudaMemcpyDeviceToHost, s));
     // inside a stream capture the record becomes a node of the graph (an external event),
@@ -471,24 +476,14 @@ PFN_cuMemGetAddressRange_v3020 address_range_fn() {
     return fn;
 }
 
-// A device (or managed) allocation of this process, 16-byte aligned, with at least `bytes`
-// from p to the end of the allocation that contains it (a buffer carved out of a larger
-// pool allocation is checked against the pool allocation).
-bool usable_device_pointer(const void* p, size_t bytes) {
-    if (!p || (reinterpret_cast<uintptr_t>(p) & 15) != 0) return false;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return false;
-    if (auto range = address_range_fn()) {
-        CUdeviceptr base = 0;
-        size_t size = 0;
-        const CUdeviceptr d = reinterpret_cast<CUdeviceptr>(p);
-        if (range(&base, &size, d) != CUDA_SUCCESS) return false;
-        if (d + bytes > base + size) return false;
-    }
+// Byte ranges [p, p + bytes) that must not overlap (null entries are skipped).
+bool disjoint(const void* const* p, const size_t* bytes, int n) {
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+            if (!p[i] || !p[j] || !bytes[i] || !bytes[j]) continue;
+            const uintptr_t a0 = reinterpret_cast<uintptr_t>(p[i]), b0 = reinterpret_cast<uintptr_t>(p[j]);
+            if (a0 < b0 + bytes[j] && b0 < a0 + bytes[i]) return false;
+        }
     return true;
 }
 
@@ -519,14 +514,23 @@ fmlbm_status create_handle(const fmlbm_mixture* mixture, const fmlbm_lattice* la
     if (ext) {
         h->owns_buffers = false;
         for (int k = 0; k < 2; ++k) {
-            const bool g0_ok = g0b ? usable_device_pointer(ext->g0[k], g0b) : ext->g0[k] == nullptr;
-            if (!usable_device_pointer(ext->g[k], gb) || !g0_ok || !usable_device_pointer(ext->F[k], fb)) {
+            const bool g0_ok = g0b ? fmlbm_internal_usable_device_pointer(ext->g0[k], g0b, h->device)
+                                   : ext->g0[k] == nullptr;
+            if (!fmlbm_internal_usable_device_pointer(ext->g[k], gb, h->device) || !g0_ok ||
+                !fmlbm_internal_usable_device_pointer(ext->F[k], fb, h->device)) {
                 delete h;
                 return FMLBM_E_INVALID_ARG;
             }
             h->g[k] = ext->g[k];
             h->g0[k] = ext->g0[k];
             h->F[k] = ext->F[k];
+        }
+        // the step reads one buffer of each pair while it writes the other
+        const void* ptrs[6] = {ext->g[0], ext->g[1], ext->g0[0], ext->g0[1], ext->F[0], ext->F[1]};
+        const size_t sizes[6] = {gb, gb, g0b, g0b, fb, fb};
+        if (!disjoint(ptrs, sizes, 6)) {
+            delete h;
+            return FMLBM_E_INVALID_ARG;
         }
     }
     for (int k = 0; k < 2 && ok && !ext; ++k) {
@@ -570,6 +574,30 @@ fmlbm_status create_handle(const fmlbm_mixture* mixture, const fmlbm_lattice* la
 }
 
 }  // namespace
+
+// A device (or managed) allocation of this process on `device`, aligned to `align` bytes (a
+// power of two), with at
+// least `bytes` from p to the end of the allocation that contains it (a buffer carved out
+// of a larger pool allocation is checked against the pool allocation).  Memory of another
+// GPU is refused: a kernel would reach it over NVLink with peer access, or fault without.
+bool fmlbm_internal_usable_device_pointer(const void* p, size_t bytes, int device, size_t align) {
+    if (!p || (reinterpret_cast<uintptr_t>(p) & (align - 1)) != 0) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return false;
+    if (a.type == cudaMemoryTypeDevice && a.device != device) return false;
+    if (auto range = address_range_fn()) {
+        CUdeviceptr base = 0;
+        size_t size = 0;
+        const CUdeviceptr d = reinterpret_cast<CUdeviceptr>(p);
+        if (range(&base, &size, d) != CUDA_SUCCESS) return false;
+        if (d + bytes > base + size) return false;
+    }
+    return true;
+}
 
 bool fmlbm_internal_mixture_constants(const fmlbm_mixture& m, MixConst* mc, std::string* why) {
     return mixture_constants(m, mc, why);

@@ -121,12 +121,11 @@ cudaError_t launch_batch_step(const fmlbm_batch* b, int ty, int grid) {
 
 template <int ST, int NC>
 cudaError_t launch_batch_reduce_nc(const fmlbm_batch* b) {
-    using Real = typename StoreTraits<ST>::Real;
     batch_reduce<NC, ST><<<b->nwork, dim3(kTX, 8), 0, b->stream>>>(b->d_lat, b->d_work, b->nwork, b->d_prev,
-                                                                   reinterpret_cast<Real*>(b->d_partial));
+                                                                   b->d_partial);
     const int total = b->capacity * (NC + 2);
-    batch_reduce_final<NC, Real><<<(total + 127) / 128, 128, 0, b->stream>>>(
-        b->d_lat, b->capacity, reinterpret_cast<const Real*>(b->d_partial), b->d_out);
+    batch_reduce_final<NC><<<(total + 127) / 128, 128, 0, b->stream>>>(b->d_lat, b->capacity, b->d_partial,
+                                                                         b->d_out);
     return cudaGetLastError();
 }
 template <int ST>
@@ -335,8 +334,10 @@ extern "C" {
 fmlbm_status fmlbm_batch_create(int32_t n_components, int32_t precision, int32_t capacity, void* cuda_stream,
                                 fmlbm_batch** out) {
     if (!out || n_components < 1 || n_components > FMLBM_MAX_COMPONENTS || capacity < 1 || capacity > (1 << 20) ||
-        precision < FMLBM_FP64 || precision > FMLBM_BF16DEV)
+        precision < FMLBM_FP64 || precision > FMLBM_BF16DEV_LNF64)
         return FMLBM_E_INVALID_ARG;
+    // the forms with ln f in double run the single-lattice plain step only
+    if (precision == FMLBM_FP16DEV_LNF64 || precision == FMLBM_BF16DEV_LNF64) return FMLBM_E_UNSUPPORTED;
     *out = nullptr;
     fmlbm_batch* b = new (std::nothrow) fmlbm_batch();
     if (!b) return FMLBM_E_OOM;

@@ -73,12 +73,14 @@ __global__ void batch_advance(BatchLattice* __restrict__ lat, int n) {
 }
 
 // Per-item partial sums (NC + 2 doubles: sum rho_i, sum (rho - rho_prev)^2, sum rho^2) over
-// the item's tile of 32 x tile_y nodes, then rho_prev <- rho.  The items of one lattice
-// are contiguous, so batch_reduce_final sums each lattice in a fixed order.
+// the item's tile of 32 x tile_y nodes, then rho_prev <- rho, with the node sums, the warp
+// tree and the double strip sums of reduce_partial (the rows of a taller tile go through the
+// same compensated sums before the tree).  The items of one lattice are contiguous, so
+// batch_reduce_final sums each lattice in a fixed order.
 template <int NC, int ST>
 __global__ void __launch_bounds__(kTX* 8) batch_reduce(BatchLattice* __restrict__ lat, const WorkItem* __restrict__ work,
                                                        int nwork, void* const* __restrict__ rho_prev,
-                                                       typename StoreTraits<ST>::Real* __restrict__ partial) {
+                                                       double* __restrict__ partial) {
     using Real = typename StoreTraits<ST>::Real;
     const int w = blockIdx.x;
     if (w >= nwork) return;
@@ -87,9 +89,9 @@ __global__ void __launch_bounds__(kTX* 8) batch_reduce(BatchLattice* __restrict_
     const StepArgs& A = L->args[L->step & 1];
     const int nx = A.nx, ny = A.ny, nxy = nx * ny;
     Real* prev = static_cast<Real*>(rho_prev[it.lattice]);
-    Real acc[NC + 2];
+    Sum2<Real> acc[NC + 2];
 #pragma unroll
-    for (int k = 0; k < NC + 2; ++k) acc[k] = Real(0);
+    for (int k = 0; k < NC + 2; ++k) acc[k] = s2_of(Real(0));
     if (L->active) {
         for (int ry = threadIdx.y; ry < L->tile_y; ry += 8) {
             const int x = it.x0 + threadIdx.x, y = it.y0 + ry;
@@ -101,33 +103,30 @@ __global__ void __launch_bounds__(kTX* 8) batch_reduce(BatchLattice* __restrict_
                 Real pv[NC];
 #pragma unroll
                 for (int i = 0; i < NC; ++i) pv[i] = prev[(size_t)i * nxy + node];
+                Sum2<Real> a[NC + 2];
+                diag_node<NC, Real>(r, pv, 1, a);
 #pragma unroll
-                for (int i = 0; i < NC; ++i) {
-                    acc[i] += r[i];
-                    acc[NC + 1] += r[i] * r[i];
-                    const Real d = r[i] - pv[i];
-                    acc[NC] += d * d;
-                }
+                for (int k = 0; k < NC + 2; ++k) acc[k] = s2_add(acc[k], a[k]);
 #pragma unroll
                 for (int i = 0; i < NC; ++i) prev[(size_t)i * nxy + node] = r[i];
             }
         }
     }
-    __shared__ Real red[8][NC + 2];
+    __shared__ Sum2<Real> red[8][NC + 2];
     diag_warp<NC, Real>(acc, red[threadIdx.y]);
     __syncthreads();
     const int tid = threadIdx.y * kTX + threadIdx.x;
-    if (tid < NC + 2) partial[(size_t)w * (NC + 2) + tid] = diag_strip<NC, Real>(red, 0, tid);
+    if (tid < NC + 2) partial[(size_t)w * (NC + 2) + tid] = diag_strip<NC, Real>(red, 0, tid, 0);
 }
 
-template <int NC, typename Real>
-__global__ void batch_reduce_final(const BatchLattice* __restrict__ lat, int n, const Real* __restrict__ partial,
+template <int NC>
+__global__ void batch_reduce_final(const BatchLattice* __restrict__ lat, int n, const double* __restrict__ partial,
                                    double* __restrict__ out) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n * (NC + 2)) return;
     const int l = k / (NC + 2), q = k % (NC + 2);
     double v = 0.0;
-    for (int w = lat[l].item0; w < lat[l].item0 + lat[l].nitems; ++w) v += (double)partial[(size_t)w * (NC + 2) + q];
+    for (int w = lat[l].item0; w < lat[l].item0 + lat[l].nitems; ++w) v += partial[(size_t)w * (NC + 2) + q];
     out[k] = v;
 }
 

@@ -11,3 +11,6 @@
 bool fmlbm_internal_mixture_constants(const fmlbm_mixture& m, fmlbm::MixConst* mc, std::string* why);
 // Validity of a lattice description for n components.
 bool fmlbm_internal_lattice_ok(const fmlbm_lattice& L, int nc, std::string* why);
+// A device (or managed) allocation on `device`, aligned to `align` bytes, with at least
+// `bytes` from p to the end of the allocation that contains it.
+bool fmlbm_internal_usable_device_pointer(const void* p, size_t bytes, int device, size_t align = 16);

@@ -42,6 +42,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "fmlbm_lanes.cuh"
 
 namespace fmlbm {
@@ -49,7 +51,11 @@ namespace fmlbm {
 constexpr int kMaxC = 4;
 constexpr int kTX = 32;  // tile width = one warp
 
-enum Storage { ST_F64 = 0, ST_F32 = 1, ST_F16DEV = 2, ST_BF16DEV = 3 };
+// Storage forms of the kernels.  The _X forms store like the 16-bit forms and evaluate the
+// fugacity terms of ln f in double (node_lnf_st).
+enum Storage { ST_F64 = 0, ST_F32 = 1, ST_F16DEV = 2, ST_BF16DEV = 3, ST_F16DEV_X = 4, ST_BF16DEV_X = 5 };
+template <int ST> constexpr bool kDev16 = ST == ST_F16DEV || ST == ST_BF16DEV || ST == ST_F16DEV_X || ST == ST_BF16DEV_X;
+template <int ST> constexpr bool kLnf64 = ST == ST_F16DEV_X || ST == ST_BF16DEV_X;
 
 // D2Q9: a = 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1)
 __host__ __device__ __forceinline__ constexpr int ex(int a) {
@@ -174,6 +180,8 @@ template <> struct StoreTraits<ST_F64> { using Real = double; using Elem = doubl
 template <> struct StoreTraits<ST_F32> { using Real = float; using Elem = float; };
 template <> struct StoreTraits<ST_F16DEV> { using Real = float; using Elem = __half; };
 template <> struct StoreTraits<ST_BF16DEV> { using Real = float; using Elem = __nv_bfloat16; };
+template <> struct StoreTraits<ST_F16DEV_X> { using Real = float; using Elem = __half; };
+template <> struct StoreTraits<ST_BF16DEV_X> { using Real = float; using Elem = __nv_bfloat16; };
 
 __device__ __forceinline__ float to_real(__half v) { return __half2float(v); }
 __device__ __forceinline__ float to_real(__nv_bfloat16 v) { return __bfloat162float(v); }
@@ -335,6 +343,25 @@ struct Tile {
     E v[NC][Hh][W];
 };
 
+// ln f of a node in the storage form's arithmetic: float (or double) lanes as node_lnf; the
+// _X forms evaluate the fugacity terms (mixing sums, the repulsion and attraction terms and
+// their logarithms) in double from the float densities, with the double mixture constants,
+// and round ln f and beta to float once.
+template <int NC, bool LNF64, typename Real>
+__device__ __forceinline__ Real node_lnf_st(const StepArgs& A, const MixConstT<Real>& m, const Real* rt, Real* lnf) {
+    if constexpr (LNF64) {
+        double rd[NC], ld[NC];
+#pragma unroll
+        for (int i = 0; i < NC; ++i) rd[i] = (double)rt[i];
+        const double beta = node_lnf<NC, double>(A.mixd, rd, ld);
+#pragma unroll
+        for (int i = 0; i < NC; ++i) lnf[i] = (Real)ld[i];
+        return (Real)beta;
+    } else {
+        return node_lnf<NC, Real>(m, rt, lnf);
+    }
+}
+
 // A field on a 64 x TY tile plus an H-node halo, stored in pair slots for the paired step:
 // slot s of a row holds the columns (s - H, s - H + 32) of the tile (column 0 = the tile's
 // first) as one float2, so that a thread's two nodes, and the same neighbour of both, are
@@ -445,7 +472,7 @@ struct StepSmem {
 // The same step also addresses the distribution planes through the launch's plane
 // pointers (Planes, load_gp / store_gp).
 template <int NC, int ST, int TY>
-constexpr bool kParkLast = ST != ST_F64 && NC == 2 && TY == 8;
+constexpr bool kParkLast = ST != ST_F64 && !kLnf64<ST> && NC == 2 && TY == 8;
 template <int NC, int ST, int TY>
 constexpr size_t park_bytes() {
     return kParkLast<NC, ST, TY> ? (size_t)9 * TY * kTX * sizeof(typename StoreTraits<ST>::Real) : 0;
@@ -565,7 +592,7 @@ __device__ __forceinline__ void domain_check(const StepArgs& A, const V* rt, con
 
 // Phase 1, the node owned by this thread: rho_i and the first moment (step 1, returned in
 // r, jx, jy) and rho~, ln f (steps 2-5) from its nine pulled values per component.
-template <int NC, int TY, typename Real>
+template <int NC, int TY, typename Real, bool LNF64 = false>
 __device__ __forceinline__ void phase1_node(const StepArgs& A, const MixConstT<Real>& m, StepSmem<Real, NC, TY>& S,
                                             const Real (&g)[NC][9], Real (&r)[NC], Real& jx, Real& jy, int tx, int ty,
                                             bool valid, int gx, int gy) {
@@ -577,7 +604,7 @@ __device__ __forceinline__ void phase1_node(const StepArgs& A, const MixConstT<R
         rt[i] = vmul(r[i], m.invM[i]);
         S.rt.v[i][ty + 2][tx + 2] = rt[i];
     }
-    const Real beta = node_lnf<NC, Real>(m, rt, lnf);
+    const Real beta = node_lnf_st<NC, LNF64, Real>(A, m, rt, lnf);
 #pragma unroll
     for (int i = 0; i < NC; ++i) S.lf.v[i][ty + 1][tx + 1] = lnf[i];
     domain_check<NC, Real>(A, rt, lnf, beta, gx, 0, gy, valid ? 1u : 0u);
@@ -604,9 +631,9 @@ __device__ __forceinline__ void ring_position(int r, int& bx, int& by) {
 }
 
 // Phase 1, a halo ring node: rho~ from its summed densities; ln f on the inner 1-node ring.
-template <int NC, int TY, typename Real>
-__device__ __forceinline__ void phase1_ring(const MixConstT<Real>& m, StepSmem<Real, NC, TY>& S, Real (&rt)[NC],
-                                            int bx, int by) {
+template <int NC, int TY, typename Real, bool LNF64 = false>
+__device__ __forceinline__ void phase1_ring(const StepArgs& A, const MixConstT<Real>& m, StepSmem<Real, NC, TY>& S,
+                                            Real (&rt)[NC], int bx, int by) {
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
         rt[i] = vmul(rt[i], m.invM[i]);
@@ -614,7 +641,7 @@ __device__ __forceinline__ void phase1_ring(const MixConstT<Real>& m, StepSmem<R
     }
     if (bx >= 1 && bx <= kTX + 2 && by >= 1 && by <= TY + 2) {
         Real lnf[NC];
-        node_lnf<NC, Real>(m, rt, lnf);
+        node_lnf_st<NC, LNF64, Real>(A, m, rt, lnf);
 #pragma unroll
         for (int i = 0; i < NC; ++i) S.lf.v[i][by - 1][bx - 1] = lnf[i];
     }
@@ -871,14 +898,59 @@ __device__ __forceinline__ void phase1_global(const StepArgs& A, const MixConstT
         }
     }
     if constexpr (RING_FIRST) {
-        if (has_ring) phase1_ring<NC, TY, Real>(m, S, rr, bx, by);
-        phase1_node<NC, TY, Real>(A, m, S, g, r, jx, jy, tx, ty, valid, gxn, gyn);
+        if (has_ring) phase1_ring<NC, TY, Real, kLnf64<ST>>(A, m, S, rr, bx, by);
+        phase1_node<NC, TY, Real, kLnf64<ST>>(A, m, S, g, r, jx, jy, tx, ty, valid, gxn, gyn);
     } else {
-        phase1_node<NC, TY, Real>(A, m, S, g, r, jx, jy, tx, ty, valid, gxn, gyn);
+        phase1_node<NC, TY, Real, kLnf64<ST>>(A, m, S, g, r, jx, jy, tx, ty, valid, gxn, gyn);
         if (has_ring) {
             pull_ring();
-            phase1_ring<NC, TY, Real>(m, S, rr, bx, by);
+            phase1_ring<NC, TY, Real, kLnf64<ST>>(A, m, S, rr, bx, by);
         }
+    }
+}
+
+// ---- compensated sums of the diagnostics ----
+// The masses and residual sums are accumulated in double precision from the strip level up
+// (8 warp rows of 32 nodes).  Below that, in a warp, a float lane carries each sum as an
+// unevaluated pair hi + lo of floats (float-float, about 44 significant bits) built from exact
+// sums and products, which costs a few FP32 instructions per node instead of FP64 ones (GB300
+// executes about 2 FP64 operations per clock per SM, 1/64 of its FP32 rate).  Double lanes (the
+// FP64 storage) sum in plain double, lo staying 0.
+template <typename V>
+struct Sum2 {
+    V hi, lo;
+};
+template <typename V> constexpr bool kCompensated = !std::is_same<LaneE<V>, double>::value;
+
+template <typename V>
+__device__ __forceinline__ Sum2<V> s2_of(V a) { return {a, vbc<V>(LaneE<V>(0))}; }
+// s + e = a + b exactly (Knuth's two-sum)
+template <typename V>
+__device__ __forceinline__ Sum2<V> two_sum(V a, V b) {
+    if constexpr (!kCompensated<V>) {
+        return s2_of(vadd(a, b));
+    } else {
+        const V s = vadd(a, b), bb = vsub(s, a);
+        return {s, vadd(vsub(a, vsub(s, bb)), vsub(b, bb))};
+    }
+}
+// p + e = a b exactly (the rounding error of a product is a fused multiply-add away)
+template <typename V>
+__device__ __forceinline__ Sum2<V> two_prod(V a, V b) {
+    const V p = vmul(a, b);
+    if constexpr (!kCompensated<V>) return s2_of(p);
+    else return {p, vfma(a, b, vneg(p))};
+}
+// (a.hi + a.lo) + (b.hi + b.lo), renormalised so that |lo| <= ulp(hi) / 2
+template <typename V>
+__device__ __forceinline__ Sum2<V> s2_add(Sum2<V> a, Sum2<V> b) {
+    if constexpr (!kCompensated<V>) {
+        return s2_of(vadd(a.hi, b.hi));
+    } else {
+        const Sum2<V> t = two_sum(a.hi, b.hi);
+        const V e = vadd(t.lo, vadd(a.lo, b.lo));
+        const V hi = vadd(t.hi, e);
+        return {hi, vsub(e, vsub(hi, t.hi))};
     }
 }
 
@@ -888,14 +960,20 @@ __device__ __forceinline__ void phase1_global(const StepArgs& A, const MixConstT
 // N x nx x ny values) and early: a read guarded by the flag was issued only after the
 // pulled sums had arrived and made the reduction about three times slower.
 template <int NC, typename V>
-__device__ __forceinline__ void diag_node(const V (&r)[NC], const V (&pv)[NC], int have_prev, V (&acc)[NC + 2]) {
-    using E = LaneE<V>;
+__device__ __forceinline__ void diag_node(const V (&r)[NC], const V (&pv)[NC], int have_prev, Sum2<V> (&acc)[NC + 2]) {
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
-        acc[i] = r[i];
-        acc[NC + 1] = i == 0 ? vmul(r[0], r[0]) : vfma(r[i], r[i], acc[NC + 1]);
-        const V d = have_prev ? vsub(r[i], pv[i]) : vbc<V>(E(0));
-        acc[NC] = i == 0 ? vmul(d, d) : vfma(d, d, acc[NC]);
+        acc[i] = s2_of(r[i]);
+        const Sum2<V> sq = two_prod(r[i], r[i]);
+        acc[NC + 1] = i == 0 ? sq : s2_add(acc[NC + 1], sq);
+        Sum2<V> d2 = s2_of(vbc<V>(LaneE<V>(0)));
+        if (have_prev) {
+            // d = r - pv exactly as dh + dl; d^2 = dh^2 + 2 dh dl to the working precision
+            const Sum2<V> d = two_sum(r[i], vneg(pv[i]));
+            d2 = two_prod(d.hi, d.hi);
+            if constexpr (kCompensated<V>) d2.lo = vfma(vadd(d.hi, d.hi), d.lo, d2.lo);
+        }
+        acc[NC] = i == 0 ? d2 : s2_add(acc[NC], d2);
     }
 }
 
@@ -905,26 +983,33 @@ __device__ __forceinline__ float2 shfl_down(float2 v, int o) {
     return make_float2(__shfl_down_sync(0xffffffffu, v.x, o), __shfl_down_sync(0xffffffffu, v.y, o));
 }
 
-// Warp sums of acc (a fixed shuffle tree in the arithmetic type) into one row of a
-// per-block table.  No FP64 instruction for float storage: on GB300 a handful of FP64
-// conversions per warp made the fused step three times slower.
+// Warp sums of acc (a fixed shuffle tree) into one row of a per-block table.
 template <int NC, typename V>
-__device__ __forceinline__ void diag_warp(const V (&acc)[NC + 2], V* row) {
+__device__ __forceinline__ void diag_warp(const Sum2<V> (&acc)[NC + 2], Sum2<V>* row) {
 #pragma unroll
     for (int k = 0; k < NC + 2; ++k) {
-        V v = acc[k];
+        Sum2<V> v = acc[k];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v = vadd(v, shfl_down(v, o));
+        for (int o = 16; o > 0; o >>= 1) {
+            Sum2<V> w;
+            w.hi = shfl_down(v.hi, o);
+            w.lo = kCompensated<V> ? shfl_down(v.lo, o) : v.lo;
+            v = s2_add(v, w);
+        }
         if ((threadIdx.x & 31) == 0) row[k] = v;
     }
 }
 
-// Sum of eight consecutive rows of that table, in row order (one 32 x 8 strip).
+// Sum in double of eight consecutive rows of that table, in row order (one 32 x 8 strip), for
+// lane l of the lane type.
 template <int NC, typename V>
-__device__ __forceinline__ V diag_strip(const V (*red)[NC + 2], int row0, int k) {
-    V v = red[row0][k];
+__device__ __forceinline__ double diag_strip(const Sum2<V> (*red)[NC + 2], int row0, int k, int l) {
+    double v = 0.0;
 #pragma unroll
-    for (int w = 1; w < 8; ++w) v = vadd(v, red[row0 + w][k]);
+    for (int w = 0; w < 8; ++w) {
+        v += (double)lane(red[row0 + w][k].hi, l);
+        if constexpr (kCompensated<V>) v += (double)lane(red[row0 + w][k].lo, l);
+    }
     return v;
 }
 
@@ -948,11 +1033,11 @@ template <int NC, typename Real, int TY>
 __device__ __forceinline__ void diag_tile(const StepArgs& A, const Real (&r)[NC], const Real* pv_s, int tx, int ty,
                                           int gxn, int gyn, int y0, int tile_row, int tile_col, int tiles_x) {
     static_assert(TY % 8 == 0, "diagnostics strips of 8 rows");
-    __shared__ Real dred[TY][NC + 2];
+    __shared__ Sum2<Real> dred[TY][NC + 2];
     const int nx = A.nx, ny = A.ny, tid = ty * kTX + tx;
-    Real acc[NC + 2];
+    Sum2<Real> acc[NC + 2];
 #pragma unroll
-    for (int k = 0; k < NC + 2; ++k) acc[k] = Real(0);
+    for (int k = 0; k < NC + 2; ++k) acc[k] = s2_of(Real(0));
     if (gxn < nx && gyn < ny) {
         asm volatile("cp.async.wait_all;\n" ::: "memory");
         Real pv[NC];
@@ -970,8 +1055,8 @@ __device__ __forceinline__ void diag_tile(const StepArgs& A, const Real (&r)[NC]
     if (tid < STRIPS * (NC + 2)) {
         const int sub = tid / (NC + 2), k = tid % (NC + 2);
         if (y0 + 8 * sub < ny)
-            static_cast<Real*>(A.diag_partial)[((size_t)(tile_row * STRIPS + sub) * tiles_x + tile_col) * (NC + 2) + k] =
-                diag_strip<NC, Real>(dred, 8 * sub, k);
+            static_cast<double*>(A.diag_partial)[((size_t)(tile_row * STRIPS + sub) * tiles_x + tile_col) * (NC + 2) + k] =
+                diag_strip<NC, Real>(dred, 8 * sub, k, 0);
     }
 }
 
@@ -1081,27 +1166,24 @@ __global__ void convert_g(StepArgs A, const double* __restrict__ gin_d, double* 
 
 // Deterministic reductions over a lattice: one thread per node on the same 32 x 8 tiling
 // as the step (so the block count, and with it the summation order, depends only on
-// the lattice shape).  Each block writes NC + 2 sums: sum rho_i, sum (rho - rho_prev)^2,
+// the lattice shape).  Each block writes NC + 2 double sums: sum rho_i, sum (rho - rho_prev)^2,
 // sum rho^2; then rho_prev <- rho.  reduce_final adds the block rows in a fixed order.
 // A fused step asked for the diagnostics of the state it reads writes the same partial
-// sums, bit for bit (same node sums, same shuffle tree, same strips).
-// Per node, within a warp (a pairwise shuffle tree) and over the eight warps of a strip the
-// sums run in the storage arithmetic type; reduce_final promotes the strip sums to double,
-// so FP32 lattices pay no FP64 arithmetic in the per-node kernels.  rho_prev and the
-// partial sums hold values of that same type.
+// sums, bit for bit (same node sums, same shuffle tree, same strips).  The sums are exact
+// to about 44 bits within a warp (float-float for float storage) and double from the
+// strips up; rho_prev holds values of the storage arithmetic type.
 constexpr int kRedTY = 8;
 
 template <int NC, int ST>
 __global__ void __launch_bounds__(kTX* kRedTY) reduce_partial(StepArgs A,
                                                                typename StoreTraits<ST>::Real* __restrict__ rho_prev,
-                                                               int have_prev,
-                                                               typename StoreTraits<ST>::Real* __restrict__ partial) {
+                                                               int have_prev, double* __restrict__ partial) {
     using Real = typename StoreTraits<ST>::Real;
     const int nx = A.nx, ny = A.ny, nxy = nx * ny;
     const int x = blockIdx.x * kTX + threadIdx.x, y = blockIdx.y * kRedTY + threadIdx.y;
-    Real acc[NC + 2];
+    Sum2<Real> acc[NC + 2];
 #pragma unroll
-    for (int k = 0; k < NC + 2; ++k) acc[k] = Real(0);
+    for (int k = 0; k < NC + 2; ++k) acc[k] = s2_of(Real(0));
     if (x < nx && y < ny) {
         const bool inner = x >= 1 && x + 1 < nx && y >= 1 && y + 1 < ny;
         Real pv[NC];
@@ -1113,23 +1195,23 @@ __global__ void __launch_bounds__(kTX* kRedTY) reduce_partial(StepArgs A,
 #pragma unroll
         for (int i = 0; i < NC; ++i) rho_prev[(size_t)i * nxy + (size_t)y * nx + x] = r[i];
     }
-    __shared__ Real red[kRedTY][NC + 2];
+    __shared__ Sum2<Real> red[kRedTY][NC + 2];
     diag_warp<NC, Real>(acc, red[threadIdx.y]);
     __syncthreads();
     const int tid = threadIdx.y * kTX + threadIdx.x;
     if (tid < NC + 2)
-        partial[(size_t)(blockIdx.y * gridDim.x + blockIdx.x) * (NC + 2) + tid] = diag_strip<NC, Real>(red, 0, tid);
+        partial[(size_t)(blockIdx.y * gridDim.x + blockIdx.x) * (NC + 2) + tid] = diag_strip<NC, Real>(red, 0, tid, 0);
 }
 
 constexpr int kFinalThreads = 256;
 
-template <int NC, typename Real>
-__global__ void __launch_bounds__(kFinalThreads) reduce_final(const Real* __restrict__ partial, int nblocks,
+template <int NC>
+__global__ void __launch_bounds__(kFinalThreads) reduce_final(const double* __restrict__ partial, int nblocks,
                                                                double* __restrict__ out) {
     // block k sums quantity k over all strips in double: fixed strided order, then a fixed tree
     const int k = blockIdx.x;
     double v = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += kFinalThreads) v += (double)partial[(size_t)b * (NC + 2) + k];
+    for (int b = threadIdx.x; b < nblocks; b += kFinalThreads) v += partial[(size_t)b * (NC + 2) + k];
     __shared__ double red[kFinalThreads / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);

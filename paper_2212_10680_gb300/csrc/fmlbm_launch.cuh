@@ -60,30 +60,25 @@ cudaError_t launch_init(const StepArgs& A, int nc, const double* rho, cudaStream
 template <int ST>
 cudaError_t launch_convert(const StepArgs& A, int nc, const double* gin_d, double* gout_d, bool to_storage,
                            cudaStream_t s);
-// rho_prev and partial: values of the storage arithmetic type (double for FP64, else
-// float); rho_prev NC * nx * ny of them, partial (NC + 2) * reduce_blocks(nx, ny).
+// rho_prev: NC * nx * ny values of the storage arithmetic type (double for FP64, else float);
+// partial: (NC + 2) * reduce_blocks(nx, ny) doubles.
 template <int ST>
 cudaError_t launch_reduce(const StepArgs& A, int nc, void* rho_prev, int have_prev, void* partial,
                           double* out, cudaStream_t s);
 
-// The fixed-order final sum alone, for partial sums a fused step wrote (A.diag_partial).
-template <typename Real>
-inline cudaError_t launch_reduce_final_t(int nc, const void* partial, int nb, double* out, cudaStream_t s) {
-    const Real* p = static_cast<const Real*>(partial);
+// The fixed-order final sum alone, for partial sums a fused step wrote (A.diag_partial):
+// (NC + 2) doubles per 32 x 8 strip.
+inline cudaError_t launch_reduce_final(int nc, const void* partial, int nx, int ny, double* out, cudaStream_t s) {
+    const int nb = reduce_blocks(nx, ny);
+    const double* p = static_cast<const double*>(partial);
     switch (nc) {
-        case 1: reduce_final<1, Real><<<1 + 2, kFinalThreads, 0, s>>>(p, nb, out); break;
-        case 2: reduce_final<2, Real><<<2 + 2, kFinalThreads, 0, s>>>(p, nb, out); break;
-        case 3: reduce_final<3, Real><<<3 + 2, kFinalThreads, 0, s>>>(p, nb, out); break;
-        case 4: reduce_final<4, Real><<<4 + 2, kFinalThreads, 0, s>>>(p, nb, out); break;
+        case 1: reduce_final<1><<<1 + 2, kFinalThreads, 0, s>>>(p, nb, out); break;
+        case 2: reduce_final<2><<<2 + 2, kFinalThreads, 0, s>>>(p, nb, out); break;
+        case 3: reduce_final<3><<<3 + 2, kFinalThreads, 0, s>>>(p, nb, out); break;
+        case 4: reduce_final<4><<<4 + 2, kFinalThreads, 0, s>>>(p, nb, out); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
-}
-inline cudaError_t launch_reduce_final(int nc, bool fp64, const void* partial, int nx, int ny, double* out,
-                                       cudaStream_t s) {
-    const int nb = reduce_blocks(nx, ny);
-    return fp64 ? launch_reduce_final_t<double>(nc, partial, nb, out, s)
-                : launch_reduce_final_t<float>(nc, partial, nb, out, s);
 }
 
 #define FMLBM_DEFINE_LAUNCHERS(ST)                                                                        \
@@ -96,7 +91,7 @@ inline cudaError_t launch_reduce_final(int nc, bool fp64, const void* partial, i
         auto k = fused_step<NC, ST, TY, MOM, STD>;                                                        \
         FMLBM_ENSURE_SMEM(k, smem);                                                                       \
         dim3 grid((A.nx + kTX - 1) / kTX, (A.ny + TY - 1) / TY);                                          \
-        const Planes P = make_planes(A, NC, ST == ST_F16DEV || ST == ST_BF16DEV,                          \
+        const Planes P = make_planes(A, NC, kDev16<ST>,                                                   \
                                      ST == ST_F64 ? 8 : (ST == ST_F32 ? 4 : 2));                          \
         k<<<grid, dim3(kTX, TY), smem, s>>>(A, P);                                                        \
         return cudaGetLastError();                                                                        \
@@ -163,9 +158,9 @@ inline cudaError_t launch_reduce_final(int nc, bool fp64, const void* partial, i
         using Real = typename StoreTraits<ST>::Real;                                                      \
         dim3 grid((A.nx + kTX - 1) / kTX, (A.ny + kRedTY - 1) / kRedTY);                                  \
         reduce_partial<NC, ST><<<grid, dim3(kTX, kRedTY), 0, s>>>(A, static_cast<Real*>(rho_prev),        \
-                                                                   have_prev, static_cast<Real*>(partial)); \
-        reduce_final<NC, Real><<<NC + 2, kFinalThreads, 0, s>>>(static_cast<const Real*>(partial),        \
-                                                                 reduce_blocks(A.nx, A.ny), out);         \
+                                                                   have_prev, static_cast<double*>(partial)); \
+        reduce_final<NC><<<NC + 2, kFinalThreads, 0, s>>>(static_cast<const double*>(partial),             \
+                                                          reduce_blocks(A.nx, A.ny), out);                \
         return cudaGetLastError();                                                                        \
     }                                                                                                     \
     template <>                                                                                           \

@@ -298,10 +298,10 @@ __global__ void __launch_bounds__(kTX* TY, NPARK > 0 ? 4 : 3) fused_step_pair(St
     // ---- diagnostics of the state this step read (uniform in diag) ----
     if (diag) {
         static_assert(TY % 8 == 0, "diagnostics strips of 8 rows");
-        __shared__ V dred[TY][NC + 2];
-        V acc[NC + 2];
+        __shared__ Sum2<V> dred[TY][NC + 2];
+        Sum2<V> acc[NC + 2];
 #pragma unroll
-        for (int k = 0; k < NC + 2; ++k) acc[k] = vbc<V>(0.f);
+        for (int k = 0; k < NC + 2; ++k) acc[k] = s2_of(vbc<V>(0.f));
         if (valid0) {
             asm volatile("cp.async.wait_all;\n" ::: "memory");
             V pv[NC];
@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(kTX* TY, NPARK > 0 ? 4 : 3) fused_step_pair(St
             diag_node<NC, V>(r, pv, A.have_prev, acc);
             if (!valid1)
 #pragma unroll
-                for (int k = 0; k < NC + 2; ++k) acc[k].y = 0.f;
+                for (int k = 0; k < NC + 2; ++k) acc[k].hi.y = acc[k].lo.y = 0.f;
             float* prev = static_cast<float*>(A.rho_prev);
             const int node0 = gy * nx + gx0;
 #pragma unroll
@@ -327,11 +327,9 @@ __global__ void __launch_bounds__(kTX* TY, NPARK > 0 ? 4 : 3) fused_step_pair(St
             const int half = tid / (STRIPS * (NC + 2)), q = tid % (STRIPS * (NC + 2));
             const int sub = q / (NC + 2), k = q % (NC + 2);
             const int col = 2 * blockIdx.x + half;
-            if (col < tiles_x && y0 + 8 * sub < ny) {
-                const V s = diag_strip<NC, V>(dred, 8 * sub, k);
-                static_cast<float*>(A.diag_partial)[((size_t)(blockIdx.y * STRIPS + sub) * tiles_x + col) * (NC + 2) +
-                                                    k] = half == 0 ? s.x : s.y;
-            }
+            if (col < tiles_x && y0 + 8 * sub < ny)
+                static_cast<double*>(A.diag_partial)[((size_t)(blockIdx.y * STRIPS + sub) * tiles_x + col) * (NC + 2) +
+                                                     k] = diag_strip<NC, V>(dred, 8 * sub, k, half);
         }
     }
 }

@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kTX* TY, MINB)
                         const Real v = stage_value<NC, ST, TY>(st, i, a, by + 1 - ey(a), bx + 2 - ex(a));
                         rt[i] = a == 0 ? v : vadd(rt[i], v);  // the order of pull_rho
                     }
-                phase1_ring<NC, TY, Real>(m, S, rt, bx, by);
+                phase1_ring<NC, TY, Real>(A, m, S, rt, bx, by);
             }
         } else {
             phase1_global<NC, ST, TY>(A, m, S, g, r, jx, jy, x0, y0, is_inner(x0, y0), tx, ty, tid);

@@ -21,7 +21,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfmlbm.s
 
 EOS = {"pr": 0, "srk": 1, "vdw": 2}
 STENCIL = {"isotropic": 0, "central": 1}
-PRECISION = {"fp64": 0, "fp32": 1, "fp16dev": 2, "bf16dev": 3}
+PRECISION = {"fp64": 0, "fp32": 1, "fp16dev": 2, "bf16dev": 3, "fp16dev_lnf64": 4, "bf16dev_lnf64": 5}
 VELOCITY_FORCE = {"lagged": 0, "current": 1}
 FORMULATION = {"well_balanced": 0, "standard": 1}
 STATUS = {0: "FMLBM_OK", 1: "FMLBM_E_INVALID_ARG", 2: "FMLBM_E_OOM", 3: "FMLBM_E_CUDA",

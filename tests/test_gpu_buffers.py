@@ -66,6 +66,9 @@ def test_caller_buffers_are_checked(fm):
         ("fp32", dict(g=[host.ctypes.data] * 2, g0=None, force=_addr(ft))),              # host memory
         ("fp32", dict(g=_addr(gt), g0=_addr(g0t), force=_addr(ft))),                     # a = 0 planes not used
         ("bf16dev", dict(g=_addr(gt), g0=None, force=_addr(ft))),                        # a = 0 planes missing
+        ("fp32", dict(g=[_addr(gt)[0]] * 2, g0=None, force=_addr(ft))),                  # both steps in one buffer
+        ("fp32", dict(g=_addr(gt), g0=None, force=[_addr(ft)[1]] * 2)),                  # one force buffer twice
+        ("fp32", dict(g=_addr(gt), g0=None, force=[_addr(gt)[0], _addr(ft)[1]])),        # force inside g
     ]
     for prec, bufs in bad:
         with pytest.raises(fm.FmlbmError) as ei:

@@ -10,11 +10,11 @@ The densities carry the sum of the nine rounding errors of each node.
 import numpy as np
 import pytest
 
-from cases import run_oracle, slab_state_binary, workloads
+from cases import oracle_mixture, run_oracle, slab_state_binary, workloads
 
 pytestmark = pytest.mark.gpu
 
-EPS16 = {"fp16dev": 2.0 ** -11, "bf16dev": 2.0 ** -8}
+EPS16 = {"fp16dev": 2.0 ** -11, "bf16dev": 2.0 ** -8, "fp16dev_lnf64": 2.0 ** -11, "bf16dev_lnf64": 2.0 ** -8}
 
 
 @pytest.fixture(scope="module")
@@ -25,7 +25,7 @@ def fm():
     return fmlbm
 
 
-@pytest.mark.parametrize("precision", ["fp16dev", "bf16dev"])
+@pytest.mark.parametrize("precision", ["fp16dev", "bf16dev", "fp16dev_lnf64", "bf16dev_lnf64"])
 def test_deviation_storage_parity(fm, precision):
     mixd, rho = slab_state_binary(70, 37, seed=11)
     rec = (1, 5, 20)
@@ -47,7 +47,7 @@ def test_deviation_storage_parity(fm, precision):
     lat.close()
 
 
-@pytest.mark.parametrize("precision", ["fp16dev", "bf16dev"])
+@pytest.mark.parametrize("precision", ["fp16dev", "bf16dev", "bf16dev_lnf64"])
 def test_deviation_storage_conserves_mass_to_float_rounding(fm, precision):
     wl = workloads()["ternary"]
     from paper_2212_10680_gb300 import inputs
@@ -62,3 +62,26 @@ def test_deviation_storage_conserves_mass_to_float_rounding(fm, precision):
     # the rounding of the streamed deviations over the run
     assert np.max(np.abs(m1 / m0 - 1)) < 200 * EPS16[precision] * 0.05
     lat.close()
+
+
+@pytest.mark.parametrize("precision", ["fp16dev_lnf64", "bf16dev_lnf64"])
+def test_lnf64_forms_evaluate_ln_f_in_double(fm, precision):
+    # The _LNF64 forms evaluate ln f (Eq. eqfugupdatePR) in double from the float densities and
+    # round it to float once: at every node it is the definition (the oracle's ln f at the same
+    # densities, in FP64) rounded to float, to within one float ulp.  The all-float form carries
+    # the rounding of its float evaluation on top (several ulp at some nodes).
+    from oracle.eos import lnf_density_form
+    mixd, rho = slab_state_binary(70, 37, seed=12)
+    assert mixd["M"] == [1.0, 1.0]          # rho~_i = rho_i: the densities are the GPU's own floats
+    worst = {}
+    for prec in (precision, precision.replace("_lnf64", "")):
+        lat = fm.Lattice(fm.mixture_from_dict(mixd), 70, 37, 1.0, "isotropic", prec, "lagged")
+        lat.init(rho)
+        lat.step(3)
+        r, _, lnf = lat.moments()
+        lat.close()
+        ref = lnf_density_form(oracle_mixture(mixd), r).astype(np.float32)
+        ulp = np.spacing(np.abs(ref))
+        worst[prec] = float(np.max(np.abs(lnf.astype(np.float32) - ref) / ulp))
+    assert worst[precision] <= 1.0, worst
+    assert worst[precision.replace("_lnf64", "")] > worst[precision], worst

@@ -20,7 +20,7 @@ from cases import slab_state_binary
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5}
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp16dev": 1e-5, "bf16dev": 1e-5}
 # D2Q9 directions in the library's order
 E = [(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)]
 
@@ -41,26 +41,35 @@ def env():
     return torch, fmlbm
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16dev", "bf16dev"])
 def test_noalloc_matches_diagnostics_twice(env, precision):
     torch, fm = env
     nx, ny = 96, 40
     mixd, rho = slab_state_binary(nx, ny, seed=21)
     n = len(mixd["Tc"])
-    dtype = torch.float64 if precision == "fp64" else torch.float32
+    dtype = torch.float64 if precision == "fp64" else torch.float32   # the storage arithmetic type
+    dev16 = {"fp16dev": torch.float16, "bf16dev": torch.bfloat16}.get(precision)
     lat = fm.Lattice(fm.mixture_from_dict(mixd), nx, ny, 1.0, "isotropic", precision, "lagged")
     lat.init(rho)
-    rho_prev = torch.zeros(n * ny * nx, dtype=dtype, device="cuda")   # the storage arithmetic type
+    rho_prev = torch.zeros(n * ny * nx, dtype=dtype, device="cuda")
     out = torch.zeros(n + 2, dtype=torch.float64, device="cuda")
     have_prev = False
     for steps in (10, 7):
         lat.step(steps)
         g, _ = lat.distributions()
         mass_ref, res_ref, _ = lat.diagnostics()
-        buf = torch.tensor(storage_layout(g), dtype=dtype, device="cuda").contiguous()
+        stored = storage_layout(g)
+        g0 = None
+        if dev16 is None:
+            buf = torch.tensor(stored, dtype=dtype, device="cuda").contiguous()
+        else:
+            # the deviation forms keep a = 0 in float planes [N][ny][nx] and a = 1..8 in 16-bit
+            # planes [N][8][ny][nx]; the handle's values convert exactly to either
+            buf = torch.tensor(stored[:, 1:], dtype=dev16, device="cuda").contiguous()
+            g0 = torch.tensor(stored[:, 0], dtype=torch.float32, device="cuda").contiguous()
         torch.cuda.synchronize()
-        fm.fmlbm_diagnostics_noalloc(n, nx, ny, precision, buf.data_ptr(), 0, rho_prev.data_ptr(), have_prev,
-                                     out.data_ptr(), 0)
+        fm.fmlbm_diagnostics_noalloc(n, nx, ny, precision, buf.data_ptr(), 0 if g0 is None else g0.data_ptr(),
+                                     rho_prev.data_ptr(), have_prev, out.data_ptr(), 0)
         torch.cuda.synchronize()
         res = out.cpu().numpy()
         mass = res[:n]
@@ -84,3 +93,14 @@ def test_noalloc_rejects_lattices_beyond_its_fixed_scratch(env):
     assert ei.value.status == 1
     with pytest.raises(fm.FmlbmError):
         fm.fmlbm_diagnostics_noalloc(2, 8, 8, "fp32", 0, 0, tiny.data_ptr(), False, tiny.data_ptr(), 0)
+    # buffers smaller than the lattice, host memory, and the deviation forms without their a = 0 planes
+    with pytest.raises(fm.FmlbmError) as ei:
+        fm.fmlbm_diagnostics_noalloc(2, 64, 64, "fp32", tiny.data_ptr(), 0, tiny.data_ptr(), False, tiny.data_ptr(), 0)
+    assert ei.value.status == 1
+    host = np.zeros(1 << 16, dtype=np.float64)
+    with pytest.raises(fm.FmlbmError) as ei:
+        fm.fmlbm_diagnostics_noalloc(1, 4, 4, "fp64", host.ctypes.data, 0, tiny.data_ptr(), False, tiny.data_ptr(), 0)
+    assert ei.value.status == 1
+    with pytest.raises(fm.FmlbmError) as ei:
+        fm.fmlbm_diagnostics_noalloc(1, 4, 4, "bf16dev", tiny.data_ptr(), 0, tiny.data_ptr(), False, tiny.data_ptr(), 0)
+    assert ei.value.status == 1
