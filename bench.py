@@ -31,7 +31,9 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-ALGO_BYTES = {"fp64": 144.0, "fp32": 72.0, "fp16dev": 40.0, "bf16dev": 40.0}  # per component-node update
+# per component-node update: one read and one write of the nine distributions
+ALGO_BYTES = {"fp64": 144.0, "fp32": 72.0, "fp16dev": 40.0, "bf16dev": 40.0, "fp16dev_lnf64": 40.0,
+              "bf16dev_lnf64": 40.0}
 L2_FLUSH_BYTES = 256 << 20
 KERNEL_SOURCES = ["paper_2212_10680_gb300/csrc/fmlbm_lanes.cuh", "paper_2212_10680_gb300/csrc/fmlbm_kernels.cuh",
                   "paper_2212_10680_gb300/csrc/fmlbm_pair.cuh", "paper_2212_10680_gb300/csrc/fmlbm_launch.cuh",

@@ -93,9 +93,12 @@ def test_noalloc_rejects_lattices_beyond_its_fixed_scratch(env):
     assert ei.value.status == 1
     with pytest.raises(fm.FmlbmError):
         fm.fmlbm_diagnostics_noalloc(2, 8, 8, "fp32", 0, 0, tiny.data_ptr(), False, tiny.data_ptr(), 0)
-    # buffers smaller than the lattice, host memory, and the deviation forms without their a = 0 planes
+    # buffers smaller than the lattice (a 512 x 512 lattice needs 19 MB: more than the whole
+    # allocator segment the small tensor lives in, which is what the check can see), host
+    # memory, and the deviation forms without their a = 0 planes
     with pytest.raises(fm.FmlbmError) as ei:
-        fm.fmlbm_diagnostics_noalloc(2, 64, 64, "fp32", tiny.data_ptr(), 0, tiny.data_ptr(), False, tiny.data_ptr(), 0)
+        fm.fmlbm_diagnostics_noalloc(2, 512, 512, "fp32", tiny.data_ptr(), 0, tiny.data_ptr(), False,
+                                     tiny.data_ptr(), 0)
     assert ei.value.status == 1
     host = np.zeros(1 << 16, dtype=np.float64)
     with pytest.raises(fm.FmlbmError) as ei:
