@@ -461,6 +461,39 @@ fmlbm_status fmlbm_server_stats(fmlbm_server* s, int32_t* queued, int32_t* runni
 /* Stops the worker (unfinished requests are dropped) and frees everything.  NULL-safe. */
 void fmlbm_server_destroy(fmlbm_server* s);
 
+/* ------------------------------------------------------------------------------------
+ * Domain decomposition of one lattice into y-slabs.  The streaming of Eq. eqLBEMCa
+ * (Section III.B, step 9) is periodic; a lattice split into slabs needs, before each step,
+ * the rows of its neighbours its update reads.  The fused step reads distributions up to
+ * three rows away from a node (the pulls of the 2-node halo of rho~ of steps 6-7), so each
+ * slab holds its own ny / nslabs rows plus three ghost rows above and below (a lattice of
+ * ny / nslabs + 6 rows stepped by the ordinary fused step), and after every step the ghost
+ * rows of every distribution plane are refreshed from the neighbouring slabs' boundary rows
+ * by cudaMemcpy2DAsync copies (the halo exchange; between devices these would be peer
+ * copies).  The slabs' own rows then evolve bit for bit as the undivided lattice does.  All
+ * slabs live on the current device and step on cuda_stream (NULL: legacy default stream).
+ * ------------------------------------------------------------------------------------ */
+typedef struct fmlbm_decomp fmlbm_decomp;
+
+/* The rows [*y0, *y0 + *rows) of the global lattice that slab `slab` of `nslabs` owns (no GPU
+ * needed).  FMLBM_E_INVALID_ARG unless ny is a multiple of nslabs with at least 3 rows per
+ * slab. */
+fmlbm_status fmlbm_decomp_slab_rows(int32_t ny, int32_t nslabs, int32_t slab, int32_t* y0, int32_t* rows);
+/* Creates nslabs slab lattices of the global lattice (its nx, ny, tau, stencil, precision,
+ * velocity force, formulation) for the mixture, each with its own device buffers. */
+fmlbm_status fmlbm_decomp_create(const fmlbm_mixture* mixture, const fmlbm_lattice* lattice, int32_t nslabs,
+                                 void* cuda_stream, fmlbm_decomp** out);
+/* Fluid at rest (as fmlbm_init) from the global densities rho_host [N][ny][nx] (host, copied). */
+fmlbm_status fmlbm_decomp_init(fmlbm_decomp* d, const double* rho_host);
+/* nsteps time steps of every slab, each followed by the halo exchange (asynchronous). */
+fmlbm_status fmlbm_decomp_step(fmlbm_decomp* d, int64_t nsteps);
+/* The global post-streaming distributions [N][9][ny][nx] and stored force [2][ny][nx],
+ * gathered from the slabs' own rows (either pointer may be NULL; host outputs; synchronises). */
+fmlbm_status fmlbm_decomp_get_distributions(fmlbm_decomp* d, double* g_host, double* force_host);
+const char* fmlbm_decomp_last_error(const fmlbm_decomp* d);
+/* Frees the slabs and their buffers (synchronises).  NULL-safe. */
+void fmlbm_decomp_destroy(fmlbm_decomp* d);
+
 const char* fmlbm_status_str(fmlbm_status s);
 const char* fmlbm_last_error(const fmlbm_handle* h);
 

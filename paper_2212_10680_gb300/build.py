@@ -19,7 +19,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libfmlbm.so")
 
 SOURCES = ["api.cu", "step_f64.cu", "step_f32.cu", "step_f16.cu", "step_bf16.cu", "step_f16x.cu", "step_bf16x.cu",
-           "noalloc.cu", "batch.cu", "serve.cu"]
+           "noalloc.cu", "batch.cu", "serve.cu", "decomp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no multiply-add is formed that the source does not write.  The step kernels
 # spell out every fused multiply-add (fmlbm_lanes.cuh), so that the one-node and the paired

@@ -145,6 +145,15 @@ def _load() -> ctypes.CDLL:
         "fmlbm_status_str": ([ctypes.c_int], ctypes.c_char_p),
         "fmlbm_last_error": ([H], ctypes.c_char_p),
         "fmlbm_version": ([], ctypes.c_char_p),
+        "fmlbm_decomp_slab_rows": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "fmlbm_decomp_create": ([ctypes.POINTER(fmlbm_mixture), ctypes.POINTER(fmlbm_lattice), ctypes.c_int32,
+                                 ctypes.c_void_p, ctypes.POINTER(H)], ctypes.c_int),
+        "fmlbm_decomp_init": ([H, dp], ctypes.c_int),
+        "fmlbm_decomp_step": ([H, ctypes.c_int64], ctypes.c_int),
+        "fmlbm_decomp_get_distributions": ([H, dp, dp], ctypes.c_int),
+        "fmlbm_decomp_last_error": ([H], ctypes.c_char_p),
+        "fmlbm_decomp_destroy": ([H], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -540,6 +549,61 @@ class Lattice:
         if self.h:
             fmlbm_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- domain decomposition of one lattice into y-slabs (fmlbm.h: fmlbm_decomp_*) ----
+
+def fmlbm_decomp_slab_rows(ny: int, nslabs: int, slab: int):
+    """(first row, row count) of the global lattice that slab `slab` owns; needs no GPU."""
+    y0, rows = ctypes.c_int32(), ctypes.c_int32()
+    _check(LIB.fmlbm_decomp_slab_rows(ny, nslabs, slab, ctypes.byref(y0), ctypes.byref(rows)),
+           "fmlbm_decomp_slab_rows")
+    return y0.value, rows.value
+
+
+def _dcheck(status: int, where: str, d=None):
+    if status != 0:
+        msg = LIB.fmlbm_decomp_last_error(d).decode() if d else ""
+        raise FmlbmError(status, where, msg)
+
+
+class Decomposition:
+    """One lattice split into nslabs y-slabs with ghost rows exchanged after every step."""
+
+    def __init__(self, mixture: fmlbm_mixture, nx: int, ny: int, tau: float, nslabs: int, stencil: str = "isotropic",
+                 precision: str = "fp32", velocity_force: str = "lagged", stream: int = 0):
+        self.n, self.nx, self.ny = mixture.n_components, nx, ny
+        lat = make_lattice(nx, ny, tau, stencil, precision, velocity_force)
+        self.d = ctypes.c_void_p()
+        _dcheck(LIB.fmlbm_decomp_create(ctypes.byref(mixture), ctypes.byref(lat), nslabs, ctypes.c_void_p(stream or None),
+                                        ctypes.byref(self.d)), "fmlbm_decomp_create")
+
+    def init(self, rho: np.ndarray):
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        _dcheck(LIB.fmlbm_decomp_init(self.d, rho.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+                "fmlbm_decomp_init", self.d)
+
+    def step(self, n: int = 1):
+        _dcheck(LIB.fmlbm_decomp_step(self.d, n), "fmlbm_decomp_step", self.d)
+
+    def distributions(self):
+        g = np.empty((self.n, 9, self.ny, self.nx))
+        F = np.empty((2, self.ny, self.nx))
+        dp_ = ctypes.POINTER(ctypes.c_double)
+        _dcheck(LIB.fmlbm_decomp_get_distributions(self.d, g.ctypes.data_as(dp_), F.ctypes.data_as(dp_)),
+                "fmlbm_decomp_get_distributions", self.d)
+        return g, F
+
+    def close(self):
+        if self.d:
+            LIB.fmlbm_decomp_destroy(self.d)
+            self.d = None
 
     def __del__(self):
         try:

@@ -89,3 +89,44 @@ def test_timeline_downsampling_keeps_the_ends():
     assert len(out) == 5 and out[0] == [0.0, 0] and out[-1] == [0.99, 990]
     assert bench._downsample(pts[:3], 40) == [[0.0, 0], [0.01, 10], [0.02, 20]]
     assert bench._downsample([], 40) == []
+
+
+def _slab_rank_main(rank, world, port, out_dir, ny):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    from paper_2212_10680_gb300 import fmlbm
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        y0, rows = fmlbm.fmlbm_decomp_slab_rows(ny, world, rank)      # host-only: no GPU
+        parts = [None] * world
+        dist.all_gather_object(parts, (y0, rows))
+        with open(os.path.join(out_dir, f"slab{rank}.json"), "w") as f:
+            json.dump(dict(mine=[y0, rows], all=parts), f)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,ny", [(2, 64), (2, 6), (3, 36)])
+def test_slab_rows_over_gloo_ranks(tmp_path, world, ny):
+    # one y-slab of a decomposed lattice per rank: the slabs cover the rows once, in rank
+    # order, and the three ghost rows below and above a rank's slab are the boundary rows of
+    # ranks r - 1 and r + 1 (periodic), which the halo exchange brings in
+    import torch.multiprocessing as mp
+    mp.start_processes(_slab_rank_main, args=(world, _free_port(), str(tmp_path), ny), nprocs=world, join=True,
+                       start_method="spawn")
+    got = [json.load(open(tmp_path / f"slab{r}.json")) for r in range(world)]
+    parts = [tuple(p) for p in got[0]["all"]]
+    assert all([tuple(p) for p in g["all"]] == parts for g in got)
+    owner = {}
+    for r, (y0, rows) in enumerate(parts):
+        assert tuple(got[r]["mine"]) == (y0, rows)
+        for y in range(y0, y0 + rows):
+            assert y not in owner
+            owner[y] = r
+    assert sorted(owner) == list(range(ny))
+    for r, (y0, rows) in enumerate(parts):
+        below = [(y0 - k) % ny for k in (3, 2, 1)]
+        above = [(y0 + rows + k) % ny for k in (0, 1, 2)]
+        assert {owner[y] for y in below} == {(r - 1) % world}
+        assert {owner[y] for y in above} == {(r + 1) % world}
