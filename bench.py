@@ -276,35 +276,32 @@ def run_reference(args, w, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args, w, rank, world, dist):
-    import torch
-    from paper_2212_10680_gb300 import fmlbm
-
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
-    torch.cuda.set_device(dev)
-    stream = torch.cuda.current_stream()
-    prec = args.precision or w["precision"]
+def _device_steps(fmlbm, torch, w, prec, steps, warmup, stream, dev, variant=None, autotune=True, flush=None,
+                  dist=None, tile_y=0):
+    """K single-step launches of one lattice of workload w timed with CUDA events on the
+    launching stream (L2 flushed between them, untimed), after the warm-up (and the
+    autotuner's trial steps, which are real steps).  Returns the per-step times and the
+    kernel choice; the lattice is closed."""
     n = len(w["mixture"]["Tc"])
-    nx, ny = w["nx"], w["ny"]
-    nodes = nx * ny
-    lat = fmlbm.Lattice(fmlbm.mixture_from_dict(w["mixture"]), nx, ny, w["tau"], w["stencil"], prec, "lagged",
-                        stream=stream.cuda_stream)
-    if args.tile_y:
-        fmlbm.fmlbm_set_tile_height(lat.h, args.tile_y)
+    lat = fmlbm.Lattice(fmlbm.mixture_from_dict(w["mixture"]), w["nx"], w["ny"], w["tau"], w["stencil"], prec,
+                        "lagged", stream=stream.cuda_stream)
+    if tile_y:
+        fmlbm.fmlbm_set_tile_height(lat.h, tile_y)
     rho_dev = torch.from_numpy(w["rho"]).to(dev)
     fmlbm.fmlbm_init_device(lat.h, rho_dev.data_ptr())
     tuned = None
-    if args.variant:
-        fmlbm.fmlbm_set_step_variant(lat.h, args.variant)
-    else:
-        # the autotuner's trial steps are real (untimed) steps, part of the warm-up
+    if variant:
+        fmlbm.fmlbm_set_step_variant(lat.h, variant)
+    elif autotune:
         v, ty, ms = fmlbm.fmlbm_autotune(lat.h, 5)
         tuned = dict(variant=v, tile_y=ty, ms_per_step=ms)
-    variant = fmlbm.fmlbm_get_step_variant(lat.h)
-    lat.step(args.warmup)
+    chosen = fmlbm.fmlbm_get_step_variant(lat.h)
+    lat.step(warmup)
     lat.synchronize()
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    del rho_dev
+    if flush is None:
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
 
     def barrier():
         if dist is not None:
@@ -313,7 +310,7 @@ def run_ours(args, w, rank, world, dist):
 
     barrier()
     with ClockSampler(dev.index) as clk:
-        for k in range(args.steps):
+        for k in range(steps):
             # evict the previous step's data from L2 (untimed): write a buffer twice the L2
             # size, then read it, so that the lines left in L2 are clean and none is the step's
             # (after a write alone the timed step would also pay the write-back of 129 MB of
@@ -326,6 +323,154 @@ def run_ours(args, w, rank, world, dist):
         barrier()
     ms = [a.elapsed_time(b) for a, b in ev]
     lat.synchronize()
+    lat.close()
+    return dict(ms=ms, variant=chosen, tuned=tuned, clocks=clk.summary(), n=n, nodes=w["nx"] * w["ny"])
+
+
+def _e2e_rate(fmlbm, torch, w, prec, steps, stream, dev, dist=None):
+    """The same metric end to end through the C ABI with host buffers: fmlbm_init from pinned
+    host memory, then per step one fmlbm_step and one fmlbm_diagnostics_async, each ticket read
+    with fmlbm_diagnostics_wait three steps later (the device-to-host copy of masses, residual
+    and error latch); every step's result reaches the host inside the timed region."""
+    n = len(w["mixture"]["Tc"])
+    lat = fmlbm.Lattice(fmlbm.mixture_from_dict(w["mixture"]), w["nx"], w["ny"], w["tau"], w["stencil"], prec,
+                        "lagged", stream=stream.cuda_stream)
+    rho_np = torch.from_numpy(w["rho"]).pin_memory().numpy()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fmlbm.fmlbm_init(lat.h, rho_np)
+    tickets = []
+    for k in range(steps):
+        fmlbm.fmlbm_step(lat.h, 1)
+        tickets.append(fmlbm.fmlbm_diagnostics_async(lat.h))
+        if k >= 3:
+            fmlbm.fmlbm_diagnostics_wait(lat.h, tickets[k - 3], n)
+    for t in tickets[max(0, steps - 3):]:
+        fmlbm.fmlbm_diagnostics_wait(lat.h, t, n)
+    torch.cuda.synchronize()
+    el = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    lat.close()
+    world = dist.get_world_size() if dist is not None else 1
+    nodes = w["nx"] * w["ny"]
+    return dict(value=n * nodes * steps * world / el / 1e9, unit="component-GLUPS", steps=steps,
+                h2d_bytes_per_step=n * nodes * 8 / steps, d2h_bytes_per_step=64)
+
+
+def _oracle_worker(args):
+    """One process: the FP64 oracle as it stands on a sample lattice of a workload, for about
+    `seconds`; returns component-node updates and elapsed seconds."""
+    wname, size, seconds = args
+    w = workload(wname)
+    from oracle import lbm
+    from oracle.eos import Mixture
+    d = w["mixture"]
+    n = len(d["Tc"])
+    mix = Mixture(d["eos"], d["R"], d["T"], Tc=d["Tc"], Pc=d["Pc"], omega=d["omega"], M=d["M"], kappa=d["kappa"],
+                  kij=np.asarray(d["kij"]).reshape(n, n))
+    lat = lbm.Lattice(tau=w["tau"], stencil=w["stencil"], velocity_force="lagged")
+    rho = sample_field(w, size)
+    g, F = lbm.init_at_rest(rho)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        g, F = lbm.step(g, mix, lat, F)
+        steps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    return n * size * size * steps, time.perf_counter() - t0, steps
+
+
+def cpu_oracle_all_cores(wname: str, seconds: float = 8.0, size: int = 256):
+    """The oracle on every host core: one independent sample lattice per core (a pool of
+    spawned processes; the oracle itself is single-threaded numpy), aggregate rate."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(cores, initializer=_pool_init) as pool:
+        res = pool.map(_oracle_worker, [(wname, size, seconds)] * cores)
+    units = sum(r[0] for r in res)
+    el = max(r[1] for r in res)
+    return dict(value=units / el / 1e9, unit="component-GLUPS", cores=cores, kind="oracle",
+                sample=f"{cores} processes, each {min(r[2] for r in res)}-{max(r[2] for r in res)} FP64 oracle steps "
+                       f"of its own {size}x{size} lattice of the workload's mixture and initial-field recipe "
+                       f"({el:.1f} s, numpy, one thread each)")
+
+
+def _pool_init():
+    os.environ["OMP_NUM_THREADS"] = "1"
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+
+
+def small_binary_fp64(fmlbm, torch, stream, dev, gpu_steps=2000, oracle_steps=20):
+    """The small parity configuration (64 x 64 binary slab, FP64, tau 1): GPU and oracle
+    milliseconds per step on the same lattice (the GPU run is latency-bound: 4,096 nodes)."""
+    from paper_2212_10680_gb300 import inputs
+    wl = json.load(open(os.path.join(ROOT, "tests", "golden", "workloads.json")))["binary"]
+    rho = inputs.with_noise(inputs.slab(wl["slab"]["rt_vapour"], wl["slab"]["rt_liquid"], 64, 64, 0.5, 4.0), 0.01, 1)
+    lat = fmlbm.Lattice(fmlbm.mixture_from_dict(wl["mixture"]), 64, 64, 1.0, "isotropic", "fp64", "lagged",
+                        stream=stream.cuda_stream)
+    lat.init(rho)
+    lat.step(10)
+    lat.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(gpu_steps)
+    e1.record(stream)
+    lat.synchronize()
+    gpu_ms = e0.elapsed_time(e1) / gpu_steps
+    lat.close()
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from oracle import lbm
+    from oracle.eos import Mixture
+    d = wl["mixture"]
+    mix = Mixture(d["eos"], d["R"], d["T"], Tc=d["Tc"], Pc=d["Pc"], omega=d["omega"], M=d["M"], kappa=d["kappa"],
+                  kij=np.asarray(d["kij"]).reshape(2, 2))
+    g, F = lbm.init_at_rest(rho)
+    olat = lbm.Lattice(tau=1.0, stencil="isotropic", velocity_force="lagged")
+    t0 = time.perf_counter()
+    for _ in range(oracle_steps):
+        g, F = lbm.step(g, mix, olat, F)
+    oracle_ms = 1e3 * (time.perf_counter() - t0) / oracle_steps
+    return dict(workload="binary PR flat slab 64x64, FP64, tau 1, isotropic, lagged", gpu_ms_per_step=gpu_ms,
+                gpu_steps=gpu_steps, oracle_ms_per_step=oracle_ms, oracle_steps=oracle_steps,
+                note="GPU: launch-bound (4,096 nodes per step); oracle: numpy, one thread")
+
+
+def ternary_forms(fmlbm, torch, stream, dev, steps, warmup, flush):
+    """The 4096 x 4096 ternary slab in every storage form: component-GLUPS and the fraction of
+    the measured HBM bandwidth by each form's own algorithmic bytes."""
+    w = workload("ternary4096")
+    peak = measured_peaks()
+    out = {}
+    for prec in ("fp32", "fp16dev", "bf16dev", "bf16dev_lnf64"):
+        k = max(3, steps // 2) if prec.endswith("lnf64") else steps
+        r = _device_steps(fmlbm, torch, w, prec, k, warmup, stream, dev, variant="plain", flush=flush)
+        per = sum(r["ms"]) / 1e3 / k
+        achieved = ALGO_BYTES[prec] * r["n"] * r["nodes"] / per / 1e9
+        out[prec] = dict(value=r["n"] * r["nodes"] / per / 1e9, unit="component-GLUPS", ms_per_step=1e3 * per,
+                         steps=k, roofline=dict(bound="hbm", achieved=achieved, peak=peak["hbm_gbs"], unit="GB/s",
+                                                frac=achieved / peak["hbm_gbs"],
+                                                algorithmic_bytes_per_component_node=ALGO_BYTES[prec]),
+                         clocks=r["clocks"])
+    return dict(workload=w["name"] + ", tau 1, isotropic, lagged, plain step", forms=out)
+
+
+def run_ours(args, w, rank, world, dist):
+    import torch
+    from paper_2212_10680_gb300 import fmlbm
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    prec = args.precision or w["precision"]
+    n = len(w["mixture"]["Tc"])
+    nx, ny = w["nx"], w["ny"]
+    nodes = nx * ny
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    r = _device_steps(fmlbm, torch, w, prec, args.steps, args.warmup, stream, dev, variant=args.variant,
+                      flush=flush, dist=dist, tile_y=args.tile_y)
+    ms, variant, tuned = r["ms"], r["variant"], r["tuned"]
     total_s = max_over_ranks(sum(ms) / 1e3, dist, dev)
     units = n * nodes * args.steps * world
     value = units / total_s / 1e9
@@ -337,38 +482,26 @@ def run_ours(args, w, rank, world, dist):
                                                                                                      "fused_step")
     # the committed counters describe the workload at its own size only
     traffic = None if args.size else profile_traffic(kernel_name, args.workload, prec)
+    e2e = _e2e_rate(fmlbm, torch, w, prec, args.steps, stream, dev, dist)
+    e2e_long = _e2e_rate(fmlbm, torch, w, prec, max(args.steps, args.e2e_steps), stream, dev, dist)
 
-    # end to end through the public API with host buffers: H2D of the initial field from
-    # pinned memory, then per step one update and the D2H read of that step's diagnostics
-    # (component masses, residual, error latch).  Each state's diagnostics are requested
-    # asynchronously, computed inside the next step's kernel (final sum and copy on the
-    # handle's diagnostics stream) and read three steps behind, so the GPU never waits for
-    # the host; every step's result reaches the host inside the timed region (the last one
-    # by the separate reduction).
-    rho_pinned = torch.from_numpy(w["rho"]).pin_memory()
-    rho_np = rho_pinned.numpy()
-    e2e_steps = args.steps
-    barrier()
-    t0 = time.perf_counter()
-    fmlbm.fmlbm_init(lat.h, rho_np)
-    tickets = []
-    for k in range(e2e_steps):
-        fmlbm.fmlbm_step(lat.h, 1)
-        tickets.append(fmlbm.fmlbm_diagnostics_async(lat.h))
-        if k >= 3:
-            fmlbm.fmlbm_diagnostics_wait(lat.h, tickets[k - 3], n)
-    for t in tickets[max(0, e2e_steps - 3):]:
-        fmlbm.fmlbm_diagnostics_wait(lat.h, t, n)
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
-    e2e_value = n * nodes * e2e_steps * world / e2e_s / 1e9
-    lat.close()
+    configs = None
+    if world == 1 and not args.no_configs and args.workload == "droplet1024":
+        configs = dict(small_binary_fp64=small_binary_fp64(fmlbm, torch, stream, dev),
+                       ternary_4096=ternary_forms(fmlbm, torch, stream, dev, max(10, min(args.steps, 20)),
+                                                  max(3, args.warmup), flush))
+        del flush
+        torch.cuda.empty_cache()
+        configs["batch_sweep"] = run_batch(args, rank, world, dist, summary=True)
+        configs["serving"] = run_serve(args, rank, world, dist, summary=True)
 
     if rank != 0:
         return
-    cpu = None
+    cpu = cpu_all = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_rate(w, args.cpu_seconds)
+        cpu_all = cpu_oracle_all_cores(args.workload, seconds=args.cpu_seconds / 2)
+        cpu["all_cores"] = cpu_all
     line = dict(
         metric="component-GLUPS", value=value, unit="component-GLUPS", n_gpus=world, steps=args.steps,
         warmup=args.warmup, ms_per_step=1e3 * total_s / args.steps, higher_is_better=True, scaling="weak",
@@ -385,11 +518,14 @@ def run_ours(args, w, rank, world, dist):
                       algorithmic_bytes_per_component_node=ALGO_BYTES[prec],
                       kernel=kernel_name),
         cpu_baseline=cpu,
-        e2e=dict(value=e2e_value, unit="component-GLUPS",
-                 # one copy per step of the result block: N + 2 sums (room for 4 + 2) and the error latch
-                 h2d_bytes_per_step=n * nodes * 8 / e2e_steps, d2h_bytes_per_step=64),
+        e2e=dict(value=e2e["value"], unit=e2e["unit"], h2d_bytes_per_step=e2e["h2d_bytes_per_step"],
+                 d2h_bytes_per_step=e2e["d2h_bytes_per_step"]),
+        e2e_amortized=dict(e2e_long, note="the same loop over more steps: the one-time fmlbm_init (16.8 MB from "
+                                          "pinned host memory) spread over them"),
         gpu_launches=args.steps,
-        clocks=clk.summary(),
+        clocks=r["clocks"],
+        configs=configs,
+        host=dict(nproc=os.cpu_count()),
     )
     print(json.dumps(line), flush=True)
 
@@ -398,12 +534,23 @@ def _stats_pct(values, q):
     return float(np.percentile(np.asarray(values), q)) if len(values) else None
 
 
-def run_batch(args, rank, world, dist=None):
+def _summary_args(args, **over):
+    """A copy of the command-line arguments with the given fields replaced."""
+    a = argparse.Namespace(**vars(args))
+    for k, v in over.items():
+        setattr(a, k, v)
+    return a
+
+
+def run_batch(args, rank, world, dist=None, summary=False):
     """Batched P-x sweep: 256 independent binary lattices (side ~ U{64..512}, feeds z1 swept
     0.05..0.95 at fixed T), one persistent multi-lattice step per time step, graph-captured
     chunks, per-lattice retirement; against the same lattices run one after another with
     single-lattice handles and the same retirement rule.  Under torchrun each rank takes a
     contiguous share of the 256 lattices (the total is fixed: strong scaling)."""
+    if summary:
+        # a short sweep for the main benchmark line: 64 of the recipe's lattices, 2,000 steps
+        args = _summary_args(args, batch_lattices=64, max_steps=2000, check_every=500, tol=1e-5, precision=None)
     import torch
     from paper_2212_10680_gb300 import fmlbm, inputs
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
@@ -494,6 +641,8 @@ def run_batch(args, rank, world, dist=None):
                         kind="plain per-lattice loop, same chunks and retirement rule"),
         speedup_vs_sequential=t_seq / t_batch,
     )
+    if summary:
+        return line
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -507,11 +656,16 @@ def _downsample(points: list, k: int) -> list:
     return [[round(t, 3), int(v)] for t, v in points]
 
 
-def run_serve(args, rank, world, dist=None):
+def run_serve(args, rank, world, dist=None, summary=False):
     """Serving: Poisson arrivals of binary and ternary VLE requests (templates with random T
     and feed, side ~ U{64..1024}); continuous batching servers, one per component count;
     against a FIFO loop that runs one request at a time with a single-lattice handle.  Under
     torchrun rank r serves requests r, r + N, ... (the same arrival stream, thinned)."""
+    if summary:
+        # a short serving run for the main benchmark line, at an offered load the batching
+        # server keeps up with: 60 requests, sides up to 512, 2,000 steps each
+        args = _summary_args(args, requests=60, rate=args.summary_rate, max_side=512, max_steps=2000,
+                             check_every=500, tol=1e-5)
     import threading as th
     import torch
     from paper_2212_10680_gb300 import fmlbm, inputs
@@ -614,6 +768,8 @@ def run_serve(args, rank, world, dist=None):
         fifo_baseline=dict(value=R / seq_wall, unit="solves/s", p50_s=_stats_pct(seq_lat, 50),
                            p99_s=_stats_pct(seq_lat, 99), seconds=seq_wall),
     )
+    if summary:
+        return line
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -628,7 +784,7 @@ def main():
     ap.add_argument("--size", type=int, default=0, help="scale the workload's lattice to size x size (profiling)")
     ap.add_argument("--precision", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--tile-y", type=int, default=0, help="override the fused step's tile height (8 or 16)")
     ap.add_argument("--variant", default=None, choices=["auto", "plain", "tma", "tma_tile", "pair"], help="step kernel variant")
     ap.add_argument("--batch-lattices", type=int, default=256)
@@ -640,6 +796,9 @@ def main():
     ap.add_argument("--max-side", type=int, default=1024)
     ap.add_argument("--slots", type=int, default=256)
     ap.add_argument("--budget-gb", type=float, default=64.0)
+    ap.add_argument("--e2e-steps", type=int, default=500, help="steps of the amortized end-to-end figure")
+    ap.add_argument("--no-configs", action="store_true", help="only the headline workload (no per-config objects)")
+    ap.add_argument("--summary-rate", type=float, default=30.0, help="offered load (req/s) of the serving summary")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

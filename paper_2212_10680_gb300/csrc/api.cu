@@ -63,6 +63,7 @@ struct fmlbm_handle {
     bool tma_maps = false;           // tensor maps of both buffers were encoded
     bool owns_buffers = true;        // false: g, g0 and F belong to the caller (fmlbm_create_with_buffers)
     long long wait_polls = kMaxPolls;  // bound of a wait for a tile copy (bulk-copy step forms)
+    int check_y0 = 0, check_y1 = 0;    // rows the domain check covers (check_y1 = 0: all)
     CUtensorMap tmap[2][2];          // [buffer][0: float planes, 1: 16-bit planes]
     std::string last_error;
 };
@@ -195,6 +196,8 @@ StepArgs make_args(const fmlbm_handle* h, int src) {
     A.Fout = h->F[src ^ 1];
     A.err = h->err_dev;
     A.wait_polls = h->wait_polls;
+    A.check_y0 = h->check_y0;
+    A.check_y1 = h->check_y1;
     MixConst mc = h->mc;
     mc.omega = 1.0 / h->lattice.tau;
     mc.fcoef = 1.0 - 0.5 / h->lattice.tau;
@@ -597,6 +600,11 @@ bool fmlbm_internal_usable_device_pointer(const void* p, size_t bytes, int devic
         if (d + bytes > base + size) return false;
     }
     return true;
+}
+
+void fmlbm_internal_set_check_rows(fmlbm_handle* h, int y0, int y1) {
+    h->check_y0 = y0;
+    h->check_y1 = y1;
 }
 
 bool fmlbm_internal_mixture_constants(const fmlbm_mixture& m, MixConst* mc, std::string* why) {

@@ -9,7 +9,9 @@
 // (same inputs, same arithmetic); the ghost rows are overwritten after every step by the
 // neighbours' boundary rows -- plain cudaMemcpy2DAsync copies of every distribution plane
 // (one copy per plane group and neighbour), the halo exchange a multi-GPU split does with
-// peer copies.  Here every slab lives on the current device.
+// peer copies.  The ghost rows' own update (from pulls that wrap around the slab) is
+// discarded, so the domain check of each slab covers its own rows only.  Here every slab
+// lives on the current device.
 #include <cstring>
 #include <new>
 #include <string>
@@ -150,6 +152,7 @@ fmlbm_status fmlbm_decomp_create(const fmlbm_mixture* mixture, const fmlbm_latti
             delete d;
             return st;
         }
+        fmlbm_internal_set_check_rows(s.h, kGhost, kGhost + rows);
     }
     *out = d;
     return FMLBM_OK;

@@ -14,3 +14,6 @@ bool fmlbm_internal_lattice_ok(const fmlbm_lattice& L, int nc, std::string* why)
 // A device (or managed) allocation on `device`, aligned to `align` bytes, with at least
 // `bytes` from p to the end of the allocation that contains it.
 bool fmlbm_internal_usable_device_pointer(const void* p, size_t bytes, int device, size_t align = 16);
+// Restricts the domain check of a handle's steps to rows [y0, y1) (y1 = 0: all rows): a slab
+// of a decomposed lattice checks its own rows, not its ghost rows.
+void fmlbm_internal_set_check_rows(fmlbm_handle* h, int y0, int y1);

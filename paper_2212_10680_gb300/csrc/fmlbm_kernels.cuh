@@ -138,9 +138,15 @@ struct StepArgs {
     void* diag_partial;
     void* rho_prev;  // [N][ny][nx] in the storage arithmetic type
     int have_prev;
+    // rows [check_y0, check_y1) whose nodes the domain check covers (check_y1 = 0: all); a slab
+    // of a decomposed lattice leaves out its ghost rows, whose update is discarded
+    int check_y0, check_y1;
     int pad0;
     long long wait_polls;  // polls of a bounded wait for a tile copy (bulk-copy step forms)
 };
+__device__ __forceinline__ bool checked_row(const StepArgs& A, int y) {
+    return A.check_y1 == 0 || (y >= A.check_y0 && y < A.check_y1);
+}
 
 // The base address of every distribution plane of A.gin / A.gout, a second launch
 // parameter of the single-lattice step only (in StepArgs it made the batch kernel, which
@@ -607,7 +613,7 @@ __device__ __forceinline__ void phase1_node(const StepArgs& A, const MixConstT<R
     const Real beta = node_lnf_st<NC, LNF64, Real>(A, m, rt, lnf);
 #pragma unroll
     for (int i = 0; i < NC; ++i) S.lf.v[i][ty + 1][tx + 1] = lnf[i];
-    domain_check<NC, Real>(A, rt, lnf, beta, gx, 0, gy, valid ? 1u : 0u);
+    domain_check<NC, Real>(A, rt, lnf, beta, gx, 0, gy, valid && checked_row(A, gy) ? 1u : 0u);
 }
 
 // Ring position r (0 <= r < 4 (TW + 4) + 4 TY) -> box coordinates (bx, by) of the 2-node halo

@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(kTX* TY, NPARK > 0 ? 4 : 3) fused_step_pair(St
         const V beta = node_lnf<NC, V>(m, rt, lnf);
 #pragma unroll
         for (int i = 0; i < NC; ++i) pair_put2(S.lf, i, ty + 1, tx, lnf[i]);
-        domain_check<NC, V>(A, rt, lnf, beta, gx0, kTX, gy, vmask);
+        domain_check<NC, V>(A, rt, lnf, beta, gx0, kTX, gy, checked_row(A, gy) ? vmask : 0u);
     }
     __syncthreads();
 
