@@ -798,7 +798,7 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=64.0)
     ap.add_argument("--e2e-steps", type=int, default=500, help="steps of the amortized end-to-end figure")
     ap.add_argument("--no-configs", action="store_true", help="only the headline workload (no per-config objects)")
-    ap.add_argument("--summary-rate", type=float, default=30.0, help="offered load (req/s) of the serving summary")
+    ap.add_argument("--summary-rate", type=float, default=40.0, help="offered load (req/s) of the serving summary")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -421,11 +421,12 @@ double* result_slot(const fmlbm_handle* h, int64_t ticket) { return h->diag_dev 
 fmlbm_status enqueue_diag_tail(fmlbm_handle* h, int64_t ticket, cudaStream_t s, bool final_sum, bool capturing) {
     DiagSlot& sl = h->slot[ticket % kDiagSlots];
     double* host = h->diag_host + (size_t)(ticket % kDiagSlots) * kDiagWords;
+    // the final sum writes the sums and, after them, the error latch into the result slot
+    // (the standalone reduction did the same), so one copy brings both to the host
     if (final_sum)
         FM_CUDA(h, launch_reduce_final(h->nc, partial_set(h, ticket), h->lattice.nx, h->lattice.ny,
-                                       result_slot(h, ticket), s));
-    FM_CUDA(h, cudaMemcpyAsync(host, result_slot(h, ticket), (kMaxC + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
-    FM_CUDA(h, cudaMemcpyAsync(host + kMaxC + 2, h->err_dev, sizeof(ErrorLatch), cudaMemcpyDeviceToHost, s));
+                                       result_slot(h, ticket), s, h->err_dev));
+    FM_CUDA(h, cudaMemcpyAsync(host, result_slot(h, ticket), kDiagWords * sizeof(double), cudaMemcpyDeviceToHost, s));
     // inside a stream capture the record becomes a node of the graph (an external event),
     // so fmlbm_diagnostics_wait can wait for it after the graph is launched
     if (capturing)

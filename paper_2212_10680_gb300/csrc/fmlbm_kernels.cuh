@@ -1211,11 +1211,20 @@ __global__ void __launch_bounds__(kTX* kRedTY) reduce_partial(StepArgs A,
 
 constexpr int kFinalThreads = 256;
 
+// latch (may be null): the handle's error latch, copied after the sums (at out + kMaxC + 2) so
+// that one device-to-host copy brings a request's results and the error state together.
 template <int NC>
 __global__ void __launch_bounds__(kFinalThreads) reduce_final(const double* __restrict__ partial, int nblocks,
-                                                               double* __restrict__ out) {
+                                                               double* __restrict__ out,
+                                                               const ErrorLatch* __restrict__ latch) {
     // block k sums quantity k over all strips in double: fixed strided order, then a fixed tree
     const int k = blockIdx.x;
+    if (latch != nullptr && k == 0 && threadIdx.x == 0) {
+        const volatile int* src = reinterpret_cast<const volatile int*>(latch);
+        int* dst = reinterpret_cast<int*>(out + kMaxC + 2);
+#pragma unroll
+        for (int q = 0; q < (int)(sizeof(ErrorLatch) / sizeof(int)); ++q) dst[q] = src[q];
+    }
     double v = 0.0;
     for (int b = threadIdx.x; b < nblocks; b += kFinalThreads) v += partial[(size_t)b * (NC + 2) + k];
     __shared__ double red[kFinalThreads / 32];

@@ -67,15 +67,16 @@ cudaError_t launch_reduce(const StepArgs& A, int nc, void* rho_prev, int have_pr
                           double* out, cudaStream_t s);
 
 // The fixed-order final sum alone, for partial sums a fused step wrote (A.diag_partial):
-// (NC + 2) doubles per 32 x 8 strip.
-inline cudaError_t launch_reduce_final(int nc, const void* partial, int nx, int ny, double* out, cudaStream_t s) {
+// (NC + 2) doubles per 32 x 8 strip; latch (may be null): copied to out + kMaxC + 2.
+inline cudaError_t launch_reduce_final(int nc, const void* partial, int nx, int ny, double* out, cudaStream_t s,
+                                       const ErrorLatch* latch = nullptr) {
     const int nb = reduce_blocks(nx, ny);
     const double* p = static_cast<const double*>(partial);
     switch (nc) {
-        case 1: reduce_final<1><<<1 + 2, kFinalThreads, 0, s>>>(p, nb, out); break;
-        case 2: reduce_final<2><<<2 + 2, kFinalThreads, 0, s>>>(p, nb, out); break;
-        case 3: reduce_final<3><<<3 + 2, kFinalThreads, 0, s>>>(p, nb, out); break;
-        case 4: reduce_final<4><<<4 + 2, kFinalThreads, 0, s>>>(p, nb, out); break;
+        case 1: reduce_final<1><<<1 + 2, kFinalThreads, 0, s>>>(p, nb, out, latch); break;
+        case 2: reduce_final<2><<<2 + 2, kFinalThreads, 0, s>>>(p, nb, out, latch); break;
+        case 3: reduce_final<3><<<3 + 2, kFinalThreads, 0, s>>>(p, nb, out, latch); break;
+        case 4: reduce_final<4><<<4 + 2, kFinalThreads, 0, s>>>(p, nb, out, latch); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -160,7 +161,7 @@ inline cudaError_t launch_reduce_final(int nc, const void* partial, int nx, int 
         reduce_partial<NC, ST><<<grid, dim3(kTX, kRedTY), 0, s>>>(A, static_cast<Real*>(rho_prev),        \
                                                                    have_prev, static_cast<double*>(partial)); \
         reduce_final<NC><<<NC + 2, kFinalThreads, 0, s>>>(static_cast<const double*>(partial),             \
-                                                          reduce_blocks(A.nx, A.ny), out);                \
+                                                          reduce_blocks(A.nx, A.ny), out, A.err);         \
         return cudaGetLastError();                                                                        \
     }                                                                                                     \
     template <>                                                                                           \
