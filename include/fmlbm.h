@@ -121,7 +121,7 @@ typedef struct fmlbm_mixture {
 } fmlbm_mixture;
 
 typedef struct fmlbm_lattice {
-    int32_t nx, ny;                       /* 1 .. 2^16 each, nx*ny*N*9 < 2^31        */
+    int32_t nx, ny;                       /* 1 .. 2^16 each, nx*ny <= 2^30            */
     double tau;                           /* BGK relaxation time, > 0.5              */
     int32_t stencil;                      /* fmlbm_stencil                           */
     int32_t precision;                    /* fmlbm_precision                         */

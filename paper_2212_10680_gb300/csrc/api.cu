@@ -159,7 +159,9 @@ bool mixture_constants(const fmlbm_mixture& m, MixConst* mc, std::string* why) {
 
 bool lattice_ok(const fmlbm_lattice& L, int nc, std::string* why) {
     if (L.nx < 1 || L.ny < 1 || L.nx > 65536 || L.ny > 65536) { *why = "nx, ny must be 1..65536"; return false; }
-    if ((double)L.nx * L.ny * nc * 9 >= 2147483647.0) { *why = "lattice too large"; return false; }
+    // node indices within a plane are 32-bit (plane offsets are 64-bit or plane base
+    // addresses); the two force planes of a 2^30-node lattice still index below 2^31
+    if ((double)L.nx * L.ny > 1073741824.0) { *why = "lattice too large: more than 2^30 nodes"; return false; }
     if (!(L.tau > 0.5)) { *why = "tau must exceed 0.5"; return false; }
     if (L.stencil != FMLBM_STENCIL_ISOTROPIC && L.stencil != FMLBM_STENCIL_CENTRAL) { *why = "unknown stencil"; return false; }
     if (L.precision < FMLBM_FP64 || L.precision > FMLBM_BF16DEV_LNF64) { *why = "unknown precision"; return false; }

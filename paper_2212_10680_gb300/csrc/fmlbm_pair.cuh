@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kTX* TY, NPARK > 0 ? 4 : 3) fused_step_pair(St
             }
             if (diag)
 #pragma unroll
-                for (int i = 0; i < NC; ++i) cp_async_elem(&pv_s[(i * TY + ty) * kTX + tx].x, prev + i * nxy + node);
+                for (int i = 0; i < NC; ++i) cp_async_elem(&pv_s[(i * TY + ty) * kTX + tx].x, prev + (size_t)i * nxy + node);
         }
         if (valid1) {
             const int node = gy * nx + gx1;
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kTX* TY, NPARK > 0 ? 4 : 3) fused_step_pair(St
             }
             if (diag)
 #pragma unroll
-                for (int i = 0; i < NC; ++i) cp_async_elem(&pv_s[(i * TY + ty) * kTX + tx].y, prev + i * nxy + node);
+                for (int i = 0; i < NC; ++i) cp_async_elem(&pv_s[(i * TY + ty) * kTX + tx].y, prev + (size_t)i * nxy + node);
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
@@ -315,8 +315,8 @@ __global__ void __launch_bounds__(kTX* TY, NPARK > 0 ? 4 : 3) fused_step_pair(St
             const int node0 = gy * nx + gx0;
 #pragma unroll
             for (int i = 0; i < NC; ++i) {
-                prev[i * nxy + node0] = r[i].x;
-                if (valid1) prev[i * nxy + node0 + kTX] = r[i].y;
+                prev[(size_t)i * nxy + node0] = r[i].x;
+                if (valid1) prev[(size_t)i * nxy + node0 + kTX] = r[i].y;
             }
         }
         diag_warp<NC, V>(acc, dred[ty]);

@@ -103,7 +103,7 @@ extern "C" fmlbm_status fmlbm_diagnostics_noalloc(int32_t n_components, int32_t 
     if (precision == FMLBM_FP16DEV_LNF64) precision = FMLBM_FP16DEV;
     if (precision == FMLBM_BF16DEV_LNF64) precision = FMLBM_BF16DEV;
     if ((precision == FMLBM_FP16DEV || precision == FMLBM_BF16DEV) && !g0_device) return FMLBM_E_INVALID_ARG;
-    if ((double)nx * ny * n_components * 9 >= 2147483647.0) return FMLBM_E_INVALID_ARG;
+    if ((double)nx * ny > 1073741824.0) return FMLBM_E_INVALID_ARG;
     // the fixed scratch holds one row of n_components + 2 partial sums per 32 x 8 tile
     const size_t need = (size_t)reduce_blocks(nx, ny) * (size_t)(n_components + 2);
     if (need > kNoallocScratchDoubles) return FMLBM_E_INVALID_ARG;

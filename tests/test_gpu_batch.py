@@ -161,3 +161,31 @@ def test_batch_autotune_keeps_results(fm):
     ref = _single(fm, mixd, rho, steps + 10, "fp32", 16)[0]
     assert np.array_equal(g, ref)
     fm.fmlbm_batch_destroy(b)
+
+
+def test_batch_against_the_oracle_on_ragged_lattices(fm):
+    # three lattices of different shapes (ragged in both directions, one narrower than a tile)
+    # and mixtures in one batch, each against the FP64 oracle on the same seeded input: the
+    # FP32 bound of the single-lattice parity tests, normwise and element by element
+    from cases import mixture_dict, run_oracle, smooth_state
+    from test_gpu_parity import EPS32, elementwise_ratio
+    cases = [((70, 37), mixture_dict(n=2, Tr=1.05, kappa_scale=0.5, M=[1.0, 1.7], kij=0.03)),
+             ((40, 24), mixture_dict(n=2, Tr=1.1, kappa_scale=0.3)),
+             ((21, 50), mixture_dict(n=2, eos="srk", Tr=1.05, kappa_scale=0.5))]
+    b = fm.fmlbm_batch_create(2, "fp32", 4)
+    slots = []
+    for k, ((nx, ny), mixd) in enumerate(cases):
+        rho = smooth_state(2, nx, ny, seed=60 + k)
+        slots.append((fm.fmlbm_batch_add(b, fm.mixture_from_dict(mixd), fm.make_lattice(nx, ny, 0.9, "isotropic",
+                                                                                        "fp32", "lagged"), rho),
+                      rho, mixd))
+    fm.fmlbm_batch_step(b, 20)
+    for slot, rho, mixd in slots:
+        ny, nx = rho.shape[1:]
+        g = np.empty((2, 9, ny, nx))
+        F = np.empty((2, ny, nx))
+        fm.fmlbm_batch_get_distributions(b, slot, g, F)
+        ora = run_oracle(mixd, rho, 0.9, "isotropic", "lagged", 20, (20,))[20]
+        assert np.max(np.abs(g - ora["g"])) <= 1e-5 * np.max(np.abs(ora["g"])), (nx, ny)
+        assert elementwise_ratio(g, ora["g"], 1e-5, EPS32) <= 1.0, (nx, ny)
+    fm.fmlbm_batch_destroy(b)

@@ -94,3 +94,38 @@ def test_undersized_caller_buffers_are_rejected(fm):
     # the full-size buffers are accepted
     lat = fm.Lattice(mix, nx, ny, 1.0, "isotropic", "fp32", "lagged", buffers=dict(g=_addr(gt), g0=None, force=_addr(ft)))
     lat.close()
+
+
+def test_handles_on_two_threads_with_large_shared_tiles(fm):
+    # Launch attributes are kept per device and set safely from any thread: two threads
+    # create and step their own lattices at the same time with 32-row tiles of four FP64
+    # components (the step then needs more than 48 KB of dynamic shared memory), and each
+    # gets the result of the same lattice stepped alone.
+    import threading
+    from cases import mixture_dict, smooth_state
+    mixd = mixture_dict(n=4, Tr=1.05, kappa_scale=0.5)
+    rho = smooth_state(4, 40, 64, seed=70)
+
+    def run(out, k):
+        try:
+            lat = fm.Lattice(fm.mixture_from_dict(mixd), 40, 64, 1.0, "isotropic", "fp64", "lagged")
+            fm.fmlbm_set_step_variant(lat.h, "plain")
+            fm.fmlbm_set_tile_height(lat.h, 32)
+            lat.init(rho)
+            lat.step(10)
+            out[k] = lat.distributions()
+            lat.close()
+        except Exception as e:  # reported below
+            out[k] = e
+
+    out = [None, None]
+    ts = [threading.Thread(target=run, args=(out, k)) for k in range(2)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not any(isinstance(o, Exception) for o in out), out
+    ref = [None]
+    run(ref, 0)
+    for o in out:
+        assert np.array_equal(o[0], ref[0][0]) and np.array_equal(o[1], ref[0][1])
