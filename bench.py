@@ -493,7 +493,12 @@ def run_ours(args, w, rank, world, dist):
         del flush
         torch.cuda.empty_cache()
         configs["batch_sweep"] = run_batch(args, rank, world, dist, summary=True)
+        # two offered loads: about 0.7 of the batching servers' capacity (the plain FIFO loop,
+        # about 1.9 requests/s on these requests, is overloaded there), and one below the FIFO
+        # loop's capacity, where both keep up
         configs["serving"] = run_serve(args, rank, world, dist, summary=True)
+        configs["serving_low_load"] = run_serve(_summary_args(args, summary_rate=args.summary_rate_low), rank,
+                                                world, dist, summary=True)
 
     if rank != 0:
         return
@@ -542,15 +547,37 @@ def _summary_args(args, **over):
     return a
 
 
+def _phase_dev(liquid, vapour, st):
+    """Largest relative deviation of a retired lattice's two phases (molar densities) from the
+    flash state it started from (stored in tests/golden/workloads.json; the equilibrium of the
+    lattice sits at a slightly shifted pressure, Section V.A, so this is a check of scale)."""
+    dl = np.abs(np.asarray(liquid) / np.asarray(st["rt_liquid"]) - 1.0)
+    dv = np.abs(np.asarray(vapour) / np.asarray(st["rt_vapour"]) - 1.0)
+    return float(max(dl.max(), dv.max()))
+
+
+# The first feed of the stored sweep (z1 = 0.05 + 0.9 k / 255) the batched sweep uses: the
+# unperturbed slabs of the feeds below z1 = 0.11 leave the EOS domain within a few hundred
+# steps on wide lattices (FP64 and FP32 alike), so the sweep spans z1 = 0.12 .. 0.95.
+SWEEP_FIRST = 20
+
+
 def run_batch(args, rank, world, dist=None, summary=False):
-    """Batched P-x sweep: 256 independent binary lattices (side ~ U{64..512}, feeds z1 swept
-    0.05..0.95 at fixed T), one persistent multi-lattice step per time step, graph-captured
+    """Batched P-x sweep: independent binary lattices (side ~ U{64..max_side}, feeds z1 swept
+    0.12..0.95 at fixed T), one persistent multi-lattice step per time step, graph-captured
     chunks, per-lattice retirement; against the same lattices run one after another with
-    single-lattice handles and the same retirement rule.  Under torchrun each rank takes a
-    contiguous share of the 256 lattices (the total is fixed: strong scaling)."""
+    single-lattice handles and the same retirement rule.  Each lattice starts as Section V.B
+    starts an envelope point: the flat interface of Eq. eqInit (W = 4) between the flash phases
+    at S_V = 0.5, unperturbed.  A lattice retires when its phase measure (the mean of ln rho_i
+    over the nodes, per component) changes by less than tol over a check interval
+    (FMLBM_CRITERION_PHASE); the density residual does not settle, because the slab keeps a
+    rigid sloshing motion that nothing damps in a periodic box.  Under torchrun each rank takes
+    a contiguous share of the lattices (the total is fixed: strong scaling)."""
     if summary:
-        # a short sweep for the main benchmark line: 64 of the recipe's lattices, 2,000 steps
-        args = _summary_args(args, batch_lattices=64, max_steps=2000, check_every=500, tol=1e-5, precision=None)
+        # a short sweep for the main benchmark line: 32 of the recipe's feeds on lattices of
+        # side 64..192
+        args = _summary_args(args, batch_lattices=32, batch_max_side=192, max_steps=args.max_steps,
+                             check_every=500, tol=args.tol, precision=None)
     import torch
     from paper_2212_10680_gb300 import fmlbm, inputs
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
@@ -560,14 +587,14 @@ def run_batch(args, rank, world, dist=None, summary=False):
     n = len(mixd["Tc"])
     nlat = args.batch_lattices
     rng = np.random.default_rng(4)
-    sides = rng.integers(64, 513, nlat)
+    sides = rng.integers(64, args.batch_max_side + 1, nlat)
     mine = list(shard(nlat, rank, world))
-    fields = {}
+    fields, states = {}, {}
     for k in mine:
-        st = wl["binary_sweep"][int(round(k * 255 / max(nlat - 1, 1)))]
+        st = wl["binary_sweep"][SWEEP_FIRST + int(round(k * (255 - SWEEP_FIRST) / max(nlat - 1, 1)))]
         L = int(sides[k])
-        fields[k] = inputs.with_noise(inputs.slab(st["rt_vapour"], st["rt_liquid"], L, L, 0.5, 4.0), 0.01, 4,
-                                      lattice=k)
+        states[k] = st
+        fields[k] = inputs.slab(st["rt_vapour"], st["rt_liquid"], L, L, 0.5, 4.0)
     mix = fmlbm.mixture_from_dict(mixd)
     prec = args.precision or "fp32"
 
@@ -577,8 +604,9 @@ def run_batch(args, rank, world, dist=None, summary=False):
         torch.cuda.synchronize()
 
     ty = blocks = None
-    units, status_mine = 0, []
+    units, status_mine, steps_mine, dev_mine, failed_mine = 0, [], [], [], []
     b = fmlbm.fmlbm_batch_create(n, prec, max(len(mine), 1))
+    fmlbm.fmlbm_batch_set_criterion(b, args.criterion)
     for k in mine:
         L = int(sides[k])
         fmlbm.fmlbm_batch_add(b, mix, fmlbm.make_lattice(L, L, 1.0, "isotropic", prec), fields[k])
@@ -592,53 +620,86 @@ def run_batch(args, rank, world, dist=None, summary=False):
         steps, res, st = fmlbm.fmlbm_batch_run(b, len(mine), args.max_steps, args.check_every, args.tol)
         torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
-    fmlbm.fmlbm_batch_destroy(b)
     if mine:
         units = sum(n * int(sides[k]) ** 2 * (int(steps[j]) - tuned_steps[j]) for j, k in enumerate(mine))
         status_mine = [int(v) for v in st]
+        steps_mine = [int(v) for v in steps]
+        failed_mine = [[k, round(states[k]["z"][0], 4), int(sides[k]), fmlbm.STATUS[status_mine[j]], steps_mine[j]]
+                       for j, k in enumerate(mine) if status_mine[j] != 0]
+        # the answer of a sample of the retired solves against the flash they started from
+        for j, k in enumerate(mine):
+            if status_mine[j] == 0 and j % max(1, len(mine) // 8) == 0:
+                liq, vap = fmlbm.fmlbm_batch_phases(b, j, n)
+                dev_mine.append(_phase_dev(liq, vap, states[k]))
+    fmlbm.fmlbm_batch_destroy(b)
     t_batch = max_over_ranks(t_batch, dist, dev)
     units = sum_over_ranks(units, dist, dev)
     statuses = np.array(gather_lists(status_mine, dist), dtype=np.int64)
-    max_steps_done = int(max_over_ranks(int(np.max(steps)) if mine else 0, dist, dev))
+    steps_all = np.array(gather_lists(steps_mine, dist), dtype=np.int64)
+    devs = gather_lists(dev_mine, dist)
+    failed = gather_lists(failed_mine, dist)
+    max_steps_done = int(steps_all.max()) if steps_all.size else 0
 
-    # the plain per-lattice loop: one handle at a time, same chunking and retirement rule
-    seq_units, seq_status = 0, []
+    # the plain per-lattice loop: one handle at a time, the same check interval and
+    # retirement rule (the phase measure of fmlbm_phase_measure, or the residual)
+    seq_units, seq_status, seq_steps = 0, [], []
     barrier()
     t0 = time.perf_counter()
-    for k in mine:
+    for j, k in enumerate(mine):
         L = int(sides[k])
         lat = fmlbm.Lattice(mix, L, L, 1.0, "isotropic", prec, "lagged")
         lat.init(fields[k])
-        lat.diagnostics()
-        done, status = 0, 0
+        # the steps the batch autotuner took before the batch's first check, so that both
+        # check the same states
+        done, status = tuned_steps[j], 0
         try:
+            lat.step(done)
+            lam = lat.phase_measure() if args.criterion == "phase" else None
+            lat.diagnostics()
             while done < args.max_steps:
                 lat.step(args.check_every)
                 done += args.check_every
-                _, r, _ = lat.diagnostics()
-                if r < args.tol:
+                if args.criterion == "phase":
+                    now = lat.phase_measure()
+                    measure = float(np.max(np.abs(now - lam)))
+                    lam = now
+                else:
+                    measure = lat.diagnostics()[1]
+                if measure < args.tol:
                     break
             else:
                 status = fmlbm.E_NOT_CONVERGED
         except fmlbm.FmlbmError as e:
             status = e.status
-        seq_units += n * L * L * done
+        seq_units += n * L * L * (done - tuned_steps[j])
         seq_status.append(status)
+        seq_steps.append(done)
         lat.close()
     torch.cuda.synchronize()
     t_seq = max_over_ranks(time.perf_counter() - t0, dist, dev)
     seq_units = sum_over_ranks(seq_units, dist, dev)
+    seq_steps_all = np.array(gather_lists(seq_steps, dist), dtype=np.int64)
     counts = {fmlbm.STATUS[int(v)]: int((statuses == v).sum()) for v in np.unique(statuses)}
+    ok = statuses == 0
     line = dict(
         metric="batched VLE solves/sec", value=nlat / t_batch, unit="solves/s", n_gpus=world,
         steps=max_steps_done, warmup=3, ms_per_step=None, higher_is_better=True, scaling="strong",
         vs_baseline=None, dtype="f64" if prec == "fp64" else "f32", data="synthetic",
-        config=dict(workload=f"batched P-x sweep: {nlat} binary PR lattices, side U{{64..512}}, z1 0.05..0.95, "
-                             f"flat slab, tau 1.0", precision=prec, max_steps=args.max_steps,
-                    check_every=args.check_every, tol=args.tol, autotune=dict(tile_y=ty, blocks=blocks)),
+        config=dict(workload=f"batched P-x sweep: {nlat} binary PR lattices, side U{{64..{args.batch_max_side}}}, "
+                             f"z1 0.12..0.95, flat slab of Eq. eqInit (W 4, unperturbed), tau 1.0",
+                    precision=prec, max_steps=args.max_steps, check_every=args.check_every, tol=args.tol,
+                    criterion=args.criterion, autotune=dict(tile_y=ty, blocks=blocks)),
         aggregate_glups=units / t_batch / 1e9, seconds=t_batch, statuses=counts,
+        retired_ok_fraction=float(ok.mean()) if statuses.size else None,
+        not_ok=dict(fields=["lattice", "z1", "side", "status", "steps"], rows=failed),
+        steps_to_retire=dict(median=int(np.median(steps_all[ok])) if ok.any() else None,
+                             max=int(steps_all[ok].max()) if ok.any() else None),
+        phase_vs_start_flash=dict(sample=len(devs), max_rel=max(devs) if devs else None,
+                                  median_rel=float(np.median(devs)) if devs else None),
         sequential=dict(value=nlat / t_seq, unit="solves/s", seconds=t_seq, aggregate_glups=seq_units / t_seq / 1e9,
-                        kind="plain per-lattice loop, same chunks and retirement rule"),
+                        kind="plain per-lattice loop, same check interval and retirement rule",
+                        same_retirement_step=int((seq_steps_all == steps_all).sum()) if seq_steps_all.size ==
+                        steps_all.size else None),
         speedup_vs_sequential=t_seq / t_batch,
     )
     if summary:
@@ -658,14 +719,16 @@ def _downsample(points: list, k: int) -> list:
 
 def run_serve(args, rank, world, dist=None, summary=False):
     """Serving: Poisson arrivals of binary and ternary VLE requests (templates with random T
-    and feed, side ~ U{64..1024}); continuous batching servers, one per component count;
-    against a FIFO loop that runs one request at a time with a single-lattice handle.  Under
-    torchrun rank r serves requests r, r + N, ... (the same arrival stream, thinned)."""
+    and feed, side ~ U{64..max_side}); continuous batching servers, one per component count;
+    against a FIFO loop that runs one request at a time with a single-lattice handle and the
+    same retirement rule.  Each request starts from the unperturbed flat interface of Eq.
+    eqInit between its flash phases and retires at the convergence criterion (by default the
+    phase-measure change over a check interval below tol).  Under torchrun rank r serves
+    requests r, r + N, ... (the same arrival stream, thinned)."""
     if summary:
-        # a short serving run for the main benchmark line, at an offered load the batching
-        # server keeps up with: 60 requests, sides up to 512, 2,000 steps each
-        args = _summary_args(args, requests=60, rate=args.summary_rate, max_side=512, max_steps=2000,
-                             check_every=500, tol=1e-5)
+        # a short serving run for the main benchmark line, at an offered load below the
+        # batching server's capacity: 48 requests, sides up to 192
+        args = _summary_args(args, requests=48, rate=args.summary_rate, max_side=192, check_every=500)
     import threading as th
     import torch
     from paper_2212_10680_gb300 import fmlbm, inputs
@@ -684,15 +747,15 @@ def run_serve(args, rank, world, dist=None, summary=False):
         side = int(rng.integers(64, args.max_side + 1))
         if k not in mine:
             continue
-        rho = inputs.with_noise(inputs.slab(t["slab"]["rt_vapour"], t["slab"]["rt_liquid"], side, side, 0.5, 4.0),
-                                0.01, 5, lattice=k)
+        rho = inputs.slab(t["slab"]["rt_vapour"], t["slab"]["rt_liquid"], side, side, 0.5, 4.0)
         reqs[k] = dict(k=k, n=len(t["mixture"]["Tc"]), mix=fmlbm.mixture_from_dict(t["mixture"]), side=side,
                        rho=rho, t=float(arrive[k]))
     if dist is not None:
         dist.barrier()
     prec = "fp32"
     servers = {nc: fmlbm.fmlbm_server_create(nc, prec, args.slots, args.check_every, args.tol, args.max_steps,
-                                             int(args.budget_gb * (1 << 30))) for nc in (2, 3)}
+                                             int(args.budget_gb * (1 << 30)), criterion=args.criterion)
+               for nc in (2, 3)}
     results = []
     timeline = []          # (seconds, device bytes admitted over both servers), every >= 50 ms
 
@@ -725,8 +788,9 @@ def run_serve(args, rank, world, dist=None, summary=False):
                            dist, dev)
     status_all = gather_lists([r["status"] for r in results], dist)
 
-    # FIFO baseline: the same arrivals, one request at a time through a single-lattice handle
-    seq_lat = []
+    # FIFO baseline: the same arrivals, one request at a time through a single-lattice handle,
+    # the same check interval and retirement rule
+    seq_lat, seq_status = [], []
     if dist is not None:
         dist.barrier()
     t0 = time.perf_counter()
@@ -736,37 +800,54 @@ def run_serve(args, rank, world, dist=None, summary=False):
             time.sleep(wait)
         lat = fmlbm.Lattice(r["mix"], r["side"], r["side"], 1.0, "isotropic", prec, "lagged")
         lat.init(r["rho"])
-        lat.diagnostics()
-        done = 0
+        done, status = 0, 0
         try:
-            while done < args.max_steps:
+            lat.diagnostics()
+            lam = lat.phase_measure() if args.criterion == "phase" else None
+            while True:
                 lat.step(args.check_every)
                 done += args.check_every
-                if lat.diagnostics()[1] < args.tol:
+                if args.criterion == "phase":
+                    now = lat.phase_measure()
+                    measure = float(np.max(np.abs(now - lam)))
+                    lam = now
+                else:
+                    measure = lat.diagnostics()[1]
+                if measure < args.tol:
                     break
-        except fmlbm.FmlbmError:
-            pass
+                if done >= args.max_steps:
+                    status = fmlbm.E_NOT_CONVERGED
+                    break
+        except fmlbm.FmlbmError as e:
+            status = e.status
         lat.close()
         seq_lat.append(time.perf_counter() - t0 - r["t"])
+        seq_status.append(status)
     seq_wall = max_over_ranks(time.perf_counter() - t0, dist, dev)
     seq_lat = gather_lists(seq_lat, dist)
-    counts = {}
+    seq_status = gather_lists(seq_status, dist)
+    counts, seq_counts = {}, {}
     for s_ in status_all:
         counts[fmlbm.STATUS[s_]] = counts.get(fmlbm.STATUS[s_], 0) + 1
+    for s_ in seq_status:
+        seq_counts[fmlbm.STATUS[s_]] = seq_counts.get(fmlbm.STATUS[s_], 0) + 1
+
     line = dict(
         metric="served VLE solves/sec", value=R / wall, unit="solves/s", n_gpus=world, steps=args.max_steps,
         warmup=0, ms_per_step=None, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
         data="synthetic", config=dict(
             workload=f"Poisson arrivals ({args.rate}/s) of {R} binary/ternary PR VLE requests, side "
-                     f"U{{64..{args.max_side}}}, T U[0.80,0.92] Tc1 (binary) / U[0.85,0.92] Tc1 (ternary)",
-            slots=args.slots, chunk_steps=args.check_every, tol=args.tol, max_steps=args.max_steps,
-            hbm_budget_gb=args.budget_gb),
+                     f"U{{64..{args.max_side}}}, T U[0.80,0.92] Tc1 (binary) / U[0.85,0.92] Tc1 (ternary), "
+                     f"flat slab of Eq. eqInit (W 4, unperturbed)",
+            slots=args.slots, chunk_steps=args.check_every, tol=args.tol, criterion=args.criterion,
+            max_steps=args.max_steps, hbm_budget_gb=args.budget_gb),
+        retired_ok_fraction=counts.get("FMLBM_OK", 0) / max(len(status_all), 1),
         p50_s=_stats_pct(lat_s, 50), p99_s=_stats_pct(lat_s, 99), aggregate_glups=units / wall / 1e9,
         gpu_busy_fraction={str(k): v / wall for k, v in busy.items()}, statuses=counts, seconds=wall,
         admitted_bytes=dict(max=max((b for _, b in timeline), default=0), budget=int(args.budget_gb * (1 << 30)),
                             timeline=_downsample(timeline, 40), note="rank 0's servers, sampled every >= 50 ms"),
         fifo_baseline=dict(value=R / seq_wall, unit="solves/s", p50_s=_stats_pct(seq_lat, 50),
-                           p99_s=_stats_pct(seq_lat, 99), seconds=seq_wall),
+                           p99_s=_stats_pct(seq_lat, 99), seconds=seq_wall, statuses=seq_counts),
     )
     if summary:
         return line
@@ -788,9 +869,12 @@ def main():
     ap.add_argument("--tile-y", type=int, default=0, help="override the fused step's tile height (8 or 16)")
     ap.add_argument("--variant", default=None, choices=["auto", "plain", "tma", "tma_tile", "pair"], help="step kernel variant")
     ap.add_argument("--batch-lattices", type=int, default=256)
-    ap.add_argument("--max-steps", type=int, default=4000)
+    ap.add_argument("--batch-max-side", type=int, default=512)
+    ap.add_argument("--max-steps", type=int, default=300000)
     ap.add_argument("--check-every", type=int, default=500)
-    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--tol", type=float, default=2e-6,
+                    help="retirement threshold of the convergence measure over one check interval")
+    ap.add_argument("--criterion", default="phase", choices=["phase", "residual"])
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--max-side", type=int, default=1024)
@@ -798,7 +882,9 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=64.0)
     ap.add_argument("--e2e-steps", type=int, default=500, help="steps of the amortized end-to-end figure")
     ap.add_argument("--no-configs", action="store_true", help="only the headline workload (no per-config objects)")
-    ap.add_argument("--summary-rate", type=float, default=40.0, help="offered load (req/s) of the serving summary")
+    ap.add_argument("--summary-rate", type=float, default=7.0, help="offered load (req/s) of the serving summary")
+    ap.add_argument("--summary-rate-low", type=float, default=1.5,
+                    help="offered load (req/s) of the second serving summary (below the FIFO loop's capacity)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -129,6 +129,20 @@ typedef struct fmlbm_lattice {
     int32_t formulation;                  /* fmlbm_formulation                       */
 } fmlbm_lattice;
 
+/* Convergence criteria of batches and servers (the paper runs fixed step counts, Sections
+ * V.A-V.C; a criterion is this library's).  RESIDUAL (default): the residual of
+ * fmlbm_diagnostics over a check interval, ||rho(t) - rho(t - D)||_2 / ||rho(t)||_2.
+ * PHASE: the change of the phase measure over a check interval,
+ * max_i |lambda_i(t) - lambda_i(t - D)| with lambda_i = (1 / (nx ny)) sum_x ln rho_i(x)
+ * (fmlbm_phase_measure): the volume-averaged relative change of each component's density.
+ * It follows every change of the coexisting phases (their densities, compositions and
+ * volumes) but not a rigid motion of the density field.  A flat or curved interface in a
+ * periodic box keeps the net momentum the initial transient gave it (the discrete force sums
+ * to zero only at equilibrium, and viscosity does not damp a rigid motion), so it drifts or
+ * sloshes by a fraction of a node and keeps the RESIDUAL near 1e-3 while the phases no
+ * longer change. */
+typedef enum fmlbm_criterion { FMLBM_CRITERION_RESIDUAL = 0, FMLBM_CRITERION_PHASE = 1 } fmlbm_criterion;
+
 typedef struct fmlbm_handle fmlbm_handle;
 
 /* Creates a lattice: validates the mixture (Appendix C parameters) and lattice,
@@ -228,6 +242,14 @@ fmlbm_status fmlbm_diagnostics(fmlbm_handle* h, double* mass, double* residual, 
 fmlbm_status fmlbm_diagnostics_async(fmlbm_handle* h, int64_t* ticket);
 fmlbm_status fmlbm_diagnostics_wait(fmlbm_handle* h, int64_t ticket, double* mass, double* residual,
                                     int64_t* step);
+
+/* The phase measure of the current state: lambda[i] = (1 / (nx ny)) sum_x ln rho_i(x) for each
+ * component (natural logarithm of the mass densities; a deterministic, fixed-order reduction,
+ * double from each 32 x 8 strip up; float logarithms for the float storage forms).  The change of
+ * lambda between two states is the PHASE convergence measure (fmlbm_criterion).  lambda:
+ * host [N].  Reads the state only (the residual snapshot of fmlbm_diagnostics is not touched);
+ * synchronises the handle's stream and reports a latched error. */
+fmlbm_status fmlbm_phase_measure(fmlbm_handle* h, double* lambda);
 
 /* First node that left the EOS domain since the last init (after a call returned
  * FMLBM_E_NONPHYSICAL): component, x, y. */
@@ -365,12 +387,19 @@ fmlbm_status fmlbm_batch_step(fmlbm_batch* b, int64_t nsteps);
  * fmlbm_batch_slot_info.  The first check after a slot is added sets its snapshot
  * (residual +inf). */
 fmlbm_status fmlbm_batch_check(fmlbm_batch* b);
-/* Runs every active slot until it retires: residual < tol at a check (every check_every
- * steps, one graph launch per chunk), a latched error, or max_steps reached
- * (FMLBM_E_NOT_CONVERGED).  Outputs per slot (arrays of capacity entries, may be NULL):
- * steps taken, last residual, status. */
+/* Runs every active slot until it retires: the batch's convergence measure (fmlbm_criterion:
+ * the residual, or the phase-measure change, over the last check interval) < tol at a check
+ * (every check_every steps, one graph launch per chunk), a latched error, or max_steps
+ * reached (FMLBM_E_NOT_CONVERGED).  Outputs per slot (arrays of capacity entries, may be
+ * NULL): steps taken, last value of the convergence measure, status. */
 fmlbm_status fmlbm_batch_run(fmlbm_batch* b, int64_t max_steps, int32_t check_every, double tol,
                              int64_t* steps_out, double* residual_out, int32_t* status_out);
+/* The convergence measure fmlbm_batch_run compares with its tol (fmlbm_criterion; default
+ * FMLBM_CRITERION_RESIDUAL).  Applies from the next retirement decision on. */
+fmlbm_status fmlbm_batch_set_criterion(fmlbm_batch* b, int32_t criterion);
+/* Change of the phase measure of a slot over the last check interval (+inf before a second
+ * check, NaN after a latched error); every check computes it beside the residual. */
+fmlbm_status fmlbm_batch_slot_phase_change(fmlbm_batch* b, int32_t slot, double* change);
 /* One graph-launched chunk of steps for every active slot followed by a check (the body
  * of fmlbm_batch_run without the retirement decisions; synchronises). */
 fmlbm_status fmlbm_batch_run_chunk(fmlbm_batch* b, int32_t steps);
@@ -393,11 +422,16 @@ const char* fmlbm_batch_last_error(const fmlbm_batch* b);
 void fmlbm_batch_destroy(fmlbm_batch* b);
 
 /* The two phases of a slot's current state, a vapour-liquid solve's answer: the molar
- * densities rho~_i = rho_i / M_i at the node of largest total molar density (rho_liquid[N])
- * and at the node of smallest (rho_vapour[N]); ties go to the lowest node index (row-major).
- * Either pointer may be NULL.  Host outputs; synchronises the batch's stream.  At an
- * equilibrated flat or curved interface these are the bulk phases (the node extremes of a
- * still-noisy field are not). */
+ * densities rho~_i = rho_i / M_i averaged over the 2 x 2 block of nodes (nodes 2bx, 2bx + 1
+ * by 2by, 2by + 1, periodic at an odd edge) of largest total molar density (rho_liquid[N]) and
+ * over the block of smallest (rho_vapour[N]); ties go to the lowest block index (row-major).
+ * Block means, not node values: the force differences every field over two nodes (Eqs.
+ * eqforcefinal, eq1stder), so a field alternating from node to node feels no force, and at
+ * rest the well-balanced equilibrium (rho_0 = 0) keeps each node's mass in its rest
+ * population; a checkerboard that the transient of a sharp interface excites therefore stays
+ * in both bulk phases, neither sublattice is in equilibrium on its own, and the block mean
+ * is the thermodynamic state.  Either pointer may be NULL.  Host outputs; synchronises the
+ * batch's stream. */
 fmlbm_status fmlbm_batch_phases(fmlbm_batch* b, int32_t slot, double* rho_liquid, double* rho_vapour);
 
 /* ------------------------------------------------------------------------------------
@@ -405,7 +439,8 @@ fmlbm_status fmlbm_batch_phases(fmlbm_batch* b, int32_t slot, double* rho_liquid
  * A worker thread owns a batch; between chunks of chunk_steps steps it admits queued
  * requests in arrival order while a slot is free and their device bytes
  * (fmlbm_lattice_bytes) fit hbm_budget_bytes, and retires each running lattice at its
- * own criterion (residual < tol at a check, a latched error, or max_steps).  A request's
+ * own criterion (the configured convergence measure < tol at a check, a latched error, or
+ * max_steps).  A request's
  * result does not depend on what else is running.  All server functions are
  * thread-safe and never block on the GPU.
  * ------------------------------------------------------------------------------------ */
@@ -416,11 +451,11 @@ typedef struct fmlbm_server_config {
     int32_t precision;         /* and this storage precision                      */
     int32_t max_slots;         /* lattices running at once                        */
     int32_t chunk_steps;       /* steps between admission / retirement decisions   */
-    double tol;                /* residual at which a lattice retires             */
+    double tol;                /* convergence measure at which a lattice retires  */
     int64_t max_steps;         /* step limit per request (FMLBM_E_NOT_CONVERGED)  */
     size_t hbm_budget_bytes;   /* device bytes the running lattices may hold      */
     int32_t queue_capacity;    /* queued requests beyond which submit is BUSY     */
-    int32_t reserved;
+    int32_t criterion;         /* fmlbm_criterion of the retirement check          */
 } fmlbm_server_config;
 
 typedef struct fmlbm_request {
@@ -437,11 +472,11 @@ typedef struct fmlbm_result {
     int32_t status;            /* FMLBM_OK (converged), FMLBM_E_NOT_CONVERGED, FMLBM_E_NONPHYSICAL, ... */
     int32_t n_components;
     int64_t steps;
-    double residual;
+    double residual;           /* last value of the server's convergence measure   */
     double t_submit, t_admit, t_done;   /* seconds on the server's steady clock */
     /* the two phases at retirement (fmlbm_batch_phases; zeros for FMLBM_E_NONPHYSICAL):
-     * molar densities rho~_i at the densest and the least dense node; the compositions
-     * are rho~_i / sum_j rho~_j */
+     * block-mean molar densities rho~_i at the densest and the least dense 2 x 2 block; the
+     * compositions are rho~_i / sum_j rho~_j */
     double rho_liquid[FMLBM_MAX_COMPONENTS];
     double rho_vapour[FMLBM_MAX_COMPONENTS];
 } fmlbm_result;

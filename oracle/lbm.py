@@ -274,6 +274,16 @@ def component_mass(g: np.ndarray) -> np.ndarray:
     return g.sum(axis=(1, 2, 3))
 
 
+def phase_measure(rho: np.ndarray) -> np.ndarray:
+    """Phase measure of a state: lambda_i = mean over the nodes of ln rho_i, per component
+    (rho has shape (N, ny, nx)).  Its change between two states, max_i |d lambda_i|, is the
+    volume-averaged relative change of each component's density: it follows the phases
+    (densities, compositions, volumes) but not a rigid motion of the field, since a sum of a
+    smooth function of the densities over a periodic lattice does not change when the field
+    moves.  A convergence measure of this build (the paper runs fixed step counts)."""
+    return np.log(rho).reshape(rho.shape[0], -1).mean(axis=1)
+
+
 def residual(rho_now: np.ndarray, rho_before: np.ndarray) -> float:
     """Convergence measure: ||rho(t) - rho(t - D)||_2 / ||rho(t)||_2 over all nodes and
     components (the paper runs fixed step counts; this criterion is this build's)."""

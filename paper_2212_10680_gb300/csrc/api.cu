@@ -358,6 +358,16 @@ cudaError_t dispatch_reduce(fmlbm_handle* h, const StepArgs& A, void* partial, d
     }
 }
 
+cudaError_t dispatch_lnrho(fmlbm_handle* h, const StepArgs& A, double* partial, double* out) {
+    switch (h->lattice.precision) {
+        case FMLBM_FP64: return launch_lnrho<ST_F64>(A, h->nc, partial, out, h->stream);
+        case FMLBM_FP32: return launch_lnrho<ST_F32>(A, h->nc, partial, out, h->stream);
+        case FMLBM_FP16DEV:
+        case FMLBM_FP16DEV_LNF64: return launch_lnrho<ST_F16DEV>(A, h->nc, partial, out, h->stream);
+        default: return launch_lnrho<ST_BF16DEV>(A, h->nc, partial, out, h->stream);
+    }
+}
+
 // Synchronise the stream and turn a latched kernel error into a status.
 fmlbm_status sync_and_check(fmlbm_handle* h) {
     FM_CUDA(h, cudaMemcpyAsync(h->err_host, h->err_dev, sizeof(ErrorLatch), cudaMemcpyDeviceToHost, h->stream));
@@ -854,6 +864,25 @@ fmlbm_status fmlbm_moments(fmlbm_handle* h, double* rho, double* u, double* lnf)
     cudaFreeAsync(d, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "moments");
     return sync_and_check(h);
+}
+
+fmlbm_status fmlbm_phase_measure(fmlbm_handle* h, double* lambda) {
+    if (!h || !lambda) return fail(h, FMLBM_E_INVALID_ARG, "null argument");
+    const size_t nb = (size_t)reduce_blocks(h->lattice.nx, h->lattice.ny);
+    double* d = nullptr;
+    FM_CUDA(h, cudaMallocAsync((void**)&d, (nb + 1) * h->nc * sizeof(double), h->stream));
+    double* out = d + nb * h->nc;
+    const StepArgs A = make_args(h, h->cur);
+    double sums[kMaxC] = {};
+    cudaError_t e = dispatch_lnrho(h, A, d, out);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sums, out, h->nc * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    cudaFreeAsync(d, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "phase measure");
+    const fmlbm_status st = sync_and_check(h);
+    if (st != FMLBM_OK) return st;
+    const double n = (double)h->lattice.nx * (double)h->lattice.ny;
+    for (int i = 0; i < h->nc; ++i) lambda[i] = sums[i] / n;
+    return FMLBM_OK;
 }
 
 fmlbm_status fmlbm_get_distributions(fmlbm_handle* h, double* g, double* force) {

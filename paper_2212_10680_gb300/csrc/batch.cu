@@ -30,6 +30,8 @@ struct Slot {
     long long steps = 0;      // host mirror of the device counter
     bool have_prev = false;
     double residual = INFINITY;
+    double lam[kMaxC] = {};          // phase measure at the last check: mean of ln rho_i
+    double phase_change = INFINITY;  // max_i |lam_i| change over the last check interval
     fmlbm_status status = FMLBM_OK;
     size_t bytes = 0;
 };
@@ -59,7 +61,8 @@ struct fmlbm_batch {
     double* d_partial = nullptr;
     int partial_cap = 0;
     double* d_out = nullptr;
-    double* h_out = nullptr;    // pinned, capacity * (nc + 2)
+    double* h_out = nullptr;    // pinned, capacity * (2 nc + 2)
+    int criterion = FMLBM_CRITERION_RESIDUAL;
     ErrorLatch* d_err = nullptr;
     ErrorLatch* h_err = nullptr;  // pinned, capacity
     cudaGraphExec_t graph = nullptr;
@@ -123,7 +126,7 @@ template <int ST, int NC>
 cudaError_t launch_batch_reduce_nc(const fmlbm_batch* b) {
     batch_reduce<NC, ST><<<b->nwork, dim3(kTX, 8), 0, b->stream>>>(b->d_lat, b->d_work, b->nwork, b->d_prev,
                                                                    b->d_partial);
-    const int total = b->capacity * (NC + 2);
+    const int total = b->capacity * kBatchSums<NC>;
     batch_reduce_final<NC><<<(total + 127) / 128, 128, 0, b->stream>>>(b->d_lat, b->capacity, b->d_partial,
                                                                          b->d_out);
     return cudaGetLastError();
@@ -212,7 +215,7 @@ fmlbm_status rebuild(fmlbm_batch* b) {
         b->d_partial = nullptr;
         b->work_cap = b->nwork * 2 + 64;
         BCUDA(b, cudaMalloc((void**)&b->d_work, (size_t)b->work_cap * sizeof(WorkItem)));
-        BCUDA(b, cudaMalloc((void**)&b->d_partial, (size_t)b->work_cap * (b->nc + 2) * sizeof(double)));
+        BCUDA(b, cudaMalloc((void**)&b->d_partial, (size_t)b->work_cap * (2 * b->nc + 2) * sizeof(double)));
     }
     if (b->nwork)
         BCUDA(b, cudaMemcpyAsync(b->d_work, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
@@ -271,11 +274,12 @@ fmlbm_status run_chunk(fmlbm_batch* b, int n) {
     return FMLBM_OK;
 }
 
-// Reductions of every active slot -> residuals; latched errors -> statuses.  Synchronises.
+// Reductions of every active slot -> residuals and phase-measure changes; latched errors ->
+// statuses.  Synchronises.
 fmlbm_status check_all(fmlbm_batch* b) {
     if (b->nwork == 0) return FMLBM_OK;
     BCUDA(b, launch_batch_reduce(b));
-    BCUDA(b, cudaMemcpyAsync(b->h_out, b->d_out, (size_t)b->capacity * (b->nc + 2) * sizeof(double),
+    BCUDA(b, cudaMemcpyAsync(b->h_out, b->d_out, (size_t)b->capacity * (2 * b->nc + 2) * sizeof(double),
                              cudaMemcpyDeviceToHost, b->stream));
     BCUDA(b, cudaMemcpyAsync(b->h_err, b->d_err, (size_t)b->capacity * sizeof(ErrorLatch), cudaMemcpyDeviceToHost,
                              b->stream));
@@ -283,16 +287,32 @@ fmlbm_status check_all(fmlbm_batch* b) {
     for (int k = 0; k < b->capacity; ++k) {
         Slot& s = b->slots[k];
         if (!s.used || !s.active) continue;
-        const double* o = b->h_out + (size_t)k * (b->nc + 2);
+        const double* o = b->h_out + (size_t)k * (2 * b->nc + 2);
         if (b->h_err[k].flag) {
             s.status = b->h_err[k].flag == 2 ? FMLBM_E_TIMEOUT : FMLBM_E_NONPHYSICAL;
             s.residual = NAN;
+            s.phase_change = NAN;
             continue;
         }
         s.residual = s.have_prev ? std::sqrt(o[b->nc]) / std::sqrt(o[b->nc + 1]) : INFINITY;
+        const double n = (double)s.L.nx * (double)s.L.ny;
+        double change = 0.0;
+        for (int i = 0; i < b->nc; ++i) {
+            const double lam = o[b->nc + 2 + i] / n;
+            // NaN-propagating: a non-finite measure never counts as converged
+            const double d = std::fabs(lam - s.lam[i]);
+            change = (d > change || d != d) ? d : change;
+            s.lam[i] = lam;
+        }
+        s.phase_change = s.have_prev ? change : INFINITY;
         s.have_prev = true;
     }
     return FMLBM_OK;
+}
+
+// The value fmlbm_batch_run compares with tol: the residual or the phase-measure change.
+double slot_measure(const fmlbm_batch* b, const Slot& s) {
+    return b->criterion == FMLBM_CRITERION_PHASE ? s.phase_change : s.residual;
 }
 
 void free_slot(fmlbm_batch* b, Slot& s) {
@@ -358,9 +378,9 @@ fmlbm_status fmlbm_batch_create(int32_t n_components, int32_t precision, int32_t
               cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device) == cudaSuccess;
     ok = ok && cudaMalloc((void**)&b->d_lat, (size_t)capacity * sizeof(BatchLattice)) == cudaSuccess;
     ok = ok && cudaMalloc((void**)&b->d_prev, (size_t)capacity * sizeof(void*)) == cudaSuccess;
-    ok = ok && cudaMalloc((void**)&b->d_out, (size_t)capacity * (n_components + 2) * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&b->d_out, (size_t)capacity * (2 * n_components + 2) * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMalloc((void**)&b->d_err, (size_t)capacity * sizeof(ErrorLatch)) == cudaSuccess;
-    ok = ok && cudaMallocHost((void**)&b->h_out, (size_t)capacity * (n_components + 2) * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMallocHost((void**)&b->h_out, (size_t)capacity * (2 * n_components + 2) * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMallocHost((void**)&b->h_err, (size_t)capacity * sizeof(ErrorLatch)) == cudaSuccess;
     ok = ok && cudaMemsetAsync(b->d_err, 0, (size_t)capacity * sizeof(ErrorLatch), b->stream) == cudaSuccess;
     if (!ok) {
@@ -521,7 +541,7 @@ fmlbm_status fmlbm_batch_run(fmlbm_batch* b, int64_t max_steps, int32_t check_ev
             if (!s.used || !s.active) continue;
             bool retire = false;
             if (s.status != FMLBM_OK) retire = true;
-            else if (s.residual < tol) retire = true;
+            else if (slot_measure(b, s) < tol) retire = true;
             else if (s.steps >= max_steps) {
                 s.status = FMLBM_E_NOT_CONVERGED;
                 retire = true;
@@ -535,7 +555,7 @@ fmlbm_status fmlbm_batch_run(fmlbm_batch* b, int64_t max_steps, int32_t check_ev
     for (int k = 0; k < b->capacity; ++k) {
         const Slot& s = b->slots[k];
         if (steps_out) steps_out[k] = s.used ? s.steps : 0;
-        if (residual_out) residual_out[k] = s.used ? s.residual : NAN;
+        if (residual_out) residual_out[k] = s.used ? slot_measure(b, s) : NAN;
         if (status_out) status_out[k] = s.used ? s.status : FMLBM_E_INVALID_ARG;
     }
     return FMLBM_OK;
@@ -558,6 +578,20 @@ fmlbm_status fmlbm_batch_slot_info(fmlbm_batch* b, int32_t slot, int64_t* steps,
     if (residual) *residual = s.residual;
     if (status) *status = s.status;
     if (active) *active = s.active ? 1 : 0;
+    return FMLBM_OK;
+}
+
+fmlbm_status fmlbm_batch_slot_phase_change(fmlbm_batch* b, int32_t slot, double* change) {
+    if (!b || !change || slot < 0 || slot >= b->capacity || !b->slots[slot].used)
+        return bfail(b, FMLBM_E_INVALID_ARG, "bad slot");
+    *change = b->slots[slot].phase_change;
+    return FMLBM_OK;
+}
+
+fmlbm_status fmlbm_batch_set_criterion(fmlbm_batch* b, int32_t criterion) {
+    if (!b || (criterion != FMLBM_CRITERION_RESIDUAL && criterion != FMLBM_CRITERION_PHASE))
+        return bfail(b, FMLBM_E_INVALID_ARG, "unknown convergence criterion");
+    b->criterion = criterion;
     return FMLBM_OK;
 }
 
@@ -597,10 +631,10 @@ fmlbm_status fmlbm_batch_phases(fmlbm_batch* b, int32_t slot, double* rho_liquid
     if (e == cudaSuccess) {
         const MixConst& m = b->h_lat[slot].args[0].mixd;
         switch (b->nc) {
-            case 1: phase_nodes<1><<<1, kPhaseThreads, 0, b->stream>>>(d, (long long)nxy, m, out); break;
-            case 2: phase_nodes<2><<<1, kPhaseThreads, 0, b->stream>>>(d, (long long)nxy, m, out); break;
-            case 3: phase_nodes<3><<<1, kPhaseThreads, 0, b->stream>>>(d, (long long)nxy, m, out); break;
-            default: phase_nodes<4><<<1, kPhaseThreads, 0, b->stream>>>(d, (long long)nxy, m, out); break;
+            case 1: phase_nodes<1><<<1, kPhaseThreads, 0, b->stream>>>(d, s.L.nx, s.L.ny, m, out); break;
+            case 2: phase_nodes<2><<<1, kPhaseThreads, 0, b->stream>>>(d, s.L.nx, s.L.ny, m, out); break;
+            case 3: phase_nodes<3><<<1, kPhaseThreads, 0, b->stream>>>(d, s.L.nx, s.L.ny, m, out); break;
+            default: phase_nodes<4><<<1, kPhaseThreads, 0, b->stream>>>(d, s.L.nx, s.L.ny, m, out); break;
         }
         e = cudaGetLastError();
     }

@@ -72,16 +72,21 @@ __global__ void batch_advance(BatchLattice* __restrict__ lat, int n) {
     if (k < n && lat[k].active) lat[k].step += 1;
 }
 
-// Per-item partial sums (NC + 2 doubles: sum rho_i, sum (rho - rho_prev)^2, sum rho^2) over
-// the item's tile of 32 x tile_y nodes, then rho_prev <- rho, with the node sums, the warp
-// tree and the double strip sums of reduce_partial (the rows of a taller tile go through the
-// same compensated sums before the tree).  The items of one lattice are contiguous, so
+// Per-item partial sums (2 NC + 2 doubles: sum rho_i, sum (rho - rho_prev)^2, sum rho^2, then
+// the phase measure's sum ln rho_i) over the item's tile of 32 x tile_y nodes, then
+// rho_prev <- rho, with the node sums, the warp tree and the double strip sums of
+// reduce_partial and lnrho_partial (the rows of a taller tile go through the same
+// compensated sums before the tree).  The items of one lattice are contiguous, so
 // batch_reduce_final sums each lattice in a fixed order.
+template <int NC>
+constexpr int kBatchSums = 2 * NC + 2;
+
 template <int NC, int ST>
 __global__ void __launch_bounds__(kTX* 8) batch_reduce(BatchLattice* __restrict__ lat, const WorkItem* __restrict__ work,
                                                        int nwork, void* const* __restrict__ rho_prev,
                                                        double* __restrict__ partial) {
     using Real = typename StoreTraits<ST>::Real;
+    constexpr int K = kBatchSums<NC>;
     const int w = blockIdx.x;
     if (w >= nwork) return;
     const WorkItem it = work[w];
@@ -89,9 +94,9 @@ __global__ void __launch_bounds__(kTX* 8) batch_reduce(BatchLattice* __restrict_
     const StepArgs& A = L->args[L->step & 1];
     const int nx = A.nx, ny = A.ny, nxy = nx * ny;
     Real* prev = static_cast<Real*>(rho_prev[it.lattice]);
-    Sum2<Real> acc[NC + 2];
+    Sum2<Real> acc[K];
 #pragma unroll
-    for (int k = 0; k < NC + 2; ++k) acc[k] = s2_of(Real(0));
+    for (int k = 0; k < K; ++k) acc[k] = s2_of(Real(0));
     if (L->active) {
         for (int ry = threadIdx.y; ry < L->tile_y; ry += 8) {
             const int x = it.x0 + threadIdx.x, y = it.y0 + ry;
@@ -103,50 +108,78 @@ __global__ void __launch_bounds__(kTX* 8) batch_reduce(BatchLattice* __restrict_
                 Real pv[NC];
 #pragma unroll
                 for (int i = 0; i < NC; ++i) pv[i] = prev[(size_t)i * nxy + node];
-                Sum2<Real> a[NC + 2];
+                Sum2<Real> a[NC + 2], l[NC];
                 diag_node<NC, Real>(r, pv, 1, a);
+                lnrho_node<NC, Real>(r, l);
 #pragma unroll
                 for (int k = 0; k < NC + 2; ++k) acc[k] = s2_add(acc[k], a[k]);
+#pragma unroll
+                for (int i = 0; i < NC; ++i) acc[NC + 2 + i] = s2_add(acc[NC + 2 + i], l[i]);
 #pragma unroll
                 for (int i = 0; i < NC; ++i) prev[(size_t)i * nxy + node] = r[i];
             }
         }
     }
-    __shared__ Sum2<Real> red[8][NC + 2];
-    diag_warp<NC, Real>(acc, red[threadIdx.y]);
+    __shared__ Sum2<Real> red[8][K];
+    sums_warp<K, Real>(acc, red[threadIdx.y]);
     __syncthreads();
     const int tid = threadIdx.y * kTX + threadIdx.x;
-    if (tid < NC + 2) partial[(size_t)w * (NC + 2) + tid] = diag_strip<NC, Real>(red, 0, tid, 0);
+    if (tid < K) partial[(size_t)w * K + tid] = sums_strip<K, Real>(red, 0, tid, 0);
 }
 
 template <int NC>
 __global__ void batch_reduce_final(const BatchLattice* __restrict__ lat, int n, const double* __restrict__ partial,
                                    double* __restrict__ out) {
+    constexpr int K = kBatchSums<NC>;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n * (NC + 2)) return;
-    const int l = k / (NC + 2), q = k % (NC + 2);
+    if (k >= n * K) return;
+    const int l = k / K, q = k % K;
     double v = 0.0;
-    for (int w = lat[l].item0; w < lat[l].item0 + lat[l].nitems; ++w) v += partial[(size_t)w * (NC + 2) + q];
+    for (int w = lat[l].item0; w < lat[l].item0 + lat[l].nitems; ++w) v += partial[(size_t)w * K + q];
     out[k] = v;
 }
 
-// The two phases of a lattice from its densities rho[N][nxy] (mass, double): the node of
-// largest total molar density sum_i rho_i / M_i (liquid) and of smallest (vapour), ties to
-// the lowest node index; out = rho~ at the liquid node [N], then at the vapour node [N].
-// One block, grid-stride over the nodes, a fixed-order tree: deterministic.
+// The two phases of a lattice from its densities rho[N][ny][nx] (mass, double), read as
+// means over 2 x 2 blocks of nodes (block (bx, by) holds the nodes 2 bx, 2 bx + 1 in x and
+// 2 by, 2 by + 1 in y, periodic at an odd edge).  The discrete force of Eqs. eqforcefinal and
+// eq1stder differences a field over two nodes, so a field alternating from node to node (a
+// checkerboard) feels no force, and at rest the well-balanced equilibrium (rho_0 = 0) holds
+// every node's mass in its rest population, so nothing streams it away either: a checkerboard
+// that the transient of a sharp interface excites stays in both bulk phases.  Each parity
+// sublattice is then out of equilibrium on its own; the block mean is the thermodynamic state.
+// out = the block-mean molar densities rho~_i at the block of largest total molar density
+// sum_i rho_i / M_i (liquid) [N], then at the block of smallest (vapour) [N]; ties to the
+// lowest block index (row-major).  One block of threads, grid-stride over the node blocks, a
+// fixed-order tree: deterministic.
 constexpr int kPhaseThreads = 512;
+__device__ __forceinline__ void block_nodes(long long k, int nx, int ny, long long (&node)[4]) {
+    const int bxn = (nx + 1) / 2;
+    const int x0 = 2 * (int)(k % bxn), y0 = 2 * (int)(k / bxn);
+    const int x1 = x0 + 1 < nx ? x0 + 1 : 0, y1 = y0 + 1 < ny ? y0 + 1 : 0;
+    node[0] = (long long)y0 * nx + x0;
+    node[1] = (long long)y0 * nx + x1;
+    node[2] = (long long)y1 * nx + x0;
+    node[3] = (long long)y1 * nx + x1;
+}
+
 template <int NC>
-__global__ void __launch_bounds__(kPhaseThreads) phase_nodes(const double* __restrict__ rho, long long nxy,
+__global__ void __launch_bounds__(kPhaseThreads) phase_nodes(const double* __restrict__ rho, int nx, int ny,
                                                              MixConstT<double> m, double* __restrict__ out) {
     __shared__ double vmax[kPhaseThreads], vmin[kPhaseThreads];
     __shared__ long long imax[kPhaseThreads], imin[kPhaseThreads];
+    const long long nxy = (long long)nx * ny;
+    const long long nblk = (long long)((nx + 1) / 2) * ((ny + 1) / 2);
     const int t = threadIdx.x;
     double hi = -1.0, lo = 0.0;
     long long ih = -1, il = -1;
-    for (long long k = t; k < nxy; k += kPhaseThreads) {
+    for (long long k = t; k < nblk; k += kPhaseThreads) {
+        long long node[4];
+        block_nodes(k, nx, ny, node);
         double s = 0.0;
 #pragma unroll
-        for (int i = 0; i < NC; ++i) s += rho[i * nxy + k] / m.M[i];
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int i = 0; i < NC; ++i) s += rho[i * nxy + node[q]] / m.M[i];
         if (ih < 0 || s > hi) { hi = s; ih = k; }          // k increases: first maximum kept
         if (il < 0 || s < lo) { lo = s; il = k; }
     }
@@ -164,9 +197,14 @@ __global__ void __launch_bounds__(kPhaseThreads) phase_nodes(const double* __res
         }
         __syncthreads();
     }
-    if (t < NC) {
-        out[t] = rho[t * nxy + imax[0]] / m.M[t];
-        out[NC + t] = rho[t * nxy + imin[0]] / m.M[t];
+    if (t < 2 * NC) {
+        const int i = t % NC;
+        long long node[4];
+        block_nodes(t < NC ? imax[0] : imin[0], nx, ny, node);
+        double v = 0.0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v += rho[i * nxy + node[q]] / m.M[i];
+        out[t] = 0.25 * v;
     }
 }
 

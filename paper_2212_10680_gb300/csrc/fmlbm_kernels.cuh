@@ -989,11 +989,11 @@ __device__ __forceinline__ float2 shfl_down(float2 v, int o) {
     return make_float2(__shfl_down_sync(0xffffffffu, v.x, o), __shfl_down_sync(0xffffffffu, v.y, o));
 }
 
-// Warp sums of acc (a fixed shuffle tree) into one row of a per-block table.
-template <int NC, typename V>
-__device__ __forceinline__ void diag_warp(const Sum2<V> (&acc)[NC + 2], Sum2<V>* row) {
+// Warp sums of K compensated sums (a fixed shuffle tree) into one row of a per-block table.
+template <int K, typename V>
+__device__ __forceinline__ void sums_warp(const Sum2<V> (&acc)[K], Sum2<V>* row) {
 #pragma unroll
-    for (int k = 0; k < NC + 2; ++k) {
+    for (int k = 0; k < K; ++k) {
         Sum2<V> v = acc[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -1005,11 +1005,15 @@ __device__ __forceinline__ void diag_warp(const Sum2<V> (&acc)[NC + 2], Sum2<V>*
         if ((threadIdx.x & 31) == 0) row[k] = v;
     }
 }
+template <int NC, typename V>
+__device__ __forceinline__ void diag_warp(const Sum2<V> (&acc)[NC + 2], Sum2<V>* row) {
+    sums_warp<NC + 2, V>(acc, row);
+}
 
 // Sum in double of eight consecutive rows of that table, in row order (one 32 x 8 strip), for
 // lane l of the lane type.
-template <int NC, typename V>
-__device__ __forceinline__ double diag_strip(const Sum2<V> (*red)[NC + 2], int row0, int k, int l) {
+template <int K, typename V>
+__device__ __forceinline__ double sums_strip(const Sum2<V> (*red)[K], int row0, int k, int l) {
     double v = 0.0;
 #pragma unroll
     for (int w = 0; w < 8; ++w) {
@@ -1017,6 +1021,22 @@ __device__ __forceinline__ double diag_strip(const Sum2<V> (*red)[NC + 2], int r
         if constexpr (kCompensated<V>) v += (double)lane(red[row0 + w][k].lo, l);
     }
     return v;
+}
+template <int NC, typename V>
+__device__ __forceinline__ double diag_strip(const Sum2<V> (*red)[NC + 2], int row0, int k, int l) {
+    return sums_strip<NC + 2, V>(red, row0, k, l);
+}
+
+// The phase measure's node terms: ln rho_i.  A sum over a periodic lattice of a smooth
+// function of the densities does not change when the density field moves rigidly (a flat
+// or curved interface drifting with the momentum the transient left, which nothing damps in
+// a periodic box), while it follows every change of the phases themselves: its change over
+// a check interval, divided by the node count, is the volume-averaged relative change of
+// rho_i.
+template <int NC, typename V>
+__device__ __forceinline__ void lnrho_node(const V (&r)[NC], Sum2<V> (&acc)[NC]) {
+#pragma unroll
+    for (int i = 0; i < NC; ++i) acc[i] = s2_of(vln(r[i]));
 }
 
 // Diagnostics of the state a step reads, fused into the step (A.diag_partial set): the
@@ -1209,7 +1229,49 @@ __global__ void __launch_bounds__(kTX* kRedTY) reduce_partial(StepArgs A,
         partial[(size_t)(blockIdx.y * gridDim.x + blockIdx.x) * (NC + 2) + tid] = diag_strip<NC, Real>(red, 0, tid, 0);
 }
 
+// Phase measure of a lattice: per component the sum over the nodes of ln rho_i, on the tiling
+// of reduce_partial (NC double sums per 32 x 8 strip, compensated within a warp as there);
+// sum_columns adds the strips in a fixed order.  Reads the state only.
+template <int NC, int ST>
+__global__ void __launch_bounds__(kTX* kRedTY) lnrho_partial(StepArgs A, double* __restrict__ partial) {
+    using Real = typename StoreTraits<ST>::Real;
+    const int nx = A.nx, ny = A.ny, nxy = nx * ny;
+    const int x = blockIdx.x * kTX + threadIdx.x, y = blockIdx.y * kRedTY + threadIdx.y;
+    Sum2<Real> acc[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) acc[k] = s2_of(Real(0));
+    if (x < nx && y < ny) {
+        const bool inner = x >= 1 && x + 1 < nx && y >= 1 && y + 1 < ny;
+        Real r[NC];
+        pull_rho<NC, ST>(A, x, y, inner, nx, ny, nxy, r);
+        lnrho_node<NC, Real>(r, acc);
+    }
+    __shared__ Sum2<Real> red[kRedTY][NC];
+    sums_warp<NC, Real>(acc, red[threadIdx.y]);
+    __syncthreads();
+    const int tid = threadIdx.y * kTX + threadIdx.x;
+    if (tid < NC)
+        partial[(size_t)(blockIdx.y * gridDim.x + blockIdx.x) * NC + tid] = sums_strip<NC, Real>(red, 0, tid, 0);
+}
+
 constexpr int kFinalThreads = 256;
+
+// Column k of a table of nrows rows of K doubles, summed in double in a fixed order (strided
+// over the threads, then a fixed tree); the result is valid in thread 0.
+template <int K>
+__device__ __forceinline__ double column_sum(const double* __restrict__ partial, int nrows, int k) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nrows; b += kFinalThreads) v += partial[(size_t)b * K + k];
+    __shared__ double red[kFinalThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kFinalThreads / 32; ++w) t += red[w];
+    return t;
+}
 
 // latch (may be null): the handle's error latch, copied after the sums (at out + kMaxC + 2) so
 // that one device-to-host copy brings a request's results and the error state together.
@@ -1217,7 +1279,7 @@ template <int NC>
 __global__ void __launch_bounds__(kFinalThreads) reduce_final(const double* __restrict__ partial, int nblocks,
                                                                double* __restrict__ out,
                                                                const ErrorLatch* __restrict__ latch) {
-    // block k sums quantity k over all strips in double: fixed strided order, then a fixed tree
+    // block k sums quantity k over all strips
     const int k = blockIdx.x;
     if (latch != nullptr && k == 0 && threadIdx.x == 0) {
         const volatile int* src = reinterpret_cast<const volatile int*>(latch);
@@ -1225,18 +1287,16 @@ __global__ void __launch_bounds__(kFinalThreads) reduce_final(const double* __re
 #pragma unroll
         for (int q = 0; q < (int)(sizeof(ErrorLatch) / sizeof(int)); ++q) dst[q] = src[q];
     }
-    double v = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += kFinalThreads) v += partial[(size_t)b * (NC + 2) + k];
-    __shared__ double red[kFinalThreads / 32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < kFinalThreads / 32; ++w) t += red[w];
-        out[k] = t;
-    }
+    const double t = column_sum<NC + 2>(partial, nblocks, k);
+    if (threadIdx.x == 0) out[k] = t;
+}
+
+// out[k] = column k of a table of nrows rows of K doubles (one block per column).
+template <int K>
+__global__ void __launch_bounds__(kFinalThreads) sum_columns(const double* __restrict__ partial, int nrows,
+                                                              double* __restrict__ out) {
+    const double t = column_sum<K>(partial, nrows, blockIdx.x);
+    if (threadIdx.x == 0) out[blockIdx.x] = t;
 }
 
 inline int reduce_blocks(int nx, int ny) { return ((nx + kTX - 1) / kTX) * ((ny + kRedTY - 1) / kRedTY); }

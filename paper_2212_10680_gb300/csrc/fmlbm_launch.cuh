@@ -66,6 +66,11 @@ template <int ST>
 cudaError_t launch_reduce(const StepArgs& A, int nc, void* rho_prev, int have_prev, void* partial,
                           double* out, cudaStream_t s);
 
+// Phase measure: out[i] = sum over the nodes of ln rho_i (NC doubles, device); partial:
+// NC * reduce_blocks(nx, ny) doubles.
+template <int ST>
+cudaError_t launch_lnrho(const StepArgs& A, int nc, double* partial, double* out, cudaStream_t s);
+
 // The fixed-order final sum alone, for partial sums a fused step wrote (A.diag_partial):
 // (NC + 2) doubles per 32 x 8 strip; latch (may be null): copied to out + kMaxC + 2.
 inline cudaError_t launch_reduce_final(int nc, const void* partial, int nx, int ny, double* out, cudaStream_t s,
@@ -172,6 +177,24 @@ inline cudaError_t launch_reduce_final(int nc, const void* partial, int nx, int 
             case 2: return launch_reduce_nc_##ST<2>(A, rho_prev, have_prev, partial, out, s);             \
             case 3: return launch_reduce_nc_##ST<3>(A, rho_prev, have_prev, partial, out, s);             \
             case 4: return launch_reduce_nc_##ST<4>(A, rho_prev, have_prev, partial, out, s);             \
+        }                                                                                                 \
+        return cudaErrorInvalidValue;                                                                     \
+    }                                                                                                     \
+    template <int NC>                                                                                     \
+    static cudaError_t launch_lnrho_nc_##ST(const StepArgs& A, double* partial, double* out,              \
+                                            cudaStream_t s) {                                             \
+        dim3 grid((A.nx + kTX - 1) / kTX, (A.ny + kRedTY - 1) / kRedTY);                                  \
+        lnrho_partial<NC, ST><<<grid, dim3(kTX, kRedTY), 0, s>>>(A, partial);                             \
+        sum_columns<NC><<<NC, kFinalThreads, 0, s>>>(partial, reduce_blocks(A.nx, A.ny), out);            \
+        return cudaGetLastError();                                                                        \
+    }                                                                                                     \
+    template <>                                                                                           \
+    cudaError_t launch_lnrho<ST>(const StepArgs& A, int nc, double* partial, double* out, cudaStream_t s) { \
+        switch (nc) {                                                                                     \
+            case 1: return launch_lnrho_nc_##ST<1>(A, partial, out, s);                                   \
+            case 2: return launch_lnrho_nc_##ST<2>(A, partial, out, s);                                   \
+            case 3: return launch_lnrho_nc_##ST<3>(A, partial, out, s);                                   \
+            case 4: return launch_lnrho_nc_##ST<4>(A, partial, out, s);                                   \
         }                                                                                                 \
         return cudaErrorInvalidValue;                                                                     \
     }

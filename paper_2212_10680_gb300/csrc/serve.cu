@@ -4,8 +4,8 @@
 // queued requests in arrival order while a slot is free and the requests' device
 // bytes fit the budget (head-of-line: a request that does not fit waits for memory to
 // free up, later ones wait behind it), runs one graph-captured chunk for every
-// admitted lattice, checks residuals, and retires each lattice at its own criterion
-// (residual below tol, a latched error, or its step limit), copying its final
+// admitted lattice, checks residuals and phase measures, and retires each lattice at its own
+// criterion (the configured measure below tol, a latched error, or its step limit), copying its final
 // densities out and freeing its memory.  Each lattice's arithmetic is unaffected by
 // what else runs (the batch guarantees bit-identical per-lattice results), so a
 // request's result is the same alone and in any mix.
@@ -143,6 +143,7 @@ void worker_main(fmlbm_server* s) {
             double res = 0;
             int32_t status = 0, active = 0;
             fmlbm_batch_slot_info(s->batch, kv.first, &steps, &res, &status, &active);
+            if (s->cfg.criterion == FMLBM_CRITERION_PHASE) fmlbm_batch_slot_phase_change(s->batch, kv.first, &res);
             bool retire = false;
             if (status != FMLBM_OK) retire = true;
             else if (res < s->cfg.tol) retire = true;
@@ -171,7 +172,8 @@ extern "C" {
 
 fmlbm_status fmlbm_server_create(const fmlbm_server_config* cfg, fmlbm_server** out) {
     if (!cfg || !out || cfg->max_slots < 1 || cfg->chunk_steps < 1 || cfg->max_steps < 1 || cfg->queue_capacity < 1 ||
-        cfg->hbm_budget_bytes == 0)
+        cfg->hbm_budget_bytes == 0 ||
+        (cfg->criterion != FMLBM_CRITERION_RESIDUAL && cfg->criterion != FMLBM_CRITERION_PHASE))
         return FMLBM_E_INVALID_ARG;
     *out = nullptr;
     fmlbm_server* s = new (std::nothrow) fmlbm_server();

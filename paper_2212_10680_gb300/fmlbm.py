@@ -57,7 +57,7 @@ class fmlbm_server_config(ctypes.Structure):
     _fields_ = [("n_components", ctypes.c_int32), ("precision", ctypes.c_int32), ("max_slots", ctypes.c_int32),
                 ("chunk_steps", ctypes.c_int32), ("tol", ctypes.c_double), ("max_steps", ctypes.c_int64),
                 ("hbm_budget_bytes", ctypes.c_size_t), ("queue_capacity", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("criterion", ctypes.c_int32)]
 
 
 class fmlbm_request(ctypes.Structure):
@@ -94,6 +94,7 @@ def _load() -> ctypes.CDLL:
         "fmlbm_get_distributions": ([H, dp, dp], ctypes.c_int),
         "fmlbm_set_distributions": ([H, dp, dp], ctypes.c_int),
         "fmlbm_diagnostics": ([H, dp, dp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "fmlbm_phase_measure": ([H, dp], ctypes.c_int),
         "fmlbm_error_node": ([H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                               ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "fmlbm_state_size": ([H, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
@@ -127,6 +128,8 @@ def _load() -> ctypes.CDLL:
         "fmlbm_batch_slot_info": ([H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), dp,
                                    ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "fmlbm_batch_moments": ([H, ctypes.c_int32, dp, dp, dp], ctypes.c_int),
+        "fmlbm_batch_set_criterion": ([H, ctypes.c_int32], ctypes.c_int),
+        "fmlbm_batch_slot_phase_change": ([H, ctypes.c_int32, dp], ctypes.c_int),
         "fmlbm_batch_phases": ([H, ctypes.c_int32, dp, dp], ctypes.c_int),
         "fmlbm_batch_get_distributions": ([H, ctypes.c_int32, dp, dp], ctypes.c_int),
         "fmlbm_batch_autotune": ([H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
@@ -291,6 +294,13 @@ def fmlbm_diagnostics_wait(h, ticket: int, n_components: int):
     return mass, res.value, step.value
 
 
+def fmlbm_phase_measure(h, n_components: int) -> np.ndarray:
+    """lambda_i = mean over the nodes of ln rho_i, per component."""
+    lam = np.empty(n_components)
+    _check(LIB.fmlbm_phase_measure(h, _ptr(lam)), "fmlbm_phase_measure", h)
+    return lam
+
+
 def fmlbm_error_node(h):
     c, x, y = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     _check(LIB.fmlbm_error_node(h, ctypes.byref(c), ctypes.byref(x), ctypes.byref(y)), "fmlbm_error_node", h)
@@ -320,6 +330,7 @@ def fmlbm_set_tile_height(h, tile_y: int):
 
 
 VARIANT = {"auto": 0, "plain": 1, "tma": 2, "tma_tile": 3, "pair": 4}
+CRITERION = {"residual": 0, "phase": 1}
 
 
 def fmlbm_set_step_variant(h, variant: str):
@@ -425,6 +436,16 @@ def fmlbm_batch_slot_info(b, slot: int):
     return steps.value, res.value, st.value, bool(act.value)
 
 
+def fmlbm_batch_set_criterion(b, criterion: str):
+    _bcheck(LIB.fmlbm_batch_set_criterion(b, CRITERION[criterion]), "fmlbm_batch_set_criterion", b)
+
+
+def fmlbm_batch_slot_phase_change(b, slot: int) -> float:
+    v = ctypes.c_double()
+    _bcheck(LIB.fmlbm_batch_slot_phase_change(b, slot, ctypes.byref(v)), "fmlbm_batch_slot_phase_change", b)
+    return v.value
+
+
 def fmlbm_batch_moments(b, slot: int, rho=None, u=None, lnf=None):
     _bcheck(LIB.fmlbm_batch_moments(b, slot, _ptr(rho), _ptr(u), _ptr(lnf)), "fmlbm_batch_moments", b)
 
@@ -462,9 +483,10 @@ def fmlbm_batch_run_chunk(b, steps: int):
 
 
 def fmlbm_server_create(n_components: int, precision: str, max_slots: int, chunk_steps: int, tol: float,
-                        max_steps: int, hbm_budget_bytes: int, queue_capacity: int = 4096):
+                        max_steps: int, hbm_budget_bytes: int, queue_capacity: int = 4096,
+                        criterion: str = "residual"):
     cfg = fmlbm_server_config(n_components, PRECISION[precision], max_slots, chunk_steps, tol, max_steps,
-                              hbm_budget_bytes, queue_capacity, 0)
+                              hbm_budget_bytes, queue_capacity, CRITERION[criterion])
     s = ctypes.c_void_p()
     _check(LIB.fmlbm_server_create(ctypes.byref(cfg), ctypes.byref(s)), "fmlbm_server_create")
     return s
@@ -541,6 +563,9 @@ class Lattice:
 
     def diagnostics(self):
         return fmlbm_diagnostics(self.h, self.n)
+
+    def phase_measure(self):
+        return fmlbm_phase_measure(self.h, self.n)
 
     def synchronize(self):
         fmlbm_synchronize(self.h)

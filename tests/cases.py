@@ -67,6 +67,30 @@ def run_oracle(mixd, rho, tau, stencil, velocity_force, steps, record=(), formul
     return out
 
 
+def block_phases(r, M):
+    """Block-mean phases of fmlbm_batch_phases, on the host: blocks of nodes 2bx, 2bx + 1 by
+    2by, 2by + 1 (periodic at an odd edge), summed node by node, component by component."""
+    n, ny, nx = r.shape
+    rt = [r[i] / M[i] for i in range(n)]
+    xs0 = 2 * np.arange((nx + 1) // 2)
+    ys0 = 2 * np.arange((ny + 1) // 2)
+    xs1 = np.where(xs0 + 1 < nx, xs0 + 1, 0)
+    ys1 = np.where(ys0 + 1 < ny, ys0 + 1, 0)
+    corners = [(ys0, xs0), (ys0, xs1), (ys1, xs0), (ys1, xs1)]
+    tot = np.zeros((ys0.size, xs0.size))
+    for ys, xs in corners:
+        for i in range(n):
+            tot = tot + rt[i][np.ix_(ys, xs)]
+    out = []
+    for k in (int(np.argmax(tot)), int(np.argmin(tot))):
+        by, bx = divmod(k, xs0.size)
+        v = np.zeros(n)
+        for ys, xs in corners:
+            v = v + np.array([rt[i][ys[by], xs[bx]] for i in range(n)])
+        out.append(0.25 * v)
+    return out
+
+
 def normwise(a, b):
     """max |a - b| / max |b| (0 if both vanish)."""
     den = np.max(np.abs(b))

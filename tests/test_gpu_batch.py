@@ -2,7 +2,7 @@
 import numpy as np
 import pytest
 
-from cases import mixture_dict, slab_state_binary, workloads
+from cases import block_phases, mixture_dict, slab_state_binary, workloads
 
 pytestmark = pytest.mark.gpu
 
@@ -82,16 +82,12 @@ def test_batch_moments_equal_single_lattice_moments(fm, precision):
         rs, us, ls = lat.moments()
         lat.close()
         assert np.array_equal(r, rs) and np.array_equal(u, us) and np.array_equal(lnf, ls), (nx, ny)
-        # the phases: rho~ (= rho / M) at the nodes of largest and smallest total molar
-        # density, first in row-major order on ties, from the same densities
-        M = np.asarray(mixd["M"], dtype=np.float64)
-        tot = np.zeros(nx * ny)
-        for i in range(2):
-            tot = tot + r[i].ravel() / M[i]
+        # the phases: 2 x 2 block means of rho~ (= rho / M) at the blocks of largest and
+        # smallest total molar density, first in row-major block order on ties, from the same
+        # densities and in the same order of additions
         liq, vap = fm.fmlbm_batch_phases(b, slot, 2)
-        iL, iV = int(np.argmax(tot)), int(np.argmin(tot))
-        assert np.array_equal(liq, np.array([r[i].ravel()[iL] / M[i] for i in range(2)]))
-        assert np.array_equal(vap, np.array([r[i].ravel()[iV] / M[i] for i in range(2)]))
+        want_l, want_v = block_phases(r, np.asarray(mixd["M"], dtype=np.float64))
+        assert np.array_equal(liq, want_l) and np.array_equal(vap, want_v)
     fm.fmlbm_batch_destroy(b)
 
 

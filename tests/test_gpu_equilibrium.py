@@ -79,10 +79,12 @@ def test_droplet_1024_fp32_against_the_flash(fm):
     # FP32, tau 1, 1% noise) after 50,000 steps.  The curved interface compresses the liquid,
     # so the flat flash is not the liquid's reference: the vapour far from the droplet is
     # compared with the flash at its own pressure, and the droplet centre with the far vapour
-    # (equal fugacities across the interface).  Tolerances: the method's discretisation error
-    # at this sharp interface (the flat slab of the same mixture at 0.8 Tc1 is off by 2-3 % in
-    # density and 1e-2 in ln f); FP32 cannot reach a 1e-8 residual and the droplet still
-    # carries spurious currents of about 1e-4.  The droplet keeps its size (crossing radius),
+    # (equal fugacities across the interface).  The bulk phases are read as means over 4 x 4
+    # windows: the sharp interface leaves a node-to-node alternation in both phases that the
+    # force does not see (the flat slab of the same mixture is 2-3 % off the flash node by node,
+    # 1e-4 as a mean over node pairs).  Tolerance 1e-2: measured 4.8e-3 in density and
+    # composition and 7.5e-3 in ln f after 50,000 steps, with the droplet still relaxing and
+    # carrying spurious currents of about 1e-4 (FP32 cannot reach a 1e-8 residual).  The droplet keeps its size (crossing radius),
     # and Eq. eqMCsigma over its own profile gives the sigma of a flat interface of the same
     # mixture (a strip run alongside) to 2 %: at R / W ~ 50 the tension does not depend on
     # the curvature.
@@ -97,12 +99,17 @@ def test_droplet_1024_fp32_against_the_flash(fm):
     r, u, lnf = lat.moments()
     lat.close()
     c = n // 2
-    L = r[:, c - 2:c + 3, c - 2:c + 3].mean(axis=(1, 2))      # droplet centre (M = 1: molar)
-    V = r[:, 0:5, 0:5].mean(axis=(1, 2))                      # farthest from the droplet
+    # 4 x 4 windows: an even number of nodes of each parity, so the node-to-node alternation
+    # the sharp interface leaves in the bulk phases averages out
+    L = r[:, c - 2:c + 2, c - 2:c + 2].mean(axis=(1, 2))      # droplet centre (M = 1: molar)
+    V = r[:, 0:4, 0:4].mean(axis=(1, 2))                      # farthest from the droplet
     f = flash(mix, float(pressure(mix, V)), [0.5, 0.5])
-    assert np.max(np.abs(V / f["rtV"] - 1)) < 2e-2
-    assert np.max(np.abs((V / V.sum() - f["y"]) / f["y"])) < 2e-2
-    assert np.max(np.abs(lnf_density_form(mix, L) - lnf_density_form(mix, V))) < 2e-2
+    print("droplet: vapour density", np.max(np.abs(V / f["rtV"] - 1)), "composition",
+          np.max(np.abs((V / V.sum() - f["y"]) / f["y"])), "ln f across",
+          np.max(np.abs(lnf_density_form(mix, L) - lnf_density_form(mix, V))))
+    assert np.max(np.abs(V / f["rtV"] - 1)) < 1e-2
+    assert np.max(np.abs((V / V.sum() - f["y"]) / f["y"])) < 1e-2
+    assert np.max(np.abs(lnf_density_form(mix, L) - lnf_density_form(mix, V))) < 1e-2
     row = r[:, c, :].astype(np.float64)                        # crosses two interfaces
     R = crossing_radius(row.sum(axis=0), c, 0.5 * (L.sum() + V.sum()))
     assert 190 < R < 210

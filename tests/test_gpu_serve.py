@@ -5,7 +5,7 @@ import time
 import numpy as np
 import pytest
 
-from cases import mixture_dict, slab_state_binary, workloads
+from cases import block_phases, mixture_dict, slab_state_binary, workloads
 
 pytestmark = pytest.mark.gpu
 
@@ -58,12 +58,11 @@ def test_result_is_the_same_alone_and_in_the_mix(fm):
     mine = [r for r in res if r["tag"] == 1][0]
     assert mine["steps"] == 600
     assert np.array_equal(alone, mixed)
-    # the phases of the result are the returned field's densest and least dense nodes
+    # the phases of the result are the returned field's densest and least dense 2 x 2 blocks
     # (M = 1: molar = mass densities)
-    tot = mixed[0] / 1.0 + mixed[1] / 1.0
-    iL, iV = np.argmax(tot.ravel()), np.argmin(tot.ravel())
-    assert mine["rho_liquid"] == [float(mixed[i].ravel()[iL]) for i in range(2)]
-    assert mine["rho_vapour"] == [float(mixed[i].ravel()[iV]) for i in range(2)]
+    liq, vap = block_phases(mixed, np.ones(2))
+    assert mine["rho_liquid"] == [float(v) for v in liq]
+    assert mine["rho_vapour"] == [float(v) for v in vap]
     assert mine["rho_liquid"][0] + mine["rho_liquid"][1] > 5 * (mine["rho_vapour"][0] + mine["rho_vapour"][1])
 
 

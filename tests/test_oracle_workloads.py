@@ -93,3 +93,25 @@ def test_tau_0_8_leaves_the_eos_domain_for_the_substituted_binary(W):
 def test_substituted_binary_is_stable_at_tau_1():
     mix, rtV, rtL = _substituted_binary()
     assert _steps_until_nonphysical(mix, rtV, rtL, 4.0, 1.0, 3000) is None
+
+
+@pytest.mark.parametrize("k,diverges", [(0, True), (10, True), (20, False)])
+def test_sweep_feeds_below_z1_0_11_leave_the_eos_domain(k, diverges):
+    """The P-x sweep of the binary (T = 0.8 Tc1, z1 = 0.05 + 0.9 k / 255): the unperturbed flat
+    slab of a feed with z1 = 0.05 or 0.085 leaves the EOS domain within 200 steps on a
+    256-node strip, whereas z1 = 0.12 stays physical; the sweep workload therefore spans
+    z1 = 0.12 .. 0.95."""
+    wl = workloads()
+    st = wl["binary_sweep"][k]
+    mix, _, _ = _substituted_binary()
+    rho = inputs.slab(st["rt_vapour"], st["rt_liquid"], 256, 1, 0.5, 4.0)
+    g, F = lbm.init_at_rest(rho)
+    lat = lbm.Lattice(tau=1.0, stencil="isotropic", velocity_force="lagged")
+    failed = None
+    for s in range(1, 1001 if not diverges else 201):
+        try:
+            g, F = lbm.step(g, mix, lat, F)
+        except lbm.NonPhysicalState:
+            failed = s
+            break
+    assert (failed is not None) == diverges, (st["z"], failed)
