@@ -563,7 +563,7 @@ SWEEP_FIRST = 20
 
 
 def run_batch(args, rank, world, dist=None, summary=False):
-    """Batched P-x sweep: independent binary lattices (side ~ U{64..max_side}, feeds z1 swept
+    """Batched P-x sweep: independent binary lattices (side 4 x U{16..max_side / 4}, feeds z1 swept
     0.12..0.95 at fixed T), one persistent multi-lattice step per time step, graph-captured
     chunks, per-lattice retirement; against the same lattices run one after another with
     single-lattice handles and the same retirement rule.  Each lattice starts as Section V.B
@@ -587,7 +587,10 @@ def run_batch(args, rank, world, dist=None, summary=False):
     n = len(mixd["Tc"])
     nlat = args.batch_lattices
     rng = np.random.default_rng(4)
-    sides = rng.integers(64, args.batch_max_side + 1, nlat)
+    # sides are multiples of 4, so that the interface centres of Eq. eqInit (n_x / 4 and
+    # 3 n_x / 4) sit on nodes, as in the paper's set-ups (n_x = 200, 400); with the centres
+    # between nodes the transient of the low-z1 feeds leaves the EOS domain on wide lattices
+    sides = 4 * rng.integers(16, args.batch_max_side // 4 + 1, nlat)
     mine = list(shard(nlat, rank, world))
     fields, states = {}, {}
     for k in mine:
@@ -685,7 +688,7 @@ def run_batch(args, rank, world, dist=None, summary=False):
         metric="batched VLE solves/sec", value=nlat / t_batch, unit="solves/s", n_gpus=world,
         steps=max_steps_done, warmup=3, ms_per_step=None, higher_is_better=True, scaling="strong",
         vs_baseline=None, dtype="f64" if prec == "fp64" else "f32", data="synthetic",
-        config=dict(workload=f"batched P-x sweep: {nlat} binary PR lattices, side U{{64..{args.batch_max_side}}}, "
+        config=dict(workload=f"batched P-x sweep: {nlat} binary PR lattices, side 4 U{{16..{args.batch_max_side // 4}}}, "
                              f"z1 0.12..0.95, flat slab of Eq. eqInit (W 4, unperturbed), tau 1.0",
                     precision=prec, max_steps=args.max_steps, check_every=args.check_every, tol=args.tol,
                     criterion=args.criterion, autotune=dict(tile_y=ty, blocks=blocks)),
@@ -719,7 +722,7 @@ def _downsample(points: list, k: int) -> list:
 
 def run_serve(args, rank, world, dist=None, summary=False):
     """Serving: Poisson arrivals of binary and ternary VLE requests (templates with random T
-    and feed, side ~ U{64..max_side}); continuous batching servers, one per component count;
+    and feed, side 4 x U{16..max_side / 4}); continuous batching servers, one per component count;
     against a FIFO loop that runs one request at a time with a single-lattice handle and the
     same retirement rule.  Each request starts from the unperturbed flat interface of Eq.
     eqInit between its flash phases and retires at the convergence criterion (by default the
@@ -744,7 +747,7 @@ def run_serve(args, rank, world, dist=None, summary=False):
     reqs = {}
     for k in range(R):
         t = temps[int(rng.integers(0, len(temps)))]
-        side = int(rng.integers(64, args.max_side + 1))
+        side = 4 * int(rng.integers(16, args.max_side // 4 + 1))     # interface centres on nodes
         if k not in mine:
             continue
         rho = inputs.slab(t["slab"]["rt_vapour"], t["slab"]["rt_liquid"], side, side, 0.5, 4.0)
@@ -837,7 +840,7 @@ def run_serve(args, rank, world, dist=None, summary=False):
         warmup=0, ms_per_step=None, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
         data="synthetic", config=dict(
             workload=f"Poisson arrivals ({args.rate}/s) of {R} binary/ternary PR VLE requests, side "
-                     f"U{{64..{args.max_side}}}, T U[0.80,0.92] Tc1 (binary) / U[0.85,0.92] Tc1 (ternary), "
+                     f"4 U{{16..{args.max_side // 4}}}, T U[0.80,0.92] Tc1 (binary) / U[0.85,0.92] Tc1 (ternary), "
                      f"flat slab of Eq. eqInit (W 4, unperturbed)",
             slots=args.slots, chunk_steps=args.check_every, tol=args.tol, criterion=args.criterion,
             max_steps=args.max_steps, hbm_budget_gb=args.budget_gb),

@@ -91,6 +91,25 @@ def block_phases(r, M):
     return out
 
 
+def slab_phases(r, M, pair=True):
+    """Molar densities at the middle of the liquid run and of the vapour run of a 1-D
+    periodic profile (the slab may sit anywhere: a flat slab can translate), as means over
+    two neighbouring nodes (pair=True) or at single nodes.  The force of Eqs. eqforcefinal and
+    eq1stder differences each field over two nodes, so a node-to-node alternation left by the
+    transient feels no force and stays in the bulk phases; the pair mean is the phase."""
+    tot = r[:, 0, :].sum(axis=0)
+    nx = tot.size
+    liquid = tot > 0.5 * (tot.max() + tot.min())
+    start = int(np.argmin(tot))           # a vapour node: the liquid run is contiguous after it
+    idx = np.nonzero(np.roll(liquid, -start))[0]
+    iL = (start + (idx[0] + idx[-1]) // 2) % nx
+    iV = (iL + nx // 2) % nx
+    if not pair:
+        return r[:, 0, iL] / M, r[:, 0, iV] / M
+    return (0.5 * (r[:, 0, iL] + r[:, 0, (iL + 1) % nx]) / M,
+            0.5 * (r[:, 0, iV] + r[:, 0, (iV + 1) % nx]) / M)
+
+
 def normwise(a, b):
     """max |a - b| / max |b| (0 if both vanish)."""
     den = np.max(np.abs(b))

@@ -26,7 +26,7 @@ import numpy as np
 import pytest
 from scipy.optimize import curve_fit
 
-from cases import oracle_mixture, paper_cases, paper_mixture
+from cases import oracle_mixture, paper_cases, paper_mixture, slab_phases
 from oracle.eos import lnf_density_form, pressure
 from oracle.flash import flash, vapour_volume_fraction, volume_roots
 from oracle.interface import crossing_radius, interfacial_tension, lamb_period
@@ -54,19 +54,6 @@ def _relax(fm, mixd, rho, tau, steps, precision="fp64", stencil="central"):
     return r, u, lnf
 
 
-def _bulk_phases(r, M):
-    """Molar densities at the middle of the liquid run and of the vapour run of a 1-D
-    periodic profile (the slab may sit anywhere: a flat slab can translate)."""
-    tot = r[:, 0, :].sum(axis=0)
-    nx = tot.size
-    liquid = tot > 0.5 * (tot.max() + tot.min())
-    start = int(np.argmin(tot))           # a vapour node: the liquid run is contiguous after it
-    idx = np.nonzero(np.roll(liquid, -start))[0]
-    iL = (start + (idx[0] + idx[-1]) // 2) % nx
-    iV = (iL + nx // 2) % nx
-    return r[:, 0, iL] / M, r[:, 0, iV] / M
-
-
 def _errors_percent(mix, M, L, V, z):
     """Relative errors (%) of Eq. eqerror against the flash at the vapour's pressure."""
     f = flash(mix, float(pressure(mix, V)), z)
@@ -88,35 +75,61 @@ def _flat_case(c, eos):
 @pytest.mark.parametrize("eos", ["pr", "srk"])
 def test_v_a_propane_pentane_flat_interface(fm, eos):
     # paper (Table tabcase1error): every relative error below 3e-4 %, after 1e6 steps.
-    # Here, after the same 1e6 FP64 steps: up to about 3e-3 % (GB300; after 5e5 steps the
-    # bulk is still relaxing, up to 0.04 %); bound 0.01 %.
+    # Here, after the same 1e6 FP64 steps, bulk phases as node-pair means: density 2.7e-4 % /
+    # 1.4e-4 %, compositions 1.0e-3 % / 5.3e-4 % (PR / SRK; after 5e5 steps the bulk is still
+    # relaxing, up to 0.04 %); bound 2e-3 %.  Single nodes carry the alternation of the two
+    # node parities (3.5e-5 / 8.8e-5 of the density) and stay about 5e-4 % / 2e-3 % off.
     c = CASES["c3c5_flat"]
     mixd, mix, M, rho = _flat_case(c, eos)
     r, u, _ = _relax(fm, mixd, rho, c["tau"], c["steps"])
-    L, V = _bulk_phases(r, M)
+    L, V = slab_phases(r, M)
     dens, comp = _errors_percent(mix, M, L, V, c["z"])
     print(eos, "density error %", dens, "composition error %", comp)
-    assert np.max(dens) < 0.01 and np.max(comp) < 0.01, (dens, comp)
+    assert np.max(dens) < 2e-3 and np.max(comp) < 2e-3, (dens, comp)
     assert np.max(np.abs(lnf_density_form(mix, L) - lnf_density_form(mix, V))) < 1e-4
 
 
+def test_v_a_error_against_steps(fm):
+    """V.A (PR) out to 2e6 steps: the pair-mean phases keep converging to the flash at the
+    lattice's pressure (measured 1.8e-7 % in density, 6.6e-7 % in composition at 2e6 steps,
+    1.3e-8 % / 4.8e-8 % at 4e6), far below Table tabcase1error's 3e-4 %, while single nodes
+    stop near 5e-4 % / 2e-3 % from 1e6 steps on: the gap between the paper's table and a
+    node-by-node reading is the alternation of the node parities, not unfinished relaxation."""
+    c = CASES["c3c5_flat"]
+    mixd, mix, M, rho = _flat_case(c, "pr")
+    lat = fm.Lattice(fm.mixture_from_dict(mixd), c["nx"], c["ny"], c["tau"], "central", "fp64", "lagged")
+    lat.init(rho)
+    node_err = []
+    for target in (1000000, 2000000):
+        lat.step(1000000)
+        r, u, _ = lat.moments()
+        pair = _errors_percent(mix, M, *slab_phases(r, M), c["z"])
+        node = _errors_percent(mix, M, *slab_phases(r, M, pair=False), c["z"])
+        node_err.append(max(np.max(node[0]), np.max(node[1])))
+        print(target, "pair %", pair, "node %", node)
+    lat.close()
+    assert np.max(pair[0]) < 1e-5 and np.max(pair[1]) < 1e-5, pair
+    assert node_err[1] > 1e-4 and abs(node_err[1] / node_err[0] - 1) < 0.5, node_err
+
+
 def test_v_c_methane_ethane_propane_flat_interface(fm):
-    # paper (Table tabcase3): density errors 0.07 %, composition errors up to 0.92 %.
-    # Here, after 3e5 FP64 steps: density 0.07-0.16 %, compositions up to about 1 % (the
-    # same pattern: ethane and propane carry the largest errors); bounds 0.3 % and 1.5 %.
+    # paper (Table tabcase3, after 1e6 steps): density errors 0.07 %, composition errors up to
+    # 0.92 %.  Here, after the same 1e6 FP64 steps, bulk phases as node-pair means: density
+    # 0.078 %, compositions up to 0.91 % (single nodes: 0.14 % and 1.6 %, the alternation of
+    # the node parities is 1.2e-3 of the density); bounds 0.1 % and 1.0 %.
     # The thin liquid slab (vapour fraction 0.78) translates slowly, so the bulk phases
     # are located on the profile rather than at fixed nodes.
     # The overall composition for the flash is the lattice's own (three components: the
     # phase compositions depend on it).
     c = CASES["c1c2c3_flat"]
     mixd, mix, M, rho = _flat_case(c, "pr")
-    r, u, _ = _relax(fm, mixd, rho, c["tau"], 300000)
-    L, V = _bulk_phases(r, M)
+    r, u, _ = _relax(fm, mixd, rho, c["tau"], 1000000)
+    L, V = slab_phases(r, M)
     z = (r / M[:, None, None]).sum(axis=(1, 2))
     dens, comp = _errors_percent(mix, M, L, V, z / z.sum())
     print("ternary density error %", dens, "composition error %", comp)
-    assert np.max(dens) < 0.3, dens
-    assert np.max(comp) < 1.5, comp
+    assert np.max(dens) < 0.1, dens
+    assert np.max(comp) < 1.0, comp
 
 
 def test_v_d_spinodal_decomposition_iso_fugacity(fm):
@@ -220,7 +233,7 @@ def test_v_b_c2_c5_envelopes_in_one_batch(fm):
     worst = []
     for slot, T, p, mix, M in runs:
         fm.fmlbm_batch_moments(b, slot, r)
-        L, V = _bulk_phases(r, M)
+        L, V = slab_phases(r, M)
         f = flash(mix, float(pressure(mix, V)), [0.5, 0.5])
         err = 100.0 * max(abs(L[0] / L.sum() - f["x"][0]) / f["x"][0], abs(V[0] / V.sum() - f["y"][0]) / f["y"][0])
         ratio = (L * M).sum() / (V * M).sum()
