@@ -281,9 +281,11 @@ __device__ __forceinline__ int wrap(int v, int n) {
 //   vdW: b_i / (v - b_m) = b_i rho~ / (1 - beta),  2 S_i / (RT v) = 2 S_i rho~ / RT
 // (each logarithm takes a ratio whose relative rounding is a few ulp, so merging the
 // printed logarithms pairwise costs no accuracy).  Lane arithmetic: one node per lane.
-// Returns beta (for the domain check).
+// Returns beta (for the domain check).  eos >= 0: that EOS (a constant the caller passes, so
+// that the branches below fold away); -1: the mixture's.
 template <int NC, typename V, typename E>
-__device__ __forceinline__ V node_lnf(const MixConstT<E>& m, const V* rt, V* lnf) {
+__device__ __forceinline__ V node_lnf(const MixConstT<E>& m, const V* rt, V* lnf, int eos = -1) {
+    const int kind = eos >= 0 ? eos : m.eos;
     V rtot = rt[0];
 #pragma unroll
     for (int i = 1; i < NC; ++i) rtot = vadd(rtot, rt[i]);
@@ -304,7 +306,7 @@ __device__ __forceinline__ V node_lnf(const MixConstT<E>& m, const V* rt, V* lnf
     const V one = vbc<V>(E(1));
     const V invomb = vrcp(vsub(one, beta));
     const V lead = vmul(vbc<V>(m.RT), invomb);
-    if (m.eos == 2) {
+    if (kind == 2) {
         const V rb1 = vmul(rtot, invomb);               // rho~ / (1 - beta)
         const V m2rt = vbc<V>(E(-2) * m.invRT);
 #pragma unroll
@@ -315,7 +317,7 @@ __device__ __forceinline__ V node_lnf(const MixConstT<E>& m, const V* rt, V* lnf
     const V att = vmul(vmul(aam_rt2, inv), vbc<V>(m.invRT));   // (a alpha)_m rho~ / RT
     V rep, lr;
     E pref;
-    if (m.eos == 0) {
+    if (kind == 0) {
         const E s2 = E(1.4142135623730950488);
         const V den = vfma(beta, vsub(vbc<V>(E(2)), beta), one);   // 1 + 2 beta - beta^2
         rep = vfma(vneg(att), vrcp(den), vmul(beta, invomb));
@@ -354,17 +356,18 @@ struct Tile {
 // their logarithms) in double from the float densities, with the double mixture constants,
 // and round ln f and beta to float once.
 template <int NC, bool LNF64, typename Real>
-__device__ __forceinline__ Real node_lnf_st(const StepArgs& A, const MixConstT<Real>& m, const Real* rt, Real* lnf) {
+__device__ __forceinline__ Real node_lnf_st(const StepArgs& A, const MixConstT<Real>& m, const Real* rt, Real* lnf,
+                                            int eos = -1) {
     if constexpr (LNF64) {
         double rd[NC], ld[NC];
 #pragma unroll
         for (int i = 0; i < NC; ++i) rd[i] = (double)rt[i];
-        const double beta = node_lnf<NC, double>(A.mixd, rd, ld);
+        const double beta = node_lnf<NC, double>(A.mixd, rd, ld, eos);
 #pragma unroll
         for (int i = 0; i < NC; ++i) lnf[i] = (Real)ld[i];
         return (Real)beta;
     } else {
-        return node_lnf<NC, Real>(m, rt, lnf);
+        return node_lnf<NC, Real>(m, rt, lnf, eos);
     }
 }
 
@@ -524,8 +527,8 @@ __device__ __forceinline__ void cp_async_elem(E* dst_smem, const E* src) {
 
 template <typename Real, int NC, int TY>
 __device__ __forceinline__ void prefetch_force(const StepArgs& A, StepSmem<Real, NC, TY>& S, int tx, int ty, int gxn,
-                                               int gyn) {
-    if (A.lagged && gxn < A.nx && gyn < A.ny) {
+                                               int gyn, int lagged = -1) {
+    if ((lagged >= 0 ? lagged != 0 : A.lagged != 0) && gxn < A.nx && gyn < A.ny) {
         const size_t nxy = (size_t)A.nx * A.ny, node = (size_t)gyn * A.nx + gxn;
         const Real* Fin = static_cast<const Real*>(A.Fin);
         cp_async_elem(&S.Fl[0][ty][tx], Fin + node);
@@ -601,7 +604,7 @@ __device__ __forceinline__ void domain_check(const StepArgs& A, const V* rt, con
 template <int NC, int TY, typename Real, bool LNF64 = false>
 __device__ __forceinline__ void phase1_node(const StepArgs& A, const MixConstT<Real>& m, StepSmem<Real, NC, TY>& S,
                                             const Real (&g)[NC][9], Real (&r)[NC], Real& jx, Real& jy, int tx, int ty,
-                                            bool valid, int gx, int gy) {
+                                            bool valid, int gx, int gy, int eos = -1) {
     Real rt[NC], lnf[NC];
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
@@ -610,7 +613,7 @@ __device__ __forceinline__ void phase1_node(const StepArgs& A, const MixConstT<R
         rt[i] = vmul(r[i], m.invM[i]);
         S.rt.v[i][ty + 2][tx + 2] = rt[i];
     }
-    const Real beta = node_lnf_st<NC, LNF64, Real>(A, m, rt, lnf);
+    const Real beta = node_lnf_st<NC, LNF64, Real>(A, m, rt, lnf, eos);
 #pragma unroll
     for (int i = 0; i < NC; ++i) S.lf.v[i][ty + 1][tx + 1] = lnf[i];
     domain_check<NC, Real>(A, rt, lnf, beta, gx, 0, gy, valid && checked_row(A, gy) ? 1u : 0u);
@@ -639,7 +642,7 @@ __device__ __forceinline__ void ring_position(int r, int& bx, int& by) {
 // Phase 1, a halo ring node: rho~ from its summed densities; ln f on the inner 1-node ring.
 template <int NC, int TY, typename Real, bool LNF64 = false>
 __device__ __forceinline__ void phase1_ring(const StepArgs& A, const MixConstT<Real>& m, StepSmem<Real, NC, TY>& S,
-                                            Real (&rt)[NC], int bx, int by) {
+                                            Real (&rt)[NC], int bx, int by, int eos = -1) {
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
         rt[i] = vmul(rt[i], m.invM[i]);
@@ -647,7 +650,7 @@ __device__ __forceinline__ void phase1_ring(const StepArgs& A, const MixConstT<R
     }
     if (bx >= 1 && bx <= kTX + 2 && by >= 1 && by <= TY + 2) {
         Real lnf[NC];
-        node_lnf_st<NC, LNF64, Real>(A, m, rt, lnf);
+        node_lnf_st<NC, LNF64, Real>(A, m, rt, lnf, eos);
 #pragma unroll
         for (int i = 0; i < NC; ++i) S.lf.v[i][by - 1][bx - 1] = lnf[i];
     }
@@ -818,7 +821,7 @@ __device__ __forceinline__ void phase3(const StepArgs& A, const MixConstT<typena
                                        const typename StoreTraits<ST>::Real (&rho)[NC],
                                        typename StoreTraits<ST>::Real jx, typename StoreTraits<ST>::Real jy, int tx,
                                        int ty, int gxn, int gyn, const typename StoreTraits<ST>::Real* park = nullptr,
-                                       const Planes* P = nullptr) {
+                                       const Planes* P = nullptr, int stencil = -1, int lagged = -1) {
     using Real = typename StoreTraits<ST>::Real;
     const int nx = A.nx, nxy = A.nx * A.ny;
     const int node = gyn * nx + gxn;
@@ -826,13 +829,14 @@ __device__ __forceinline__ void phase3(const StepArgs& A, const MixConstT<typena
     auto geth = [&](int i, Real (&h)[9]) { pulled_all<NC, TY, PARK, Real>(g, park, i, tid, h); };
     auto store = [&](int i, int a, Real v) { store_gsel<ST, PP>(A, P, i, a, node, nxy, v); };
     Real Ftx, Fty, ux, uy;
-    if (A.lagged) {  // F(t - 1), copied by prefetch_force
+    const int sten = stencil >= 0 ? stencil : A.stencil;
+    if (lagged >= 0 ? lagged != 0 : A.lagged != 0) {  // F(t - 1), copied by prefetch_force
         asm volatile("cp.async.wait_all;\n" ::: "memory");
         const Real Fpx = S.Fl[0][ty][tx], Fpy = S.Fl[1][ty][tx];
-        phase3_core<NC, !MOMENTS, STD, true, Real>(m, A.stencil, S.G, S.rt, tx + 1, ty + 1, 0, rho, jx, jy, geth, Fpx,
+        phase3_core<NC, !MOMENTS, STD, true, Real>(m, sten, S.G, S.rt, tx + 1, ty + 1, 0, rho, jx, jy, geth, Fpx,
                                                    Fpy, store, Ftx, Fty, ux, uy);
     } else {
-        phase3_core<NC, !MOMENTS, STD, false, Real>(m, A.stencil, S.G, S.rt, tx + 1, ty + 1, 0, rho, jx, jy, geth,
+        phase3_core<NC, !MOMENTS, STD, false, Real>(m, sten, S.G, S.rt, tx + 1, ty + 1, 0, rho, jx, jy, geth,
                                                     Real(0), Real(0), store, Ftx, Fty, ux, uy);
     }
     if constexpr (MOMENTS) {
@@ -854,14 +858,17 @@ __device__ __forceinline__ void phase3(const StepArgs& A, const MixConstT<typena
 
 // Phase 1 from global memory for one tile: pull of the owned node (into g, its densities
 // into r) and of the halo ring (rho~ only), with periodic wrap unless the tile is inner.
-template <int NC, int ST, int TY, bool PP = false>
+// INNER = 1 / 0: the tile is / is not inner, known where the code is compiled (a separate code
+// path for the wrap-free tiles); -1: the argument says.
+template <int NC, int ST, int TY, bool PP = false, int INNER = -1>
 __device__ __forceinline__ void phase1_global(const StepArgs& A, const MixConstT<typename StoreTraits<ST>::Real>& m,
                                               StepSmem<typename StoreTraits<ST>::Real, NC, TY>& S,
                                               typename StoreTraits<ST>::Real (&g)[NC][9],
                                               typename StoreTraits<ST>::Real (&r)[NC],
                                               typename StoreTraits<ST>::Real& jx, typename StoreTraits<ST>::Real& jy,
-                                              int x0, int y0, bool inner, int tx, int ty, int tid,
-                                              const Planes* P = nullptr) {
+                                              int x0, int y0, bool inner_arg, int tx, int ty, int tid,
+                                              const Planes* P = nullptr, int eos = -1) {
+    const bool inner = INNER >= 0 ? INNER == 1 : inner_arg;
     using Real = typename StoreTraits<ST>::Real;
     constexpr int NT = kTX * TY;
     const int nx = A.nx, ny = A.ny, nxy = nx * ny;
@@ -904,13 +911,13 @@ __device__ __forceinline__ void phase1_global(const StepArgs& A, const MixConstT
         }
     }
     if constexpr (RING_FIRST) {
-        if (has_ring) phase1_ring<NC, TY, Real, kLnf64<ST>>(A, m, S, rr, bx, by);
-        phase1_node<NC, TY, Real, kLnf64<ST>>(A, m, S, g, r, jx, jy, tx, ty, valid, gxn, gyn);
+        if (has_ring) phase1_ring<NC, TY, Real, kLnf64<ST>>(A, m, S, rr, bx, by, eos);
+        phase1_node<NC, TY, Real, kLnf64<ST>>(A, m, S, g, r, jx, jy, tx, ty, valid, gxn, gyn, eos);
     } else {
-        phase1_node<NC, TY, Real, kLnf64<ST>>(A, m, S, g, r, jx, jy, tx, ty, valid, gxn, gyn);
+        phase1_node<NC, TY, Real, kLnf64<ST>>(A, m, S, g, r, jx, jy, tx, ty, valid, gxn, gyn, eos);
         if (has_ring) {
             pull_ring();
-            phase1_ring<NC, TY, Real, kLnf64<ST>>(A, m, S, rr, bx, by);
+            phase1_ring<NC, TY, Real, kLnf64<ST>>(A, m, S, rr, bx, by, eos);
         }
     }
 }
@@ -1088,11 +1095,18 @@ __device__ __forceinline__ void diag_tile(const StepArgs& A, const Real (&r)[NC]
 
 // MOMENTS = true: compute the macroscopic fields of the current state instead of
 // advancing it (no distribution or force store).
-template <int NC, int ST, int TY, bool MOMENTS, bool STD = false>
+// SPEC = true: the instantiation for the Peng-Robinson EOS, isotropic stencils and the lagged
+// velocity reading (well-balanced formulation), compiled with those choices as constants (no
+// branches on them) and with separate code paths for wrap-free and edge tiles; the launcher
+// picks it only for lattices with those options.  The arithmetic is the generic kernel's.
+template <int NC, int ST, int TY, bool MOMENTS, bool STD = false, bool SPEC = false>
 // Float arithmetic: 1024 resident threads per SM (64 registers a thread), measured faster
 // than trading occupancy for registers (77 registers and three 8-row blocks per SM were 7%
-// slower for three components) or registers for occupancy (48 registers spill).  The FP64
-// reference path keeps what the compiler chooses.
+// slower for three components) or registers for occupancy (48 registers spill).  More
+// resident blocks did not help where they fit either: the specialised two-component step
+// fits 40 registers without spilling, but six blocks per SM ran 5% slower than five (more
+// warps contend for the same L1 and L2 traffic).  The FP64 reference path keeps what the
+// compiler chooses.
 __global__ void __launch_bounds__(kTX* TY, ST == ST_F64 ? 1 : (kParkLast<NC, ST, TY> ? 5 : 1024 / (kTX * TY)))
     fused_step(StepArgs A, Planes P) {
     using Real = typename StoreTraits<ST>::Real;
@@ -1112,16 +1126,28 @@ __global__ void __launch_bounds__(kTX* TY, ST == ST_F64 ? 1 : (kParkLast<NC, ST,
     // diagnostics: the density snapshot of this thread's node, copied like the force (a load
     // issued after phase 3 stalled the whole step about 2x)
     Real* pv_s = reinterpret_cast<Real*>(smem_raw + sizeof(StepSmem<Real, NC, TY>) + park_bytes<NC, ST, TY>());
+    static_assert(!SPEC || (!MOMENTS && !STD), "the specialised step advances the well-balanced scheme");
+    const int eos = SPEC ? 0 : -1;               // Peng-Robinson
+    const int stencil = SPEC ? 0 : A.stencil;    // isotropic
+    const int lagged = SPEC ? 1 : -1;
     if constexpr (!MOMENTS) diag_prefetch<NC, Real, TY>(A, pv_s, tx, ty, gxn, gyn);
-    prefetch_force<Real, NC, TY>(A, S, tx, ty, gxn, gyn);
+    prefetch_force<Real, NC, TY>(A, S, tx, ty, gxn, gyn, lagged);
     Real g[NC][9], r[NC], jx, jy;
-    phase1_global<NC, ST, TY, PARK>(A, m, S, g, r, jx, jy, x0, y0, inner, tx, ty, tid, &P);
+    if constexpr (SPEC) {
+        if (inner)
+            phase1_global<NC, ST, TY, PARK, 1>(A, m, S, g, r, jx, jy, x0, y0, true, tx, ty, tid, &P, eos);
+        else
+            phase1_global<NC, ST, TY, PARK, 0>(A, m, S, g, r, jx, jy, x0, y0, false, tx, ty, tid, &P, eos);
+    } else {
+        phase1_global<NC, ST, TY, PARK>(A, m, S, g, r, jx, jy, x0, y0, inner, tx, ty, tid, &P);
+    }
     if constexpr (PARK) park_store<TY, Real>(g[NC - 1], park, tid);
     __syncthreads();
-    phase2<NC, TY, Real>(m, S, A.stencil, tid);
+    phase2<NC, TY, Real>(m, S, stencil, tid);
     __syncthreads();
     if (gxn < nx && gyn < ny)
-        phase3<NC, ST, TY, MOMENTS, STD, PARK, PARK>(A, m, S, g, r, jx, jy, tx, ty, gxn, gyn, park, &P);
+        phase3<NC, ST, TY, MOMENTS, STD, PARK, PARK>(A, m, S, g, r, jx, jy, tx, ty, gxn, gyn, park, &P, stencil,
+                                                     lagged);
     if constexpr (!MOMENTS) {
         if (A.diag_partial != nullptr)  // uniform: diagnostics of the state this step read
             diag_tile<NC, Real, TY>(A, r, pv_s, tx, ty, gxn, gyn, y0, blockIdx.y, blockIdx.x, gridDim.x);

@@ -87,14 +87,22 @@ inline cudaError_t launch_reduce_final(int nc, const void* partial, int nx, int 
     return cudaGetLastError();
 }
 
+// The specialised step (fused_step<..., SPEC = true>): float and 16-bit storage, 8-row tiles,
+// for lattices with the Peng-Robinson EOS, isotropic stencils, the lagged velocity reading and
+// the well-balanced formulation.
+template <int ST> constexpr bool kSpecStep = ST == ST_F32 || ST == ST_F16DEV || ST == ST_BF16DEV;
+inline bool spec_options(const StepArgs& A) {
+    return A.mixd.eos == 0 && A.stencil == 0 && A.lagged != 0 && A.standard == 0;
+}
+
 #define FMLBM_DEFINE_LAUNCHERS(ST)                                                                        \
-    template <int NC, bool MOM, int TY, bool STD = false>                                                 \
+    template <int NC, bool MOM, int TY, bool STD = false, bool SPEC = false>                              \
     static cudaError_t launch_step_nc_##ST(const StepArgs& A, cudaStream_t s) {                           \
         using Real = typename StoreTraits<ST>::Real;                                                      \
         /* + the parked values and the diagnostics snapshot copy of the tile's nodes */                 \
         constexpr size_t smem = sizeof(StepSmem<Real, NC, TY>) + park_bytes<NC, ST, TY>() +                \
                                 (MOM ? 0 : (size_t)NC * TY * kTX * sizeof(Real));                         \
-        auto k = fused_step<NC, ST, TY, MOM, STD>;                                                        \
+        auto k = fused_step<NC, ST, TY, MOM, STD, SPEC>;                                                  \
         FMLBM_ENSURE_SMEM(k, smem);                                                                       \
         dim3 grid((A.nx + kTX - 1) / kTX, (A.ny + TY - 1) / TY);                                          \
         const Planes P = make_planes(A, NC, kDev16<ST>,                                                   \
@@ -116,6 +124,9 @@ inline cudaError_t launch_reduce_final(int nc, const void* partial, int nx, int 
             return moments ? launch_step_nc_##ST<NC, true, kTileYLarge>(A, s)                             \
                            : launch_step_nc_##ST<NC, false, kTileYLarge>(A, s);                           \
         if (tile_y == kTileYHuge && !moments) return launch_step_nc_##ST<NC, false, kTileYHuge>(A, s);    \
+        if constexpr (kSpecStep<ST>) {                                                                    \
+            if (!moments && spec_options(A)) return launch_step_nc_##ST<NC, false, kTileYSmall, false, true>(A, s); \
+        }                                                                                                 \
         return moments ? launch_step_nc_##ST<NC, true, kTileYSmall>(A, s)                                 \
                        : launch_step_nc_##ST<NC, false, kTileYSmall>(A, s);                               \
     }                                                                                                     \
