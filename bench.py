@@ -456,6 +456,37 @@ def ternary_forms(fmlbm, torch, stream, dev, steps, warmup, flush):
     return dict(workload=w["name"] + ", tau 1, isotropic, lagged, plain step", forms=out)
 
 
+def temporal_blocking(fmlbm, torch, stream, dev, flush, reps=10, k=20):
+    """The binary droplet workload advanced K steps per fmlbm_step call, by single-step launches
+    (plain) and by one multi-step launch (temporal blocking): ms per step of each, L2 flushed
+    before every timed call.  The two give bit-identical states."""
+    w = workload("droplet1024")
+    out = {}
+    for variant in ("plain", "multi"):
+        lat = fmlbm.Lattice(fmlbm.mixture_from_dict(w["mixture"]), w["nx"], w["ny"], w["tau"], w["stencil"], "fp32",
+                            "lagged", stream=stream.cuda_stream)
+        rho_dev = torch.from_numpy(w["rho"]).to(dev)
+        fmlbm.fmlbm_init_device(lat.h, rho_dev.data_ptr())
+        fmlbm.fmlbm_set_step_variant(lat.h, variant)
+        lat.step(2 * k)
+        lat.synchronize()
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            flush.sum()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fmlbm.fmlbm_step(lat.h, k)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1) / k)
+        lat.synchronize()
+        lat.close()
+        per = sum(ms) / len(ms)
+        out[variant] = dict(ms_per_step=per, value=2 * w["nx"] * w["ny"] / (per * 1e-3) / 1e9, unit="component-GLUPS")
+    return dict(workload=w["name"] + f", FP32, {k} steps per call", steps_per_call=k, reps=reps, **out)
+
+
 def run_ours(args, w, rank, world, dist):
     import torch
     from paper_2212_10680_gb300 import fmlbm
@@ -489,7 +520,8 @@ def run_ours(args, w, rank, world, dist):
     if world == 1 and not args.no_configs and args.workload == "droplet1024":
         configs = dict(small_binary_fp64=small_binary_fp64(fmlbm, torch, stream, dev),
                        ternary_4096=ternary_forms(fmlbm, torch, stream, dev, max(10, min(args.steps, 20)),
-                                                  max(3, args.warmup), flush))
+                                                  max(3, args.warmup), flush),
+                       temporal_blocking=temporal_blocking(fmlbm, torch, stream, dev, flush))
         del flush
         torch.cuda.empty_cache()
         configs["batch_sweep"] = run_batch(args, rank, world, dist, summary=True)
@@ -870,7 +902,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--tile-y", type=int, default=0, help="override the fused step's tile height (8 or 16)")
-    ap.add_argument("--variant", default=None, choices=["auto", "plain", "tma", "tma_tile", "pair"], help="step kernel variant")
+    ap.add_argument("--variant", default=None, choices=["auto", "plain", "tma", "tma_tile", "pair", "multi"], help="step kernel variant")
     ap.add_argument("--batch-lattices", type=int, default=256)
     ap.add_argument("--batch-max-side", type=int, default=512)
     ap.add_argument("--max-steps", type=int, default=300000)

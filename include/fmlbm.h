@@ -284,11 +284,23 @@ fmlbm_status fmlbm_set_tile_height(fmlbm_handle* h, int32_t tile_y);
  * the other forms on the workloads measured on GB300; fmlbm_autotune measures the lattice
  * at hand instead.  Every form performs the same operations per node, each rounded once,
  * and gives the same bits.  Asking for a form where it is not available returns
- * FMLBM_E_UNSUPPORTED. */
+ * FMLBM_E_UNSUPPORTED.
+ * MULTI (temporal blocking of the periodic update of Eq. eqLBEMCa, Section III.B steps 1-9):
+ * the steps of one fmlbm_step call run in a single cooperative launch whose blocks stay
+ * resident; a 32 x 8 tile advances to step s + 1 as soon as its 3 x 3 neighbourhood of tiles
+ * has completed step s (bounded waits on per-tile step counters; a wait that runs out latches
+ * FMLBM_E_TIMEOUT, reported by the next synchronising call, and the lattice state is then
+ * undefined), so consecutive steps overlap and a step reads much of the previous step's
+ * output from L2.  Results are bit-identical to single steps.  Available for FP32, FP16DEV
+ * and BF16DEV storage with the Peng-Robinson EOS, isotropic stencils, the lagged velocity
+ * reading and the well-balanced formulation; a call of one step, and the step that serves
+ * a pending fmlbm_diagnostics_async request, run as single launches.  The handle keeps 8 bytes
+ * of device memory per tile for the counters (allocated on first use). */
 typedef enum fmlbm_step_variant {
     FMLBM_VARIANT_AUTO = 0, FMLBM_VARIANT_PLAIN = 1, FMLBM_VARIANT_TMA = 2,
     FMLBM_VARIANT_TMA_TILE = 3,  /* one tile per block, single stage */
-    FMLBM_VARIANT_PAIR = 4       /* two nodes per thread, packed float arithmetic */
+    FMLBM_VARIANT_PAIR = 4,      /* two nodes per thread, packed float arithmetic */
+    FMLBM_VARIANT_MULTI = 5      /* several steps per launch (temporal blocking) */
 } fmlbm_step_variant;
 fmlbm_status fmlbm_set_step_variant(fmlbm_handle* h, int32_t variant);
 /* Autotuner: times steps_per_trial steps of every available kernel variant and tile

@@ -64,6 +64,7 @@ struct fmlbm_handle {
     bool owns_buffers = true;        // false: g, g0 and F belong to the caller (fmlbm_create_with_buffers)
     long long wait_polls = kMaxPolls;  // bound of a wait for a tile copy (bulk-copy step forms)
     int check_y0 = 0, check_y1 = 0;    // rows the domain check covers (check_y1 = 0: all)
+    long long* done = nullptr;         // per-tile step counters of the multi-step kernel
     CUtensorMap tmap[2][2];          // [buffer][0: float planes, 1: 16-bit planes]
     std::string last_error;
 };
@@ -217,6 +218,14 @@ bool pair_supported_for(const fmlbm_handle* h) {
         case FMLBM_BF16DEV: return pair_supported<ST_BF16DEV>(h->nc);
         default: return false;
     }
+}
+
+// The multi-step kernel: float and 16-bit storage with the options of the specialised step.
+bool multi_supported_for(const fmlbm_handle* h) {
+    const int p = h->lattice.precision;
+    return (p == FMLBM_FP32 || p == FMLBM_FP16DEV || p == FMLBM_BF16DEV) && h->mc.eos == 0 &&
+           h->lattice.stencil == FMLBM_STENCIL_ISOTROPIC && h->lattice.velocity_force == FMLBM_FORCE_LAGGED &&
+           h->lattice.formulation == FMLBM_WELL_BALANCED;
 }
 
 bool tma_supported_for(int precision, int nc) {
@@ -395,6 +404,7 @@ void release(fmlbm_handle* h) {
     }
     if (h->rho_prev) cudaFree(h->rho_prev);
     if (h->partial) cudaFree(h->partial);
+    if (h->done) cudaFree(h->done);
     if (h->diag_dev) cudaFree(h->diag_dev);
     if (h->diag_host) cudaFreeHost(h->diag_host);
     for (int k = 0; k < kDiagSlots; ++k)
@@ -732,6 +742,25 @@ fmlbm_status fmlbm_step(fmlbm_handle* h, int64_t nsteps) {
         capturing = cap != cudaStreamCaptureStatusNone;
     }
     for (int64_t k = 0; k < nsteps; ++k) {
+        if (nsteps - k >= 2 && h->pending < 0 && resolved_variant(h) == FMLBM_VARIANT_MULTI) {
+            // the remaining steps in one launch (at most 2^30 per launch)
+            if (!h->done)
+                FM_CUDA(h, cudaMalloc(&h->done, (size_t)multi_tiles(h->lattice.nx, h->lattice.ny) * sizeof(long long)));
+            const int64_t left = nsteps - k;
+            const int n = left > (int64_t(1) << 30) ? (1 << 30) : (int)left;
+            const StepArgs A0 = make_args(h, h->cur), A1 = make_args(h, h->cur ^ 1);
+            cudaError_t e;
+            switch (h->lattice.precision) {
+                case FMLBM_FP32: e = launch_steps_multi<ST_F32>(A0, A1, h->nc, n, h->done, h->stream); break;
+                case FMLBM_FP16DEV: e = launch_steps_multi<ST_F16DEV>(A0, A1, h->nc, n, h->done, h->stream); break;
+                default: e = launch_steps_multi<ST_BF16DEV>(A0, A1, h->nc, n, h->done, h->stream); break;
+            }
+            FM_CUDA(h, e);
+            h->cur ^= n & 1;
+            h->step += n;
+            k += n - 1;
+            continue;
+        }
         StepArgs A = make_args(h, h->cur);
         const int64_t fused = h->pending;
         if (fused >= 0) {  // this step also reduces the state it reads
@@ -770,12 +799,14 @@ fmlbm_status fmlbm_set_tile_height(fmlbm_handle* h, int32_t tile_y) {
 }
 
 fmlbm_status fmlbm_set_step_variant(fmlbm_handle* h, int32_t variant) {
-    if (!h || variant < FMLBM_VARIANT_AUTO || variant > FMLBM_VARIANT_PAIR)
+    if (!h || variant < FMLBM_VARIANT_AUTO || variant > FMLBM_VARIANT_MULTI)
         return fail(h, FMLBM_E_INVALID_ARG, "unknown step variant");
     if ((variant == FMLBM_VARIANT_TMA || variant == FMLBM_VARIANT_TMA_TILE) && !h->tma_maps)
         return fail(h, FMLBM_E_UNSUPPORTED, "no TMA step for this precision, component count or lattice shape");
     if (variant == FMLBM_VARIANT_PAIR && !pair_supported_for(h))
         return fail(h, FMLBM_E_UNSUPPORTED, "no paired step for this precision or formulation");
+    if (variant == FMLBM_VARIANT_MULTI && !multi_supported_for(h))
+        return fail(h, FMLBM_E_UNSUPPORTED, "no multi-step kernel for this precision, EOS or options");
     h->variant = variant;
     return FMLBM_OK;
 }
@@ -784,8 +815,9 @@ fmlbm_status fmlbm_autotune(fmlbm_handle* h, int32_t steps_per_trial, int32_t* v
                             double* ms_per_step) {
     if (!h || steps_per_trial < 1) return fail(h, FMLBM_E_INVALID_ARG, "bad argument");
     struct Cand { int variant, tile_y; };
-    Cand cands[6];
+    Cand cands[7];
     int nc = 0;
+    if (steps_per_trial >= 2 && multi_supported_for(h)) cands[nc++] = Cand{FMLBM_VARIANT_MULTI, kTileYSmall};
     if (pair_supported_for(h)) cands[nc++] = Cand{FMLBM_VARIANT_PAIR, kTileYSmall};
     for (int ty : {kTileYSmall, kTileYLarge, kTileYHuge})
         if (ty <= 16 || h->lattice.ny >= 64) cands[nc++] = Cand{FMLBM_VARIANT_PLAIN, ty};

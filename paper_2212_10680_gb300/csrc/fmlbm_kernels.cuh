@@ -217,18 +217,34 @@ __device__ __forceinline__ typename StoreTraits<ST>::Real load_g(const StepArgs&
     }
 }
 
+// Loads cached in L2 only (ld.global.cg), for data that other multiprocessors write during the
+// same launch (the multi-step kernel): the L1 of this multiprocessor may hold stale copies.
+template <typename E> __device__ __forceinline__ E ldcg(const E* p) { return __ldcg(p); }
+template <> __device__ __forceinline__ __half ldcg<__half>(const __half* p) {
+    const unsigned short b = __ldcg(reinterpret_cast<const unsigned short*>(p));
+    return __ushort_as_half(b);
+}
+template <> __device__ __forceinline__ __nv_bfloat16 ldcg<__nv_bfloat16>(const __nv_bfloat16* p) {
+    const unsigned short b = __ldcg(reinterpret_cast<const unsigned short*>(p));
+    return __ushort_as_bfloat16(b);
+}
+template <bool CG, typename E> __device__ __forceinline__ E ldsel(const E* p) {
+    if constexpr (CG) return ldcg(p);
+    else return ldg(p);
+}
+
 // The same through the plane base addresses of the launch's parameters and a 32-bit node
 // index: each access address is then a single multiply-add onto a parameter, where the
 // forms above compute a 64-bit plane offset (two-component step: +1.5% on GB300; with
-// three components it cost registers and spilled).
-template <int ST>
+// three components it cost registers and spilled).  CG: L2-only loads (ldcg).
+template <int ST, bool CG = false>
 __device__ __forceinline__ typename StoreTraits<ST>::Real load_gp(const Planes& P, int i, int a, int node) {
     using Elem = typename StoreTraits<ST>::Elem;
     if constexpr (ST == ST_F64 || ST == ST_F32) {
-        return to_real(ldg(static_cast<const Elem*>(P.in[i * 9 + a]) + node));
+        return to_real(ldsel<CG>(static_cast<const Elem*>(P.in[i * 9 + a]) + node));
     } else {
-        if (a == 0) return ldg(P.g0in[i] + node);
-        return to_real(ldg(static_cast<const Elem*>(P.in[i * 8 + a - 1]) + node));
+        if (a == 0) return ldsel<CG>(P.g0in[i] + node);
+        return to_real(ldsel<CG>(static_cast<const Elem*>(P.in[i * 8 + a - 1]) + node));
     }
 }
 template <int ST>
@@ -546,7 +562,7 @@ __device__ __forceinline__ int pull_src(int a, int wx, int wy, int xm, int xp, i
 
 // Sum of the pulled distributions of component i at node (wx, wy) (wrapped coordinates),
 // in direction order (sum9).
-template <int NC, int ST, bool PP = false>
+template <int NC, int ST, bool PP = false, bool CG = false>
 __device__ __forceinline__ void pull_rho(const StepArgs& A, int wx, int wy, bool inner, int nx, int ny, int nxy,
                                          typename StoreTraits<ST>::Real* rs, const Planes* P = nullptr) {
     const int node = wy * nx + wx;
@@ -562,7 +578,7 @@ __device__ __forceinline__ void pull_rho(const StepArgs& A, int wx, int wy, bool
         const int src = inner ? node - ey(a) * nx - ex(a) : pull_src(a, wx, wy, xm, xp, ym, yp, nx);
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
-            const auto v = PP ? load_gp<ST>(*P, i, a, src) : load_g<ST>(A, i, a, (size_t)src, (size_t)nxy);
+            const auto v = PP ? load_gp<ST, CG>(*P, i, a, src) : load_g<ST>(A, i, a, (size_t)src, (size_t)nxy);
             rs[i] = a == 0 ? v : vadd(rs[i], v);
         }
     }
@@ -860,7 +876,7 @@ __device__ __forceinline__ void phase3(const StepArgs& A, const MixConstT<typena
 // into r) and of the halo ring (rho~ only), with periodic wrap unless the tile is inner.
 // INNER = 1 / 0: the tile is / is not inner, known where the code is compiled (a separate code
 // path for the wrap-free tiles); -1: the argument says.
-template <int NC, int ST, int TY, bool PP = false, int INNER = -1>
+template <int NC, int ST, int TY, bool PP = false, int INNER = -1, bool CG = false>
 __device__ __forceinline__ void phase1_global(const StepArgs& A, const MixConstT<typename StoreTraits<ST>::Real>& m,
                                               StepSmem<typename StoreTraits<ST>::Real, NC, TY>& S,
                                               typename StoreTraits<ST>::Real (&g)[NC][9],
@@ -889,7 +905,7 @@ __device__ __forceinline__ void phase1_global(const StepArgs& A, const MixConstT
         ring_position<TY>(tid, bx, by);
         const int wx = inner ? x0 - 2 + bx : wrap(x0 - 2 + bx, nx);
         const int wy = inner ? y0 - 2 + by : wrap(y0 - 2 + by, ny);
-        pull_rho<NC, ST, PP>(A, wx, wy, inner, nx, ny, nxy, rr, P);
+        pull_rho<NC, ST, PP, CG>(A, wx, wy, inner, nx, ny, nxy, rr, P);
     };
     if (RING_FIRST && has_ring) pull_ring();
     {
@@ -907,7 +923,7 @@ __device__ __forceinline__ void phase1_global(const StepArgs& A, const MixConstT
             const int src = inner ? node - ey(a) * nx - ex(a) : pull_src(a, wx, wy, xm, xp, ym, yp, nx);
 #pragma unroll
             for (int i = 0; i < NC; ++i)
-                g[i][a] = PP ? load_gp<ST>(*P, i, a, src) : load_g<ST>(A, i, a, (size_t)src, (size_t)nxy);
+                g[i][a] = PP ? load_gp<ST, CG>(*P, i, a, src) : load_g<ST>(A, i, a, (size_t)src, (size_t)nxy);
         }
     }
     if constexpr (RING_FIRST) {

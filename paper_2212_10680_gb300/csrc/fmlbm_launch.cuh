@@ -4,6 +4,7 @@
 
 #include <atomic>
 
+#include "fmlbm_multi.cuh"
 #include "fmlbm_pair.cuh"
 #include "fmlbm_tma.cuh"
 
@@ -54,6 +55,15 @@ template <int ST>
 cudaError_t launch_step_pair(const StepArgs& A, int nc, cudaStream_t s);
 template <int ST>
 bool pair_supported(int nc);
+// K time steps in one cooperative launch of the multi-step kernel (fmlbm_multi.cuh): A0 the
+// arguments of the first step (reading the current buffer), A1 those of the second.  done:
+// at least multi_tiles(nx, ny) counters of device scratch (reset here, on the stream).
+// Float and 16-bit storage, the specialised options only (spec_options); otherwise
+// cudaErrorNotSupported.
+template <int ST>
+cudaError_t launch_steps_multi(const StepArgs& A0, const StepArgs& A1, int nc, int nsteps, long long* done,
+                               cudaStream_t s);
+inline int multi_tiles(int nx, int ny) { return ((nx + kTX - 1) / kTX) * ((ny + kTileYSmall - 1) / kTileYSmall); }
 
 template <int ST>
 cudaError_t launch_init(const StepArgs& A, int nc, const double* rho, cudaStream_t s);
@@ -273,6 +283,44 @@ inline bool spec_options(const StepArgs& A) {
         return false;                                                                                     \
     }
 
+
+#define FMLBM_DEFINE_MULTI_LAUNCHER(ST)                                                                   \
+    template <int NC>                                                                                     \
+    static cudaError_t launch_multi_nc_##ST(const StepArgs& A0, const StepArgs& A1, int nsteps,           \
+                                            long long* done, cudaStream_t s) {                            \
+        constexpr int TY = kTileYSmall;                                                                   \
+        constexpr size_t smem = sizeof(StepSmem<float, NC, TY>) + park_bytes<NC, ST, TY>();               \
+        auto k = fused_steps<NC, ST, TY>;                                                                 \
+        FMLBM_ENSURE_SMEM(k, smem);                                                                       \
+        int dev = 0, sms = 0, per_sm = 0;                                                                 \
+        cudaError_t e = cudaGetDevice(&dev);                                                              \
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);      \
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTX * TY, smem); \
+        if (e != cudaSuccess) return e;                                                                   \
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;                                             \
+        const int ntiles = multi_tiles(A0.nx, A0.ny);                                                     \
+        const int grid = ntiles < sms * per_sm ? ntiles : sms * per_sm;                                   \
+        e = cudaMemsetAsync(done, 0, (size_t)ntiles * sizeof(long long), s);                              \
+        if (e != cudaSuccess) return e;                                                                   \
+        Planes P0 = make_planes(A0, NC, ST != ST_F32, ST == ST_F32 ? 4 : 2);                              \
+        Planes P1 = make_planes(A1, NC, ST != ST_F32, ST == ST_F32 ? 4 : 2);                              \
+        StepArgs a0 = A0, a1 = A1;                                                                        \
+        long long base = 0;                                                                               \
+        void* args[] = {&a0, &a1, &P0, &P1, &nsteps, &base, &done};                                       \
+        return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k), dim3(grid), dim3(kTX, TY), args, smem, s); \
+    }                                                                                                     \
+    template <>                                                                                           \
+    cudaError_t launch_steps_multi<ST>(const StepArgs& A0, const StepArgs& A1, int nc, int nsteps,        \
+                                       long long* done, cudaStream_t s) {                                 \
+        if (!spec_options(A0)) return cudaErrorNotSupported;                                              \
+        switch (nc) {                                                                                     \
+            case 1: return launch_multi_nc_##ST<1>(A0, A1, nsteps, done, s);                             \
+            case 2: return launch_multi_nc_##ST<2>(A0, A1, nsteps, done, s);                              \
+            case 3: return launch_multi_nc_##ST<3>(A0, A1, nsteps, done, s);                              \
+            case 4: return launch_multi_nc_##ST<4>(A0, A1, nsteps, done, s);                              \
+        }                                                                                                 \
+        return cudaErrorInvalidValue;                                                                     \
+    }
 
 // Components parked in shared memory by the paired step: registers hold the others'
 // pulled values of both nodes between phases 1 and 3.

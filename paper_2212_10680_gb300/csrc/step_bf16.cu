@@ -5,4 +5,5 @@ namespace fmlbm {
 FMLBM_DEFINE_LAUNCHERS(ST_BF16DEV)
 FMLBM_DEFINE_TMA_LAUNCHER(ST_BF16DEV)
 FMLBM_DEFINE_PAIR_LAUNCHER(ST_BF16DEV)
+FMLBM_DEFINE_MULTI_LAUNCHER(ST_BF16DEV)
 }  // namespace fmlbm

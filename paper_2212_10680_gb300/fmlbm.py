@@ -31,6 +31,7 @@ E_NONPHYSICAL = 4
 E_TIMEOUT = 5
 E_NOT_CONVERGED = 7
 E_BUSY = 6
+E_UNSUPPORTED = 8
 
 
 class FmlbmError(RuntimeError):
@@ -329,7 +330,7 @@ def fmlbm_set_tile_height(h, tile_y: int):
     _check(LIB.fmlbm_set_tile_height(h, tile_y), "fmlbm_set_tile_height", h)
 
 
-VARIANT = {"auto": 0, "plain": 1, "tma": 2, "tma_tile": 3, "pair": 4}
+VARIANT = {"auto": 0, "plain": 1, "tma": 2, "tma_tile": 3, "pair": 4, "multi": 5}
 CRITERION = {"residual": 0, "phase": 1}
 
 
@@ -340,7 +341,7 @@ def fmlbm_set_step_variant(h, variant: str):
 def fmlbm_get_step_variant(h) -> str:
     v = ctypes.c_int32()
     _check(LIB.fmlbm_get_step_variant(h, ctypes.byref(v)), "fmlbm_get_step_variant", h)
-    return {1: "plain", 2: "tma", 3: "tma_tile", 4: "pair"}[v.value]
+    return {1: "plain", 2: "tma", 3: "tma_tile", 4: "pair", 5: "multi"}[v.value]
 
 
 def fmlbm_set_wait_limit(h, polls: int):
@@ -351,7 +352,7 @@ def fmlbm_autotune(h, steps_per_trial: int = 5):
     v, ty, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
     _check(LIB.fmlbm_autotune(h, steps_per_trial, ctypes.byref(v), ctypes.byref(ty), ctypes.byref(ms)),
            "fmlbm_autotune", h)
-    return {1: "plain", 2: "tma", 3: "tma_tile", 4: "pair"}[v.value], ty.value, ms.value
+    return {1: "plain", 2: "tma", 3: "tma_tile", 4: "pair", 5: "multi"}[v.value], ty.value, ms.value
 
 
 def fmlbm_synchronize(h):
