@@ -37,7 +37,7 @@ ALGO_BYTES = {"fp64": 144.0, "fp32": 72.0, "fp16dev": 40.0, "bf16dev": 40.0, "fp
 L2_FLUSH_BYTES = 256 << 20
 KERNEL_SOURCES = ["paper_2212_10680_gb300/csrc/fmlbm_lanes.cuh", "paper_2212_10680_gb300/csrc/fmlbm_kernels.cuh",
                   "paper_2212_10680_gb300/csrc/fmlbm_pair.cuh", "paper_2212_10680_gb300/csrc/fmlbm_launch.cuh",
-                  "paper_2212_10680_gb300/csrc/fmlbm_tma.cuh"]
+                  "paper_2212_10680_gb300/csrc/fmlbm_tma.cuh", "paper_2212_10680_gb300/csrc/fmlbm_multi.cuh"]
 
 
 # ---- ranks (torchrun): independent problems are split, timings reduced; no data exchange ----
@@ -451,6 +451,7 @@ def ternary_forms(fmlbm, torch, stream, dev, steps, warmup, flush):
         out[prec] = dict(value=r["n"] * r["nodes"] / per / 1e9, unit="component-GLUPS", ms_per_step=1e3 * per,
                          steps=k, roofline=dict(bound="hbm", achieved=achieved, peak=peak["hbm_gbs"], unit="GB/s",
                                                 frac=achieved / peak["hbm_gbs"],
+                                                traffic=profile_traffic("fused_step", "ternary4096", prec),
                                                 algorithmic_bytes_per_component_node=ALGO_BYTES[prec]),
                          clocks=r["clocks"])
     return dict(workload=w["name"] + ", tau 1, isotropic, lagged, plain step", forms=out)
