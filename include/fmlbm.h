@@ -182,7 +182,11 @@ fmlbm_status fmlbm_create_with_buffers(const fmlbm_mixture* mixture, const fmlbm
 
 /* Fluid at rest: g_{a,i} = g^eq_{a,i}(rho_i, u = 0) (Eq. eqLBEMCb with rho_0 = 0,
  * i.e. rho_i in a = 0 and 0 elsewhere), stored force 0, step counter 0.
- * rho_host: [N][ny][nx] component MASS densities on the host, copied. */
+ * rho_host: [N][ny][nx] component MASS densities on the host, copied: free to reuse on return.
+ * Page-locked memory mapped in the current context (cudaHostAlloc, cudaHostRegister) is read in
+ * place by the initialisation kernel and the call waits for it (it synchronises the handle's
+ * stream); other host memory is staged through a temporary device buffer from the stream-ordered
+ * pool. */
 fmlbm_status fmlbm_init(fmlbm_handle* h, const double* rho_host);
 
 /* As fmlbm_init, with rho_device a device pointer of the same layout (read on

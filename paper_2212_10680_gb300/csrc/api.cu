@@ -718,6 +718,18 @@ fmlbm_status fmlbm_init_device(fmlbm_handle* h, const double* rho_device) {
 fmlbm_status fmlbm_init(fmlbm_handle* h, const double* rho_host) {
     if (!h || !rho_host) return fail(h, FMLBM_E_INVALID_ARG, "null argument");
     const size_t bytes = (size_t)h->nc * h->lattice.nx * h->lattice.ny * sizeof(double);
+    // Page-locked host memory that this context has mapped: the initialisation kernel reads the
+    // densities in place (over the device's link to host memory; no device copy, no allocation),
+    // and the call waits for it so that the buffer is free again on return.
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, rho_host) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+        at.devicePointer != nullptr) {
+        fmlbm_status s = fmlbm_init_device(h, static_cast<const double*>(at.devicePointer));
+        if (s != FMLBM_OK) return s;
+        FM_CUDA(h, cudaStreamSynchronize(h->stream));
+        return FMLBM_OK;
+    }
+    cudaGetLastError();  // an unregistered pointer leaves no error behind
     double* d = nullptr;
     FM_CUDA(h, cudaMallocAsync((void**)&d, bytes, h->stream));
     cudaError_t e = cudaMemcpyAsync(d, rho_host, bytes, cudaMemcpyHostToDevice, h->stream);

@@ -129,3 +129,24 @@ def test_handles_on_two_threads_with_large_shared_tiles(fm):
     run(ref, 0)
     for o in out:
         assert np.array_equal(o[0], ref[0][0]) and np.array_equal(o[1], ref[0][1])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16dev"])
+def test_init_from_page_locked_host_memory(fm, precision):
+    # page-locked host densities are read in place by the initialisation kernel; the call waits
+    # for the read, so the buffer may be overwritten on return: the state equals the one
+    # initialised from ordinary (pageable) host memory
+    import torch
+    mixd, rho = slab_state_binary(100, 60, seed=8)
+    pinned = torch.from_numpy(rho.copy()).pin_memory()
+    pinned_np = pinned.numpy()
+    out = []
+    for src in (rho, pinned_np):
+        lat = fm.Lattice(fm.mixture_from_dict(mixd), 100, 60, 1.0, "isotropic", precision, "lagged")
+        lat.init(src)
+        if src is pinned_np:
+            pinned.fill_(-1.0)
+        lat.step(3)
+        out.append(lat.distributions())
+        lat.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
