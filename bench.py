@@ -329,9 +329,10 @@ def _device_steps(fmlbm, torch, w, prec, steps, warmup, stream, dev, variant=Non
 
 def _e2e_rate(fmlbm, torch, w, prec, steps, stream, dev, dist=None):
     """The same metric end to end through the C ABI with host buffers: fmlbm_init from pinned
-    host memory, then per step one fmlbm_step and one fmlbm_diagnostics_async, each ticket read
-    with fmlbm_diagnostics_wait three steps later (the device-to-host copy of masses, residual
-    and error latch); every step's result reaches the host inside the timed region."""
+    host memory, then fmlbm_step_diagnostics for all the steps (each step computes the masses
+    and residual of the state it reads, and each step's row, with the error latch, is copied to
+    the host and read there, three steps behind); every step's result reaches the host inside
+    the timed region."""
     n = len(w["mixture"]["Tc"])
     lat = fmlbm.Lattice(fmlbm.mixture_from_dict(w["mixture"]), w["nx"], w["ny"], w["tau"], w["stencil"], prec,
                         "lagged", stream=stream.cuda_stream)
@@ -341,14 +342,7 @@ def _e2e_rate(fmlbm, torch, w, prec, steps, stream, dev, dist=None):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     fmlbm.fmlbm_init(lat.h, rho_np)
-    tickets = []
-    for k in range(steps):
-        fmlbm.fmlbm_step(lat.h, 1)
-        tickets.append(fmlbm.fmlbm_diagnostics_async(lat.h))
-        if k >= 3:
-            fmlbm.fmlbm_diagnostics_wait(lat.h, tickets[k - 3], n)
-    for t in tickets[max(0, steps - 3):]:
-        fmlbm.fmlbm_diagnostics_wait(lat.h, t, n)
+    fmlbm.fmlbm_step_diagnostics(lat.h, steps, n)
     torch.cuda.synchronize()
     el = max_over_ranks(time.perf_counter() - t0, dist, dev)
     lat.close()
@@ -548,8 +542,8 @@ def run_ours(args, w, rank, world, dist):
         config=dict(workload=w["name"], nx=nx, ny=ny, n_components=n, tau=w["tau"], stencil=w["stencil"],
                     precision=prec, velocity_force="lagged", step_kernel=variant, autotune=tuned,
                     l2="flushed between timed steps (256 MB write, then read: clean lines, none of the step's)",
-                    e2e="per step fmlbm_step + fmlbm_diagnostics_async, results read three steps behind "
-                        "with fmlbm_diagnostics_wait",
+                    e2e="fmlbm_init from pinned host memory, then fmlbm_step_diagnostics: every step's masses, "
+                        "residual and error latch copied to the host",
                     timing="CUDA events around each fused launch on the launching stream"),
         roofline=dict(bound="hbm", achieved=achieved, peak=peak["hbm_gbs"], unit="GB/s",
                       frac=achieved / peak["hbm_gbs"], traffic=traffic, peak_source=peak["source"],

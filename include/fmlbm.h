@@ -244,6 +244,14 @@ fmlbm_status fmlbm_diagnostics(fmlbm_handle* h, double* mass, double* residual, 
  * has expired (FMLBM_E_INVALID_ARG), as has a request whose state fmlbm_init,
  * fmlbm_set_distributions or fmlbm_set_state replaced before it was computed. */
 fmlbm_status fmlbm_diagnostics_async(fmlbm_handle* h, int64_t* ticket);
+/* nsteps time steps (as fmlbm_step) with the diagnostics of every state a step reads, in one
+ * call: the loop fmlbm_diagnostics_async, fmlbm_step(h, 1), and fmlbm_diagnostics_wait three
+ * requests behind, run inside the library, so each step's diagnostics are computed inside the
+ * step and reach the host without a host round trip per step.  mass: host [nsteps][N], residual:
+ * host [nsteps] (caller-owned; row k describes the state step k reads, the values
+ * fmlbm_diagnostics_async / _wait give for it).  Returns when every row has arrived; a latched
+ * FMLBM_E_NONPHYSICAL or FMLBM_E_TIMEOUT is returned with the rows before it filled. */
+fmlbm_status fmlbm_step_diagnostics(fmlbm_handle* h, int64_t nsteps, double* mass, double* residual);
 fmlbm_status fmlbm_diagnostics_wait(fmlbm_handle* h, int64_t ticket, double* mass, double* residual,
                                     int64_t* step);
 

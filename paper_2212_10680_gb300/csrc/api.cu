@@ -1040,6 +1040,31 @@ fmlbm_status fmlbm_diagnostics(fmlbm_handle* h, double* mass, double* residual, 
     return fmlbm_diagnostics_wait(h, t, mass, residual, step);
 }
 
+fmlbm_status fmlbm_step_diagnostics(fmlbm_handle* h, int64_t nsteps, double* mass, double* residual) {
+    if (!h || nsteps < 0 || (nsteps > 0 && (!mass || !residual))) return fail(h, FMLBM_E_INVALID_ARG, "bad argument");
+    // the per-step loop of fmlbm_diagnostics_async / fmlbm_step / fmlbm_diagnostics_wait, with
+    // each result read three steps behind (the four kept results), so that the device always has
+    // steps queued while the host reads
+    constexpr int64_t kBehind = kDiagSlots - 1;
+    int64_t tickets[kDiagSlots];
+    fmlbm_status first_error = FMLBM_OK;
+    auto read = [&](int64_t k) {
+        const fmlbm_status s = fmlbm_diagnostics_wait(h, tickets[k % kDiagSlots], mass + k * h->nc, residual + k,
+                                                      nullptr);
+        if (s != FMLBM_OK && first_error == FMLBM_OK) first_error = s;
+        return s;
+    };
+    for (int64_t k = 0; k < nsteps; ++k) {
+        fmlbm_status s = fmlbm_diagnostics_async(h, &tickets[k % kDiagSlots]);
+        if (s == FMLBM_OK) s = fmlbm_step(h, 1);
+        if (s != FMLBM_OK) return s;
+        if (k >= kBehind && read(k - kBehind) != FMLBM_OK) return first_error;
+    }
+    for (int64_t k = nsteps > kBehind ? nsteps - kBehind : 0; k < nsteps; ++k)
+        if (read(k) != FMLBM_OK) return first_error;
+    return FMLBM_OK;
+}
+
 fmlbm_status fmlbm_error_node(fmlbm_handle* h, int32_t* comp, int32_t* x, int32_t* y) {
     if (!h) return FMLBM_E_INVALID_ARG;
     FM_CUDA(h, cudaMemcpyAsync(h->err_host, h->err_dev, sizeof(ErrorLatch), cudaMemcpyDeviceToHost, h->stream));

@@ -1006,27 +1006,50 @@ __device__ __forceinline__ void diag_node(const V (&r)[NC], const V (&pv)[NC], i
     }
 }
 
-__device__ __forceinline__ float shfl_down(float v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
-__device__ __forceinline__ double shfl_down(double v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
-__device__ __forceinline__ float2 shfl_down(float2 v, int o) {
-    return make_float2(__shfl_down_sync(0xffffffffu, v.x, o), __shfl_down_sync(0xffffffffu, v.y, o));
+__device__ __forceinline__ float shfl_xor(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ float2 shfl_xor(float2 v, int o) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+template <typename V>
+__device__ __forceinline__ Sum2<V> shfl_xor(const Sum2<V>& v, int o) {
+    Sum2<V> w;
+    w.hi = shfl_xor(v.hi, o);
+    w.lo = kCompensated<V> ? shfl_xor(v.lo, o) : v.lo;
+    return w;
 }
 
-// Warp sums of K compensated sums (a fixed shuffle tree) into one row of a per-block table.
+// Warp sums of K compensated sums into one row of a per-block table (a fixed order, so every
+// kernel that reduces the same nodes gets the same bits).  A transposed reduction: with the K
+// sums padded to a power of two KP, at each of the first log2 KP levels (lane distances 16, 8,
+// ...) a lane keeps half of its sums, receives its partner's copies of them and adds them, and
+// passes the other half to the partner, so each pair-sum is formed once; then each group of
+// 32 / KP lanes holds one sum and finishes it with a butterfly.  About 2 KP adds per lane in
+// all, where a butterfly per sum takes 5 levels for each of the K sums.
+constexpr int pow2_at_least(int k) { return k <= 1 ? 1 : 2 * pow2_at_least((k + 1) / 2); }
 template <int K, typename V>
 __device__ __forceinline__ void sums_warp(const Sum2<V> (&acc)[K], Sum2<V>* row) {
+    static_assert(K >= 1 && K <= 32, "up to 32 sums per warp");
+    constexpr int KP = pow2_at_least(K);
+    const int lane = threadIdx.x & 31;
+    Sum2<V> v[KP];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        Sum2<V> v = acc[k];
+    for (int j = 0; j < KP; ++j) v[j] = j < K ? acc[j] : s2_of(vbc<V>(LaneE<V>(0)));
+    int q = 0;  // index of the first sum this lane still holds
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            Sum2<V> w;
-            w.hi = shfl_down(v.hi, o);
-            w.lo = kCompensated<V> ? shfl_down(v.lo, o) : v.lo;
-            v = s2_add(v, w);
+    for (int h = KP / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int j = 0; j < h; ++j) {
+            const Sum2<V> keep = upper ? v[j + h] : v[j];
+            const Sum2<V> send = upper ? v[j] : v[j + h];
+            v[j] = s2_add(keep, shfl_xor(send, o));
         }
-        if ((threadIdx.x & 31) == 0) row[k] = v;
+        q += upper ? h : 0;
     }
+#pragma unroll
+    for (int o = 16 / KP; o >= 1; o >>= 1) v[0] = s2_add(v[0], shfl_xor(v[0], o));
+    if ((lane & (32 / KP - 1)) == 0 && q < K) row[q] = v[0];
 }
 template <int NC, typename V>
 __device__ __forceinline__ void diag_warp(const Sum2<V> (&acc)[NC + 2], Sum2<V>* row) {

@@ -96,6 +96,7 @@ def _load() -> ctypes.CDLL:
         "fmlbm_set_distributions": ([H, dp, dp], ctypes.c_int),
         "fmlbm_diagnostics": ([H, dp, dp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
         "fmlbm_phase_measure": ([H, dp], ctypes.c_int),
+        "fmlbm_step_diagnostics": ([H, ctypes.c_int64, dp, dp], ctypes.c_int),
         "fmlbm_error_node": ([H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                               ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "fmlbm_state_size": ([H, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
@@ -284,6 +285,14 @@ def fmlbm_diagnostics_async(h) -> int:
     t = ctypes.c_int64()
     _check(LIB.fmlbm_diagnostics_async(h, ctypes.byref(t)), "fmlbm_diagnostics_async", h)
     return t.value
+
+
+def fmlbm_step_diagnostics(h, nsteps: int, n_components: int):
+    """nsteps steps with every step's diagnostics: masses [nsteps][N], residuals [nsteps]."""
+    mass = np.empty((max(nsteps, 0), n_components))
+    res = np.empty(max(nsteps, 0))
+    _check(LIB.fmlbm_step_diagnostics(h, nsteps, _ptr(mass), _ptr(res)), "fmlbm_step_diagnostics", h)
+    return mass, res
 
 
 def fmlbm_diagnostics_wait(h, ticket: int, n_components: int):

@@ -161,3 +161,37 @@ def test_request_served_inside_a_captured_graph(fm):
     g, F = lat.distributions()
     assert np.array_equal(g, g_ref) and np.array_equal(F, F_ref)
     lat.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16dev"])
+def test_step_diagnostics_matches_the_per_step_loop(fm, precision):
+    # fmlbm_step_diagnostics runs the per-step loop (ask, step, read three behind) inside the
+    # library: the same rows, bit for bit, and the same final state; 0, 1, 2 and 9 steps
+    # (fewer steps than the kept results, and more)
+    mixd, rho = slab_state_binary(100, 60, seed=12)
+    n = len(mixd["Tc"])
+    for nsteps in (0, 1, 2, 9):
+        ref, got = [], []
+        lat = fm.Lattice(fm.mixture_from_dict(mixd), 100, 60, 1.0, "isotropic", precision, "lagged")
+        lat.init(rho)
+        tickets = []
+        for k in range(nsteps):
+            tickets.append(fm.fmlbm_diagnostics_async(lat.h))
+            lat.step(1)
+            if k >= 3:  # four results are kept: read three behind
+                m, r, _ = fm.fmlbm_diagnostics_wait(lat.h, tickets[k - 3], n)
+                ref.append((m, r))
+        for t in tickets[max(0, nsteps - 3):]:
+            m, r, _ = fm.fmlbm_diagnostics_wait(lat.h, t, n)
+            ref.append((m, r))
+        g0 = lat.distributions()
+        lat.close()
+        lat = fm.Lattice(fm.mixture_from_dict(mixd), 100, 60, 1.0, "isotropic", precision, "lagged")
+        lat.init(rho)
+        mass, res = fm.fmlbm_step_diagnostics(lat.h, nsteps, n)
+        g1 = lat.distributions()
+        lat.close()
+        assert mass.shape == (nsteps, n) and res.shape == (nsteps,)
+        for k, (m, r) in enumerate(ref):
+            assert np.array_equal(mass[k], m) and (res[k] == r or (np.isinf(res[k]) and np.isinf(r))), (nsteps, k)
+        assert np.array_equal(g0[0], g1[0]) and np.array_equal(g0[1], g1[1])
