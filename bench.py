@@ -183,6 +183,17 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_running(self, timeout: float = 10.0):
+        """Return once the sampler has printed its first sample: nvidia-smi's start-up then no
+        longer overlaps the timed work that follows, while the sampling still covers it."""
+        self.wait_samples(1, timeout)
+
+    def wait_samples(self, n: int, timeout: float = 2.0):
+        """Wait until at least n samples have arrived (a sample after the timed work brackets it)."""
+        t0 = time.perf_counter()
+        while self.proc and len(self.lines) < n and time.perf_counter() - t0 < timeout:
+            time.sleep(0.005)
+
     def __exit__(self, *a):
         if self.proc:
             self.proc.terminate()
@@ -308,8 +319,10 @@ def _device_steps(fmlbm, torch, w, prec, steps, warmup, stream, dev, variant=Non
             dist.barrier()
         torch.cuda.synchronize()
 
-    barrier()
     with ClockSampler(dev.index) as clk:
+        clk.wait_running()
+        barrier()
+        n_before = len(clk.lines)
         for k in range(steps):
             # evict the previous step's data from L2 (untimed): write a buffer twice the L2
             # size, then read it, so that the lines left in L2 are clean and none is the step's
@@ -321,6 +334,7 @@ def _device_steps(fmlbm, torch, w, prec, steps, warmup, stream, dev, variant=Non
             fmlbm.fmlbm_step(lat.h, 1)
             ev[k][1].record(stream)
         barrier()
+        clk.wait_samples(n_before + 1)
     ms = [a.elapsed_time(b) for a, b in ev]
     lat.synchronize()
     lat.close()
