@@ -194,8 +194,9 @@ fmlbm_status fmlbm_init(fmlbm_handle* h, const double* rho_host);
 fmlbm_status fmlbm_init_device(fmlbm_handle* h, const double* rho_device);
 
 /* Enqueues nsteps (>= 0) full time steps (steps 1-9 of Section III.B, one fused
- * kernel launch per step) on the handle's stream.  Asynchronous: kernel-side
- * errors surface at the next synchronising call. */
+ * kernel launch per step; one launch for all of them with FMLBM_VARIANT_MULTI) on the
+ * handle's stream.  Asynchronous: kernel-side errors surface at the next synchronising
+ * call. */
 fmlbm_status fmlbm_step(fmlbm_handle* h, int64_t nsteps);
 
 /* Macroscopic fields of the current state (steps 1-7 without collision):
@@ -321,7 +322,7 @@ fmlbm_status fmlbm_set_step_variant(fmlbm_handle* h, int32_t variant);
  * Outputs (may be NULL): chosen variant, tile height, ms per step. */
 fmlbm_status fmlbm_autotune(fmlbm_handle* h, int32_t steps_per_trial, int32_t* variant, int32_t* tile_y,
                             double* ms_per_step);
-/* The kernel fmlbm_step will use (PLAIN, TMA, TMA_TILE or PAIR). */
+/* The kernel fmlbm_step will use (PLAIN, TMA, TMA_TILE, PAIR or MULTI). */
 fmlbm_status fmlbm_get_step_variant(fmlbm_handle* h, int32_t* variant);
 
 /* Bound of the device-side waits of the TMA step forms for a tile's bulk copy, in polls of
