@@ -558,7 +558,8 @@ def run_ours(args, w, rank, world, dist):
                     l2="flushed between timed steps (256 MB write, then read: clean lines, none of the step's)",
                     e2e="fmlbm_init from pinned host memory, then fmlbm_step_diagnostics: every step's masses, "
                         "residual and error latch copied to the host",
-                    timing="CUDA events around each fused launch on the launching stream"),
+                    timing="CUDA events around each fused launch on the launching stream",
+                    step_ms_spread=dict(median=statistics.median(ms), min=min(ms), max=max(ms))),
         roofline=dict(bound="hbm", achieved=achieved, peak=peak["hbm_gbs"], unit="GB/s",
                       frac=achieved / peak["hbm_gbs"], traffic=traffic, peak_source=peak["source"],
                       algorithmic_bytes_per_component_node=ALGO_BYTES[prec],
